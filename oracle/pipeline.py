@@ -1,0 +1,109 @@
+"""End-to-end oracle: rays -> pre-DOE trace -> DOE step -> post-DOE trace
+-> sensor, per job, float64, chunked over incident rays.
+
+Chunking only bounds memory: every incident ray's contribution is computed
+independently and the per-chunk images are added.
+"""
+import math
+
+import numpy as np
+import torch
+
+from . import geometry as G
+from . import doe as DO
+from . import sensor as S
+
+
+def job_rays(job, z_start, n_object=1.0, idx=None):
+    """Collimated grid of one job (see rwinputs.Job): o, d, a = 1,
+    OPL = n_object (d . o).  `idx` selects a subset of ray indices."""
+    n = job.grid_n
+    if idx is None:
+        idx = np.arange(n * n)
+    idx = torch.as_tensor(np.asarray(idx, dtype=np.int64))
+    ix = (idx % n).to(torch.float64)
+    iy = (idx // n).to(torch.float64)
+    x = job.x0 + (ix - (n - 1) / 2.0) * job.spacing
+    y = job.y0 + (iy - (n - 1) / 2.0) * job.spacing
+    z = torch.full_like(x, float(z_start))
+    dv = torch.tensor([math.tan(job.theta_x), math.tan(job.theta_y), 1.0], dtype=torch.float64)
+    dv = dv / torch.linalg.norm(dv)
+    o = torch.stack([x, y, z], -1)
+    d = dv[None, :].expand_as(o).clone()
+    N = o.shape[0]
+    return {"o": o, "d": d, "a": torch.ones(N, dtype=torch.complex128),
+            "opl": n_object * (o * d).sum(-1), "alive": torch.ones(N, dtype=torch.bool)}
+
+
+def params_of(system, requires_grad=False):
+    return [G.surface_params(s, requires_grad) for s in system.surfaces]
+
+
+def map_tensors(system, phi=None, amp=None):
+    doe = system.doe
+    if phi is None:
+        phi = torch.from_numpy(np.asarray(doe.phi, dtype=np.float64))
+    if amp is None and doe.amp is not None:
+        amp = torch.from_numpy(np.asarray(doe.amp, dtype=np.float64))
+    return phi, amp
+
+
+def emit_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0):
+    """Pre-DOE trace + DOE step for (a subset of) one job's rays."""
+    di = system.doe_index
+    ray = job_rays(job, z_start, system.n_object, idx)
+    ray, n_in = G.trace(ray, params[:di], torch.tensor(system.n_object, dtype=torch.float64))
+    n_out = params[di]["n_after"]
+    ids = (np.arange(job.n_rays) if idx is None else np.asarray(idx)) + ray_base
+    return DO.doe_step(ray, params[di], system.doe, phi, amp, job.lam, n_in, n_out,
+                       ray_ids=ids, coherent=system.sensor.coherent), n_out
+
+
+def psf_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0, chunk=256):
+    """Sensor image [ny, nx] of one job (intensity)."""
+    sen = system.sensor
+    di = system.doe_index
+    nx, ny = sen.nx, sen.ny
+    n_rays = job.n_rays if idx is None else len(idx)
+    all_idx = np.arange(job.n_rays) if idx is None else np.asarray(idx)
+    img = torch.zeros(nx * ny, dtype=torch.float64)
+    field = torch.zeros(nx * ny, dtype=torch.complex128)
+    for c0 in range(0, n_rays, chunk):
+        sub = all_idx[c0:c0 + chunk]
+        em, n_out = emit_job(system, job, z_start, params, phi, amp, sub, ray_base)
+        dsec = em["d"]
+        shp = dsec.shape[:-1]
+        Nin = shp[0]
+        nsec = int(np.prod(shp[1:]))
+        o = em["o"][:, None, :].expand(Nin, nsec, 3).reshape(-1, 3)
+        ray = {"o": o, "d": dsec.reshape(-1, 3), "a": em["a"].reshape(-1),
+               "opl": em["opl"][:, None].expand(Nin, nsec).reshape(-1),
+               "alive": em["alive"].reshape(-1)}
+        ray, n_s = G.trace(ray, params[di + 1:], n_out)
+        x, y, opl = S.to_sensor(ray["o"], ray["d"], ray["opl"], sen.z, n_s)
+        if sen.coherent:
+            field = field + S.coherent_field(x, y, opl, ray["d"], ray["a"], ray["alive"],
+                                             nx, ny, sen.pitch, job.sensor_cx,
+                                             job.sensor_cy, job.lam, n_s, sen.window)
+        else:
+            w = ray["a"].real ** 2 + ray["a"].imag ** 2
+            img = img + S.splat_incoherent(x, y, w, ray["alive"], nx, ny, sen.pitch,
+                                           job.sensor_cx, job.sensor_cy)
+    if sen.coherent:
+        img = field.real ** 2 + field.imag ** 2
+    return img.reshape(ny, nx)
+
+
+def psf(workload, params=None, phi=None, amp=None, subsets=None, chunk=256):
+    """PSF stack [njob, ny, nx].  subsets[j] optionally lists ray indices of job j."""
+    system = workload.system
+    if params is None:
+        params = params_of(system)
+    phi, amp = map_tensors(system, phi, amp)
+    out = []
+    base = 0
+    for j, job in enumerate(workload.jobs):
+        idx = None if subsets is None else subsets[j]
+        out.append(psf_job(system, job, workload.z_start, params, phi, amp, idx, base, chunk))
+        base += job.n_rays
+    return torch.stack(out, 0)

@@ -1,0 +1,416 @@
+"""Pins of the FP64 oracle against closed forms and independent references.
+
+Each test fixes a part of the oracle with something other than the oracle
+itself: the grating equation and Fourier-series efficiencies, Parseval,
+a plane wave's spectrum, the lensmaker's thick-lens focus, the Cartesian
+ellipsoid, scalar Snell at a tilted facet, angular-spectrum propagation
+(NumPy FFT), finite differences, Monte-Carlo unbiasedness, published
+Philox known answers and the paper's worked curvature-bound example.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import rwinputs as R
+from oracle import doe as DO
+from oracle import geometry as G
+from oracle import loss as L
+from oracle import pipeline as P
+from oracle import sensor as S
+from oracle.philox import philox4x32_10, sample_uniforms
+
+from physics_refs import (asm_propagate, binary_grating_efficiency, staircase_efficiency,
+                          thick_lens_bfl)
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+F64 = torch.float64
+
+
+def _ray(o, d):
+    o = torch.as_tensor(np.atleast_2d(o), dtype=F64)
+    d = torch.as_tensor(np.atleast_2d(d), dtype=F64)
+    d = d / torch.linalg.norm(d, dim=-1, keepdim=True)
+    N = o.shape[0]
+    return {"o": o, "d": d, "a": torch.ones(N, dtype=torch.complex128),
+            "opl": torch.zeros(N, dtype=F64), "alive": torch.ones(N, dtype=torch.bool)}
+
+
+# ------------------------------------------------------------------ Philox
+def test_philox_known_answers():
+    rows = [ln.split() for ln in open(os.path.join(GOLD, "philox4x32_10_kat.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = philox4x32_10(*v[:6])
+        assert [int(o) for o in out] == v[6:]
+
+
+def test_uniforms_open_interval_and_stream_layout():
+    u = sample_uniforms(seed=(7 << 32) | 11, rng_offset=3, ray_ids=[0, 5], n_draws=3, n_bins=9)
+    assert u.shape == (2, 3, 9)
+    assert (u > 0).all() and (u < 1).all()
+    # bin j uses word j & 3 of counter (j >> 2, draw, ray, offset)
+    w = philox4x32_10(6 >> 2, 2, 5, 3, 11, 7)
+    assert u[1, 2, 6] == ((int(w[6 & 3]) >> 9) + 0.5) * 2.0 ** -23
+
+
+# ------------------------------------------------------------------ gratings (P1, P1b)
+@pytest.mark.parametrize("theta_deg", [0.0, 10.0])
+def test_binary_grating_orders_and_efficiencies(theta_deg):
+    w = R.configs.c1(n_side=4, angles_deg=(theta_deg,))
+    sysm, job = w.system, w.jobs[0]
+    em, _ = P.emit_job(sysm, job, w.z_start, P.params_of(sysm), *P.map_tensors(sysm))
+    U = em["U"]
+    eta = U.abs() ** 2                                   # [N, jv, ju]
+    D = sysm.doe.D
+    c = D // 2
+    lam, period = job.lam, 16 * sysm.doe.pitch
+    for r in range(U.shape[0]):
+        assert abs(float(eta[r].sum()) - 1.0) < 1e-12    # Parseval, phase-only map
+        for m in range(-7, 8):
+            e = float(eta[r, c, c + 2 * m])
+            assert e == pytest.approx(binary_grating_efficiency(m, 16), abs=1e-12)
+            if m % 2:
+                dvec = em["d"][r, c, c + 2 * m]
+                s_out = float(dvec[0])
+                assert s_out == pytest.approx(math.sin(job.theta_x) + m * lam / period,
+                                              abs=1e-13)
+                assert float(dvec[1]) == pytest.approx(0.0, abs=1e-15)
+        # everything off the j_v = 0 row and off even j_u bins is empty
+        off = eta[r].clone()
+        off[c, c - 14:c + 15:2] = 0
+        assert float(off.max()) < 1e-24
+    assert bool(em["alive"].all())   # every bin propagates, even at 10 degrees
+
+
+def test_blazed_staircase_efficiencies():
+    H = W = 128
+    phi = R.staircase_grating(H, W, n_levels=4, px_per_level=2)
+    doe = R.DOE(phi=phi, pitch=0.5e-3, D=32)
+    sysm = R.System([R.Surface(R.PLANE, 0.0)], 0, doe, R.Sensor(1.0, 8, 8, 1e-3))
+    job = R.Job(lam=550e-6, grid_n=3, spacing=1.7e-3)
+    em, _ = P.emit_job(sysm, job, -0.1, P.params_of(sysm), *P.map_tensors(sysm))
+    eta = em["U"].abs() ** 2
+    c = 16
+    for m in range(-3, 5):
+        j = 4 * m            # period 8 px -> order m at bin 32/8 m
+        if -16 <= j < 16:
+            assert float(eta[0, c, c + j]) == pytest.approx(staircase_efficiency(m, 4, 2),
+                                                             abs=1e-12)
+    assert float(eta[0].sum()) == pytest.approx(1.0, abs=1e-12)
+
+
+# ------------------------------------------------------------------ spectrum (P2)
+def test_parseval_random_complex_patch():
+    g = torch.Generator().manual_seed(3)
+    T = torch.randn(5, 16, 16, dtype=F64, generator=g) + 1j * torch.randn(
+        5, 16, 16, dtype=F64, generator=g)
+    # offsets of a uniform pixel grid from an arbitrary hit point
+    s0 = torch.rand(5, 1, dtype=F64, generator=g) * 1e-3 - 8e-3
+    s = s0 + torch.arange(16, dtype=F64)[None] * 1e-3
+    U = DO.spectrum(T, s, s.flip(0), 1e-3)
+    lhs = (U.abs() ** 2).sum((1, 2))
+    rhs = (T.abs() ** 2).mean((1, 2))
+    assert torch.allclose(lhs, rhs, rtol=1e-12)
+
+
+def test_plane_wave_has_single_bin_referenced_to_hit():
+    """T = exp(i k_m x) on the grid -> U~ = exp(i k_m x_P) at bin m, 0 elsewhere."""
+    D, p = 16, 1e-3
+    m = 3
+    km = 2 * math.pi * m / (D * p)
+    xP, yP = 0.37 * p, -0.21 * p
+    xa = (torch.arange(D, dtype=F64) - D / 2 + 0.5) * p
+    T = torch.polar(torch.ones(D, dtype=F64), km * xa)[None, :].expand(D, D)[None]
+    U = DO.spectrum(T, (xa - xP)[None], (xa - yP)[None], p)[0]
+    c = D // 2
+    expect = complex(math.cos(km * xP), math.sin(km * xP))
+    assert complex(U[c, c + m]) == pytest.approx(expect, abs=1e-13)
+    U2 = U.clone()
+    U2[c, c + m] = 0
+    assert float(U2.abs().max()) < 1e-13
+
+
+# ------------------------------------------------------------------ refraction (P3)
+def test_thick_singlet_paraxial_focus():
+    s = R.configs._singlet(0.0)
+    prm = [G.surface_params(x) for x in s]
+    bfl, f = thick_lens_bfl(R.configs.N_BK7, 20.0, -20.0, 3.0)
+    assert f == pytest.approx(19.857, abs=1e-3)
+    h = 1e-5
+    ray, _ = G.trace(_ray([h, 0, -1.0], [0, 0, 1]), prm, torch.tensor(1.0, dtype=F64))
+    t = -ray["o"][0, 0] / ray["d"][0, 0]
+    zf = float(ray["o"][0, 2] + t * ray["d"][0, 2])
+    assert zf == pytest.approx(3.0 + bfl, abs=1e-7)
+
+
+def test_cartesian_ellipsoid_focuses_all_axial_rays():
+    """k = -1/n^2 ellipsoid: every axial ray refracts to z = n R / (n - 1)."""
+    n, Rv = 1.5, 10.0
+    s = R.Surface(R.ASPHERE, 0.0, c=1 / Rv, k=-1 / n ** 2, n_after=n)
+    prm = [G.surface_params(s)]
+    hs = np.array([0.1, 1.0, 2.5, 4.0, 5.5])
+    o = np.stack([hs, np.zeros_like(hs), -np.ones_like(hs)], -1)
+    ray, _ = G.trace(_ray(o, np.tile([0, 0, 1.0], (len(hs), 1))), prm,
+                     torch.tensor(1.0, dtype=F64))
+    t = -ray["o"][:, 0] / ray["d"][:, 0]
+    zf = ray["o"][:, 2] + t * ray["d"][:, 2]
+    assert torch.allclose(zf, torch.full_like(zf, n * Rv / (n - 1)), atol=1e-11)
+    assert bool(ray["alive"].all())
+
+
+def test_polynomial_asphere_hit_and_scalar_snell():
+    """c = 0, A4 only: the axial ray at height h hits z = A4 h^4 and leaves at
+    angle theta_i - theta_t from the axis, with tan(theta_i) the facet slope."""
+    A4, n = 2e-3, 1.6
+    s = R.Surface(R.ASPHERE, 0.0, c=0.0, A=(A4, 0, 0, 0), n_after=n)
+    prm = [G.surface_params(s)]
+    for h in (0.5, 1.5, 2.2):
+        ray, _ = G.trace(_ray([h, 0, -1.0], [0, 0, 1.0]), prm, torch.tensor(1.0, dtype=F64))
+        assert float(ray["o"][0, 2]) == pytest.approx(A4 * h ** 4, abs=1e-13)
+        th_i = math.atan(4 * A4 * h ** 3)
+        th_t = math.asin(math.sin(th_i) / n)
+        ang = math.atan2(float(ray["d"][0, 0]), float(ray["d"][0, 2]))
+        assert ang == pytest.approx(-(th_i - th_t), abs=1e-13)
+
+
+def test_newton_asphere_equals_sphere_when_k_and_A_vanish():
+    s1 = R.Surface(R.SPHERE, 2.0, c=1 / 15.0, n_after=1.7)
+    s2 = R.Surface(R.ASPHERE, 2.0, c=1 / 15.0, n_after=1.7)
+    rng = np.random.default_rng(1)
+    o = np.concatenate([rng.uniform(-3, 3, (50, 2)), np.zeros((50, 1))], 1)
+    d = np.concatenate([rng.uniform(-0.2, 0.2, (50, 2)), np.ones((50, 1))], 1)
+    r1, _ = G.trace(_ray(o, d), [G.surface_params(s1)], torch.tensor(1.0, dtype=F64))
+    r2, _ = G.trace(_ray(o, d), [G.surface_params(s2)], torch.tensor(1.0, dtype=F64))
+    assert torch.allclose(r1["o"], r2["o"], atol=1e-12)
+    assert torch.allclose(r1["d"], r2["d"], atol=1e-12)
+
+
+def test_trace_is_reversible():
+    """Mirror the system (z -> -z), send the exit rays back: they return to
+    their start points with reversed directions and the same optical path."""
+    s = R.configs._singlet(5.0) + R.configs._singlet(10.0)
+    prm = [G.surface_params(x) for x in s]
+    rng = np.random.default_rng(2)
+    o = np.concatenate([rng.uniform(-1, 1, (20, 2)), np.zeros((20, 1))], 1)
+    d = np.concatenate([rng.uniform(-0.05, 0.05, (20, 2)), np.ones((20, 1))], 1)
+    r0 = _ray(o, d)
+    r1, _ = G.trace(r0, prm, torch.tensor(1.0, dtype=F64))
+    ns = [1.0] + [x.n_after for x in s]
+    rs = [R.Surface(R.SPHERE, -s[i].z, c=-s[i].c, n_after=ns[i]) for i in reversed(range(len(s)))]
+    flip = torch.tensor([-1.0, -1.0, 1.0], dtype=F64)
+    back = {"o": r1["o"] * torch.tensor([1.0, 1.0, -1.0], dtype=F64), "d": r1["d"] * flip,
+            "a": r1["a"], "opl": torch.zeros(20, dtype=F64), "alive": r1["alive"]}
+    r2, _ = G.trace(back, [G.surface_params(x) for x in rs], torch.tensor(1.0, dtype=F64))
+    t = -r2["o"][:, 2] / r2["d"][:, 2]
+    xy = r2["o"][:, :2] + t[:, None] * r2["d"][:, :2]
+    assert bool(r2["alive"].all())
+    assert torch.allclose(xy, r0["o"][:, :2], atol=1e-12)
+    assert torch.allclose(r2["d"] * flip, r0["d"], atol=1e-13)
+    assert torch.allclose(r2["opl"] + t, r1["opl"], atol=1e-12)
+
+
+# ------------------------------------------------------------------ special case T = 1 (P4)
+def test_unit_transmission_reduces_to_refractive_spot_diagram():
+    w = R.configs.c2(n_side=6, D=16, lams=(550e-6,), fields_deg=(1.0,), sensor_n=64,
+                     map_side=128)
+    sysm = w.system
+    sysm.doe.phi = np.zeros_like(sysm.doe.phi)
+    sysm.sensor.pitch = 20e-3
+    prm = P.params_of(sysm)
+    job = w.jobs[0]
+    em, _ = P.emit_job(sysm, job, w.z_start, prm, *P.map_tensors(sysm))
+    U = em["U"]
+    c = 8
+    assert torch.allclose(U[:, c, c], torch.ones(U.shape[0], dtype=torch.complex128), atol=1e-14)
+    U2 = U.clone()
+    U2[:, c, c] = 0
+    assert float(U2.abs().max()) < 1e-14
+    img = P.psf(w)[0]
+    ray = P.job_rays(job, w.z_start)
+    ray, n_s = G.trace(ray, prm, torch.tensor(1.0, dtype=F64))
+    x, y, _ = S.to_sensor(ray["o"], ray["d"], ray["opl"], sysm.sensor.z, n_s)
+    ref = S.splat_incoherent(x, y, torch.ones_like(x), ray["alive"], 64, 64, 20e-3, 0.0,
+                             0.0).reshape(64, 64)
+    assert torch.allclose(img, ref, atol=1e-12)
+    assert float(img.sum()) == pytest.approx(36.0, abs=1e-9)
+
+
+# ------------------------------------------------------------------ coherent Eq. 2 == ASM (P5)
+@pytest.mark.parametrize("zs", [0.02, 0.05])
+def test_coherent_sum_of_one_full_patch_equals_angular_spectrum(zs):
+    D, p, lam = 32, 1e-3, 0.8e-3
+    rng = np.random.Generator(np.random.PCG64(5))
+    phi = rng.uniform(0, 2 * math.pi, (D, D)).astype(np.float32)
+    amp = rng.uniform(0.3, 1.0, (D, D)).astype(np.float32)
+    doe = R.DOE(phi=phi, amp=amp, pitch=p, D=D, lambda0=lam)
+    sen = R.Sensor(z=zs, nx=D, ny=D, pitch=p, coherent=True)
+    sysm = R.System([R.Surface(R.PLANE, 0.0)], 0, doe, sen)
+    xP, yP = 0.31 * p, 0.77 * p                          # inside the central pixel
+    job = R.Job(lam=lam, grid_n=1, spacing=0.0, x0=xP, y0=yP)
+    w = R.systems.Workload("P5", sysm, [job], z_start=-0.01)
+    img = P.psf(w)[0].numpy()
+    T = amp.astype(np.float64) * np.exp(1j * phi.astype(np.float64))
+    ref = np.abs(asm_propagate(T, p, lam, zs)) ** 2
+    assert np.allclose(img, ref, rtol=1e-9, atol=1e-12 * ref.max())
+
+
+# ------------------------------------------------------------------ conformal frame (P7)
+def test_conformal_frame_is_sphere_normal_and_orthonormal():
+    Rs = 25.0
+    s = G.surface_params(R.Surface(R.SPHERE, 8.0, c=1 / Rs))
+    rng = np.random.default_rng(4)
+    o = np.concatenate([rng.uniform(-2, 2, (30, 2)), np.zeros((30, 1))], 1)
+    d = np.concatenate([rng.uniform(-0.3, 0.3, (30, 2)), np.ones((30, 1))], 1)
+    r = _ray(o, d)
+    t, ok = G.intersect(r["o"], r["d"], s)
+    hit = r["o"] + t[:, None] * r["d"]
+    centre = torch.tensor([0, 0, 8.0 + Rs], dtype=F64)
+    assert torch.allclose(torch.linalg.norm(hit - centre, dim=-1), torch.full((30,), Rs,
+                                                                                dtype=F64),
+                          atol=1e-12)
+    u, v, n = DO.frame(hit, s, r["d"])
+    nref = (centre - hit) / Rs                           # points +z, along the rays
+    assert torch.allclose(n, nref, atol=1e-12)
+    for a, b in ((u, v), (u, n), (v, n)):
+        assert float((a * b).sum(-1).abs().max()) < 1e-13
+    # u is the projection of x onto the tangent plane: in the plane of x and n
+    ex = torch.tensor([1.0, 0, 0], dtype=F64).expand(30, 3)
+    assert float((u * torch.cross(ex, n, dim=-1)).sum(-1).abs().max()) < 1e-13
+    assert float((u * ex).sum(-1).min()) > 0
+
+
+def test_curvature_bound_worked_example():
+    rows = [ln.split() for ln in open(os.path.join(GOLD, "curvature_bound_fig6.txt"))
+            if ln.strip() and not ln.startswith("#")]
+    D, Rr, thr = (float(x) for x in rows[0])
+    eps = math.asin(D / (2 * Rr))
+    assert eps == pytest.approx(0.0990, abs=5e-5)
+    assert eps <= thr
+    # geometric meaning: a tangent-plane point at distance D/2 from the hit sits
+    # over a sphere point whose normal is tilted by exactly arcsin(D / 2R)
+    Rs = Rr
+    rho = D / 2
+    z = Rs - math.sqrt(Rs * Rs - rho * rho)
+    nrm = np.array([-rho, 0.0, Rs - z]) / Rs
+    assert math.acos(nrm[2]) == pytest.approx(eps, abs=1e-12)
+
+
+# ------------------------------------------------------------------ Eq. 3 loss
+def test_eq3_alpha_is_the_optimal_scale_and_gradient_closed_form():
+    g = torch.Generator().manual_seed(9)
+    I = torch.rand(3, 8, 8, dtype=F64, generator=g).requires_grad_(True)
+    T = torch.rand(3, 8, 8, dtype=F64, generator=g)
+    Lv, a = L.eq3_loss(I, T)
+    for da in (-1e-3, 1e-3):
+        assert float(((a + da) * I - T).pow(2).sum()) > float(Lv)
+    Lv.backward()
+    a = a.detach()
+    assert torch.allclose(I.grad, 2 * a * (a * I.detach() - T), atol=1e-12)
+
+
+# ------------------------------------------------------------------ gradients (P8)
+def _small_c3(n_side=6):
+    w = R.configs.c3(n_side=n_side, D=16)
+    sysm = w.system
+    sysm.doe.phi = R.maps.random_phase(128, 128, 11) * 0.3 + sysm.doe.phi[:128, :128]
+    sysm.sensor.nx = sysm.sensor.ny = 48
+    sysm.sensor.pitch = 40e-3
+    w.target = R.gaussian_spots_target(1, 48, 48, seed=5, n_spots=3)
+    return w
+
+
+def test_oracle_gradient_matches_central_differences():
+    w = _small_c3()
+    sysm = w.system
+    tgt = torch.from_numpy(w.target.astype(np.float64))
+    prm = P.params_of(sysm, requires_grad=True)
+    phi = torch.from_numpy(sysm.doe.phi.astype(np.float64)).requires_grad_(True)
+
+    def loss_of(prm_, phi_):
+        img = P.psf(w, params=prm_, phi=phi_)
+        return L.eq3_loss(img, tgt)[0]
+
+    Lv = loss_of(prm, phi)
+    Lv.backward()
+    checks = [("c", 1), ("c", 4), ("z", 2), ("z", 3), ("k", 1)]
+    for name, si in checks:
+        g_ad = float(prm[si][name].grad)
+        h = 1e-6
+        base = float(prm[si][name])
+        vals = []
+        for sgn in (+1, -1):
+            p2 = P.params_of(sysm)
+            p2[si][name] = torch.tensor(base + sgn * h, dtype=F64)
+            vals.append(float(loss_of(p2, phi.detach())))
+        g_fd = (vals[0] - vals[1]) / (2 * h)
+        assert g_ad == pytest.approx(g_fd, rel=2e-4, abs=1e-6 * abs(float(Lv)) / h * 1e-6), \
+            (name, si, g_ad, g_fd)
+    # DOE phase pixels (smooth: no sampling kinks)
+    rng = np.random.default_rng(0)
+    gphi = phi.grad.numpy()
+    hot = np.argwhere(np.abs(gphi) > 1e-3 * np.abs(gphi).max())
+    for (r, c) in hot[rng.choice(len(hot), 6, replace=False)]:
+        h = 1e-6
+        vals = []
+        for sgn in (+1, -1):
+            ph2 = phi.detach().clone()
+            ph2[r, c] += sgn * h
+            vals.append(float(loss_of(P.params_of(sysm), ph2)))
+        g_fd = (vals[0] - vals[1]) / (2 * h)
+        assert gphi[r, c] == pytest.approx(g_fd, rel=1e-5, abs=1e-9 * abs(float(Lv))), (r, c)
+
+
+# ------------------------------------------------------------------ sampled emission (P9)
+def test_sampled_emission_is_unbiased_for_power():
+    w = R.configs.c2(n_side=2, D=8, lams=(550e-6,), fields_deg=(0.0,), sensor_n=32,
+                     map_side=64)
+    sysm = w.system
+    sysm.sensor.pitch = 1.0          # every secondary ray lands on the sensor
+    ref = P.psf(w)[0]
+    assert float(ref.sum()) == pytest.approx(4.0, rel=1e-12)
+    sysm.doe.emit = "sampled"
+    errs = {}
+    for n in (16, 256):
+        sysm.doe.n_ssr = n
+        acc = torch.zeros_like(ref)
+        K = 24
+        e2 = 0.0
+        for seed in range(K):
+            sysm.doe.seed = 1000 + seed
+            img = P.psf(w)[0]
+            acc += img
+            e2 += float(((img - ref) ** 2).sum())
+        errs[n] = e2 / K
+        mean = acc / K
+        # each draw carries S/N of the patch power S: the total is exact per sample
+        assert float(mean.sum()) == pytest.approx(float(ref.sum()), rel=1e-12)
+        assert float(((mean - ref) ** 2).sum()) < errs[n]
+    # Monte-Carlo error variance falls like 1/N
+    ratio = errs[16] / errs[256]
+    assert 8.0 < ratio < 32.0
+
+
+# ------------------------------------------------------------------ sensor splat
+def test_bilinear_splat_hand_computed_taps():
+    nx, ny, pitch, cx, cy = 8, 6, 2e-3, 0.1, -0.05
+    # pixel (i, j) centre: cx + (i - 3.5) pitch, cy + (j - 2.5) pitch
+    x = torch.tensor([cx + (2 - 3.5 + 0.25) * pitch, cx + (7 - 3.5 + 0.5) * pitch,
+                      cx + (-1 - 3.5 + 0.5) * pitch], dtype=F64)
+    y = torch.tensor([cy + (4 - 2.5 + 0.6) * pitch, cy + (0 - 2.5) * pitch,
+                      cy + (1 - 2.5) * pitch], dtype=F64)
+    w = torch.tensor([2.0, 1.0, 5.0], dtype=F64)
+    img = S.splat_incoherent(x, y, w, torch.ones(3, dtype=torch.bool), nx, ny, pitch,
+                             cx, cy).reshape(ny, nx)
+    ref = torch.zeros(ny, nx, dtype=F64)
+    ref[4, 2] += 2 * 0.75 * 0.4
+    ref[4, 3] += 2 * 0.25 * 0.4
+    ref[5, 2] += 2 * 0.75 * 0.6
+    ref[5, 3] += 2 * 0.25 * 0.6
+    ref[0, 7] += 1 * 0.5          # right neighbour (i = 8) is off the sensor
+    ref[1, 0] += 5 * 0.5          # left neighbour (i = -1) is off the sensor
+    assert torch.allclose(img, ref, atol=1e-12)
