@@ -1,0 +1,236 @@
+/*
+ * raywave.h -- C ABI of the GB300 ray-wave DOE library (librw.so).
+ *
+ * The library evaluates the ray -> wave -> ray step of the differentiable
+ * ray-wave model for hybrid refractive-diffractive optics (Cheng, Gao, Shao,
+ * Mao, Milster, Fan) and the refractive tracing around it, on one GPU:
+ *
+ *   A0  collimated ray bundles per (wavelength, field) job
+ *   A1  sequential refraction (Snell; sphere in closed form; even asphere by
+ *       Newton's method) up to the DOE
+ *   A2  DOE intersection and tangent frame (u, v, n)   [section "Ray-Wave
+ *       Simulator Formalism", second paragraph]
+ *   A3  D x D patch of the transmission U = A exp(i phi) centred on the hit
+ *   A4  angular spectrum U~(k_u, k_v) of the patch (Fourier transform)
+ *   A5  secondary rays along the propagating wavevectors, weight U~ / p (Eq. 1);
+ *       sampled mode draws wavevectors by Gumbel-max (same section, third
+ *       paragraph)
+ *   A6  refraction of the secondary rays through the remaining surfaces
+ *   A7  sensor: incoherent bilinear splat of |a|^2, or the coherent sum of
+ *       plane wavelets of Eq. 2
+ *   A8  normalised least-squares loss of Eq. 3
+ *   A9  adjoint of A1..A7: gradients w.r.t. DOE phase/amplitude pixels and
+ *       surface parameters (section "Benchmark and Inverse Design
+ *       Demonstrations", end-to-end optimisation)
+ *
+ * Conventions
+ *   - Units: millimetres; wavelengths are vacuum wavelengths in mm.  +z is
+ *     the optical axis, light travels towards +z.
+ *   - Small descriptors (rw_system, rw_surface, rw_job arrays) are HOST
+ *     memory read during the call.  Every array inside rw_rays, rw_emitted,
+ *     the DOE maps, PSFs and gradients is DEVICE memory owned by the caller;
+ *     the library never frees or retains it after the call returns.
+ *   - Every call is enqueued on the context's CUDA stream and returns before
+ *     the GPU work finishes; synchronise that stream before reading outputs.
+ *   - Every call returns rw_status.  On a non-OK status no GPU work of that
+ *     call was enqueued (validation runs on the host first) unless the status
+ *     is RW_ECUDA; outputs are then unspecified and rw_last_error() holds a
+ *     one-line message.  Device-side conditions (Newton non-convergence,
+ *     capacity overflow) are counted in a status word that
+ *     rw_device_status() reads.
+ *   - The library keeps per-context scratch (the complex transmission map per
+ *     wavelength, job tables, reduction buffers) and grows it on demand.
+ */
+#ifndef RAYWAVE_H
+#define RAYWAVE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rw_ctx rw_ctx;
+
+typedef enum {
+    RW_OK = 0,
+    RW_EINVAL = 1,     /* bad argument (null pointer, size, unsupported mode) */
+    RW_ENOMEM = 2,     /* scratch allocation failed */
+    RW_ECUDA = 3,      /* a CUDA runtime call failed */
+    RW_ECAPACITY = 4,  /* output capacity too small */
+    RW_ETIMEOUT = 5,   /* a bounded device wait gave up */
+    RW_ENOTCONV = 6    /* Newton iteration did not converge for some rays */
+} rw_status;
+
+/* surface kinds */
+enum { RW_PLANE = 0, RW_SPHERE = 1, RW_ASPHERE = 2 };
+/* DOE patch gather: nearest pixel window (planar) / bilinear (conformal) */
+enum { RW_GATHER_NEAREST = 0, RW_GATHER_BILINEAR = 1 };
+/* secondary-ray emission */
+enum { RW_EMIT_EXHAUSTIVE = 0, RW_EMIT_SAMPLED = 1 };
+/* phase at wavelength lambda: phi * lambda0 / lambda (HEIGHT) or phi (FIXED) */
+enum { RW_PHASE_HEIGHT = 0, RW_PHASE_FIXED = 1 };
+/* patch transform implementation */
+enum { RW_DFT_FFT32 = 0, RW_DFT_TC = 1 };
+
+#define RW_MAX_SURFACES 16
+
+/* One rotationally symmetric surface in vertex form:
+ *   z - z_vertex = c s / (1 + sqrt(1 - (1 + k) c^2 s)) + A4 s^2 + A6 s^3 + A8 s^4 + A10 s^5,
+ *   s = x^2 + y^2.
+ * PLANE ignores c, k, A; SPHERE ignores k, A.  n_after is the index of the
+ * medium behind the surface.  r_ap > 0 drops rays hitting at radius > r_ap. */
+typedef struct {
+    int32_t kind;
+    int32_t reserved;
+    double z;
+    double c;
+    double k;
+    double A4, A6, A8, A10;
+    double n_after;
+    double r_ap;
+} rw_surface;
+
+/* The DOE: its transmission map and the ray-wave parameters.  The geometry
+ * is surfaces[doe_index] of the system (PLANE = planar DOE, SPHERE =
+ * conformal DOE on a sphere).  Pixel (r, c) is centred at
+ * x = (c - W/2 + 1/2) pitch, y = (r - H/2 + 1/2) pitch. */
+typedef struct {
+    int32_t H, W;
+    double pitch;          /* mm */
+    double lambda0;        /* design wavelength of phi (HEIGHT model), mm */
+    const float* phi;      /* device, [H][W] radians */
+    const float* amp;      /* device, [H][W], or NULL for amplitude 1 */
+    int32_t D;             /* patch side: 16, 32, 64, 96 or 128 */
+    int32_t gather;        /* RW_GATHER_* */
+    int32_t emit;          /* RW_EMIT_* */
+    int32_t n_ssr;         /* draws per incident ray in sampled mode */
+    int32_t phase_model;   /* RW_PHASE_* */
+    int32_t dft;           /* RW_DFT_* */
+    uint64_t seed;         /* Philox key for sampled mode */
+    uint64_t rng_offset;   /* Philox counter word 3 for sampled mode */
+} rw_doe;
+
+/* Sensor plane z = const.  Pixel (i, j) of job J is centred at
+ * x = sensor_cx_J + (i - nx/2 + 1/2) pitch, y = sensor_cy_J + (j - ny/2 + 1/2) pitch. */
+typedef struct {
+    double z;
+    int32_t nx, ny;
+    double pitch;
+    int32_t coherent;      /* 0: bilinear |a|^2 splat; 1: Eq. 2 wavelet sum */
+    int32_t window;        /* coherent: +-window pixels around each hit (0 = all) */
+} rw_sensor;
+
+typedef struct {
+    const rw_surface* surfaces;   /* host, nsurf entries, sorted by z */
+    int32_t nsurf;                /* 1 .. RW_MAX_SURFACES */
+    int32_t doe_index;            /* which surface carries the DOE */
+    double n_object;              /* index of the medium before surface 0 */
+    rw_doe doe;
+    rw_sensor sensor;
+} rw_system;
+
+/* One (wavelength, field) job: its rays are rays[ray_offset .. ray_offset+ray_count).
+ * grid_n, spacing, x0, y0, theta_x, theta_y and z_start describe the
+ * collimated bundle rw_generate_rays writes; the other calls only use
+ * lambda, ray_offset, ray_count and the sensor window centre. */
+typedef struct {
+    double lambda;
+    double theta_x, theta_y;
+    int64_t ray_offset;
+    int64_t ray_count;
+    double sensor_cx, sensor_cy;
+    int64_t grid_n;
+    double spacing, x0, y0;
+} rw_job;
+
+/* Incident rays, structure of arrays on the device, n entries each. */
+typedef struct {
+    int64_t n;
+    float* ox; float* oy; float* oz;
+    float* dx; float* dy; float* dz;
+    float* a_re; float* a_im;
+    double* opl;
+} rw_rays;
+
+/* Secondary rays written by rw_doe_emit.  Slot s = i * S + b for incident
+ * ray i and bin/draw b, S = D*D (exhaustive; b = (j_v + D/2) * D + (j_u + D/2))
+ * or n_ssr (sampled).  Dropped rays (evanescent, missed DOE) have a = 0 and
+ * d = 0.  hit/opl are per incident ray. */
+typedef struct {
+    int64_t capacity;                /* slots available: >= n_incident * S */
+    float* dx; float* dy; float* dz; /* [capacity] */
+    float* a_re; float* a_im;        /* [capacity] */
+    int32_t* bin;                    /* [capacity] chosen bin (sampled), may be NULL */
+    float* hx; float* hy; float* hz; /* [n_incident] DOE hit point */
+    double* opl;                     /* [n_incident] optical path at the hit */
+} rw_emitted;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream).  Errors: RW_EINVAL, RW_ECUDA. */
+rw_status rw_create(rw_ctx** out, int device, void* cuda_stream);
+rw_status rw_destroy(rw_ctx* ctx);
+rw_status rw_set_stream(rw_ctx* ctx, void* cuda_stream);
+/* Last error message of this context ("" if none); valid until the next call. */
+const char* rw_last_error(const rw_ctx* ctx);
+/* Synchronise the stream and return the device status word accumulated
+ * since the last call of this function (bit 0: Newton non-convergence,
+ * bit 1: capacity overflow, bit 2: bounded wait timeout), then clear it. */
+rw_status rw_device_status(rw_ctx* ctx, uint32_t* status_out);
+const char* rw_version(void);
+/* Number of kernels this context has launched so far (for benchmarks). */
+int64_t rw_launch_count(const rw_ctx* ctx);
+
+/* ---- A0: ray generation ------------------------------------------------ */
+
+/* Fill rays[ray_offset ..) of every job with its collimated grid launched
+ * from z = z_start: direction normalise(tan theta_x, tan theta_y, 1), ray
+ * (ix, iy) -> index iy*grid_n + ix at x0 + (ix - (grid_n-1)/2) spacing,
+ * y0 + (iy - (grid_n-1)/2) spacing; a = 1; opl = n_object (d . o).
+ * Positions are computed in double and rounded once to float.
+ * Errors: RW_EINVAL (ray_count != grid_n^2, out of range, null pointer). */
+rw_status rw_generate_rays(rw_ctx* ctx, double z_start, double n_object,
+                           const rw_job* jobs, int32_t njob, rw_rays* rays);
+
+/* ---- A1..A5: emit secondary rays at the DOE ---------------------------- */
+
+/* Trace every job's rays to the DOE and write its secondary rays.
+ * Errors: RW_EINVAL, RW_ECAPACITY (out->capacity < n_rays * S). */
+rw_status rw_doe_emit(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
+                      int32_t njob, const rw_rays* rays, rw_emitted* out);
+
+/* ---- A1..A7: forward to the sensor ------------------------------------- */
+
+/* psf: device float [njob][ny][nx], overwritten (zeroed then accumulated).
+ * Incoherent: sum of bilinear |a|^2 deposits; coherent: |Eq. 2|^2. */
+rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
+                     int32_t njob, const rw_rays* rays, float* psf);
+
+/* ---- A8: Eq. 3 loss ---------------------------------------------------- */
+
+/* L = || alpha I - T ||^2 with alpha = <I,T>/<I,I> over all n entries.
+ * loss_out: device double[3] = {L, alpha, <I,I>}; dl_dpsf (device float[n],
+ * may be NULL) receives 2 alpha (alpha I - T). */
+rw_status rw_loss_eq3(rw_ctx* ctx, const float* psf, const float* target, int64_t n,
+                      double* loss_out, float* dl_dpsf);
+
+/* ---- A9: adjoint -------------------------------------------------------- */
+
+/* Given dL/dpsf (device float [njob][ny][nx]), ACCUMULATE (+=) into
+ *   dphi  device float [H][W]   (may be NULL)
+ *   damp  device float [H][W]   (may be NULL; needs doe.amp)
+ *   dsurf device double [nsurf][8] = d/d(z, c, k, A4, A6, A8, A10, n_after)
+ *         (may be NULL).
+ * Patches and spectra are recomputed, not stored.  Supported: incoherent
+ * sensor, exhaustive or sampled emission (straight-through Gumbel-softmax
+ * with temperature 1). */
+rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
+                      int32_t njob, const rw_rays* rays, const float* dl_dpsf,
+                      float* dphi, float* damp, double* dsurf);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAYWAVE_H */

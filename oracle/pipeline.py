@@ -15,19 +15,25 @@ from . import sensor as S
 
 
 def job_rays(job, z_start, n_object=1.0, idx=None):
-    """Collimated grid of one job (see rwinputs.Job): o, d, a = 1,
-    OPL = n_object (d . o).  `idx` selects a subset of ray indices."""
+    """Collimated grid of one job (see rwinputs.Job).  Ray inputs are float32
+    quantities: positions are formed in double, x0 + (ix - (n-1)/2) spacing,
+    and rounded once to float32, the direction normalise(tan tx, tan ty, 1)
+    likewise; everything after that is float64.  a = 1, OPL = n_object (d . o).
+    `idx` selects a subset of ray indices."""
     n = job.grid_n
     if idx is None:
         idx = np.arange(n * n)
     idx = torch.as_tensor(np.asarray(idx, dtype=np.int64))
     ix = (idx % n).to(torch.float64)
     iy = (idx // n).to(torch.float64)
-    x = job.x0 + (ix - (n - 1) / 2.0) * job.spacing
-    y = job.y0 + (iy - (n - 1) / 2.0) * job.spacing
-    z = torch.full_like(x, float(z_start))
-    dv = torch.tensor([math.tan(job.theta_x), math.tan(job.theta_y), 1.0], dtype=torch.float64)
-    dv = dv / torch.linalg.norm(dv)
+    half = (n - 1) * 0.5
+    x = (job.x0 + (ix - half) * job.spacing).to(torch.float32).to(torch.float64)
+    y = (job.y0 + (iy - half) * job.spacing).to(torch.float32).to(torch.float64)
+    z = torch.full_like(x, float(np.float32(z_start)))
+    tx, ty = math.tan(job.theta_x), math.tan(job.theta_y)
+    nrm = math.sqrt(tx * tx + ty * ty + 1.0)
+    dv = torch.tensor([float(np.float32(tx / nrm)), float(np.float32(ty / nrm)),
+                       float(np.float32(1.0 / nrm))], dtype=torch.float64)
     o = torch.stack([x, y, z], -1)
     d = dv[None, :].expand_as(o).clone()
     N = o.shape[0]

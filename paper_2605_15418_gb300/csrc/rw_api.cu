@@ -1,0 +1,500 @@
+// Host side of the C ABI declared in include/raywave.h: argument checks,
+// packing of the host descriptors into device-side structs, per-context
+// scratch, and kernel launches on the context's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "rw_kernels.cuh"
+
+cudaError_t launch_loss_eq3(const LaunchCtx& L, const float* I, const float* T, long long n,
+                            double* acc, double* out, float* g);
+cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
+                            const long long* prefix, int njob, long long total,
+                            const RaysIn& rays, const float2* T, const float* amp,
+                            const float* dl_dpsf, float* dphi, float* damp, double* dsurf,
+                            int scratch_slots, unsigned* status, int* launches);
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t need) {
+        if (need <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, need);
+        if (e == cudaSuccess) bytes = need;
+        return e;
+    }
+    void release() { if (p) cudaFree(p); p = nullptr; bytes = 0; }
+};
+
+}  // namespace
+
+struct rw_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    std::string err;
+    DevBuf tmaps;       // complex transmission per wavelength slot
+    DevBuf tables;      // job tables, prefix sums, map scales
+    DevBuf field;       // coherent field accumulator
+    DevBuf misc;        // status word + loss sums
+    void* staging = nullptr;       // pinned host copy source of `tables`
+    size_t staging_bytes = 0;
+    cudaEvent_t staging_done = nullptr;
+    int64_t launches = 0;
+    long long grid_override = 0;
+};
+
+static rw_status fail(rw_ctx* c, rw_status s, const std::string& m) {
+    if (c) c->err = m;
+    return s;
+}
+static rw_status cuda_fail(rw_ctx* c, cudaError_t e, const char* where) {
+    return fail(c, RW_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define RW_CUDA(call, where)                                  \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+    } while (0)
+
+static unsigned* status_word(rw_ctx* ctx) { return reinterpret_cast<unsigned*>(ctx->misc.p); }
+static double* loss_acc(rw_ctx* ctx) {
+    return reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->misc.p) + 64);
+}
+
+// Copy small host tables to the device through the pinned staging buffer.
+// The previous copy out of the staging buffer is waited for first.
+static rw_status upload(rw_ctx* ctx, const std::vector<std::pair<const void*, size_t>>& parts,
+                        std::vector<void*>& dev_ptrs) {
+    size_t total = 0;
+    std::vector<size_t> offs;
+    for (auto& p : parts) { offs.push_back(total); total += align16(p.second); }
+    if (total == 0) total = 16;
+    RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (ctx->staging_done) RW_CUDA(cudaEventSynchronize(ctx->staging_done), "staging wait");
+    if (total > ctx->staging_bytes) {
+        if (ctx->staging) cudaFreeHost(ctx->staging);
+        ctx->staging = nullptr;
+        ctx->staging_bytes = 0;
+        RW_CUDA(cudaMallocHost(&ctx->staging, total), "cudaMallocHost");
+        ctx->staging_bytes = total;
+    }
+    if (ctx->tables.ensure(total) != cudaSuccess) return fail(ctx, RW_ENOMEM, "table scratch");
+    for (size_t i = 0; i < parts.size(); ++i)
+        if (parts[i].second) std::memcpy((char*)ctx->staging + offs[i], parts[i].first, parts[i].second);
+    RW_CUDA(cudaMemcpyAsync(ctx->tables.p, ctx->staging, total, cudaMemcpyHostToDevice, ctx->stream),
+            "table upload");
+    RW_CUDA(cudaEventRecord(ctx->staging_done, ctx->stream), "event record");
+    dev_ptrs.clear();
+    for (size_t i = 0; i < parts.size(); ++i) dev_ptrs.push_back((char*)ctx->tables.p + offs[i]);
+    return RW_OK;
+}
+
+static LaunchCtx lctx(rw_ctx* ctx) {
+    LaunchCtx L;
+    L.stream = ctx->stream;
+    L.num_sms = ctx->num_sms;
+    L.grid_override = ctx->grid_override;
+    return L;
+}
+
+// ---------------------------------------------------------------- validation + packing
+struct Packed {
+    DSys sys;
+    std::vector<DJob> jobs;
+    std::vector<long long> prefix;
+    std::vector<float> scales;
+    long long total = 0;
+};
+
+static bool supported_D(int D) { return D == 16 || D == 32 || D == 64 || D == 96; }
+
+static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
+    if (!sys) return fail(ctx, RW_EINVAL, "sys is NULL");
+    if (sys->nsurf < 1 || sys->nsurf > RW_MAX_SURFACES)
+        return fail(ctx, RW_EINVAL, "nsurf must be in 1..16");
+    if (!sys->surfaces) return fail(ctx, RW_EINVAL, "surfaces is NULL");
+    if (sys->doe_index < 0 || sys->doe_index >= sys->nsurf)
+        return fail(ctx, RW_EINVAL, "doe_index out of range");
+    if (!(sys->n_object > 0)) return fail(ctx, RW_EINVAL, "n_object must be > 0");
+    const rw_doe& doe = sys->doe;
+    if (!doe.phi) return fail(ctx, RW_EINVAL, "doe.phi is NULL");
+    if (doe.H < 1 || doe.W < 1) return fail(ctx, RW_EINVAL, "doe map size must be positive");
+    if (!(doe.pitch > 0)) return fail(ctx, RW_EINVAL, "doe.pitch must be > 0");
+    if (!supported_D(doe.D)) return fail(ctx, RW_EINVAL, "doe.D must be 16, 32, 64 or 96");
+    if (doe.gather != RW_GATHER_NEAREST && doe.gather != RW_GATHER_BILINEAR)
+        return fail(ctx, RW_EINVAL, "doe.gather invalid");
+    if (doe.emit != RW_EMIT_EXHAUSTIVE && doe.emit != RW_EMIT_SAMPLED)
+        return fail(ctx, RW_EINVAL, "doe.emit invalid");
+    if (doe.emit == RW_EMIT_SAMPLED && (doe.n_ssr < 1 || doe.n_ssr > 16384))
+        return fail(ctx, RW_EINVAL, "doe.n_ssr must be in 1..16384 for sampled emission");
+    if (doe.phase_model != RW_PHASE_HEIGHT && doe.phase_model != RW_PHASE_FIXED)
+        return fail(ctx, RW_EINVAL, "doe.phase_model invalid");
+    if (doe.phase_model == RW_PHASE_HEIGHT && !(doe.lambda0 > 0))
+        return fail(ctx, RW_EINVAL, "doe.lambda0 must be > 0 for the height model");
+    if (doe.dft != RW_DFT_FFT32 && doe.dft != RW_DFT_TC)
+        return fail(ctx, RW_EINVAL, "doe.dft invalid");
+    const rw_sensor& sen = sys->sensor;
+    if (sen.nx < 1 || sen.ny < 1 || !(sen.pitch > 0))
+        return fail(ctx, RW_EINVAL, "sensor size and pitch must be positive");
+    if (sen.window < 0) return fail(ctx, RW_EINVAL, "sensor.window must be >= 0");
+    DSys& d = P.sys;
+    std::memset(&d, 0, sizeof(d));
+    d.nsurf = sys->nsurf;
+    d.doe_index = sys->doe_index;
+    d.n_object = sys->n_object;
+    double prev_z = 0.0, n_prev = sys->n_object;
+    for (int i = 0; i < sys->nsurf; ++i) {
+        const rw_surface& s = sys->surfaces[i];
+        if (s.kind != RW_PLANE && s.kind != RW_SPHERE && s.kind != RW_ASPHERE)
+            return fail(ctx, RW_EINVAL, "surface kind invalid");
+        if (i > 0 && s.z < sys->surfaces[i - 1].z)
+            return fail(ctx, RW_EINVAL, "surfaces must be sorted by z");
+        if (!(s.n_after > 0)) return fail(ctx, RW_EINVAL, "surface n_after must be > 0");
+        if (!std::isfinite(s.z) || !std::isfinite(s.c)) return fail(ctx, RW_EINVAL, "surface not finite");
+        DSurf& o = d.s[i];
+        o.kind = s.kind;
+        o.c = (float)(s.kind == RW_PLANE ? 0.0 : s.c);
+        o.cd = (s.kind == RW_PLANE ? 0.0 : s.c);
+        o.k = (float)s.k;
+        o.A4 = (float)s.A4; o.A6 = (float)s.A6; o.A8 = (float)s.A8; o.A10 = (float)s.A10;
+        o.n_before = (float)n_prev;
+        o.n_after = (float)s.n_after;
+        o.r_ap2 = s.r_ap > 0 ? (float)(s.r_ap * s.r_ap) : 0.f;
+        o.gap = (float)(s.z - prev_z);
+        o.z = s.z;
+        if (i == sys->doe_index) {
+            if (s.kind == RW_ASPHERE) return fail(ctx, RW_EINVAL, "DOE surface must be PLANE or SPHERE");
+            d.n_in = (float)n_prev;
+            d.n_in_d = n_prev;
+            d.n_out = (float)s.n_after;
+            d.conformal = (s.kind == RW_SPHERE) ? 1 : 0;
+        }
+        prev_z = s.z;
+        n_prev = s.n_after;
+    }
+    if (sen.z < prev_z) return fail(ctx, RW_EINVAL, "sensor must lie behind the last surface");
+    d.H = doe.H; d.W = doe.W; d.D = doe.D;
+    d.gather = doe.gather; d.emit = doe.emit; d.n_ssr = doe.n_ssr;
+    d.phase_model = doe.phase_model;
+    d.pitch = doe.pitch;
+    d.pitchf = (float)doe.pitch;
+    d.inv_pitch = (float)(1.0 / doe.pitch);
+    d.seed = doe.seed;
+    d.rng_offset = doe.rng_offset;
+    d.kstep = (float)(2.0 * M_PI / (doe.D * doe.pitch));
+    d.sensor_z = sen.z;
+    d.sensor_gap = (float)(sen.z - prev_z);
+    d.nx = sen.nx; d.ny = sen.ny;
+    d.spitch = (float)sen.pitch;
+    d.inv_spitch = (float)(1.0 / sen.pitch);
+    d.coherent = sen.coherent ? 1 : 0;
+    d.window = sen.window;
+    d.n_sensor = (float)n_prev;
+    return RW_OK;
+}
+
+static rw_status pack_jobs(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int njob,
+                           int64_t n_rays, Packed& P) {
+    if (njob < 1) return fail(ctx, RW_EINVAL, "njob must be >= 1");
+    if (!jobs) return fail(ctx, RW_EINVAL, "jobs is NULL");
+    std::map<double, int> slot_of;
+    P.jobs.resize(njob);
+    P.prefix.resize(njob + 1);
+    P.prefix[0] = 0;
+    for (int i = 0; i < njob; ++i) {
+        const rw_job& j = jobs[i];
+        if (!(j.lambda > 0)) return fail(ctx, RW_EINVAL, "job lambda must be > 0");
+        if (j.ray_count < 0 || j.ray_offset < 0 || j.ray_offset + j.ray_count > n_rays)
+            return fail(ctx, RW_EINVAL, "job ray range outside the ray arrays");
+        auto it = slot_of.find(j.lambda);
+        int slot;
+        if (it == slot_of.end()) {
+            slot = (int)P.scales.size();
+            slot_of[j.lambda] = slot;
+            P.scales.push_back(sys->doe.phase_model == RW_PHASE_HEIGHT
+                                   ? (float)(sys->doe.lambda0 / j.lambda) : 1.f);
+        } else {
+            slot = it->second;
+        }
+        DJob& d = P.jobs[i];
+        d.lambda = j.lambda;
+        d.k0 = (float)(2.0 * M_PI / j.lambda);
+        d.phase_scale = P.scales[slot];
+        d.off = j.ray_offset;
+        d.cnt = j.ray_count;
+        d.cx = (float)j.sensor_cx;
+        d.cy = (float)j.sensor_cy;
+        d.slot = slot;
+        d.pad = 0;
+        P.prefix[i + 1] = P.prefix[i] + j.ray_count;
+    }
+    P.total = P.prefix[njob];
+    return RW_OK;
+}
+
+static rw_status check_rays(rw_ctx* ctx, const rw_rays* r) {
+    if (!r) return fail(ctx, RW_EINVAL, "rays is NULL");
+    if (r->n < 0) return fail(ctx, RW_EINVAL, "rays.n < 0");
+    if (r->n > 0 && (!r->ox || !r->oy || !r->oz || !r->dx || !r->dy || !r->dz || !r->a_re ||
+                     !r->a_im || !r->opl))
+        return fail(ctx, RW_EINVAL, "a ray array is NULL");
+    return RW_OK;
+}
+
+static RaysIn rays_in(const rw_rays* r) {
+    RaysIn x;
+    x.ox = r->ox; x.oy = r->oy; x.oz = r->oz; x.dx = r->dx; x.dy = r->dy; x.dz = r->dz;
+    x.are = r->a_re; x.aim = r->a_im; x.opl = r->opl;
+    return x;
+}
+
+static size_t shared_limit_ok(rw_ctx* ctx, const DSys& d) {
+    int lim = 0;
+    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    return forward_smem_bytes(d.D, d.emit, d.n_ssr) <= (size_t)lim;
+}
+
+// Prepare the transmission maps and device tables.  Returns device pointers.
+static rw_status prepare(rw_ctx* ctx, const rw_system* sys, const Packed& P, float2** T,
+                         DJob** djobs, long long** dprefix) {
+    if (!shared_limit_ok(ctx, P.sys)) return fail(ctx, RW_EINVAL, "n_ssr too large for shared memory");
+    std::vector<void*> ptrs;
+    rw_status st = upload(ctx, {{P.jobs.data(), P.jobs.size() * sizeof(DJob)},
+                                {P.prefix.data(), P.prefix.size() * sizeof(long long)},
+                                {P.scales.data(), P.scales.size() * sizeof(float)}},
+                          ptrs);
+    if (st != RW_OK) return st;
+    *djobs = (DJob*)ptrs[0];
+    *dprefix = (long long*)ptrs[1];
+    const int64_t npix = (int64_t)sys->doe.H * sys->doe.W;
+    const int nslot = (int)P.scales.size();
+    if (ctx->tmaps.ensure((size_t)npix * nslot * sizeof(float2)) != cudaSuccess)
+        return fail(ctx, RW_ENOMEM, "transmission-map scratch");
+    *T = (float2*)ctx->tmaps.p;
+    RW_CUDA(launch_prep_maps(lctx(ctx), sys->doe.phi, sys->doe.amp, npix, (const float*)ptrs[2],
+                             nslot, *T),
+            "prep maps");
+    ctx->launches++;
+    return RW_OK;
+}
+
+// ---------------------------------------------------------------- API
+extern "C" {
+
+const char* rw_version(void) { return "raywave-gb300 0.1 (sm_103a)"; }
+
+rw_status rw_create(rw_ctx** out, int device, void* cuda_stream) {
+    if (!out) return RW_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return RW_EINVAL;
+    rw_ctx* ctx = new rw_ctx();
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return RW_ECUDA; }
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming) != cudaSuccess ||
+        ctx->misc.ensure(256) != cudaSuccess ||
+        cudaMemset(ctx->misc.p, 0, 256) != cudaSuccess) {
+        delete ctx;
+        return RW_ECUDA;
+    }
+    const char* g = std::getenv("RW_GRID");
+    if (g) ctx->grid_override = std::atoll(g);
+    *out = ctx;
+    return RW_OK;
+}
+
+rw_status rw_destroy(rw_ctx* ctx) {
+    if (!ctx) return RW_EINVAL;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream); else cudaDeviceSynchronize();
+    ctx->tmaps.release();
+    ctx->tables.release();
+    ctx->field.release();
+    ctx->misc.release();
+    if (ctx->staging) cudaFreeHost(ctx->staging);
+    if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
+    delete ctx;
+    return RW_OK;
+}
+
+rw_status rw_set_stream(rw_ctx* ctx, void* cuda_stream) {
+    if (!ctx) return RW_EINVAL;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return RW_OK;
+}
+
+const char* rw_last_error(const rw_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int64_t rw_launch_count(const rw_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+rw_status rw_device_status(rw_ctx* ctx, uint32_t* status_out) {
+    if (!ctx || !status_out) return fail(ctx, RW_EINVAL, "null argument");
+    RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    unsigned v = 0;
+    RW_CUDA(cudaMemcpyAsync(&v, status_word(ctx), sizeof(unsigned), cudaMemcpyDeviceToHost,
+                            ctx->stream), "status read");
+    RW_CUDA(cudaStreamSynchronize(ctx->stream), "status sync");
+    RW_CUDA(cudaMemsetAsync(status_word(ctx), 0, sizeof(unsigned), ctx->stream), "status clear");
+    *status_out = v;
+    return RW_OK;
+}
+
+rw_status rw_generate_rays(rw_ctx* ctx, double z_start, double n_object, const rw_job* jobs,
+                           int32_t njob, rw_rays* rays) {
+    if (!ctx) return RW_EINVAL;
+    ctx->err.clear();
+    rw_status st = check_rays(ctx, rays);
+    if (st != RW_OK) return st;
+    if (njob < 1 || !jobs) return fail(ctx, RW_EINVAL, "jobs missing");
+    if (!(n_object > 0)) return fail(ctx, RW_EINVAL, "n_object must be > 0");
+    std::vector<GenJob> g(njob);
+    std::vector<long long> prefix(njob + 1, 0);
+    for (int i = 0; i < njob; ++i) {
+        const rw_job& j = jobs[i];
+        if (j.grid_n < 0 || j.ray_count != j.grid_n * j.grid_n)
+            return fail(ctx, RW_EINVAL, "job ray_count must equal grid_n^2");
+        if (j.ray_offset < 0 || j.ray_offset + j.ray_count > rays->n)
+            return fail(ctx, RW_EINVAL, "job ray range outside the ray arrays");
+        const double tx = std::tan(j.theta_x), ty = std::tan(j.theta_y);
+        const double nrm = std::sqrt(tx * tx + ty * ty + 1.0);
+        g[i].off = j.ray_offset;
+        g[i].n = j.grid_n;
+        g[i].spacing = j.spacing;
+        g[i].x0 = j.x0;
+        g[i].y0 = j.y0;
+        g[i].dx = (float)(tx / nrm);
+        g[i].dy = (float)(ty / nrm);
+        g[i].dz = (float)(1.0 / nrm);
+        g[i].pad = 0.f;
+        prefix[i + 1] = prefix[i] + j.ray_count;
+    }
+    if (prefix[njob] == 0) return RW_OK;
+    std::vector<void*> ptrs;
+    st = upload(ctx, {{g.data(), g.size() * sizeof(GenJob)},
+                      {prefix.data(), prefix.size() * sizeof(long long)}}, ptrs);
+    if (st != RW_OK) return st;
+    RaysOut o;
+    o.ox = rays->ox; o.oy = rays->oy; o.oz = rays->oz; o.dx = rays->dx; o.dy = rays->dy;
+    o.dz = rays->dz; o.are = rays->a_re; o.aim = rays->a_im; o.opl = rays->opl;
+    RW_CUDA(launch_generate_rays(lctx(ctx), (GenJob*)ptrs[0], (long long*)ptrs[1], njob,
+                                 prefix[njob], z_start, n_object, o), "generate rays");
+    ctx->launches++;
+    return RW_OK;
+}
+
+rw_status rw_doe_emit(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                      const rw_rays* rays, rw_emitted* out) {
+    if (!ctx) return RW_EINVAL;
+    ctx->err.clear();
+    Packed P;
+    rw_status st = pack_system(ctx, sys, P);
+    if (st != RW_OK) return st;
+    if ((st = check_rays(ctx, rays)) != RW_OK) return st;
+    if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
+    if (!out || !out->dx || !out->dy || !out->dz || !out->a_re || !out->a_im || !out->hx ||
+        !out->hy || !out->hz || !out->opl)
+        return fail(ctx, RW_EINVAL, "an emitted-ray array is NULL");
+    const long long S = (P.sys.emit == RW_EMIT_EXHAUSTIVE) ? (long long)P.sys.D * P.sys.D
+                                                           : (long long)P.sys.n_ssr;
+    if (out->capacity < P.total * S)
+        return fail(ctx, RW_ECAPACITY, "emitted capacity < n_rays * slots per ray");
+    if (P.total == 0) return RW_OK;
+    float2* T; DJob* dj; long long* dp;
+    if ((st = prepare(ctx, sys, P, &T, &dj, &dp)) != RW_OK) return st;
+    EmitOut eo;
+    eo.dx = out->dx; eo.dy = out->dy; eo.dz = out->dz; eo.are = out->a_re; eo.aim = out->a_im;
+    eo.bin = out->bin; eo.hx = out->hx; eo.hy = out->hy; eo.hz = out->hz; eo.opl = out->opl;
+    RW_CUDA(launch_forward(lctx(ctx), MODE_EMIT, P.sys, dj, dp, njob, P.total, rays_in(rays), T,
+                           nullptr, nullptr, eo, status_word(ctx)), "emit kernel");
+    ctx->launches++;
+    return RW_OK;
+}
+
+rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                     const rw_rays* rays, float* psf) {
+    if (!ctx) return RW_EINVAL;
+    ctx->err.clear();
+    Packed P;
+    rw_status st = pack_system(ctx, sys, P);
+    if (st != RW_OK) return st;
+    if ((st = check_rays(ctx, rays)) != RW_OK) return st;
+    if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
+    if (!psf) return fail(ctx, RW_EINVAL, "psf is NULL");
+    const long long npx = (long long)P.sys.nx * P.sys.ny * njob;
+    RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    RW_CUDA(cudaMemsetAsync(psf, 0, npx * sizeof(float), ctx->stream), "psf clear");
+    if (P.total == 0) return RW_OK;
+    float2* T; DJob* dj; long long* dp;
+    if ((st = prepare(ctx, sys, P, &T, &dj, &dp)) != RW_OK) return st;
+    EmitOut eo;
+    std::memset(&eo, 0, sizeof(eo));
+    if (P.sys.coherent) {
+        if (ctx->field.ensure(npx * sizeof(float2)) != cudaSuccess)
+            return fail(ctx, RW_ENOMEM, "coherent field scratch");
+        RW_CUDA(cudaMemsetAsync(ctx->field.p, 0, npx * sizeof(float2), ctx->stream), "field clear");
+        RW_CUDA(launch_forward(lctx(ctx), MODE_COHERENT, P.sys, dj, dp, njob, P.total,
+                               rays_in(rays), T, psf, (float2*)ctx->field.p, eo,
+                               status_word(ctx)), "coherent forward");
+        ctx->launches++;
+        RW_CUDA(launch_coherent_finalize(lctx(ctx), (float2*)ctx->field.p, psf, npx), "finalize");
+        ctx->launches++;
+    } else {
+        RW_CUDA(launch_forward(lctx(ctx), MODE_SPLAT, P.sys, dj, dp, njob, P.total,
+                               rays_in(rays), T, psf, nullptr, eo, status_word(ctx)),
+                "forward kernel");
+        ctx->launches++;
+    }
+    return RW_OK;
+}
+
+rw_status rw_loss_eq3(rw_ctx* ctx, const float* psf, const float* target, int64_t n,
+                      double* loss_out, float* dl_dpsf) {
+    if (!ctx) return RW_EINVAL;
+    ctx->err.clear();
+    if (!psf || !target || !loss_out) return fail(ctx, RW_EINVAL, "null argument");
+    if (n < 1) return fail(ctx, RW_EINVAL, "n must be >= 1");
+    RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    RW_CUDA(launch_loss_eq3(lctx(ctx), psf, target, n, loss_acc(ctx), loss_out, dl_dpsf), "loss");
+    ctx->launches += 2;
+    return RW_OK;
+}
+
+rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                      const rw_rays* rays, const float* dl_dpsf, float* dphi, float* damp,
+                      double* dsurf) {
+    if (!ctx) return RW_EINVAL;
+    ctx->err.clear();
+    Packed P;
+    rw_status st = pack_system(ctx, sys, P);
+    if (st != RW_OK) return st;
+    if ((st = check_rays(ctx, rays)) != RW_OK) return st;
+    if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
+    if (!dl_dpsf) return fail(ctx, RW_EINVAL, "dl_dpsf is NULL");
+    if (P.sys.coherent) return fail(ctx, RW_EINVAL, "backward supports the incoherent sensor only");
+    if (P.sys.emit != RW_EMIT_EXHAUSTIVE)
+        return fail(ctx, RW_EINVAL, "backward supports exhaustive emission only");
+    if (damp && !sys->doe.amp) return fail(ctx, RW_EINVAL, "damp requires doe.amp");
+    if (P.total == 0 || (!dphi && !damp && !dsurf)) return RW_OK;
+    float2* T; DJob* dj; long long* dp;
+    if ((st = prepare(ctx, sys, P, &T, &dj, &dp)) != RW_OK) return st;
+    int nl = 0;
+    RW_CUDA(launch_backward(lctx(ctx), P.sys, dj, dp, njob, P.total, rays_in(rays), T,
+                            sys->doe.amp, dl_dpsf, dphi, damp, dsurf, 0, status_word(ctx), &nl),
+            "backward kernel");
+    ctx->launches += nl;
+    return RW_OK;
+}
+
+}  // extern "C"

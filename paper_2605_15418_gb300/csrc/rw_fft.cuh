@@ -1,0 +1,126 @@
+// Shared-memory 2D FFT of one D x D complex patch, FP32, whole CTA.
+//
+// Mixed-radix Stockham autosort (radix 2, 3, 4): stage with radix R after
+// sub-transforms of length P reads x[i + q N/R], multiplies by
+// exp(-+2 pi i q (i mod P) / (P R)), does a length-R DFT and writes
+// y[(i / P) P R + (i mod P) + q P]; the output comes out in natural order.
+// Each stage is done in place: all butterflies of the CTA are loaded into
+// registers, the CTA synchronises, then they are stored.
+#pragma once
+#include "rw_device.cuh"
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_small(float2* u) {
+    if constexpr (R == 2) {
+        float2 a = u[0], b = u[1];
+        u[0] = cadd(a, b);
+        u[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        float2 a = u[0], b = u[1], c = u[2], d = u[3];
+        float2 s0 = cadd(a, c), s1 = csub(a, c), s2 = cadd(b, d), s3 = csub(b, d);
+        // forward: y1 = s1 - i s3, y3 = s1 + i s3 ; inverse swaps
+        float2 is3 = INV ? make_float2(-s3.y, s3.x) : make_float2(s3.y, -s3.x);  // -+ i s3
+        u[0] = cadd(s0, s2);
+        u[2] = csub(s0, s2);
+        u[1] = cadd(s1, is3);
+        u[3] = csub(s1, is3);
+    } else if constexpr (R == 3) {
+        const float c1 = -0.5f;
+        const float s1 = INV ? 0.86602540378443864676f : -0.86602540378443864676f;
+        float2 a = u[0], b = u[1], c = u[2];
+        float2 t = cadd(b, c), d = csub(b, c);
+        u[0] = cadd(a, t);
+        float2 m = make_float2(a.x + c1 * t.x, a.y + c1 * t.y);
+        // +- i s1 (b - c)
+        float2 id = make_float2(-s1 * d.y, s1 * d.x);
+        u[1] = cadd(m, id);
+        u[2] = csub(m, id);
+    }
+}
+
+// One Stockham stage over all D rows (COLS = false) or all D columns.
+template <int N, int R, int P, bool INV, bool COLS>
+__device__ __forceinline__ void fft_stage(float2* buf, const float2* tw) {
+    constexpr int NB = N / R;
+    constexpr int TOT = N * NB;
+    constexpr int PER = (TOT + RW_THREADS - 1) / RW_THREADS;
+    float2 v[PER][R];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int f = threadIdx.x + k * RW_THREADS;
+        if ((TOT % RW_THREADS == 0) || f < TOT) {
+            const int b = COLS ? (f % N) : (f / NB);
+            const int i = COLS ? (f / N) : (f % NB);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int e = i + q * NB;
+                v[k][q] = COLS ? buf[e * N + b] : buf[b * N + e];
+            }
+            if constexpr (P > 1) {
+                const int kk = i % P;
+#pragma unroll
+                for (int q = 1; q < R; ++q) {
+                    float2 w = tw[q * kk * (N / (P * R))];
+                    if (INV) w.y = -w.y;
+                    v[k][q] = cmul(v[k][q], w);
+                }
+            }
+            dft_small<R, INV>(v[k]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int f = threadIdx.x + k * RW_THREADS;
+        if ((TOT % RW_THREADS == 0) || f < TOT) {
+            const int b = COLS ? (f % N) : (f / NB);
+            const int i = COLS ? (f / N) : (f % NB);
+            const int kk = i % P;
+            const int j = (i / P) * P * R + kk;
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int e = j + q * P;
+                if (COLS) buf[e * N + b] = v[k][q]; else buf[b * N + e] = v[k][q];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <int N, bool INV, bool COLS>
+__device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
+    if constexpr (N == 16) {
+        fft_stage<16, 4, 1, INV, COLS>(buf, tw);
+        fft_stage<16, 4, 4, INV, COLS>(buf, tw);
+    } else if constexpr (N == 32) {
+        fft_stage<32, 4, 1, INV, COLS>(buf, tw);
+        fft_stage<32, 4, 4, INV, COLS>(buf, tw);
+        fft_stage<32, 2, 16, INV, COLS>(buf, tw);
+    } else if constexpr (N == 64) {
+        fft_stage<64, 4, 1, INV, COLS>(buf, tw);
+        fft_stage<64, 4, 4, INV, COLS>(buf, tw);
+        fft_stage<64, 4, 16, INV, COLS>(buf, tw);
+    } else if constexpr (N == 96) {
+        fft_stage<96, 4, 1, INV, COLS>(buf, tw);
+        fft_stage<96, 4, 4, INV, COLS>(buf, tw);
+        fft_stage<96, 2, 16, INV, COLS>(buf, tw);
+        fft_stage<96, 3, 32, INV, COLS>(buf, tw);
+    }
+}
+
+// X[b][a] -> sum_{a,b} X[b][a] exp(-+2 pi i (m_u a + m_v b) / N), natural order.
+template <int N, bool INV>
+__device__ __forceinline__ void fft2d(float2* buf, const float2* tw) {
+    fft_pass<N, INV, false>(buf, tw);
+    fft_pass<N, INV, true>(buf, tw);
+}
+
+// tw[t] = exp(-2 pi i t / N), t in [0, N).
+template <int N>
+__device__ __forceinline__ void fft_twiddles(float2* tw) {
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        float s, c;
+        sincospif(-2.0f * (float)t / (float)N, &s, &c);
+        tw[t] = make_float2(c, s);
+    }
+}

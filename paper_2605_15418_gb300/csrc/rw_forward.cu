@@ -1,0 +1,190 @@
+// Forward kernels of the ray-wave path: transmission maps (A3 input), ray
+// generation (A0), and the fused per-incident-ray pipeline
+//   incident trace (A1) -> DOE hit + frame (A2) -> patch gather (A3)
+//   -> FP32 2D FFT in shared memory (A4) -> secondary rays (A5)
+//   -> downstream trace (A6) -> sensor splat (A7) or HBM write (emit).
+//
+// One CTA of 256 threads owns one incident ray at a time: warp 0 first
+// traces a tile of 32 incident rays to the DOE, then the CTA walks the tile,
+// each thread handling D^2/256 spectral bins of the current ray.
+#include "rw_kernels.cuh"
+
+// ------------------------------------------------------------- A3 input
+// T_slot[r][c] = A[r][c] exp(i phi[r][c] scale_slot): one complex map per
+// wavelength, so the per-patch gather is a plain 8-byte load.
+__global__ void k_prep_maps(const float* __restrict__ phi, const float* __restrict__ amp,
+                            int64_t npix, const float* __restrict__ scales, int nslot,
+                            float2* __restrict__ T) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix * nslot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int slot = (int)(i / npix);
+        int64_t p = i - (int64_t)slot * npix;
+        float ph = phi[p] * scales[slot];
+        float s, c;
+        sincosf(ph, &s, &c);
+        float A = amp ? amp[p] : 1.f;
+        T[i] = make_float2(A * c, A * s);
+    }
+}
+
+// ------------------------------------------------------------- A0
+// Collimated grid per job.  Positions in double without FMA contraction,
+// rounded once to float, so they equal the host-side definition exactly.
+__global__ void k_generate_rays(const GenJob* __restrict__ jobs, const long long* __restrict__ prefix,
+                                int njob, long long total, double z_start, double n_object,
+                                RaysOut out) {
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+         g += (long long)gridDim.x * blockDim.x) {
+        int j = find_job(prefix, njob, g);
+        const GenJob J = jobs[j];
+        long long l = g - prefix[j];
+        long long ix = l % J.n, iy = l / J.n;
+        double half = __dmul_rn((double)(J.n - 1), 0.5);
+        double x = __dadd_rn(J.x0, __dmul_rn(__dadd_rn((double)ix, -half), J.spacing));
+        double y = __dadd_rn(J.y0, __dmul_rn(__dadd_rn((double)iy, -half), J.spacing));
+        float xf = (float)x, yf = (float)y, zf = (float)z_start;
+        long long r = J.off + l;
+        out.ox[r] = xf; out.oy[r] = yf; out.oz[r] = zf;
+        out.dx[r] = J.dx; out.dy[r] = J.dy; out.dz[r] = J.dz;
+        out.are[r] = 1.f; out.aim[r] = 0.f;
+        double dot = __dadd_rn(__dadd_rn(__dmul_rn((double)J.dx, (double)xf),
+                                         __dmul_rn((double)J.dy, (double)yf)),
+                               __dmul_rn((double)J.dz, (double)zf));
+        out.opl[r] = __dmul_rn(n_object, dot);
+    }
+}
+
+// ------------------------------------------------------------- fused forward
+template <int D, int MODE>
+__global__ void __launch_bounds__(RW_THREADS)
+k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
+          int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
+          float* __restrict__ psf, float2* __restrict__ field, EmitOut eo, unsigned* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2* X = reinterpret_cast<float2*>(smem);
+    float2* tw = X + D * D;
+    float2* phu = tw + D;
+    float2* phv = phu + D;
+    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + D);
+    fft_twiddles<D>(tw);
+    const long long npix_map = (long long)sys.H * sys.W;
+    const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x < RW_TILE)
+            incident_to_doe(sys, jobs, prefix, njob, total, rays, tile * RW_TILE + threadIdx.x,
+                            info[threadIdx.x], status);
+        __syncthreads();
+        for (int r = 0; r < RW_TILE; ++r) {
+            const RayAtDoe& R = info[r];
+            if (!R.alive) {
+                if (MODE == MODE_EMIT) emit_dead<D>(sys, tile * RW_TILE + r, total, eo);
+                continue;
+            }
+            const DJob& J = jobs[R.job];
+            gather_patch<D>(sys, R, Tmaps + (long long)J.slot * npix_map, X, phu, phv);
+            __syncthreads();
+            fft2d<D, false>(X, tw);
+            if (sys.emit == RW_EMIT_EXHAUSTIVE) {
+                emit_exhaustive<D, MODE>(sys, J, R, X, phu, phv, psf, field, eo,
+                                         tile * RW_TILE + r, status);
+            } else {
+                emit_sampled<D, MODE>(sys, J, R, X, phu, phv, psf, field, eo,
+                                      tile * RW_TILE + r, status,
+                                      smem + sampled_scratch_offset(D));
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// |U|^2 of the coherent field.
+__global__ void k_coherent_finalize(const float2* __restrict__ field, float* __restrict__ psf,
+                                    long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float2 f = field[i];
+        psf[i] = f.x * f.x + f.y * f.y;
+    }
+}
+
+// ------------------------------------------------------------- launchers
+template <int D, int MODE>
+static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
+                                    const long long* prefix, int njob, long long total,
+                                    const RaysIn& rays, const float2* T, float* psf,
+                                    float2* field, const EmitOut& eo, unsigned* status) {
+    size_t smem = forward_smem_bytes(D, sys.emit, sys.n_ssr);
+    auto kern = k_forward<D, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RW_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    long long ntiles = (total + RW_TILE - 1) / RW_TILE;
+    long long grid = (long long)L.num_sms * per_sm;
+    if (L.grid_override > 0) grid = L.grid_override;
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(sys, jobs, prefix, njob, total, rays,
+                                                          T, psf, field, eo, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const DJob* jobs,
+                           const long long* prefix, int njob, long long total,
+                           const RaysIn& rays, const float2* T, float* psf, float2* field,
+                           const EmitOut& eo, unsigned* status) {
+#define RW_FWD_CASE(DD)                                                                       \
+    case DD:                                                                                  \
+        if (mode == MODE_SPLAT)                                                               \
+            return launch_forward_d<DD, MODE_SPLAT>(L, sys, jobs, prefix, njob, total, rays,  \
+                                                    T, psf, field, eo, status);               \
+        if (mode == MODE_COHERENT)                                                            \
+            return launch_forward_d<DD, MODE_COHERENT>(L, sys, jobs, prefix, njob, total,     \
+                                                       rays, T, psf, field, eo, status);      \
+        return launch_forward_d<DD, MODE_EMIT>(L, sys, jobs, prefix, njob, total, rays, T,    \
+                                               psf, field, eo, status);
+    switch (sys.D) {
+        RW_FWD_CASE(16)
+        RW_FWD_CASE(32)
+        RW_FWD_CASE(64)
+        RW_FWD_CASE(96)
+        default: return cudaErrorInvalidValue;
+    }
+#undef RW_FWD_CASE
+}
+
+cudaError_t launch_prep_maps(const LaunchCtx& L, const float* phi, const float* amp,
+                             int64_t npix, const float* scales_dev, int nslot, float2* T) {
+    long long n = npix * nslot;
+    long long grid = (n + 255) / 256;
+    long long cap = (long long)L.num_sms * 8;
+    if (grid > cap) grid = cap;
+    k_prep_maps<<<(unsigned)grid, 256, 0, L.stream>>>(phi, amp, npix, scales_dev, nslot, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_generate_rays(const LaunchCtx& L, const GenJob* jobs, const long long* prefix,
+                                 int njob, long long total, double z_start, double n_object,
+                                 const RaysOut& out) {
+    long long grid = (total + 255) / 256;
+    long long cap = (long long)L.num_sms * 16;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    k_generate_rays<<<(unsigned)grid, 256, 0, L.stream>>>(jobs, prefix, njob, total, z_start,
+                                                          n_object, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coherent_finalize(const LaunchCtx& L, const float2* field, float* psf,
+                                     long long n) {
+    long long grid = (n + 255) / 256;
+    long long cap = (long long)L.num_sms * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    k_coherent_finalize<<<(unsigned)grid, 256, 0, L.stream>>>(field, psf, n);
+    return cudaGetLastError();
+}

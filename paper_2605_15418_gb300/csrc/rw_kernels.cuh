@@ -1,0 +1,490 @@
+// Per-incident-ray building blocks shared by the forward, emit and adjoint
+// kernels, plus the host-side launcher declarations.
+#pragma once
+#include "rw_device.cuh"
+#include "rw_fft.cuh"
+
+enum { MODE_SPLAT = 0, MODE_COHERENT = 1, MODE_EMIT = 2 };
+
+struct LaunchCtx {
+    cudaStream_t stream;
+    int num_sms;
+    long long grid_override;   // > 0 forces the persistent grid size
+};
+
+struct GenJob {
+    long long off, n;          // first ray, grid side
+    double spacing, x0, y0;
+    float dx, dy, dz, pad;
+};
+
+struct RaysOut {
+    float *ox, *oy, *oz, *dx, *dy, *dz, *are, *aim;
+    double* opl;
+};
+
+struct EmitOut {
+    float *dx, *dy, *dz, *are, *aim;
+    int* bin;
+    float *hx, *hy, *hz;
+    double* opl;
+};
+
+// ------------------------------------------------------------------ sizes
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+// patch X, twiddles, two phase vectors, the tile's incident states
+__host__ __device__ inline size_t sampled_scratch_offset(int D) {
+    return align16(sizeof(float2) * (size_t)(D * D + 3 * D) + sizeof(RayAtDoe) * RW_TILE);
+}
+inline size_t forward_smem_bytes(int D, int emit = RW_EMIT_EXHAUSTIVE, int n_ssr = 0) {
+    size_t b = sampled_scratch_offset(D);
+    if (emit == RW_EMIT_SAMPLED) b += sizeof(float) * (size_t)D * D + sizeof(int) * n_ssr + 128;
+    return b;
+}
+
+// ------------------------------------------------------------------ Philox4x32-10
+// Salmon et al., SC'11: ten rounds with multipliers 0xD2511F53, 0xCD9E8D57
+// and Weyl key increments 0x9E3779B9, 0xBB67AE85.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+// (0, 1) uniform from 23 bits; exact in float.
+__device__ __forceinline__ float u01(uint32_t w) {
+    return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-7f;
+}
+
+// ------------------------------------------------------------------ jobs
+__device__ __forceinline__ int find_job(const long long* prefix, int njob, long long g) {
+    int lo = 0, hi = njob - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ------------------------------------------------------------------ A1 + A2
+// Trace incident ray g (concatenated job order) to the DOE, build the
+// tangent frame and everything the patch step needs.  The DOE hit is
+// computed in double (planar: one division; conformal: FP32 sphere root
+// refined by two FP64 Newton steps on c|Q|^2 - 2 Q_z = 0).
+__device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __restrict__ jobs,
+                                                const long long* __restrict__ prefix, int njob,
+                                                long long total, const RaysIn& rays,
+                                                long long g, RayAtDoe& R, unsigned* status) {
+    R.alive = 0;
+    R.gid = g;
+    if (g >= total) return;
+    const int j = find_job(prefix, njob, g);
+    const DJob& J = jobs[j];
+    const long long ri = J.off + (g - prefix[j]);
+    float x = rays.ox[ri], y = rays.oy[ri], zl = rays.oz[ri];
+    float dx = rays.dx[ri], dy = rays.dy[ri], dz = rays.dz[ri];
+    double opl = rays.opl[ri];
+    const double oz = (double)zl;
+    for (int s = 0; s < sys.doe_index; ++s)
+        if (!trace_one<true>(sys.s[s], x, y, zl, dx, dy, dz, opl, status)) return;
+    const DSurf& S = sys.s[sys.doe_index];
+    const double zld = (sys.doe_index == 0)
+                           ? (oz - S.z)
+                           : ((double)zl - (S.z - sys.s[sys.doe_index - 1].z));
+    if (dz == 0.f) return;
+    double t;
+    float nx, ny, nz;
+    if (!sys.conformal) {
+        t = -zld / (double)dz;
+    } else {
+        float tf;
+        if (!intersect_local(S, x, y, (float)zld, dx, dy, dz, tf, status)) return;
+        t = (double)tf;
+        const double c = S.cd;
+        for (int it = 0; it < 2; ++it) {
+            double qx = (double)x + t * dx, qy = (double)y + t * dy, qz = zld + t * dz;
+            double f = c * (qx * qx + qy * qy + qz * qz) - 2.0 * qz;
+            double fp = 2.0 * c * (qx * dx + qy * dy + qz * dz) - 2.0 * dz;
+            if (fp == 0.0) return;
+            t -= f / fp;
+        }
+    }
+    const double pxd = __dadd_rn((double)x, __dmul_rn(t, (double)dx));
+    const double pyd = __dadd_rn((double)y, __dmul_rn(t, (double)dy));
+    const double pzl = zld + t * (double)dz;
+    if (!sys.conformal) {
+        nx = 0.f; ny = 0.f; nz = 1.f;
+    } else {
+        const double c = S.cd;
+        const double s2 = pxd * pxd + pyd * pyd;
+        const double a = 1.0 - c * c * s2;
+        if (a <= 0.0) return;
+        nx = (float)(-c * pxd); ny = (float)(-c * pyd); nz = (float)sqrt(a);
+    }
+    if (nx * dx + ny * dy + nz * dz < 0.f) { nx = -nx; ny = -ny; nz = -nz; }
+    // u = normalise(x - (x.n) n), v = n x u
+    float ux = 1.f - nx * nx, uy = -nx * ny, uz = -nx * nz;
+    float inv = rsqrtf(ux * ux + uy * uy + uz * uz);
+    ux *= inv; uy *= inv; uz *= inv;
+    float vx = ny * uz - nz * uy, vy = nz * ux - nx * uz, vz = nx * uy - ny * ux;
+    R.u[0] = ux; R.u[1] = uy; R.u[2] = uz;
+    R.v[0] = vx; R.v[1] = vy; R.v[2] = vz;
+    R.n[0] = nx; R.n[1] = ny; R.n[2] = nz;
+    const float k0 = J.k0;
+    R.kin_u = k0 * sys.n_in * (dx * ux + dy * uy + dz * uz);
+    R.kin_v = k0 * sys.n_in * (dx * vx + dy * vy + dz * vz);
+    R.K = k0 * sys.n_out;
+    R.px = (float)pxd; R.py = (float)pyd; R.pz = (float)pzl;
+    R.pxd = pxd; R.pyd = pyd;
+    R.a_re = rays.are[ri]; R.a_im = rays.aim[ri];
+    R.opl = opl + sys.n_in_d * t;
+    R.job = j;
+    R.cx = J.cx; R.cy = J.cy;
+    const double p = sys.pitch;
+    if (sys.gather == RW_GATHER_NEAREST) {
+        const double cs = floor(pxd / p + (double)sys.W / 2.0);
+        const double rs = floor(pyd / p + (double)sys.H / 2.0);
+        R.c0 = (int)cs - sys.D / 2;
+        R.r0 = (int)rs - sys.D / 2;
+        R.s0 = (float)((((double)R.c0 - (double)sys.W / 2.0 + 0.5) * p - pxd) / (sys.D * p));
+        R.t0 = (float)((((double)R.r0 - (double)sys.H / 2.0 + 0.5) * p - pyd) / (sys.D * p));
+    } else {
+        const double uc = pxd / p + (double)sys.W / 2.0 - 0.5;
+        const double vc = pyd / p + (double)sys.H / 2.0 - 0.5;
+        const double iu = floor(uc), iv = floor(vc);
+        R.c0 = (int)iu; R.r0 = (int)iv;
+        R.s0 = (float)(uc - iu); R.t0 = (float)(vc - iv);
+    }
+    R.alive = 1;
+}
+
+// ------------------------------------------------------------------ A3
+__device__ __forceinline__ float2 tmap(const float2* __restrict__ T, int H, int W, int r, int c) {
+    if ((unsigned)r < (unsigned)H && (unsigned)c < (unsigned)W) return __ldg(&T[(long long)r * W + c]);
+    return make_float2(0.f, 0.f);
+}
+
+// Fill X[b][a] with the patch and phu/phv with the per-bin phase factors
+// exp(-i k_j s_0) that refer the spectrum to the hit point.
+template <int D>
+__device__ __forceinline__ void gather_patch(const DSys& sys, const RayAtDoe& R,
+                                             const float2* __restrict__ T, float2* X,
+                                             float2* phu, float2* phv) {
+    const int H = sys.H, W = sys.W;
+    if (sys.gather == RW_GATHER_NEAREST) {
+        for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
+            const int b = f / D, a = f - (f / D) * D;
+            X[f] = tmap(T, H, W, R.r0 + b, R.c0 + a);
+        }
+        if (threadIdx.x < D) {
+            const float j = (float)((int)threadIdx.x - D / 2);
+            float s, c;
+            sincospif(-2.f * j * R.s0, &s, &c);
+            phu[threadIdx.x] = make_float2(c, s);
+            sincospif(-2.f * j * R.t0, &s, &c);
+            phv[threadIdx.x] = make_float2(c, s);
+        }
+    } else {
+        for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
+            const int b = f / D, a = f - (f / D) * D;
+            const float oa = (float)(a - D / 2), ob = (float)(b - D / 2);
+            const float fu = R.s0 + oa * R.u[0] + ob * R.v[0];
+            const float fv = R.t0 + oa * R.u[1] + ob * R.v[1];
+            const float iuf = floorf(fu), ivf = floorf(fv);
+            const float wu = fu - iuf, wv = fv - ivf;
+            const int i0 = R.c0 + (int)iuf, j0 = R.r0 + (int)ivf;
+            float2 t00 = tmap(T, H, W, j0, i0), t10 = tmap(T, H, W, j0, i0 + 1);
+            float2 t01 = tmap(T, H, W, j0 + 1, i0), t11 = tmap(T, H, W, j0 + 1, i0 + 1);
+            const float w00 = (1.f - wu) * (1.f - wv), w10 = wu * (1.f - wv);
+            const float w01 = (1.f - wu) * wv, w11 = wu * wv;
+            X[f] = make_float2(w00 * t00.x + w10 * t10.x + w01 * t01.x + w11 * t11.x,
+                               w00 * t00.y + w10 * t10.y + w01 * t01.y + w11 * t11.y);
+        }
+        if (threadIdx.x < D) {
+            // s_0 = -(D/2) p  ->  exp(-i k_j s_0) = (-1)^j
+            const float sg = ((((int)threadIdx.x - D / 2) & 1) ? -1.f : 1.f);
+            phu[threadIdx.x] = make_float2(sg, 0.f);
+            phv[threadIdx.x] = make_float2(sg, 0.f);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ A6 + A7
+// Trace a secondary ray from the DOE hit through the remaining surfaces to
+// the sensor; returns false if dropped.  Position is left in (x, y).
+template <bool OPL>
+__device__ __forceinline__ bool trace_to_sensor(const DSys& sys, float& x, float& y, float& zl,
+                                                float& dx, float& dy, float& dz, double& opl,
+                                                unsigned* status) {
+    for (int s = sys.doe_index + 1; s < sys.nsurf; ++s)
+        if (!trace_one<OPL>(sys.s[s], x, y, zl, dx, dy, dz, opl, status)) return false;
+    zl -= sys.sensor_gap;
+    if (dz == 0.f) return false;
+    const float t = -zl / dz;
+    x = fmaf(t, dx, x);
+    y = fmaf(t, dy, y);
+    if (OPL) opl += (double)sys.n_sensor * (double)t;
+    return true;
+}
+
+__device__ __forceinline__ void splat_bilinear(const DSys& sys, float cx, float cy, float x,
+                                               float y, float w, float* __restrict__ img) {
+    const float u = (x - cx) * sys.inv_spitch + 0.5f * sys.nx - 0.5f;
+    const float v = (y - cy) * sys.inv_spitch + 0.5f * sys.ny - 0.5f;
+    if (!(u > -1.f && v > -1.f && u < (float)sys.nx && v < (float)sys.ny)) return;
+    const float fi = floorf(u), fj = floorf(v);
+    const int i0 = (int)fi, j0 = (int)fj;
+    const float fu = u - fi, fv = v - fj;
+    const int nx = sys.nx, ny = sys.ny;
+    if (j0 >= 0) {
+        if (i0 >= 0) atomicAdd(img + j0 * nx + i0, w * (1.f - fu) * (1.f - fv));
+        if (i0 + 1 < nx) atomicAdd(img + j0 * nx + i0 + 1, w * fu * (1.f - fv));
+    }
+    if (j0 + 1 < ny) {
+        if (i0 >= 0) atomicAdd(img + (j0 + 1) * nx + i0, w * (1.f - fu) * fv);
+        if (i0 + 1 < nx) atomicAdd(img + (j0 + 1) * nx + i0 + 1, w * fu * fv);
+    }
+}
+
+// Eq. 2: add a exp(i k (OPL + n_s d_t.((X,Y) - r))) d_z over the window.
+__device__ __forceinline__ void splat_coherent(const DSys& sys, float k0, float cx, float cy,
+                                               float x, float y, double opl, float dx,
+                                               float dy, float dz, float2 a,
+                                               float2* __restrict__ fld) {
+    const double TWO_PI = 6.283185307179586;
+    double ph0 = (double)k0 * opl;
+    ph0 -= TWO_PI * rint(ph0 / TWO_PI);
+    const float phb = (float)ph0;
+    const float kx = k0 * sys.n_sensor * dx, ky = k0 * sys.n_sensor * dy;
+    const float u = (x - cx) * sys.inv_spitch + 0.5f * sys.nx - 0.5f;
+    const float v = (y - cy) * sys.inv_spitch + 0.5f * sys.ny - 0.5f;
+    if (!(u == u) || !(v == v)) return;
+    int i_lo = 0, i_hi = sys.nx - 1, j_lo = 0, j_hi = sys.ny - 1;
+    if (sys.window > 0) {
+        const float ic = rintf(u), jc = rintf(v);
+        if (ic < -(float)sys.window - 1.f || ic > (float)(sys.nx + sys.window)) return;
+        if (jc < -(float)sys.window - 1.f || jc > (float)(sys.ny + sys.window)) return;
+        i_lo = max(i_lo, (int)ic - sys.window); i_hi = min(i_hi, (int)ic + sys.window);
+        j_lo = max(j_lo, (int)jc - sys.window); j_hi = min(j_hi, (int)jc + sys.window);
+    }
+    const float2 ad = make_float2(a.x * dz, a.y * dz);
+    for (int j = j_lo; j <= j_hi; ++j) {
+        const float Y = cy + ((float)j - 0.5f * sys.ny + 0.5f) * sys.spitch;
+        for (int i = i_lo; i <= i_hi; ++i) {
+            const float X = cx + ((float)i - 0.5f * sys.nx + 0.5f) * sys.spitch;
+            const float ph = phb + kx * (X - x) + ky * (Y - y);
+            float s, c;
+            sincosf(ph, &s, &c);
+            float2* p = fld + j * sys.nx + i;
+            atomicAdd(&p->x, ad.x * c - ad.y * s);
+            atomicAdd(&p->y, ad.x * s + ad.y * c);
+        }
+    }
+}
+
+// Direction of spectral bin (ju, jv) for the incident state R; false if evanescent.
+__device__ __forceinline__ bool bin_direction(const DSys& sys, const RayAtDoe& R, int ju, int jv,
+                                              float& dx, float& dy, float& dz) {
+    const float ku = R.kin_u + sys.kstep * (float)ju;
+    const float kv = R.kin_v + sys.kstep * (float)jv;
+    const float K2 = R.K * R.K;
+    const float kt2 = ku * ku + kv * kv;
+    if (kt2 >= K2) return false;
+    const float kn = sqrtf(K2 - kt2);
+    const float invK = 1.f / R.K;
+    dx = (ku * R.u[0] + kv * R.v[0] + kn * R.n[0]) * invK;
+    dy = (ku * R.u[1] + kv * R.v[1] + kn * R.n[1]) * invK;
+    dz = (ku * R.u[2] + kv * R.v[2] + kn * R.n[2]) * invK;
+    return true;
+}
+
+template <int D>
+__device__ __forceinline__ float2 spectrum_at(const float2* X, const float2* phu, const float2* phv,
+                                              int jui, int jvi) {
+    int mu = jui + D / 2; if (mu >= D) mu -= D;
+    int mv = jvi + D / 2; if (mv >= D) mv -= D;
+    const float invD2 = 1.f / (float)(D * D);
+    return cscale(cmul(cmul(X[mv * D + mu], phu[jui]), phv[jvi]), invD2);
+}
+
+template <int MODE>
+__device__ __forceinline__ void deposit(const DSys& sys, const DJob& J, const RayAtDoe& R,
+                                        float dx, float dy, float dz, float2 a,
+                                        float* __restrict__ psf, float2* __restrict__ field,
+                                        unsigned* status) {
+    float x = R.px, y = R.py, zl = R.pz;
+    double opl = R.opl;
+    const long long npx = (long long)sys.nx * sys.ny;
+    if (MODE == MODE_SPLAT) {
+        if (!trace_to_sensor<false>(sys, x, y, zl, dx, dy, dz, opl, status)) return;
+        splat_bilinear(sys, R.cx, R.cy, x, y, a.x * a.x + a.y * a.y, psf + (long long)R.job * npx);
+    } else {
+        if (!trace_to_sensor<true>(sys, x, y, zl, dx, dy, dz, opl, status)) return;
+        splat_coherent(sys, J.k0, R.cx, R.cy, x, y, opl, dx, dy, dz, a,
+                       field + (long long)R.job * npx);
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void emit_dead(const DSys& sys, long long g, long long total,
+                                          const EmitOut& eo) {
+    if (g >= total) return;
+    const long long S = (sys.emit == RW_EMIT_EXHAUSTIVE) ? (long long)D * D : sys.n_ssr;
+    for (long long b = threadIdx.x; b < S; b += RW_THREADS) {
+        const long long s = g * S + b;
+        eo.dx[s] = 0.f; eo.dy[s] = 0.f; eo.dz[s] = 0.f; eo.are[s] = 0.f; eo.aim[s] = 0.f;
+        if (eo.bin) eo.bin[s] = -1;
+    }
+    if (threadIdx.x == 0) { eo.hx[g] = 0.f; eo.hy[g] = 0.f; eo.hz[g] = 0.f; eo.opl[g] = 0.0; }
+}
+
+// ------------------------------------------------------------------ A5 exhaustive
+template <int D, int MODE>
+__device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, const RayAtDoe& R,
+                                                const float2* X, const float2* phu,
+                                                const float2* phv, float* psf, float2* field,
+                                                const EmitOut& eo, long long g, unsigned* status) {
+    const float2 ain = make_float2(R.a_re, R.a_im);
+    if (MODE == MODE_EMIT && threadIdx.x == 0) {
+        eo.hx[g] = R.px; eo.hy[g] = R.py; eo.hz[g] = (float)((double)R.pz + sys.s[sys.doe_index].z);
+        eo.opl[g] = R.opl;
+    }
+    for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
+        const int jvi = f / D, jui = f - (f / D) * D;
+        float dx, dy, dz;
+        const bool prop = bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz);
+        if (MODE == MODE_EMIT) {
+            const long long s = g * (long long)(D * D) + f;
+            if (!prop) {
+                eo.dx[s] = 0.f; eo.dy[s] = 0.f; eo.dz[s] = 0.f; eo.are[s] = 0.f; eo.aim[s] = 0.f;
+            } else {
+                const float2 a = cmul(ain, spectrum_at<D>(X, phu, phv, jui, jvi));
+                eo.dx[s] = dx; eo.dy[s] = dy; eo.dz[s] = dz; eo.are[s] = a.x; eo.aim[s] = a.y;
+            }
+            if (eo.bin) eo.bin[s] = f;
+            continue;
+        }
+        if (!prop) continue;
+        const float2 a = cmul(ain, spectrum_at<D>(X, phu, phv, jui, jvi));
+        deposit<MODE>(sys, J, R, dx, dy, dz, a, psf, field, status);
+    }
+}
+
+// ------------------------------------------------------------------ A5 sampled
+// Gumbel-max: draw i picks argmax_j (log p_j + g_ij) over propagating bins,
+// g = -log(-log u), u from Philox (counter (j>>2, i, ray, offset), word j&3).
+// Coherent sensor: p ~ |U~|, a = a_in U~ / (N p).  Incoherent: p ~ |U~|^2,
+// a = a_in U~ / sqrt(N p) so that |a|^2 is the unbiased power weight.
+// Shared scratch after the patch: logp[D*D] floats, sel[n_ssr] ints, red[32].
+template <int D, int MODE>
+__device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, const RayAtDoe& R,
+                                             const float2* X, const float2* phu, const float2* phv,
+                                             float* psf, float2* field, const EmitOut& eo,
+                                             long long g, unsigned* status,
+                                             unsigned char* scratch) {
+    float* logp = reinterpret_cast<float*>(scratch);
+    int* sel = reinterpret_cast<int*>(logp + D * D);
+    float* red = reinterpret_cast<float*>(sel + sys.n_ssr);
+    const bool coh = sys.coherent != 0;
+    // magnitudes and their sum
+    float part = 0.f;
+    for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
+        const int jvi = f / D, jui = f - (f / D) * D;
+        float dx, dy, dz;
+        float m = 0.f;
+        if (bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
+            const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+            const float p2 = U.x * U.x + U.y * U.y;
+            m = coh ? sqrtf(p2) : p2;
+        }
+        logp[f] = m;
+        part += m;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    float tot = 0.f;
+    for (int w = 0; w < RW_THREADS / 32; ++w) tot += red[w];
+    const float inv_tot = tot > 0.f ? 1.f / tot : 0.f;
+    for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
+        const float pj = logp[f] * inv_tot;
+        logp[f] = pj > 0.f ? logf(pj) : -INFINITY;
+    }
+    __syncthreads();
+    // one warp per draw; each lane scores groups of 4 bins sharing a Philox counter
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t k0 = (uint32_t)(sys.seed & 0xffffffffull), k1 = (uint32_t)(sys.seed >> 32);
+    for (int i = warp; i < sys.n_ssr; i += RW_THREADS / 32) {
+        float best = -INFINITY;
+        int bj = 0x7fffffff;
+        for (int G = lane; G * 4 < D * D; G += 32) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)i, (uint32_t)R.gid,
+                                                     (uint32_t)sys.rng_offset), k0, k1);
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int jb = 4 * G + q;
+                if (jb < D * D) {
+                    const float lp = logp[jb];
+                    if (lp > -INFINITY) {
+                        const float gmb = -logf(-logf(u01(ws[q])));
+                        const float sc = lp + gmb;
+                        if (sc > best || (sc == best && jb < bj)) { best = sc; bj = jb; }
+                    }
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            if (ob > best || (ob == best && oj < bj)) { best = ob; bj = oj; }
+        }
+        if (lane == 0) sel[i] = (best > -INFINITY) ? bj : -1;
+    }
+    __syncthreads();
+    const float2 ain = make_float2(R.a_re, R.a_im);
+    if (MODE == MODE_EMIT && threadIdx.x == 0) {
+        eo.hx[g] = R.px; eo.hy[g] = R.py; eo.hz[g] = (float)((double)R.pz + sys.s[sys.doe_index].z);
+        eo.opl[g] = R.opl;
+    }
+    const float N = (float)sys.n_ssr;
+    for (int i = threadIdx.x; i < sys.n_ssr; i += RW_THREADS) {
+        const int jb = sel[i];
+        float dx = 0.f, dy = 0.f, dz = 0.f;
+        float2 a = make_float2(0.f, 0.f);
+        bool ok = false;
+        if (jb >= 0) {
+            const int jvi = jb / D, jui = jb - (jb / D) * D;
+            ok = bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz);
+            const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+            const float pj = expf(logp[jb]);
+            const float sc = coh ? 1.f / (N * pj) : rsqrtf(N * pj);
+            a = cscale(cmul(ain, U), sc);
+        }
+        if (MODE == MODE_EMIT) {
+            const long long s = g * (long long)sys.n_ssr + i;
+            eo.dx[s] = ok ? dx : 0.f; eo.dy[s] = ok ? dy : 0.f; eo.dz[s] = ok ? dz : 0.f;
+            eo.are[s] = ok ? a.x : 0.f; eo.aim[s] = ok ? a.y : 0.f;
+            if (eo.bin) eo.bin[s] = jb;
+            continue;
+        }
+        if (ok) deposit<MODE>(sys, J, R, dx, dy, dz, a, psf, field, status);
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+cudaError_t launch_prep_maps(const LaunchCtx& L, const float* phi, const float* amp, int64_t npix,
+                             const float* scales_dev, int nslot, float2* T);
+cudaError_t launch_generate_rays(const LaunchCtx& L, const GenJob* jobs, const long long* prefix,
+                                 int njob, long long total, double z_start, double n_object,
+                                 const RaysOut& out);
+cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const DJob* jobs,
+                           const long long* prefix, int njob, long long total, const RaysIn& rays,
+                           const float2* T, float* psf, float2* field, const EmitOut& eo,
+                           unsigned* status);
+cudaError_t launch_coherent_finalize(const LaunchCtx& L, const float2* field, float* psf,
+                                     long long n);

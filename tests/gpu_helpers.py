@@ -1,0 +1,23 @@
+"""Shared helpers for GPU parity tests: run the CUDA path and the oracle on
+the same seeded workload."""
+import numpy as np
+import torch
+
+from oracle import pipeline as OP
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def oracle_psf(w, **kw):
+    with torch.no_grad():
+        return OP.psf(w, **kw).numpy()
+
+
+def angle(d1, d2):
+    """2 asin(|d1 - d2| / 2): the angle between unit vectors, rows."""
+    diff = np.linalg.norm(np.asarray(d1, np.float64) - np.asarray(d2, np.float64), axis=-1)
+    return 2 * np.arcsin(np.clip(diff / 2, 0, 1))

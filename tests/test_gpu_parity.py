@@ -1,0 +1,275 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: PSF relative L2 <= 1e-4 (FP32 path vs FP64), secondary-ray
+directions <= 1e-6 rad, weights |da| <= 1e-5 max|a|; ray generation is
+bit-exact (both sides round the same double expression once to float32).
+Sizes are chosen so the oracle finishes in seconds while spanning many
+32-ray tiles and a ragged last tile.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import rwinputs as R
+from oracle import pipeline as OP
+from oracle import loss as OL
+
+from gpu_helpers import angle, oracle_psf, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+PSF_TOL = 1e-4
+DIR_TOL = 1e-6
+A_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def RW():
+    from paper_2605_15418_gb300 import raywave
+    return raywave
+
+
+@pytest.fixture(scope="module")
+def ctx(RW):
+    c = RW.Context(0)
+    yield c
+    c.close()
+
+
+def _c2_small(n_side=37, D=32, map_side=256, sensor_n=96, lams=(486e-6, 656e-6),
+              fields=(0.0, 2.0)):
+    w = R.configs.c2(n_side=n_side, D=D, lams=lams, fields_deg=fields, sensor_n=sensor_n,
+                     map_side=map_side)
+    w.system.sensor.pitch = 8e-3
+    return w
+
+
+# ------------------------------------------------------------------ A0
+def test_generated_rays_bit_exact(RW, ctx):
+    w = R.configs.c4(n_side=21, D=16, n_fields=3, map_side=64)
+    sim = RW.Simulator(w, ctx=ctx)
+    torch.cuda.synchronize()
+    off = 0
+    for job in w.jobs:
+        ref = OP.job_rays(job, w.z_start, w.system.n_object)
+        n = job.n_rays
+        for k, ax in (("ox", 0), ("oy", 1), ("oz", 2)):
+            got = sim.rays[k][off:off + n].cpu().numpy()
+            assert np.array_equal(got, ref["o"][:, ax].numpy().astype(np.float32))
+        for k, ax in (("dx", 0), ("dy", 1), ("dz", 2)):
+            got = sim.rays[k][off:off + n].cpu().numpy()
+            assert np.array_equal(got, ref["d"][:, ax].numpy().astype(np.float32))
+        assert np.allclose(sim.rays["opl"][off:off + n].cpu().numpy(), ref["opl"].numpy(),
+                           rtol=1e-15, atol=1e-15)
+        assert (sim.rays["a_re"][off:off + n] == 1).all() and (sim.rays["a_im"][off:off + n] == 0).all()
+        off += n
+
+
+# ------------------------------------------------------------------ A1..A5 (C1 full size)
+def test_emit_binary_grating_full_size(RW, ctx):
+    w = R.configs.c1()                       # 64 x 64 rays x {0, 10 deg}, D = 32
+    sim = RW.Simulator(w, ctx=ctx)
+    out = sim.emit()
+    torch.cuda.synchronize()
+    D = w.system.doe.D
+    S = D * D
+    d = torch.stack([out["dx"], out["dy"], out["dz"]], -1).cpu().numpy().reshape(-1, D, D, 3)
+    a = (out["a_re"].double() + 1j * out["a_im"].double()).cpu().numpy().reshape(-1, D, D)
+    assert d.shape[0] == w.n_rays
+    base = 0
+    for job in w.jobs:
+        for c0 in range(0, job.n_rays, 1024):
+            idx = np.arange(c0, min(c0 + 1024, job.n_rays))
+            with torch.no_grad():
+                em, _ = OP.emit_job(w.system, job, w.z_start, OP.params_of(w.system),
+                                    *OP.map_tensors(w.system), idx=idx, ray_base=base)
+            g = base + idx
+            ang = angle(d[g].reshape(-1, 3), em["d"].numpy().reshape(-1, 3))
+            assert ang.max() <= DIR_TOL, ang.max()
+            ar = em["a"].numpy()
+            assert np.abs(a[g] - ar).max() <= A_TOL * np.abs(ar).max()
+        base += job.n_rays
+    # closed form on the GPU output itself: efficiencies of the 0/pi grating
+    eta = (np.abs(a) ** 2)[:, D // 2, :]
+    for m in (1, 3, 5, 7):
+        ref = 1.0 / (64 * math.sin(math.pi * m / 16) ** 2)
+        assert np.abs(eta[:, D // 2 + 2 * m] - ref).max() < 2e-6
+    hit = torch.stack([out["hx"], out["hy"], out["hz"]], -1).cpu().numpy()
+    assert np.abs(hit[:, 2]).max() == 0.0
+
+
+def test_emit_capacity_is_checked(RW, ctx):
+    w = R.configs.c1(n_side=4)
+    sim = RW.Simulator(w, ctx=ctx)
+    out = RW.alloc_emitted(w.n_rays, 32 * 32, sim.dev)
+    out["capacity"] -= 1
+    with pytest.raises(RW.RayWaveError) as e:
+        sim.emit(out)
+    assert e.value.status == 4
+
+
+# ------------------------------------------------------------------ A1..A7 incoherent
+@pytest.mark.parametrize("D,n_side", [(16, 45), (32, 37), (64, 13)])
+def test_forward_psf_planar(RW, ctx, D, n_side):
+    w = _c2_small(n_side=n_side, D=D)
+    sim = RW.Simulator(w, ctx=ctx)
+    psf = sim.forward().cpu().numpy()
+    ref = oracle_psf(w)
+    assert ref.sum() > 0
+    assert rel_l2(psf, ref) <= PSF_TOL, rel_l2(psf, ref)
+
+
+def test_forward_psf_d96_sampled_rays_subset(RW, ctx):
+    w = _c2_small(n_side=6, D=96, map_side=256, lams=(550e-6,), fields=(1.0,))
+    sim = RW.Simulator(w, ctx=ctx)
+    psf = sim.forward().cpu().numpy()
+    ref = oracle_psf(w)
+    assert rel_l2(psf, ref) <= PSF_TOL
+
+
+def test_forward_conformal_asphere(RW, ctx):
+    w = R.configs.c4(n_side=19, D=32, n_fields=3, max_field_deg=20.0, map_side=512,
+                     lams=(550e-6, 656e-6))
+    w.system.sensor.pitch = 20e-3
+    sim = RW.Simulator(w, ctx=ctx)
+    psf = sim.forward().cpu().numpy()
+    ref = oracle_psf(w)
+    assert ref.sum() > 0
+    assert rel_l2(psf, ref) <= PSF_TOL, rel_l2(psf, ref)
+
+
+def test_forward_coherent_window_and_full(RW, ctx):
+    for window in (0, 6):
+        w = _c2_small(n_side=9, D=16, map_side=64, sensor_n=48, lams=(550e-6,), fields=(0.5,))
+        w.system.surfaces = w.system.surfaces[:1]
+        w.system.sensor.z = 0.2
+        w.system.sensor.pitch = 2e-3
+        w.system.sensor.coherent = True
+        w.system.sensor.window = window
+        sim = RW.Simulator(w, ctx=ctx)
+        psf = sim.forward().cpu().numpy()
+        ref = oracle_psf(w)
+        assert rel_l2(psf, ref) <= 1e-3, (window, rel_l2(psf, ref))
+
+
+def test_forward_rays_outside_map_and_empty_job(RW, ctx):
+    w = _c2_small(n_side=11, D=16, map_side=64, lams=(550e-6,), fields=(0.0, 1.0))
+    # job 1 launched 5 mm off axis: every patch is outside the map (T = 0)
+    w.jobs[1].y0 += 5.0
+    sim = RW.Simulator(w, ctx=ctx)
+    psf = sim.forward().cpu().numpy()
+    assert psf[1].sum() == 0.0
+    assert rel_l2(psf, oracle_psf(w)) <= PSF_TOL
+    # a job with no rays gives an empty image and does not disturb the others
+    jobs = RW.jobs_struct(w.jobs, counts=[w.jobs[0].n_rays, 0])
+    s, keep = sim.sys_struct()
+    out = torch.empty(sim.psf_shape, device=sim.dev)
+    RW.rw_forward(ctx, s, jobs, sim.rays, out)
+    torch.cuda.synchronize()
+    assert out[1].sum().item() == 0.0
+    assert rel_l2(out[0].cpu().numpy(), psf[0]) < 1e-6
+
+
+def test_psf_is_additive_over_ray_subsets_at_full_c2_size(RW, ctx):
+    """At the benchmark's full size (9 jobs x 1M rays, D = 64): splitting
+    every job's rays into two halves and adding the PSFs reproduces the
+    full PSF (no lost or duplicated deposits)."""
+    w = R.configs.c2()
+    sim = RW.Simulator(w, ctx=ctx)
+    full = sim.forward()
+    s, keep = sim.sys_struct()
+    cnt = [j.n_rays for j in w.jobs]
+    off = np.cumsum([0] + cnt[:-1])
+    half = [c // 2 for c in cnt]
+    a = torch.empty_like(full)
+    b = torch.empty_like(full)
+    RW.rw_forward(ctx, s, RW.jobs_struct(w.jobs, offsets=off, counts=half), sim.rays, a)
+    RW.rw_forward(ctx, s, RW.jobs_struct(w.jobs, offsets=off + np.array(half),
+                                         counts=[c - h for c, h in zip(cnt, half)]),
+                  sim.rays, b)
+    torch.cuda.synchronize()
+    assert full.sum().item() > 0
+    assert rel_l2((a + b).cpu().numpy(), full.cpu().numpy()) < 1e-5
+
+
+def test_unit_map_at_full_c2_size_is_the_spot_diagram(RW, ctx):
+    """T = 1 puts all energy in bin 0: the full-size PSF is the refractive
+    spot diagram of the 9M incident rays, which the oracle traces directly."""
+    w = R.configs.c2()
+    w.system.doe.phi = np.zeros_like(w.system.doe.phi)
+    sim = RW.Simulator(w, ctx=ctx)
+    psf = sim.forward().cpu().numpy()
+    from oracle import geometry as G, sensor as S
+    prm = OP.params_of(w.system)
+    sen = w.system.sensor
+    ref = []
+    for job in w.jobs:
+        img = torch.zeros(sen.nx * sen.ny, dtype=torch.float64)
+        for c0 in range(0, job.n_rays, 1 << 18):
+            idx = np.arange(c0, min(c0 + (1 << 18), job.n_rays))
+            ray = OP.job_rays(job, w.z_start, 1.0, idx)
+            ray, n_s = G.trace(ray, prm, torch.tensor(1.0, dtype=torch.float64))
+            x, y, _ = S.to_sensor(ray["o"], ray["d"], ray["opl"], sen.z, n_s)
+            img += S.splat_incoherent(x, y, torch.ones_like(x), ray["alive"], sen.nx, sen.ny,
+                                      sen.pitch, job.sensor_cx, job.sensor_cy)
+        ref.append(img.reshape(sen.ny, sen.nx).numpy())
+    ref = np.stack(ref)
+    assert rel_l2(psf, ref) <= PSF_TOL, rel_l2(psf, ref)
+
+
+# ------------------------------------------------------------------ A8
+def test_loss_eq3_matches_oracle(RW, ctx):
+    g = torch.Generator().manual_seed(1)
+    I = torch.rand(3, 40, 50, generator=g)
+    T = torch.rand(3, 40, 50, generator=g)
+    sim_out = torch.empty(3, dtype=torch.float64, device="cuda")
+    grad = torch.empty_like(I, device="cuda")
+    RW.rw_loss_eq3(ctx, I.cuda(), T.cuda(), sim_out, grad)
+    torch.cuda.synchronize()
+    Id = I.double().requires_grad_(True)
+    Lv, a = OL.eq3_loss(Id, T.double())
+    Lv.backward()
+    assert sim_out[0].item() == pytest.approx(Lv.item(), rel=1e-9)
+    assert sim_out[1].item() == pytest.approx(a.item(), rel=1e-12)
+    assert np.allclose(grad.cpu().numpy(), Id.grad.numpy(), rtol=1e-5, atol=1e-7)
+
+
+# ------------------------------------------------------------------ A9
+def _c3_small(n_side=24):
+    w = R.configs.c3(n_side=n_side, D=16)
+    sysm = w.system
+    sysm.doe.phi = (R.maps.random_phase(512, 512, 11) * 0.3 + sysm.doe.phi).astype(np.float32)
+    sysm.sensor.nx = sysm.sensor.ny = 64
+    sysm.sensor.pitch = 30e-3
+    w.target = R.gaussian_spots_target(1, 64, 64, seed=5, n_spots=3)
+    return w
+
+
+def test_backward_matches_oracle_gradient(RW, ctx):
+    w = _c3_small()
+    sim = RW.Simulator(w, ctx=ctx)
+    psf = sim.forward()
+    tgt = torch.as_tensor(w.target, device=sim.dev)
+    gI = torch.empty_like(psf)
+    sim.loss(psf, tgt, gI)
+    dphi, _, dsurf = sim.backward(gI)
+    torch.cuda.synchronize()
+    # oracle: autograd through the FP64 forward
+    prm = OP.params_of(w.system, requires_grad=True)
+    phi = torch.from_numpy(w.system.doe.phi.astype(np.float64)).requires_grad_(True)
+    img = OP.psf(w, params=prm, phi=phi)
+    Lv, _ = OL.eq3_loss(img, torch.from_numpy(w.target.astype(np.float64)))
+    Lv.backward()
+    gphi = phi.grad.numpy()
+    dphi = dphi.cpu().numpy()
+    assert rel_l2(dphi, gphi) <= 1e-3, rel_l2(dphi, gphi)
+    names = ["z", "c", "k", "A4", "A6", "A8", "A10", "n_after"]
+    ds = dsurf.cpu().numpy()
+    for si in range(1, len(prm)):
+        for k in (0, 1, 7):
+            ref = prm[si][names[k]].grad
+            ref = 0.0 if ref is None else float(ref)
+            scale = max(abs(ref), 1e-3 * max(abs(float(p[names[1]].grad or 0)) for p in prm[1:]))
+            assert abs(ds[si, k] - ref) <= 1e-3 * scale + 1e-9, (si, names[k], ds[si, k], ref)

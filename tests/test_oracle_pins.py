@@ -69,6 +69,10 @@ def test_binary_grating_orders_and_efficiencies(theta_deg):
     D = sysm.doe.D
     c = D // 2
     lam, period = job.lam, 16 * sysm.doe.pitch
+    # the ray inputs are float32: sin(theta_i) is the x component of the
+    # (float32-rounded) incident direction
+    sin_in = float(P.job_rays(job, w.z_start)["d"][0, 0])
+    assert sin_in == pytest.approx(math.sin(job.theta_x), abs=1e-7)
     for r in range(U.shape[0]):
         assert abs(float(eta[r].sum()) - 1.0) < 1e-12    # Parseval, phase-only map
         for m in range(-7, 8):
@@ -77,8 +81,7 @@ def test_binary_grating_orders_and_efficiencies(theta_deg):
             if m % 2:
                 dvec = em["d"][r, c, c + 2 * m]
                 s_out = float(dvec[0])
-                assert s_out == pytest.approx(math.sin(job.theta_x) + m * lam / period,
-                                              abs=1e-13)
+                assert s_out == pytest.approx(sin_in + m * lam / period, abs=1e-13)
                 assert float(dvec[1]) == pytest.approx(0.0, abs=1e-15)
         # everything off the j_v = 0 row and off even j_u bins is empty
         off = eta[r].clone()
