@@ -45,6 +45,7 @@ struct rw_ctx {
     DevBuf tmaps;       // complex transmission per wavelength slot
     DevBuf tables;      // job tables, prefix sums, map scales
     DevBuf field;       // coherent field accumulator
+    DevBuf acc;         // double PSF accumulator
     DevBuf misc;        // status word + loss sums
     void* staging = nullptr;       // pinned host copy source of `tables`
     size_t staging_bytes = 0;
@@ -322,6 +323,7 @@ rw_status rw_destroy(rw_ctx* ctx) {
     ctx->tmaps.release();
     ctx->tables.release();
     ctx->field.release();
+    ctx->acc.release();
     ctx->misc.release();
     if (ctx->staging) cudaFreeHost(ctx->staging);
     if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
@@ -445,15 +447,21 @@ rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int3
             return fail(ctx, RW_ENOMEM, "coherent field scratch");
         RW_CUDA(cudaMemsetAsync(ctx->field.p, 0, npx * sizeof(float2), ctx->stream), "field clear");
         RW_CUDA(launch_forward(lctx(ctx), MODE_COHERENT, P.sys, dj, dp, njob, P.total,
-                               rays_in(rays), T, psf, (float2*)ctx->field.p, eo,
+                               rays_in(rays), T, nullptr, (float2*)ctx->field.p, eo,
                                status_word(ctx)), "coherent forward");
         ctx->launches++;
         RW_CUDA(launch_coherent_finalize(lctx(ctx), (float2*)ctx->field.p, psf, npx), "finalize");
         ctx->launches++;
     } else {
+        if (ctx->acc.ensure(npx * sizeof(double)) != cudaSuccess)
+            return fail(ctx, RW_ENOMEM, "PSF accumulator scratch");
+        RW_CUDA(cudaMemsetAsync(ctx->acc.p, 0, npx * sizeof(double), ctx->stream), "acc clear");
         RW_CUDA(launch_forward(lctx(ctx), MODE_SPLAT, P.sys, dj, dp, njob, P.total,
-                               rays_in(rays), T, psf, nullptr, eo, status_word(ctx)),
+                               rays_in(rays), T, (double*)ctx->acc.p, nullptr, eo,
+                               status_word(ctx)),
                 "forward kernel");
+        ctx->launches++;
+        RW_CUDA(launch_psf_finalize(lctx(ctx), (const double*)ctx->acc.p, psf, npx), "psf finalize");
         ctx->launches++;
     }
     return RW_OK;

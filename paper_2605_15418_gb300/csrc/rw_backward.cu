@@ -117,6 +117,9 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                         const float xs = fmaf(ts, ex, x), ys = fmaf(ts, ey, y);
                         float gw, gxs, gys;
                         bilinear_grad(sys, R.cx, R.cy, xs, ys, gimg, gw, gxs, gys);
+                        // the deposit is w * (bilinear weight): position gradients scale by w
+                        gxs *= w;
+                        gys *= w;
                         if (gw != 0.f || gxs != 0.f || gys != 0.f) {
                             // ---- sensor plane: xs = x + ts ex, ts = -zs / ez
                             float gx = gxs, gy = gys;

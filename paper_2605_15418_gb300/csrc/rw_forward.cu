@@ -59,7 +59,7 @@ template <int D, int MODE>
 __global__ void __launch_bounds__(RW_THREADS)
 k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
           int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
-          float* __restrict__ psf, float2* __restrict__ field, EmitOut eo, unsigned* status) {
+          double* __restrict__ psf, float2* __restrict__ field, EmitOut eo, unsigned* status) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* X = reinterpret_cast<float2*>(smem);
     float2* tw = X + D * D;
@@ -98,6 +98,14 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
     }
 }
 
+// float PSF from the double accumulator.
+__global__ void k_psf_finalize(const double* __restrict__ acc, float* __restrict__ psf,
+                               long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        psf[i] = (float)acc[i];
+}
+
 // |U|^2 of the coherent field.
 __global__ void k_coherent_finalize(const float2* __restrict__ field, float* __restrict__ psf,
                                     long long n) {
@@ -112,7 +120,7 @@ __global__ void k_coherent_finalize(const float2* __restrict__ field, float* __r
 template <int D, int MODE>
 static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                     const long long* prefix, int njob, long long total,
-                                    const RaysIn& rays, const float2* T, float* psf,
+                                    const RaysIn& rays, const float2* T, double* psf,
                                     float2* field, const EmitOut& eo, unsigned* status) {
     size_t smem = forward_smem_bytes(D, sys.emit, sys.n_ssr);
     auto kern = k_forward<D, MODE>;
@@ -135,7 +143,7 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
 
 cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const DJob* jobs,
                            const long long* prefix, int njob, long long total,
-                           const RaysIn& rays, const float2* T, float* psf, float2* field,
+                           const RaysIn& rays, const float2* T, double* psf, float2* field,
                            const EmitOut& eo, unsigned* status) {
 #define RW_FWD_CASE(DD)                                                                       \
     case DD:                                                                                  \
@@ -186,5 +194,14 @@ cudaError_t launch_coherent_finalize(const LaunchCtx& L, const float2* field, fl
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     k_coherent_finalize<<<(unsigned)grid, 256, 0, L.stream>>>(field, psf, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psf_finalize(const LaunchCtx& L, const double* acc, float* psf, long long n) {
+    long long grid = (n + 255) / 256;
+    long long cap = (long long)L.num_sms * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    k_psf_finalize<<<(unsigned)grid, 256, 0, L.stream>>>(acc, psf, n);
     return cudaGetLastError();
 }

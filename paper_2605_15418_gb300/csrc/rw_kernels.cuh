@@ -115,7 +115,7 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     }
     const double pxd = __dadd_rn((double)x, __dmul_rn(t, (double)dx));
     const double pyd = __dadd_rn((double)y, __dmul_rn(t, (double)dy));
-    const double pzl = zld + t * (double)dz;
+    const double pzl = sys.conformal ? zld + t * (double)dz : 0.0;   // planar: on the plane
     if (!sys.conformal) {
         nx = 0.f; ny = 0.f; nz = 1.f;
     } else {
@@ -231,8 +231,11 @@ __device__ __forceinline__ bool trace_to_sensor(const DSys& sys, float& x, float
     return true;
 }
 
+// Bilinear |a|^2 deposit.  The image is accumulated in double: a focal
+// pixel can receive ~1e6 deposits, and float accumulation there would drop
+// small contributions.
 __device__ __forceinline__ void splat_bilinear(const DSys& sys, float cx, float cy, float x,
-                                               float y, float w, float* __restrict__ img) {
+                                               float y, float w, double* __restrict__ img) {
     const float u = (x - cx) * sys.inv_spitch + 0.5f * sys.nx - 0.5f;
     const float v = (y - cy) * sys.inv_spitch + 0.5f * sys.ny - 0.5f;
     if (!(u > -1.f && v > -1.f && u < (float)sys.nx && v < (float)sys.ny)) return;
@@ -241,12 +244,12 @@ __device__ __forceinline__ void splat_bilinear(const DSys& sys, float cx, float 
     const float fu = u - fi, fv = v - fj;
     const int nx = sys.nx, ny = sys.ny;
     if (j0 >= 0) {
-        if (i0 >= 0) atomicAdd(img + j0 * nx + i0, w * (1.f - fu) * (1.f - fv));
-        if (i0 + 1 < nx) atomicAdd(img + j0 * nx + i0 + 1, w * fu * (1.f - fv));
+        if (i0 >= 0) atomicAdd(img + j0 * nx + i0, (double)(w * (1.f - fu) * (1.f - fv)));
+        if (i0 + 1 < nx) atomicAdd(img + j0 * nx + i0 + 1, (double)(w * fu * (1.f - fv)));
     }
     if (j0 + 1 < ny) {
-        if (i0 >= 0) atomicAdd(img + (j0 + 1) * nx + i0, w * (1.f - fu) * fv);
-        if (i0 + 1 < nx) atomicAdd(img + (j0 + 1) * nx + i0 + 1, w * fu * fv);
+        if (i0 >= 0) atomicAdd(img + (j0 + 1) * nx + i0, (double)(w * (1.f - fu) * fv));
+        if (i0 + 1 < nx) atomicAdd(img + (j0 + 1) * nx + i0 + 1, (double)(w * fu * fv));
     }
 }
 
@@ -314,7 +317,7 @@ __device__ __forceinline__ float2 spectrum_at(const float2* X, const float2* phu
 template <int MODE>
 __device__ __forceinline__ void deposit(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                         float dx, float dy, float dz, float2 a,
-                                        float* __restrict__ psf, float2* __restrict__ field,
+                                        double* __restrict__ psf, float2* __restrict__ field,
                                         unsigned* status) {
     float x = R.px, y = R.py, zl = R.pz;
     double opl = R.opl;
@@ -346,7 +349,7 @@ __device__ __forceinline__ void emit_dead(const DSys& sys, long long g, long lon
 template <int D, int MODE>
 __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                                 const float2* X, const float2* phu,
-                                                const float2* phv, float* psf, float2* field,
+                                                const float2* phv, double* psf, float2* field,
                                                 const EmitOut& eo, long long g, unsigned* status) {
     const float2 ain = make_float2(R.a_re, R.a_im);
     if (MODE == MODE_EMIT && threadIdx.x == 0) {
@@ -383,7 +386,7 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
 template <int D, int MODE>
 __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                              const float2* X, const float2* phu, const float2* phv,
-                                             float* psf, float2* field, const EmitOut& eo,
+                                             double* psf, float2* field, const EmitOut& eo,
                                              long long g, unsigned* status,
                                              unsigned char* scratch) {
     float* logp = reinterpret_cast<float*>(scratch);
@@ -484,7 +487,8 @@ cudaError_t launch_generate_rays(const LaunchCtx& L, const GenJob* jobs, const l
                                  const RaysOut& out);
 cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const DJob* jobs,
                            const long long* prefix, int njob, long long total, const RaysIn& rays,
-                           const float2* T, float* psf, float2* field, const EmitOut& eo,
+                           const float2* T, double* acc, float2* field, const EmitOut& eo,
                            unsigned* status);
+cudaError_t launch_psf_finalize(const LaunchCtx& L, const double* acc, float* psf, long long n);
 cudaError_t launch_coherent_finalize(const LaunchCtx& L, const float2* field, float* psf,
                                      long long n);

@@ -198,7 +198,9 @@ def test_unit_map_at_full_c2_size_is_the_spot_diagram(RW, ctx):
     """T = 1 puts all energy in bin 0: the full-size PSF is the refractive
     spot diagram of the 9M incident rays, which the oracle traces directly."""
     w = R.configs.c2()
-    w.system.doe.phi = np.zeros_like(w.system.doe.phi)
+    # zero phase on a map padded by D/2 on every side, so every 64 x 64 patch
+    # of the 2.048 mm bundle lies inside the map (outside the map T = 0)
+    w.system.doe.phi = np.zeros((2048 + 64, 2048 + 64), dtype=np.float32)
     sim = RW.Simulator(w, ctx=ctx)
     psf = sim.forward().cpu().numpy()
     from oracle import geometry as G, sensor as S
