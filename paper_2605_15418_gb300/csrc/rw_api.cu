@@ -144,6 +144,8 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
         return fail(ctx, RW_EINVAL, "doe.lambda0 must be > 0 for the height model");
     if (doe.dft != RW_DFT_FFT32 && doe.dft != RW_DFT_TC)
         return fail(ctx, RW_EINVAL, "doe.dft invalid");
+    if (doe.dft == RW_DFT_TC)
+        return fail(ctx, RW_EINVAL, "tensor-core patch transform is not available in this build");
     const rw_sensor& sen = sys->sensor;
     if (sen.nx < 1 || sen.ny < 1 || !(sen.pitch > 0))
         return fail(ctx, RW_EINVAL, "sensor size and pitch must be positive");
