@@ -230,6 +230,28 @@ rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
                       int32_t njob, const rw_rays* rays, const float* dl_dpsf,
                       float* dphi, float* damp, double* dsurf);
 
+/* ---- allocation-free ray generation ------------------------------------ */
+
+/* Same result as rw_generate_rays, for callers that cannot call cudaMalloc:
+ * a plugin inside a host application that owns all device memory through
+ * its own allocator, or a real-time loop that cannot afford the implicit
+ * device synchronisation of cudaMalloc.  (The paper has no counterpart;
+ * this is a deployment interface.)
+ *
+ * Needs no context and allocates nothing: the job table is copied from a
+ * stack buffer into a file-scope device array of the library sized for at
+ * most 1024 jobs (about 64 KiB, held by every GPU that loads the library
+ * until the process exits).  njob > 1024 returns RW_ECAPACITY; bad
+ * arguments return RW_EINVAL; a failing CUDA call returns RW_ECUDA.  Work is
+ * enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy default stream)
+ * of the CURRENT device.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  Every call shares the array
+ * and rewrites the part it uses, so nothing needs clearing, but calls that
+ * overlap on the GPU (different streams, no ordering) race on it. */
+rw_status rw_generate_rays_static(double z_start, double n_object, const rw_job* jobs,
+                                  int32_t njob, rw_rays* rays, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
