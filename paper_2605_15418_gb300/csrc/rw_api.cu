@@ -186,6 +186,22 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
         n_prev = s.n_after;
     }
     if (sen.z < prev_z) return fail(ctx, RW_EINVAL, "sensor must lie behind the last surface");
+    // surfaces behind the DOE for the specialised plane/sphere trace
+    d.n_post = sys->nsurf - sys->doe_index - 1;
+    d.fast_ok = d.n_post <= 8 ? 1 : 0;
+    for (int i = 0; i < d.n_post && d.fast_ok; ++i) {
+        const int si = sys->doe_index + 1 + i;
+        const rw_surface& s = sys->surfaces[si];
+        if (s.kind == RW_ASPHERE) { d.fast_ok = 0; break; }
+        PSurf& q = d.post[i];
+        q.kind = s.kind;
+        q.c = (s.kind == RW_PLANE) ? 0.f : (float)s.c;
+        q.gap = d.s[si].gap;
+        q.r_ap2 = d.s[si].r_ap2;
+        const double nb = (si == 0) ? sys->n_object : sys->surfaces[si - 1].n_after;
+        q.eta = (float)(nb / s.n_after);
+        q.inv_n_after = (float)(1.0 / s.n_after);
+    }
     d.H = doe.H; d.W = doe.W; d.D = doe.D;
     d.gather = doe.gather; d.emit = doe.emit; d.n_ssr = doe.n_ssr;
     d.phase_model = doe.phase_model;

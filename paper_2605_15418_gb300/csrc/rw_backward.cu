@@ -49,8 +49,50 @@ __device__ __forceinline__ void bilinear_grad(const DSys& sys, float cx, float c
     gy = gfv * sys.inv_spitch;
 }
 
+// Reverse of the sensor plane xs = x + ts d, ts = -zs / dz, then of the
+// emission d = (ku u + kv v + kn n) / K; accumulates dL/d(hit), dL/dkappa and
+// dL/dK of the incident ray into acc[0..5].
+__device__ __forceinline__ void sensor_plane_adjoint(float gxs, float gys, float ex, float ey,
+                                                     float ez, float ts, float& gx, float& gy,
+                                                     float& gz, float& gdx, float& gdy,
+                                                     float& gdz) {
+    gx = gxs;
+    gy = gys;
+    const float gts = gxs * ex + gys * ey;
+    gdx = gxs * ts;
+    gdy = gys * ts;
+    const float iez = 1.f / ez;
+    gz = -gts * iez;
+    gdz = -gts * ts * iez;
+}
+
+__device__ __forceinline__ void emission_adjoint(const DSys& sys, const RayAtDoe& R, int ju,
+                                                 int jv, float dx, float dy, float dz,
+                                                 float gx, float gy, float gz, float gdx,
+                                                 float gdy, float gdz, float* acc) {
+    const float ku = R.kin_u + sys.kstep * (float)ju;
+    const float kv = R.kin_v + sys.kstep * (float)jv;
+    const float K = R.K;
+    const float kn2 = fmaxf(K * K - ku * ku - kv * kv, 0.f);
+    float ikn;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ikn) : "f"(kn2));
+    const float gdu = gdx * R.u[0] + gdy * R.u[1] + gdz * R.u[2];
+    const float gdv = gdx * R.v[0] + gdy * R.v[1] + gdz * R.v[2];
+    const float gdn = gdx * R.n[0] + gdy * R.n[1] + gdz * R.n[2];
+    const float gku = (gdu - ku * ikn * gdn) * R.invK;
+    const float gkv = (gdv - kv * ikn * gdn) * R.invK;
+    const float gdd = gdx * dx + gdy * dy + gdz * dz;
+    const float gK = gdn * ikn - gdd * R.invK;
+    acc[0] += gx; acc[1] += gy; acc[2] += gz;
+    acc[3] += gku; acc[4] += gkv;
+    acc[5] += gK;
+}
+
 template <int D>
-__global__ void __launch_bounds__(RW_THREADS)
+struct BwdOcc { static constexpr int value = D == 64 ? 3 : (D == 96 ? 1 : 2); };
+
+template <int D, int NS>
+__global__ void __launch_bounds__(RW_THREADS, BwdOcc<D>::value)
 k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
            int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
            const float* __restrict__ amp, const float* __restrict__ gpsf,
@@ -69,6 +111,12 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
     float gs[RW_MAXS * RW_NGRAD];
 #pragma unroll
     for (int i = 0; i < RW_MAXS * RW_NGRAD; ++i) gs[i] = 0.f;
+    // specialised path: per-surface gradients in registers (z, c, n_after)
+    constexpr int NR = NS > 0 ? NS : 1;
+    float fz[NR], fc[NR], fn[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) { fz[i] = 0.f; fc[i] = 0.f; fn[i] = 0.f; }
+    float f_doe_n = 0.f;
     const long long npix_map = (long long)sys.H * sys.W;
     const long long npx = (long long)sys.nx * sys.ny;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
@@ -96,7 +144,50 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                 int mv = jvi + D / 2; if (mv >= D) mv -= D;
                 float2 gU = make_float2(0.f, 0.f);
                 float dx, dy, dz;
-                if (bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
+                if (NS >= 0) {
+                    if (bin_direction<true>(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
+                        const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+                        const float2 a = cmul(ain, U);
+                        const float w = a.x * a.x + a.y * a.y;
+                        SurfIn st[NR];
+                        float x = R.px, y = R.py, zl = R.pz;
+                        float ex = dx, ey = dy, ez = dz;
+                        bool ok = true;
+#pragma unroll
+                        for (int i = 0; i < NS; ++i) {
+                            if (ok) {
+                                st[i].x = x; st[i].y = y; st[i].zl = zl - sys.post[i].gap;
+                                st[i].dx = ex; st[i].dy = ey; st[i].dz = ez;
+                                ok = fast_step(sys.post[i], x, y, zl, ex, ey, ez);
+                            }
+                        }
+                        if (ok) {
+                            const float zs = zl - sys.sensor_gap;
+                            const float ts = -zs * rcp_fast(ez);
+                            const float xs = fmaf(ts, ex, x), ys = fmaf(ts, ey, y);
+                            float gw, gxs, gys;
+                            bilinear_grad(sys, R.cx, R.cy, xs, ys, gimg, gw, gxs, gys);
+                            gxs *= w;
+                            gys *= w;
+                            if (gw != 0.f || gxs != 0.f || gys != 0.f) {
+                                float gx, gy, gz, gdx, gdy, gdz;
+                                sensor_plane_adjoint(gxs, gys, ex, ey, ez, ts, gx, gy, gz, gdx,
+                                                     gdy, gdz);
+#pragma unroll
+                                for (int i = NS - 1; i >= 0; --i) {
+                                    float gnb = 0.f;
+                                    fast_step_adjoint(sys.post[i], st[i], gx, gy, gz, gdx, gdy,
+                                                      gdz, fz[i], fc[i], fn[i], gnb);
+                                    if (i > 0) fn[i > 0 ? i - 1 : 0] += gnb; else f_doe_n += gnb;
+                                }
+                                emission_adjoint(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz,
+                                                 gx, gy, gz, gdx, gdy, gdz, acc);
+                                const float2 ga = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
+                                gU = cmulc(ga, ain);
+                            }
+                        }
+                    }
+                } else if (bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
                     const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
                     const float2 a = cmul(ain, U);
                     const float w = a.x * a.x + a.y * a.y;
@@ -267,6 +358,16 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
     }
     // ---- CTA reduction of surface-parameter gradients
     if (!dsurf) return;
+    if (NS >= 0) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            const int si = sys.doe_index + 1 + i;
+            gs[si * RW_NGRAD + 0] += fz[i];
+            gs[si * RW_NGRAD + 1] += fc[i];
+            gs[si * RW_NGRAD + 7] += fn[i];
+        }
+        gs[sys.doe_index * RW_NGRAD + 7] += f_doe_n;
+    }
     __syncthreads();
     double* dred = reinterpret_cast<double*>(smem);
     for (int s = 0; s < sys.nsurf; ++s) {
@@ -291,14 +392,14 @@ inline size_t backward_smem_bytes(int D) {
     return b > red ? b : red;
 }
 
-template <int D>
+template <int D, int NS>
 static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                      const long long* prefix, int njob, long long total,
                                      const RaysIn& rays, const float2* T, const float* amp,
                                      const float* gpsf, float* dphi, float* damp, double* dsurf,
                                      unsigned* status) {
     const size_t smem = backward_smem_bytes(D);
-    auto kern = k_backward<D>;
+    auto kern = k_backward<D, NS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -323,11 +424,25 @@ cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* job
                             int /*scratch_slots*/, unsigned* status, int* launches) {
     if (sys.emit != RW_EMIT_EXHAUSTIVE) return cudaErrorNotSupported;
     *launches = 1;
+    const int ns = sys.fast_ok ? sys.n_post : -1;
+#define RW_BWD(DD, NN) \
+    launch_backward_d<DD, NN>(L, sys, jobs, prefix, njob, total, rays, T, amp, dl_dpsf, dphi, damp, dsurf, status)
+#define RW_BWD_D(DD)                                      \
+    case DD:                                              \
+        switch (ns) {                                     \
+            case 0: return RW_BWD(DD, 0);                 \
+            case 2: return RW_BWD(DD, 2);                 \
+            case 4: return RW_BWD(DD, 4);                 \
+            case 6: return RW_BWD(DD, 6);                 \
+            default: return RW_BWD(DD, -1);               \
+        }
     switch (sys.D) {
-        case 16: return launch_backward_d<16>(L, sys, jobs, prefix, njob, total, rays, T, amp, dl_dpsf, dphi, damp, dsurf, status);
-        case 32: return launch_backward_d<32>(L, sys, jobs, prefix, njob, total, rays, T, amp, dl_dpsf, dphi, damp, dsurf, status);
-        case 64: return launch_backward_d<64>(L, sys, jobs, prefix, njob, total, rays, T, amp, dl_dpsf, dphi, damp, dsurf, status);
-        case 96: return launch_backward_d<96>(L, sys, jobs, prefix, njob, total, rays, T, amp, dl_dpsf, dphi, damp, dsurf, status);
+        RW_BWD_D(16)
+        RW_BWD_D(32)
+        RW_BWD_D(64)
+        RW_BWD_D(96)
         default: return cudaErrorInvalidValue;
     }
+#undef RW_BWD_D
+#undef RW_BWD
 }

@@ -33,9 +33,18 @@ struct DSurf {
     double cd;         // curvature in double (FP64 Newton refinement)
 };
 
+// Post-DOE plane/sphere in the form the specialised trace uses.
+struct PSurf {
+    int kind;
+    float c, gap, r_ap2, eta, inv_n_after;
+};
+
 struct DSys {
     int nsurf, doe_index;
     DSurf s[RW_MAXS];
+    PSurf post[8];     // surfaces behind the DOE (when n_post <= 8, no aspheres)
+    int n_post;        // number of surfaces behind the DOE
+    int fast_ok;       // 1: post[] is valid for the specialised trace
     double n_object;
     // DOE
     int H, W, D, gather, emit, n_ssr, phase_model, conformal;
@@ -70,6 +79,7 @@ struct RayAtDoe {
     float px, py, pz;       // hit, local to the DOE vertex (z) / global (x, y)
     float u[3], v[3], n[3];
     float kin_u, kin_v, K;  // tangential incident wavevector, k0 n_out
+    float invK;
     float a_re, a_im;
     double opl;
     double pxd, pyd;        // hit in double (patch indexing)

@@ -55,8 +55,13 @@ __global__ void k_generate_rays(const GenJob* __restrict__ jobs, const long long
 }
 
 // ------------------------------------------------------------- fused forward
-template <int D, int MODE>
-__global__ void __launch_bounds__(RW_THREADS)
+// Resident CTAs per SM the register allocation is sized for (D = 96 needs
+// more registers for its FFT stages and more shared memory per CTA).
+template <int D>
+struct FwdOcc { static constexpr int value = D <= 64 ? 4 : 1; };
+
+template <int D, int MODE, int NS>
+__global__ void __launch_bounds__(RW_THREADS, FwdOcc<D>::value)
 k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
           int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
           double* __restrict__ psf, float2* __restrict__ field, EmitOut eo, unsigned* status) {
@@ -86,10 +91,10 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             __syncthreads();
             fft2d<D, false>(X, tw);
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
-                emit_exhaustive<D, MODE>(sys, J, R, X, phu, phv, psf, field, eo,
+                emit_exhaustive<D, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                          tile * RW_TILE + r, status);
             } else {
-                emit_sampled<D, MODE>(sys, J, R, X, phu, phv, psf, field, eo,
+                emit_sampled<D, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                       tile * RW_TILE + r, status,
                                       smem + sampled_scratch_offset(D));
             }
@@ -117,13 +122,13 @@ __global__ void k_coherent_finalize(const float2* __restrict__ field, float* __r
 }
 
 // ------------------------------------------------------------- launchers
-template <int D, int MODE>
+template <int D, int MODE, int NS>
 static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                     const long long* prefix, int njob, long long total,
                                     const RaysIn& rays, const float2* T, double* psf,
                                     float2* field, const EmitOut& eo, unsigned* status) {
     size_t smem = forward_smem_bytes(D, sys.emit, sys.n_ssr);
-    auto kern = k_forward<D, MODE>;
+    auto kern = k_forward<D, MODE, NS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -141,6 +146,25 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
     return cudaGetLastError();
 }
 
+// Post-DOE surface counts with a specialised (unrolled plane/sphere) trace.
+template <int D>
+static cudaError_t launch_splat(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
+                                const long long* prefix, int njob, long long total,
+                                const RaysIn& rays, const float2* T, double* psf,
+                                const EmitOut& eo, unsigned* status) {
+    if (sys.fast_ok) {
+        switch (sys.n_post) {
+            case 0: return launch_forward_d<D, MODE_SPLAT, 0>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status);
+            case 2: return launch_forward_d<D, MODE_SPLAT, 2>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status);
+            case 4: return launch_forward_d<D, MODE_SPLAT, 4>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status);
+            case 6: return launch_forward_d<D, MODE_SPLAT, 6>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status);
+            default: break;
+        }
+    }
+    return launch_forward_d<D, MODE_SPLAT, -1>(L, sys, jobs, prefix, njob, total, rays, T, psf,
+                                               nullptr, eo, status);
+}
+
 cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const DJob* jobs,
                            const long long* prefix, int njob, long long total,
                            const RaysIn& rays, const float2* T, double* psf, float2* field,
@@ -148,13 +172,13 @@ cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const 
 #define RW_FWD_CASE(DD)                                                                       \
     case DD:                                                                                  \
         if (mode == MODE_SPLAT)                                                               \
-            return launch_forward_d<DD, MODE_SPLAT>(L, sys, jobs, prefix, njob, total, rays,  \
-                                                    T, psf, field, eo, status);               \
+            return launch_splat<DD>(L, sys, jobs, prefix, njob, total, rays, T, psf, eo,      \
+                                    status);                                                  \
         if (mode == MODE_COHERENT)                                                            \
-            return launch_forward_d<DD, MODE_COHERENT>(L, sys, jobs, prefix, njob, total,     \
-                                                       rays, T, psf, field, eo, status);      \
-        return launch_forward_d<DD, MODE_EMIT>(L, sys, jobs, prefix, njob, total, rays, T,    \
-                                               psf, field, eo, status);
+            return launch_forward_d<DD, MODE_COHERENT, -1>(L, sys, jobs, prefix, njob, total, \
+                                                           rays, T, psf, field, eo, status);  \
+        return launch_forward_d<DD, MODE_EMIT, -1>(L, sys, jobs, prefix, njob, total, rays, T,\
+                                                   psf, field, eo, status);
     switch (sys.D) {
         RW_FWD_CASE(16)
         RW_FWD_CASE(32)

@@ -2,6 +2,7 @@
 // kernels, plus the host-side launcher declarations.
 #pragma once
 #include "rw_device.cuh"
+#include "rw_fast.cuh"
 #include "rw_fft.cuh"
 
 enum { MODE_SPLAT = 0, MODE_COHERENT = 1, MODE_EMIT = 2 };
@@ -138,6 +139,7 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     R.kin_u = k0 * sys.n_in * (dx * ux + dy * uy + dz * uz);
     R.kin_v = k0 * sys.n_in * (dx * vx + dy * vy + dz * vz);
     R.K = k0 * sys.n_out;
+    R.invK = 1.f / R.K;
     R.px = (float)pxd; R.py = (float)pyd; R.pz = (float)pzl;
     R.pxd = pxd; R.pyd = pyd;
     R.a_re = rays.are[ri]; R.a_im = rays.aim[ri];
@@ -290,6 +292,7 @@ __device__ __forceinline__ void splat_coherent(const DSys& sys, float k0, float 
 }
 
 // Direction of spectral bin (ju, jv) for the incident state R; false if evanescent.
+template <bool FAST = false>
 __device__ __forceinline__ bool bin_direction(const DSys& sys, const RayAtDoe& R, int ju, int jv,
                                               float& dx, float& dy, float& dz) {
     const float ku = R.kin_u + sys.kstep * (float)ju;
@@ -297,8 +300,10 @@ __device__ __forceinline__ bool bin_direction(const DSys& sys, const RayAtDoe& R
     const float K2 = R.K * R.K;
     const float kt2 = ku * ku + kv * kv;
     if (kt2 >= K2) return false;
-    const float kn = sqrtf(K2 - kt2);
-    const float invK = 1.f / R.K;
+    float kn;
+    if (FAST) asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(kn) : "f"(K2 - kt2));
+    else kn = sqrtf(K2 - kt2);
+    const float invK = R.invK;
     dx = (ku * R.u[0] + kv * R.v[0] + kn * R.n[0]) * invK;
     dy = (ku * R.u[1] + kv * R.v[1] + kn * R.n[1]) * invK;
     dz = (ku * R.u[2] + kv * R.v[2] + kn * R.n[2]) * invK;
@@ -314,7 +319,7 @@ __device__ __forceinline__ float2 spectrum_at(const float2* X, const float2* phu
     return cscale(cmul(cmul(X[mv * D + mu], phu[jui]), phv[jvi]), invD2);
 }
 
-template <int MODE>
+template <int MODE, int NS>
 __device__ __forceinline__ void deposit(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                         float dx, float dy, float dz, float2 a,
                                         double* __restrict__ psf, float2* __restrict__ field,
@@ -322,7 +327,10 @@ __device__ __forceinline__ void deposit(const DSys& sys, const DJob& J, const Ra
     float x = R.px, y = R.py, zl = R.pz;
     double opl = R.opl;
     const long long npx = (long long)sys.nx * sys.ny;
-    if (MODE == MODE_SPLAT) {
+    if (MODE == MODE_SPLAT && NS >= 0) {
+        if (!fast_to_sensor<NS>(sys, x, y, zl, dx, dy, dz)) return;
+        splat_bilinear(sys, R.cx, R.cy, x, y, a.x * a.x + a.y * a.y, psf + (long long)R.job * npx);
+    } else if (MODE == MODE_SPLAT) {
         if (!trace_to_sensor<false>(sys, x, y, zl, dx, dy, dz, opl, status)) return;
         splat_bilinear(sys, R.cx, R.cy, x, y, a.x * a.x + a.y * a.y, psf + (long long)R.job * npx);
     } else {
@@ -346,7 +354,7 @@ __device__ __forceinline__ void emit_dead(const DSys& sys, long long g, long lon
 }
 
 // ------------------------------------------------------------------ A5 exhaustive
-template <int D, int MODE>
+template <int D, int MODE, int NS>
 __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                                 const float2* X, const float2* phu,
                                                 const float2* phv, double* psf, float2* field,
@@ -359,7 +367,7 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
     for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
         const int jvi = f / D, jui = f - (f / D) * D;
         float dx, dy, dz;
-        const bool prop = bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz);
+        const bool prop = bin_direction<(NS >= 0)>(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz);
         if (MODE == MODE_EMIT) {
             const long long s = g * (long long)(D * D) + f;
             if (!prop) {
@@ -373,7 +381,7 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
         }
         if (!prop) continue;
         const float2 a = cmul(ain, spectrum_at<D>(X, phu, phv, jui, jvi));
-        deposit<MODE>(sys, J, R, dx, dy, dz, a, psf, field, status);
+        deposit<MODE, NS>(sys, J, R, dx, dy, dz, a, psf, field, status);
     }
 }
 
@@ -383,7 +391,7 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
 // Coherent sensor: p ~ |U~|, a = a_in U~ / (N p).  Incoherent: p ~ |U~|^2,
 // a = a_in U~ / sqrt(N p) so that |a|^2 is the unbiased power weight.
 // Shared scratch after the patch: logp[D*D] floats, sel[n_ssr] ints, red[32].
-template <int D, int MODE>
+template <int D, int MODE, int NS>
 __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                              const float2* X, const float2* phu, const float2* phv,
                                              double* psf, float2* field, const EmitOut& eo,
@@ -462,7 +470,7 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
         bool ok = false;
         if (jb >= 0) {
             const int jvi = jb / D, jui = jb - (jb / D) * D;
-            ok = bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz);
+            ok = bin_direction<(NS >= 0)>(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz);
             const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
             const float pj = expf(logp[jb]);
             const float sc = coh ? 1.f / (N * pj) : rsqrtf(N * pj);
@@ -475,7 +483,7 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
             if (eo.bin) eo.bin[s] = jb;
             continue;
         }
-        if (ok) deposit<MODE>(sys, J, R, dx, dy, dz, a, psf, field, status);
+        if (ok) deposit<MODE, NS>(sys, J, R, dx, dy, dz, a, psf, field, status);
     }
 }
 
