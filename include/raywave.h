@@ -106,7 +106,7 @@ typedef struct {
     int32_t emit;          /* RW_EMIT_* */
     int32_t n_ssr;         /* draws per incident ray in sampled mode */
     int32_t phase_model;   /* RW_PHASE_* */
-    int32_t dft;           /* RW_DFT_* */
+    int32_t dft;           /* RW_DFT_*: TC only in rw_patch_spectra (fused calls: FFT32) */
     uint64_t seed;         /* Philox key for sampled mode */
     uint64_t rng_offset;   /* Philox counter word 3 for sampled mode */
 } rw_doe;
@@ -207,6 +207,20 @@ rw_status rw_doe_emit(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
  * Incoherent: sum of bilinear |a|^2 deposits; coherent: |Eq. 2|^2. */
 rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
                      int32_t njob, const rw_rays* rays, float* psf);
+
+/* ---- A3..A4: patch spectra only ----------------------------------------- */
+
+/* Trace every job's rays to the DOE and write the angular spectrum of each
+ * patch, U~[j_v][j_u] referred to the hit point and normalised by 1/D^2
+ * (section "Ray-Wave Simulator Formalism", second paragraph), as complex
+ * float pairs: spectra[(i * D + (j_v + D/2)) * D + (j_u + D/2)] for incident
+ * ray i in job order; rays that miss the DOE give zeros.  doe.dft selects the
+ * implementation: RW_DFT_FFT32 (FP32 shared-memory FFT, any supported D) or
+ * RW_DFT_TC (tensor-core contraction F X F^T with a BF16x3 split and FP32
+ * accumulation, D = 64 only).  capacity counts complex entries.
+ * Errors: RW_EINVAL, RW_ECAPACITY (capacity < n_rays * D * D). */
+rw_status rw_patch_spectra(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                           const rw_rays* rays, float* spectra, int64_t capacity);
 
 /* ---- A8: Eq. 3 loss ---------------------------------------------------- */
 

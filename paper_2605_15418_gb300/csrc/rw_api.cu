@@ -17,6 +17,10 @@ cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* job
                             const RaysIn& rays, const float2* T, const float* amp,
                             const float* dl_dpsf, float* dphi, float* damp, double* dsurf,
                             int scratch_slots, unsigned* status, int* launches);
+size_t backward_smem_needed(const DSys& sys);
+cudaError_t launch_spectra(const LaunchCtx& L, const DSys& sys, int tc, const DJob* jobs,
+                           const long long* prefix, int njob, long long total, const RaysIn& rays,
+                           const float2* T, float2* out, unsigned* status);
 
 namespace {
 
@@ -50,6 +54,11 @@ struct rw_ctx {
     void* staging = nullptr;       // pinned host copy source of `tables`
     size_t staging_bytes = 0;
     cudaEvent_t staging_done = nullptr;
+    // tables uploaded while the stream is being captured into a CUDA graph:
+    // bump-allocated, never reused, so every captured copy node keeps its data
+    void* cap_host = nullptr;
+    DevBuf cap_dev;
+    size_t cap_used = 0;
     int64_t launches = 0;
     long long grid_override = 0;
 };
@@ -72,8 +81,29 @@ static double* loss_acc(rw_ctx* ctx) {
     return reinterpret_cast<double*>(reinterpret_cast<char*>(ctx->misc.p) + 64);
 }
 
+#define RW_CAPTURE_ARENA (4u << 20)
+
+static bool capturing(rw_ctx* ctx) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) return false;
+    return cs == cudaStreamCaptureStatusActive;
+}
+
+// Grow a scratch buffer; refused while the stream is being captured (run the
+// same call once eagerly first so the scratch is already large enough).
+static rw_status ensure_buf(rw_ctx* ctx, DevBuf& b, size_t need, const char* what) {
+    if (need <= b.bytes) return RW_OK;
+    if (capturing(ctx))
+        return fail(ctx, RW_EINVAL, std::string(what) +
+                                        ": scratch must grow during graph capture; run the call "
+                                        "once outside the capture first");
+    if (b.ensure(need) != cudaSuccess) return fail(ctx, RW_ENOMEM, what);
+    return RW_OK;
+}
+
 // Copy small host tables to the device through the pinned staging buffer.
-// The previous copy out of the staging buffer is waited for first.
+// The previous copy out of the staging buffer is waited for first.  During
+// stream capture the tables go through the capture arenas instead.
 static rw_status upload(rw_ctx* ctx, const std::vector<std::pair<const void*, size_t>>& parts,
                         std::vector<void*>& dev_ptrs) {
     size_t total = 0;
@@ -81,6 +111,20 @@ static rw_status upload(rw_ctx* ctx, const std::vector<std::pair<const void*, si
     for (auto& p : parts) { offs.push_back(total); total += align16(p.second); }
     if (total == 0) total = 16;
     RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    if (capturing(ctx)) {
+        if (!ctx->cap_host || ctx->cap_used + total > RW_CAPTURE_ARENA)
+            return fail(ctx, RW_ENOMEM, "graph-capture table arena exhausted (4 MiB per context)");
+        char* h = (char*)ctx->cap_host + ctx->cap_used;
+        char* dv = (char*)ctx->cap_dev.p + ctx->cap_used;
+        ctx->cap_used += total;
+        for (size_t i = 0; i < parts.size(); ++i)
+            if (parts[i].second) std::memcpy(h + offs[i], parts[i].first, parts[i].second);
+        RW_CUDA(cudaMemcpyAsync(dv, h, total, cudaMemcpyHostToDevice, ctx->stream),
+                "captured table upload");
+        dev_ptrs.clear();
+        for (size_t i = 0; i < parts.size(); ++i) dev_ptrs.push_back(dv + offs[i]);
+        return RW_OK;
+    }
     if (ctx->staging_done) RW_CUDA(cudaEventSynchronize(ctx->staging_done), "staging wait");
     if (total > ctx->staging_bytes) {
         if (ctx->staging) cudaFreeHost(ctx->staging);
@@ -89,7 +133,10 @@ static rw_status upload(rw_ctx* ctx, const std::vector<std::pair<const void*, si
         RW_CUDA(cudaMallocHost(&ctx->staging, total), "cudaMallocHost");
         ctx->staging_bytes = total;
     }
-    if (ctx->tables.ensure(total) != cudaSuccess) return fail(ctx, RW_ENOMEM, "table scratch");
+    {
+        rw_status st = ensure_buf(ctx, ctx->tables, total, "table scratch");
+        if (st != RW_OK) return st;
+    }
     for (size_t i = 0; i < parts.size(); ++i)
         if (parts[i].second) std::memcpy((char*)ctx->staging + offs[i], parts[i].first, parts[i].second);
     RW_CUDA(cudaMemcpyAsync(ctx->tables.p, ctx->staging, total, cudaMemcpyHostToDevice, ctx->stream),
@@ -144,8 +191,6 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
         return fail(ctx, RW_EINVAL, "doe.lambda0 must be > 0 for the height model");
     if (doe.dft != RW_DFT_FFT32 && doe.dft != RW_DFT_TC)
         return fail(ctx, RW_EINVAL, "doe.dft invalid");
-    if (doe.dft == RW_DFT_TC)
-        return fail(ctx, RW_EINVAL, "tensor-core patch transform is not available in this build");
     const rw_sensor& sen = sys->sensor;
     if (sen.nx < 1 || sen.ny < 1 || !(sen.pitch > 0))
         return fail(ctx, RW_EINVAL, "sensor size and pitch must be positive");
@@ -297,8 +342,9 @@ static rw_status prepare(rw_ctx* ctx, const rw_system* sys, const Packed& P, flo
     *dprefix = (long long*)ptrs[1];
     const int64_t npix = (int64_t)sys->doe.H * sys->doe.W;
     const int nslot = (int)P.scales.size();
-    if (ctx->tmaps.ensure((size_t)npix * nslot * sizeof(float2)) != cudaSuccess)
-        return fail(ctx, RW_ENOMEM, "transmission-map scratch");
+    st = ensure_buf(ctx, ctx->tmaps, (size_t)npix * nslot * sizeof(float2),
+                    "transmission-map scratch");
+    if (st != RW_OK) return st;
     *T = (float2*)ctx->tmaps.p;
     RW_CUDA(launch_prep_maps(lctx(ctx), sys->doe.phi, sys->doe.amp, npix, (const float*)ptrs[2],
                              nslot, *T),
@@ -324,7 +370,9 @@ rw_status rw_create(rw_ctx** out, int device, void* cuda_stream) {
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (cudaEventCreateWithFlags(&ctx->staging_done, cudaEventDisableTiming) != cudaSuccess ||
         ctx->misc.ensure(256) != cudaSuccess ||
-        cudaMemset(ctx->misc.p, 0, 256) != cudaSuccess) {
+        cudaMemset(ctx->misc.p, 0, 256) != cudaSuccess ||
+        cudaMallocHost(&ctx->cap_host, RW_CAPTURE_ARENA) != cudaSuccess ||
+        ctx->cap_dev.ensure(RW_CAPTURE_ARENA) != cudaSuccess) {
         delete ctx;
         return RW_ECUDA;
     }
@@ -343,6 +391,8 @@ rw_status rw_destroy(rw_ctx* ctx) {
     ctx->field.release();
     ctx->acc.release();
     ctx->misc.release();
+    ctx->cap_dev.release();
+    if (ctx->cap_host) cudaFreeHost(ctx->cap_host);
     if (ctx->staging) cudaFreeHost(ctx->staging);
     if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
     delete ctx;
@@ -421,6 +471,9 @@ rw_status rw_doe_emit(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int
     Packed P;
     rw_status st = pack_system(ctx, sys, P);
     if (st != RW_OK) return st;
+    if (sys->doe.dft == RW_DFT_TC)
+        return fail(ctx, RW_EINVAL, "the fused kernels use the FP32 FFT; the tensor-core "
+                                    "transform is available through rw_patch_spectra");
     if ((st = check_rays(ctx, rays)) != RW_OK) return st;
     if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
     if (!out || !out->dx || !out->dy || !out->dz || !out->a_re || !out->a_im || !out->hx ||
@@ -449,6 +502,9 @@ rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int3
     Packed P;
     rw_status st = pack_system(ctx, sys, P);
     if (st != RW_OK) return st;
+    if (sys->doe.dft == RW_DFT_TC)
+        return fail(ctx, RW_EINVAL, "the fused kernels use the FP32 FFT; the tensor-core "
+                                    "transform is available through rw_patch_spectra");
     if ((st = check_rays(ctx, rays)) != RW_OK) return st;
     if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
     if (!psf) return fail(ctx, RW_EINVAL, "psf is NULL");
@@ -461,8 +517,9 @@ rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int3
     EmitOut eo;
     std::memset(&eo, 0, sizeof(eo));
     if (P.sys.coherent) {
-        if (ctx->field.ensure(npx * sizeof(float2)) != cudaSuccess)
-            return fail(ctx, RW_ENOMEM, "coherent field scratch");
+        if ((st = ensure_buf(ctx, ctx->field, npx * sizeof(float2), "coherent field scratch")) !=
+            RW_OK)
+            return st;
         RW_CUDA(cudaMemsetAsync(ctx->field.p, 0, npx * sizeof(float2), ctx->stream), "field clear");
         RW_CUDA(launch_forward(lctx(ctx), MODE_COHERENT, P.sys, dj, dp, njob, P.total,
                                rays_in(rays), T, nullptr, (float2*)ctx->field.p, eo,
@@ -471,8 +528,9 @@ rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int3
         RW_CUDA(launch_coherent_finalize(lctx(ctx), (float2*)ctx->field.p, psf, npx), "finalize");
         ctx->launches++;
     } else {
-        if (ctx->acc.ensure(npx * sizeof(double)) != cudaSuccess)
-            return fail(ctx, RW_ENOMEM, "PSF accumulator scratch");
+        if ((st = ensure_buf(ctx, ctx->acc, npx * sizeof(double), "PSF accumulator scratch")) !=
+            RW_OK)
+            return st;
         RW_CUDA(cudaMemsetAsync(ctx->acc.p, 0, npx * sizeof(double), ctx->stream), "acc clear");
         RW_CUDA(launch_forward(lctx(ctx), MODE_SPLAT, P.sys, dj, dp, njob, P.total,
                                rays_in(rays), T, (double*)ctx->acc.p, nullptr, eo,
@@ -505,12 +563,19 @@ rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int
     Packed P;
     rw_status st = pack_system(ctx, sys, P);
     if (st != RW_OK) return st;
+    if (sys->doe.dft == RW_DFT_TC)
+        return fail(ctx, RW_EINVAL, "the fused kernels use the FP32 FFT; the tensor-core "
+                                    "transform is available through rw_patch_spectra");
     if ((st = check_rays(ctx, rays)) != RW_OK) return st;
     if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
     if (!dl_dpsf) return fail(ctx, RW_EINVAL, "dl_dpsf is NULL");
     if (P.sys.coherent) return fail(ctx, RW_EINVAL, "backward supports the incoherent sensor only");
-    if (P.sys.emit != RW_EMIT_EXHAUSTIVE)
-        return fail(ctx, RW_EINVAL, "backward supports exhaustive emission only");
+    {
+        int lim = 0;
+        cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+        if (backward_smem_needed(P.sys) > (size_t)lim)
+            return fail(ctx, RW_EINVAL, "patch size / n_ssr too large for the adjoint's shared memory");
+    }
     if (damp && !sys->doe.amp) return fail(ctx, RW_EINVAL, "damp requires doe.amp");
     if (P.total == 0 || (!dphi && !damp && !dsurf)) return RW_OK;
     float2* T; DJob* dj; long long* dp;
@@ -520,6 +585,31 @@ rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int
                             sys->doe.amp, dl_dpsf, dphi, damp, dsurf, 0, status_word(ctx), &nl),
             "backward kernel");
     ctx->launches += nl;
+    return RW_OK;
+}
+
+rw_status rw_patch_spectra(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                           const rw_rays* rays, float* spectra, int64_t capacity) {
+    if (!ctx) return RW_EINVAL;
+    ctx->err.clear();
+    Packed P;
+    rw_status st = pack_system(ctx, sys, P);
+    if (st != RW_OK) return st;
+    if ((st = check_rays(ctx, rays)) != RW_OK) return st;
+    if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
+    if (!spectra) return fail(ctx, RW_EINVAL, "spectra is NULL");
+    const int tc = sys->doe.dft == RW_DFT_TC;
+    if (tc && sys->doe.D != 64)
+        return fail(ctx, RW_EINVAL, "the tensor-core patch transform supports D = 64");
+    if (capacity < P.total * (int64_t)sys->doe.D * sys->doe.D)
+        return fail(ctx, RW_ECAPACITY, "spectra capacity < n_rays * D * D");
+    if (P.total == 0) return RW_OK;
+    float2* T; DJob* dj; long long* dp;
+    if ((st = prepare(ctx, sys, P, &T, &dj, &dp)) != RW_OK) return st;
+    RW_CUDA(launch_spectra(lctx(ctx), P.sys, tc, dj, dp, njob, P.total, rays_in(rays), T,
+                           (float2*)spectra, status_word(ctx)),
+            "spectra kernel");
+    ctx->launches++;
     return RW_OK;
 }
 

@@ -1,19 +1,25 @@
-// A9: adjoint of the fused forward (incoherent sensor, exhaustive emission).
+// A9: adjoint of the fused forward (incoherent sensor).
 //
 // Per incident ray the CTA recomputes the patch and its spectrum (nothing
-// from the forward is stored), then every thread, for each of its bins,
-//   re-traces the secondary ray to the sensor keeping the state entering
-//   each surface, gathers dL/dI at its four bilinear taps, and runs the
-//   hand-written reverse of the sensor plane and of every surface
-//   (implicit-function derivative of the intersection, normal, Snell);
-//   the gradient w.r.t. the amplitude a = a_in U~ gives dL/dU~, the one
-//   w.r.t. the emitted direction gives dL/dkappa and so dL/d(incident
-//   direction), the one w.r.t. the ray origin gives dL/d(hit point).
+// from the forward is stored).  For every secondary ray it re-traces to the
+// sensor keeping the state entering each surface, gathers dL/dI at the four
+// bilinear taps and runs the hand-written reverse of the sensor plane and of
+// every surface (implicit-function derivative of the intersection, normal,
+// Snell).  The gradient w.r.t. the amplitude gives dL/dU~, the one w.r.t.
+// the emitted direction gives dL/dkappa and so dL/d(incident direction),
+// the one w.r.t. the ray origin gives dL/d(hit point).
+//
+// Exhaustive emission: one secondary ray per propagating bin, a = a_in U~.
+// Sampled emission (straight-through Gumbel-softmax, temperature 1): the
+// value of each draw is the hard argmax; its gradient reaches the chosen
+// bin's weight w = U~ / sqrt(N p) directly, and every bin's log-probability
+// through the softmax Jacobian of the perturbed scores, with
+// dL/dy_ij = Re(conj(dL/da_i) a_in w_j) + dL/dd_i . dir_j.
+//
 // dL/dU~ goes through the adjoint of the patch transform (the conjugate
-// FFT) to dL/dT on the D x D patch, and dT/dphi = i (lambda0/lambda) T,
-// dT/dA = exp(i psi) give the map gradients, added to dphi/damp with
-// atomics.  Surface-parameter gradients are kept per thread and reduced
-// once per CTA into dsurf (double).
+// FFT) to dL/dT on the D x D patch; dT/dphi = i (lambda0/lambda) T and
+// dT/dA = exp(i psi) give the map gradients, added with atomics.  Surface
+// gradients are kept per thread and reduced once per CTA into dsurf.
 #include "rw_kernels.cuh"
 
 struct BwdRay {
@@ -49,23 +55,104 @@ __device__ __forceinline__ void bilinear_grad(const DSys& sys, float cx, float c
     gy = gfv * sys.inv_spitch;
 }
 
-// Reverse of the sensor plane xs = x + ts d, ts = -zs / dz, then of the
-// emission d = (ku u + kv v + kn n) / K; accumulates dL/d(hit), dL/dkappa and
-// dL/dK of the incident ray into acc[0..5].
-__device__ __forceinline__ void sensor_plane_adjoint(float gxs, float gys, float ex, float ey,
-                                                     float ez, float ts, float& gx, float& gy,
-                                                     float& gz, float& gdx, float& gdy,
-                                                     float& gdz) {
-    gx = gxs;
-    gy = gys;
-    const float gts = gxs * ex + gys * ey;
-    gdx = gxs * ts;
-    gdy = gys * ts;
-    const float iez = 1.f / ez;
-    gz = -gts * iez;
-    gdz = -gts * ts * iez;
+// Per-thread accumulators of surface-parameter gradients.
+template <int NS>
+struct SurfGrads {
+    static constexpr int NR = NS > 0 ? NS : 1;
+    float gs[RW_MAXS * RW_NGRAD];    // generic path and incident side
+    float fz[NR], fc[NR], fn[NR];    // specialised path: z, c, n_after of post[i]
+    float f_doe_n;                   // n_after of the DOE surface
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < RW_MAXS * RW_NGRAD; ++i) gs[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) { fz[i] = 0.f; fc[i] = 0.f; fn[i] = 0.f; }
+        f_doe_n = 0.f;
+    }
+};
+
+// Re-trace one secondary ray (origin = DOE hit of R, direction d, deposit
+// weight w = |a|^2) and reverse it.  On success returns dL/dw, dL/d(origin)
+// and dL/d(direction) and adds the surface-parameter gradients to SG.
+template <int NS>
+__device__ __forceinline__ bool secondary_adjoint(const DSys& sys, const RayAtDoe& R,
+                                                  const float* __restrict__ gimg, float dx,
+                                                  float dy, float dz, float w, float& gw,
+                                                  float& gx, float& gy, float& gz, float& gdx,
+                                                  float& gdy, float& gdz, SurfGrads<NS>& SG,
+                                                  unsigned* status) {
+    constexpr int NR = SurfGrads<NS>::NR;
+    float x = R.px, y = R.py, zl = R.pz;
+    float ex = dx, ey = dy, ez = dz;
+    bool ok = true;
+    if constexpr (NS >= 0) {
+        SurfIn st[NR];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            if (ok) {
+                st[i].x = x; st[i].y = y; st[i].zl = zl - sys.post[i].gap;
+                st[i].dx = ex; st[i].dy = ey; st[i].dz = ez;
+                ok = fast_step(sys.post[i], x, y, zl, ex, ey, ez);
+            }
+        }
+        if (!ok) return false;
+        const float zs = zl - sys.sensor_gap;
+        const float ts = -zs * rcp_fast(ez);
+        const float xs = fmaf(ts, ex, x), ys = fmaf(ts, ey, y);
+        float gxs, gys;
+        bilinear_grad(sys, R.cx, R.cy, xs, ys, gimg, gw, gxs, gys);
+        gxs *= w;   // the deposit is w times the tap weight
+        gys *= w;
+        if (gw == 0.f && gxs == 0.f && gys == 0.f) return false;
+        // sensor plane: xs = x + ts e, ts = -zs / ez
+        const float gts = gxs * ex + gys * ey;
+        gx = gxs; gy = gys;
+        gdx = gxs * ts; gdy = gys * ts;
+        const float iez = rcp_fast(ez);
+        gz = -gts * iez;
+        gdz = -gts * ts * iez;
+#pragma unroll
+        for (int i = NS - 1; i >= 0; --i) {
+            float gnb = 0.f;
+            fast_step_adjoint(sys.post[i], st[i], gx, gy, gz, gdx, gdy, gdz, SG.fz[i], SG.fc[i],
+                              SG.fn[i], gnb);
+            if (i > 0) SG.fn[i > 0 ? i - 1 : 0] += gnb; else SG.f_doe_n += gnb;
+        }
+        return true;
+    } else {
+        SurfIn st[RW_MAXS];
+        double dummy = 0.0;
+        for (int s = sys.doe_index + 1; s < sys.nsurf && ok; ++s) {
+            st[s].x = x; st[s].y = y; st[s].zl = zl - sys.s[s].gap;
+            st[s].dx = ex; st[s].dy = ey; st[s].dz = ez;
+            ok = trace_one<false>(sys.s[s], x, y, zl, ex, ey, ez, dummy, status);
+        }
+        if (!ok || ez == 0.f) return false;
+        const float zs = zl - sys.sensor_gap;
+        const float ts = -zs / ez;
+        const float xs = fmaf(ts, ex, x), ys = fmaf(ts, ey, y);
+        float gxs, gys;
+        bilinear_grad(sys, R.cx, R.cy, xs, ys, gimg, gw, gxs, gys);
+        gxs *= w;
+        gys *= w;
+        if (gw == 0.f && gxs == 0.f && gys == 0.f) return false;
+        const float gts = gxs * ex + gys * ey;
+        gx = gxs; gy = gys;
+        gdx = gxs * ts; gdy = gys * ts;
+        gz = -gts / ez;
+        gdz = -gts * ts / ez;
+        for (int s = sys.nsurf - 1; s > sys.doe_index; --s) {
+            float gnb = 0.f;
+            trace_one_adjoint(sys.s[s], st[s], gx, gy, gz, gdx, gdy, gdz,
+                              SG.gs + s * RW_NGRAD, &gnb);
+            SG.gs[(s - 1) * RW_NGRAD + 7] += gnb;
+        }
+        return true;
+    }
 }
 
+// Reverse of d = (ku u + kv v + kn n) / K for bin (ju, jv): adds dL/d(origin),
+// dL/dkappa_u, dL/dkappa_v and dL/dK to acc[0..5].
 __device__ __forceinline__ void emission_adjoint(const DSys& sys, const RayAtDoe& R, int ju,
                                                  int jv, float dx, float dy, float dz,
                                                  float gx, float gy, float gz, float gdx,
@@ -79,15 +166,229 @@ __device__ __forceinline__ void emission_adjoint(const DSys& sys, const RayAtDoe
     const float gdu = gdx * R.u[0] + gdy * R.u[1] + gdz * R.u[2];
     const float gdv = gdx * R.v[0] + gdy * R.v[1] + gdz * R.v[2];
     const float gdn = gdx * R.n[0] + gdy * R.n[1] + gdz * R.n[2];
-    const float gku = (gdu - ku * ikn * gdn) * R.invK;
-    const float gkv = (gdv - kv * ikn * gdn) * R.invK;
-    const float gdd = gdx * dx + gdy * dy + gdz * dz;
-    const float gK = gdn * ikn - gdd * R.invK;
     acc[0] += gx; acc[1] += gy; acc[2] += gz;
-    acc[3] += gku; acc[4] += gkv;
-    acc[5] += gK;
+    acc[3] += (gdu - ku * ikn * gdn) * R.invK;
+    acc[4] += (gdv - kv * ikn * gdn) * R.invK;
+    acc[5] += gdn * ikn - (gdx * dx + gdy * dy + gdz * dz) * R.invK;
 }
 
+// ------------------------------------------------------------------ sampled
+// Shared scratch of the sampled adjoint (after the exhaustive layout).
+__host__ __device__ inline size_t sampled_bwd_bytes(int D, int N) {
+    return (size_t)D * D * (4 + 8 + 4) + (size_t)N * (4 + 4 + 4 + 8 + 12 + 4) + 64 * 4;
+}
+
+// Block-wide sum (all threads get the result); `red` holds >= 8 floats.
+__device__ __forceinline__ float block_sum(float v, float* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float t = 0.f;
+    for (int w = 0; w < RW_THREADS / 32; ++w) t += red[w];
+    return t;
+}
+
+// Gumbel noise g = -log(-log u) of the four bins 4G..4G+3 of draw i.
+__device__ __forceinline__ void gumbel_group(const DSys& sys, long long gid, int i, int G,
+                                             float* g4) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)i, (uint32_t)gid,
+                                             (uint32_t)sys.rng_offset),
+                                  (uint32_t)(sys.seed & 0xffffffffull), (uint32_t)(sys.seed >> 32));
+    g4[0] = -logf(-logf(u01(w.x)));
+    g4[1] = -logf(-logf(u01(w.y)));
+    g4[2] = -logf(-logf(u01(w.z)));
+    g4[3] = -logf(-logf(u01(w.w)));
+}
+
+template <int D, int NS>
+__device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAtDoe& R,
+                                                    const float2* X, const float2* phu,
+                                                    const float2* phv,
+                                                    const float* __restrict__ gimg, float2* G,
+                                                    unsigned char* scr, float* acc,
+                                                    SurfGrads<NS>& SG, unsigned* status) {
+    constexpr int NB = D * D;
+    const int N = sys.n_ssr;
+    float* logp = reinterpret_cast<float*>(scr);
+    float2* gwb = reinterpret_cast<float2*>(logp + NB);
+    float* glogp = reinterpret_cast<float*>(gwb + NB);
+    int* sel = reinterpret_cast<int*>(glogp + NB);
+    float* mx = reinterpret_cast<float*>(sel + N);
+    float* zs = mx + N;
+    float2* ga = reinterpret_cast<float2*>(zs + N);
+    float* gd = reinterpret_cast<float*>(ga + N);
+    float* cdot = gd + 3 * N;
+    float* red = cdot + N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float2 ain = make_float2(R.a_re, R.a_im);
+    // ---- power weights m = |U~|^2 over propagating bins, p = m / S
+    float part = 0.f;
+    for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
+        const int jvi = f / D, jui = f - (f / D) * D;
+        float dx, dy, dz;
+        float m = 0.f;
+        if (bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
+            const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+            m = U.x * U.x + U.y * U.y;
+        }
+        logp[f] = m;
+        gwb[f] = make_float2(0.f, 0.f);
+        glogp[f] = 0.f;
+        part += m;
+    }
+    const float S = block_sum(part, red);
+    const float iS = S > 0.f ? 1.f / S : 0.f;
+    for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
+        const float p = logp[f] * iS;
+        logp[f] = p > 0.f ? logf(p) : -INFINITY;
+    }
+    __syncthreads();
+    // ---- draws: argmax, running max and partition function (warp per draw)
+    for (int i = warp; i < N; i += RW_THREADS / 32) {
+        float best = -INFINITY, z = 0.f;
+        int bj = 0x7fffffff;
+        for (int Gq = lane; Gq * 4 < NB; Gq += 32) {
+            float g4[4];
+            gumbel_group(sys, R.gid, i, Gq, g4);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int jb = 4 * Gq + q;
+                if (jb < NB && logp[jb] > -INFINITY) {
+                    const float sc = logp[jb] + g4[q];
+                    if (sc > best) {
+                        z = (best > -INFINITY ? z * __expf(best - sc) : 0.f) + 1.f;
+                        best = sc;
+                        bj = jb;
+                    } else {
+                        z += __expf(sc - best);
+                        if (sc == best && jb < bj) bj = jb;
+                    }
+                }
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const float oz = __shfl_xor_sync(0xffffffffu, z, o);
+            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+            const float nb = fmaxf(best, ob);
+            const float nz = (best > -INFINITY ? z * __expf(best - nb) : 0.f) +
+                             (ob > -INFINITY ? oz * __expf(ob - nb) : 0.f);
+            if (ob > best || (ob == best && oj < bj)) bj = oj;
+            best = nb;
+            z = nz;
+        }
+        if (lane == 0) { sel[i] = best > -INFINITY ? bj : -1; mx[i] = best; zs[i] = z; }
+    }
+    __syncthreads();
+    // ---- every draw: trace + reverse of its (hard) secondary ray
+    const float sqN = sqrtf((float)N);
+    for (int i = threadIdx.x; i < N; i += RW_THREADS) {
+        const int jb = sel[i];
+        float2 g_a = make_float2(0.f, 0.f);
+        float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+        if (jb >= 0) {
+            const int jvi = jb / D, jui = jb - (jb / D) * D;
+            float dx, dy, dz;
+            if (bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
+                const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+                const float sc = __expf(-0.5f * logp[jb]) / sqN;     // 1 / sqrt(N p)
+                const float2 a = cscale(cmul(ain, U), sc);
+                const float w = a.x * a.x + a.y * a.y;
+                float gw, gx, gy, gz;
+                if (secondary_adjoint<NS>(sys, R, gimg, dx, dy, dz, w, gw, gx, gy, gz, gdx, gdy,
+                                          gdz, SG, status)) {
+                    emission_adjoint(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz, gx, gy, gz,
+                                     gdx, gdy, gdz, acc);
+                    g_a = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
+                    // hard path: a = a_in w_jb  ->  dL/dw_jb += conj(a_in) dL/da
+                    const float2 gwv = cmulc(g_a, ain);
+                    atomicAdd(&gwb[jb].x, gwv.x);
+                    atomicAdd(&gwb[jb].y, gwv.y);
+                } else {
+                    gdx = gdy = gdz = 0.f;
+                }
+            }
+        }
+        ga[i] = g_a;
+        gd[3 * i] = gdx; gd[3 * i + 1] = gdy; gd[3 * i + 2] = gdz;
+    }
+    __syncthreads();
+    // ---- soft path: dL/dlogp_j += sum_i soft_ij (g_y_ij - sum_k soft_ik g_y_ik)
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = warp; i < N; i += RW_THREADS / 32) {
+            if (sel[i] < 0) continue;
+            const float2 gai = ga[i];
+            const float gdi0 = gd[3 * i], gdi1 = gd[3 * i + 1], gdi2 = gd[3 * i + 2];
+            if (gai.x == 0.f && gai.y == 0.f && gdi0 == 0.f && gdi1 == 0.f && gdi2 == 0.f) {
+                if (pass == 0 && lane == 0) cdot[i] = 0.f;
+                continue;
+            }
+            const float iz = 1.f / zs[i], mxi = mx[i];
+            const float ci = pass ? cdot[i] : 0.f;
+            float accd = 0.f;
+            for (int Gq = lane; Gq * 4 < NB; Gq += 32) {
+                float g4[4];
+                gumbel_group(sys, R.gid, i, Gq, g4);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int jb = 4 * Gq + q;
+                    if (jb >= NB || !(logp[jb] > -INFINITY)) continue;
+                    const float soft = __expf(logp[jb] + g4[q] - mxi) * iz;
+                    const int jvi = jb / D, jui = jb - (jb / D) * D;
+                    float dx, dy, dz;
+                    bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz);
+                    const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+                    const float2 aw = cscale(cmul(ain, U), __expf(-0.5f * logp[jb]) / sqN);
+                    const float gy = gai.x * aw.x + gai.y * aw.y + gdi0 * dx + gdi1 * dy + gdi2 * dz;
+                    if (pass == 0) accd += soft * gy;
+                    else atomicAdd(&glogp[jb], soft * (gy - ci));
+                }
+            }
+            if (pass == 0) {
+                for (int o = 16; o > 0; o >>= 1) accd += __shfl_xor_sync(0xffffffffu, accd, o);
+                if (lane == 0) cdot[i] = accd;
+            }
+        }
+        __syncthreads();
+    }
+    // ---- p = m / S, w = U~ / sqrt(N p), m = |U~|^2  ->  dL/dU~  ->  dL/dX
+    float sg = 0.f, sgp = 0.f;
+    for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
+        if (!(logp[f] > -INFINITY)) continue;
+        const int jvi = f / D, jui = f - (f / D) * D;
+        const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+        const float2 w = cscale(U, __expf(-0.5f * logp[f]) / sqN);
+        const float2 gwv = gwb[f];
+        // dL/dp from w (times p)
+        sgp += -0.5f * (gwv.x * w.x + gwv.y * w.y);
+        sg += glogp[f];
+    }
+    const float Sg = block_sum(sg, red);
+    const float Sgp = block_sum(sgp, red);
+    for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
+        const int jvi = f / D, jui = f - (f / D) * D;
+        int mu = jui + D / 2; if (mu >= D) mu -= D;
+        int mv = jvi + D / 2; if (mv >= D) mv -= D;
+        float2 gU = make_float2(0.f, 0.f);
+        if (logp[f] > -INFINITY) {
+            const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+            const float p = __expf(logp[f]);
+            const float m = p * S;
+            const float isq = __expf(-0.5f * logp[f]) / sqN;
+            const float2 w = cscale(U, isq);
+            const float2 gwv = gwb[f];
+            const float gp = -0.5f * (gwv.x * w.x + gwv.y * w.y) / p;
+            // logp = log m - log S ; p = m / S
+            const float gm = glogp[f] / m - Sg * iS + gp * iS - Sgp * iS;
+            gU = make_float2(2.f * U.x * gm + gwv.x * isq, 2.f * U.y * gm + gwv.y * isq);
+        }
+        const float2 ph = cmul(phu[jui], phv[jvi]);
+        G[mv * D + mu] = cscale(cmulc(gU, ph), 1.f / (float)(D * D));
+    }
+}
+
+// ------------------------------------------------------------------ kernel
 template <int D>
 struct BwdOcc { static constexpr int value = D == 64 ? 3 : (D == 96 ? 1 : 2); };
 
@@ -107,16 +408,10 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
     float2* G = reinterpret_cast<float2*>(smem + sampled_scratch_offset(D));
     BwdRay* bray = reinterpret_cast<BwdRay*>(G + D * D);
     float* red = reinterpret_cast<float*>(bray + RW_TILE);   // [8 warps][9]
+    unsigned char* sscr = reinterpret_cast<unsigned char*>(red + 9 * (RW_THREADS / 32));
     fft_twiddles<D>(tw);
-    float gs[RW_MAXS * RW_NGRAD];
-#pragma unroll
-    for (int i = 0; i < RW_MAXS * RW_NGRAD; ++i) gs[i] = 0.f;
-    // specialised path: per-surface gradients in registers (z, c, n_after)
-    constexpr int NR = NS > 0 ? NS : 1;
-    float fz[NR], fc[NR], fn[NR];
-#pragma unroll
-    for (int i = 0; i < NR; ++i) { fz[i] = 0.f; fc[i] = 0.f; fn[i] = 0.f; }
-    float f_doe_n = 0.f;
+    SurfGrads<NS> SG;
+    SG.zero();
     const long long npix_map = (long long)sys.H * sys.W;
     const long long npx = (long long)sys.nx * sys.ny;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
@@ -137,123 +432,39 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
             fft2d<D, false>(X, tw);
             const float2 ain = make_float2(R.a_re, R.a_im);
             const float* gimg = gpsf + (long long)R.job * npx;
-            float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
-                const int jvi = f / D, jui = f - (f / D) * D;
-                int mu = jui + D / 2; if (mu >= D) mu -= D;
-                int mv = jvi + D / 2; if (mv >= D) mv -= D;
-                float2 gU = make_float2(0.f, 0.f);
-                float dx, dy, dz;
-                if (NS >= 0) {
-                    if (bin_direction<true>(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
+            float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (sys.emit == RW_EMIT_EXHAUSTIVE) {
+                for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
+                    const int jvi = f / D, jui = f - (f / D) * D;
+                    int mu = jui + D / 2; if (mu >= D) mu -= D;
+                    int mv = jvi + D / 2; if (mv >= D) mv -= D;
+                    float2 gU = make_float2(0.f, 0.f);
+                    float dx, dy, dz;
+                    if (bin_direction<(NS >= 0)>(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
                         const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
                         const float2 a = cmul(ain, U);
                         const float w = a.x * a.x + a.y * a.y;
-                        SurfIn st[NR];
-                        float x = R.px, y = R.py, zl = R.pz;
-                        float ex = dx, ey = dy, ez = dz;
-                        bool ok = true;
-#pragma unroll
-                        for (int i = 0; i < NS; ++i) {
-                            if (ok) {
-                                st[i].x = x; st[i].y = y; st[i].zl = zl - sys.post[i].gap;
-                                st[i].dx = ex; st[i].dy = ey; st[i].dz = ez;
-                                ok = fast_step(sys.post[i], x, y, zl, ex, ey, ez);
-                            }
-                        }
-                        if (ok) {
-                            const float zs = zl - sys.sensor_gap;
-                            const float ts = -zs * rcp_fast(ez);
-                            const float xs = fmaf(ts, ex, x), ys = fmaf(ts, ey, y);
-                            float gw, gxs, gys;
-                            bilinear_grad(sys, R.cx, R.cy, xs, ys, gimg, gw, gxs, gys);
-                            gxs *= w;
-                            gys *= w;
-                            if (gw != 0.f || gxs != 0.f || gys != 0.f) {
-                                float gx, gy, gz, gdx, gdy, gdz;
-                                sensor_plane_adjoint(gxs, gys, ex, ey, ez, ts, gx, gy, gz, gdx,
-                                                     gdy, gdz);
-#pragma unroll
-                                for (int i = NS - 1; i >= 0; --i) {
-                                    float gnb = 0.f;
-                                    fast_step_adjoint(sys.post[i], st[i], gx, gy, gz, gdx, gdy,
-                                                      gdz, fz[i], fc[i], fn[i], gnb);
-                                    if (i > 0) fn[i > 0 ? i - 1 : 0] += gnb; else f_doe_n += gnb;
-                                }
-                                emission_adjoint(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz,
-                                                 gx, gy, gz, gdx, gdy, gdz, acc);
-                                const float2 ga = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
-                                gU = cmulc(ga, ain);
-                            }
-                        }
-                    }
-                } else if (bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
-                    const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
-                    const float2 a = cmul(ain, U);
-                    const float w = a.x * a.x + a.y * a.y;
-                    // ---- forward re-trace, keeping the input of every surface
-                    SurfIn st[RW_MAXS];
-                    float x = R.px, y = R.py, zl = R.pz;
-                    float ex = dx, ey = dy, ez = dz;
-                    double dummy = 0.0;
-                    bool ok = true;
-                    for (int s = sys.doe_index + 1; s < sys.nsurf && ok; ++s) {
-                        st[s].x = x; st[s].y = y; st[s].zl = zl - sys.s[s].gap;
-                        st[s].dx = ex; st[s].dy = ey; st[s].dz = ez;
-                        ok = trace_one<false>(sys.s[s], x, y, zl, ex, ey, ez, dummy, status);
-                    }
-                    if (ok && ez != 0.f) {
-                        const float zs = zl - sys.sensor_gap;
-                        const float ts = -zs / ez;
-                        const float xs = fmaf(ts, ex, x), ys = fmaf(ts, ey, y);
-                        float gw, gxs, gys;
-                        bilinear_grad(sys, R.cx, R.cy, xs, ys, gimg, gw, gxs, gys);
-                        // the deposit is w * (bilinear weight): position gradients scale by w
-                        gxs *= w;
-                        gys *= w;
-                        if (gw != 0.f || gxs != 0.f || gys != 0.f) {
-                            // ---- sensor plane: xs = x + ts ex, ts = -zs / ez
-                            float gx = gxs, gy = gys;
-                            const float gts = gxs * ex + gys * ey;
-                            float gdx = gxs * ts, gdy = gys * ts;
-                            float gz = -gts / ez;
-                            float gdz = -gts * ts / ez;
-                            // ---- surfaces in reverse
-                            for (int s = sys.nsurf - 1; s > sys.doe_index; --s) {
-                                float gnb = 0.f;
-                                trace_one_adjoint(sys.s[s], st[s], gx, gy, gz, gdx, gdy, gdz,
-                                                  gs + s * RW_NGRAD, &gnb);
-                                gs[(s - 1) * RW_NGRAD + 7] += gnb;
-                            }
-                            // ---- emission: d = (ku u + kv v + kn n) / K
-                            const float ku = R.kin_u + sys.kstep * (float)(jui - D / 2);
-                            const float kv = R.kin_v + sys.kstep * (float)(jvi - D / 2);
-                            const float K = R.K;
-                            const float kn = sqrtf(fmaxf(K * K - ku * ku - kv * kv, 0.f));
-                            const float gdu = gdx * R.u[0] + gdy * R.u[1] + gdz * R.u[2];
-                            const float gdv = gdx * R.v[0] + gdy * R.v[1] + gdz * R.v[2];
-                            const float gdn = gdx * R.n[0] + gdy * R.n[1] + gdz * R.n[2];
-                            const float gku = (gdu - ku / kn * gdn) / K;
-                            const float gkv = (gdv - kv / kn * gdn) / K;
-                            const float gdd = gdx * dx + gdy * dy + gdz * dz;
-                            const float gK = gdn / kn - gdd / K;
-                            acc[0] += gx; acc[1] += gy; acc[2] += gz;
-                            acc[3] += gku; acc[4] += gkv;
-                            acc[5] += gK;
-                            // ---- amplitude: w = |a|^2, a = a_in U
+                        float gw, gx, gy, gz, gdx, gdy, gdz;
+                        if (secondary_adjoint<NS>(sys, R, gimg, dx, dy, dz, w, gw, gx, gy, gz,
+                                                  gdx, gdy, gdz, SG, status)) {
+                            emission_adjoint(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz, gx,
+                                             gy, gz, gdx, gdy, gdz, acc);
                             const float2 ga = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
-                            gU = cmulc(ga, ain);          // conj(a_in) * g_a
+                            gU = cmulc(ga, ain);          // conj(a_in) * dL/da
                         }
                     }
+                    // dL/dX[m] = conj(phu phv) / D^2 * dL/dU~
+                    const float2 ph = cmul(phu[jui], phv[jvi]);
+                    G[mv * D + mu] = cscale(cmulc(gU, ph), 1.f / (float)(D * D));
                 }
-                // dL/dX[m] = conj(phu phv) / D^2 * dL/dU~
-                const float2 ph = cmul(phu[jui], phv[jvi]);
-                G[mv * D + mu] = cscale(cmulc(gU, ph), 1.f / (float)(D * D));
+            } else {
+                sampled_ray_adjoint<D, NS>(sys, R, X, phu, phv, gimg, G, sscr, acc, SG, status);
             }
             // ---- per-ray reduction of the geometric gradients
 #pragma unroll
             for (int k = 0; k < 6; ++k)
                 for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+            __syncthreads();
             if (lane == 0)
 #pragma unroll
                 for (int k = 0; k < 6; ++k) red[warp * 9 + k] = acc[k];
@@ -334,8 +545,8 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                 trace_one<false>(sys.s[s], x, y, zl, dx, dy, dz, dummy, status);
             }
             // index gradients of the DOE emission
-            gs[sys.doe_index * RW_NGRAD + 7] += B.gnout;
-            if (sys.doe_index > 0) gs[(sys.doe_index - 1) * RW_NGRAD + 7] += B.gnin;
+            SG.gs[sys.doe_index * RW_NGRAD + 7] += B.gnout;
+            if (sys.doe_index > 0) SG.gs[(sys.doe_index - 1) * RW_NGRAD + 7] += B.gnin;
             float gx = B.gpx, gy = B.gpy, gz = B.gpz;
             float gdx = B.gdx, gdy = B.gdy, gdz = B.gdz;
             if (!sys.conformal) {
@@ -346,33 +557,33 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                 gdx += gx * t; gdy += gy * t; gdz += gz * t;
                 gz += -gt / dz;
                 gdz += -gt * t / dz;
-                gs[sys.doe_index * RW_NGRAD + 0] += gt / dz;
+                SG.gs[sys.doe_index * RW_NGRAD + 0] += gt / dz;
                 for (int s = sys.doe_index - 1; s >= 0; --s) {
                     float gnb = 0.f;
                     trace_one_adjoint(sys.s[s], st[s], gx, gy, gz, gdx, gdy, gdz,
-                                      gs + s * RW_NGRAD, &gnb);
-                    if (s > 0) gs[(s - 1) * RW_NGRAD + 7] += gnb;
+                                      SG.gs + s * RW_NGRAD, &gnb);
+                    if (s > 0) SG.gs[(s - 1) * RW_NGRAD + 7] += gnb;
                 }
             }
         }
     }
     // ---- CTA reduction of surface-parameter gradients
     if (!dsurf) return;
-    if (NS >= 0) {
+    if constexpr (NS >= 0) {
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             const int si = sys.doe_index + 1 + i;
-            gs[si * RW_NGRAD + 0] += fz[i];
-            gs[si * RW_NGRAD + 1] += fc[i];
-            gs[si * RW_NGRAD + 7] += fn[i];
+            SG.gs[si * RW_NGRAD + 0] += SG.fz[i];
+            SG.gs[si * RW_NGRAD + 1] += SG.fc[i];
+            SG.gs[si * RW_NGRAD + 7] += SG.fn[i];
         }
-        gs[sys.doe_index * RW_NGRAD + 7] += f_doe_n;
+        SG.gs[sys.doe_index * RW_NGRAD + 7] += SG.f_doe_n;
     }
     __syncthreads();
     double* dred = reinterpret_cast<double*>(smem);
     for (int s = 0; s < sys.nsurf; ++s) {
         for (int k = 0; k < RW_NGRAD; ++k) {
-            float v = gs[s * RW_NGRAD + k];
+            float v = SG.gs[s * RW_NGRAD + k];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) dred[(s * RW_NGRAD + k) * (RW_THREADS / 32) + warp] = (double)v;
         }
@@ -385,12 +596,15 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
     }
 }
 
-inline size_t backward_smem_bytes(int D) {
+inline size_t backward_smem_bytes(int D, int emit, int n_ssr) {
     size_t b = sampled_scratch_offset(D) + sizeof(float2) * (size_t)D * D +
                sizeof(BwdRay) * RW_TILE + sizeof(float) * 9 * (RW_THREADS / 32);
+    if (emit == RW_EMIT_SAMPLED) b += sampled_bwd_bytes(D, n_ssr);
     size_t red = sizeof(double) * RW_MAXS * RW_NGRAD * (RW_THREADS / 32);
     return b > red ? b : red;
 }
+
+size_t backward_smem_needed(const DSys& sys) { return backward_smem_bytes(sys.D, sys.emit, sys.n_ssr); }
 
 template <int D, int NS>
 static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
@@ -398,7 +612,7 @@ static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const 
                                      const RaysIn& rays, const float2* T, const float* amp,
                                      const float* gpsf, float* dphi, float* damp, double* dsurf,
                                      unsigned* status) {
-    const size_t smem = backward_smem_bytes(D);
+    const size_t smem = backward_smem_bytes(D, sys.emit, sys.n_ssr);
     auto kern = k_backward<D, NS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -422,7 +636,6 @@ cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* job
                             const RaysIn& rays, const float2* T, const float* amp,
                             const float* dl_dpsf, float* dphi, float* damp, double* dsurf,
                             int /*scratch_slots*/, unsigned* status, int* launches) {
-    if (sys.emit != RW_EMIT_EXHAUSTIVE) return cudaErrorNotSupported;
     *launches = 1;
     const int ns = sys.fast_ok ? sys.n_post : -1;
 #define RW_BWD(DD, NN) \

@@ -207,6 +207,14 @@ def rw_forward(ctx, sys_struct, jobs_arr, rays, psf):
                                  C.byref(rs), _ptr(psf)), "rw_forward")
 
 
+def rw_patch_spectra(ctx, sys_struct, jobs_arr, rays, spectra):
+    ctx._stream()
+    rs = rays_struct(rays)
+    ctx.check(ctx.lib.rw_patch_spectra(ctx.h, C.byref(sys_struct), jobs_arr, len(jobs_arr),
+                                       C.byref(rs), _ptr(spectra), int(spectra.numel() // 2)),
+              "rw_patch_spectra")
+
+
 def rw_loss_eq3(ctx, psf, target, loss_out, dl_dpsf=None):
     ctx._stream()
     ctx.check(ctx.lib.rw_loss_eq3(ctx.h, _ptr(psf), _ptr(target), int(psf.numel()),
@@ -261,6 +269,15 @@ class Simulator:
         s, keep = self.sys_struct()
         rw_doe_emit(self.ctx, s, self.jobs, self.rays, out)
         return out
+
+    def spectra(self, dft=None, out=None):
+        """Patch spectra U~ [n_rays, D, D] (complex64) with the FFT or tensor cores."""
+        D = self.w.system.doe.D
+        if out is None:
+            out = torch.empty(self.n_rays, D, D, 2, dtype=torch.float32, device=self.dev)
+        s, keep = system_struct(self.w.system, self.phi, self.amp, dft or self.dft)
+        rw_patch_spectra(self.ctx, s, self.jobs, self.rays, out)
+        return torch.view_as_complex(out)
 
     def backward(self, dl_dpsf, phi=None, surfaces=None, want_amp=False):
         s, keep = self.sys_struct(phi, surfaces=surfaces)

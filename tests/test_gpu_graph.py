@@ -1,0 +1,58 @@
+"""A whole fwd + loss + bwd step captured in one CUDA graph and replayed.
+
+After one eager call has sized the scratch, every C-ABI call of the step is
+capturable: job tables go through a per-context capture arena, so the graph
+keeps valid copies of them; replays reproduce the eager results."""
+import numpy as np
+import pytest
+import torch
+
+import rwinputs as R
+
+pytestmark = pytest.mark.gpu
+
+
+def test_step_captured_in_cuda_graph_matches_eager():
+    from paper_2605_15418_gb300 import raywave as RW
+    w = R.configs.c2(n_side=48, D=32, lams=(486e-6, 656e-6), fields_deg=(0.0, 1.5),
+                     sensor_n=96, map_side=256)
+    w.system.sensor.pitch = 8e-3
+    sim = RW.Simulator(w)
+    tgt = torch.as_tensor(w.target, device=sim.dev)
+    psf = torch.empty(sim.psf_shape, device=sim.dev)
+    gI = torch.empty_like(psf)
+    loss = torch.empty(3, dtype=torch.float64, device=sim.dev)
+    dphi = torch.zeros_like(sim.phi)
+    dsurf = torch.zeros(len(w.system.surfaces), 8, dtype=torch.float64, device=sim.dev)
+    s, keep = sim.sys_struct()
+
+    def step():
+        RW.rw_generate_rays(sim.ctx, w.z_start, w.system.n_object, sim.jobs, sim.rays)
+        RW.rw_forward(sim.ctx, s, sim.jobs, sim.rays, psf)
+        RW.rw_loss_eq3(sim.ctx, psf, tgt, loss, gI)
+        dphi.zero_()
+        dsurf.zero_()
+        RW.rw_backward(sim.ctx, s, sim.jobs, sim.rays, gI, dphi, None, dsurf)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()                                   # eager: sizes the scratch
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    ref = [t.clone() for t in (psf, loss, dphi, dsurf)]
+    for t in (psf, loss, dphi, dsurf):
+        t.fill_(float("nan"))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    n0 = sim.ctx.launches
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    assert sim.ctx.launches == n0               # replays launch no new host work
+    got = [psf, loss, dphi, dsurf]
+    assert torch.allclose(got[0], ref[0], rtol=1e-5, atol=1e-6 * ref[0].abs().max().item())
+    assert torch.allclose(got[1], ref[1], rtol=1e-5)
+    assert torch.allclose(got[2], ref[2], rtol=1e-3, atol=1e-4 * ref[2].abs().max().item())
+    assert torch.allclose(got[3], ref[3], rtol=1e-3, atol=1e-6 * ref[3].abs().max().item())

@@ -313,3 +313,50 @@ def test_sampled_emission_matches_oracle(RW, ctx, coherent):
         assert np.abs(a[g][same] - ar[same]).max() <= A_TOL * np.abs(ar).max()
         base += job.n_rays
     assert agree >= total * (1 - 1e-3), (agree, total)
+
+
+def test_backward_sampled_gumbel_straight_through_matches_oracle(RW, ctx):
+    """Sampled emission: the adjoint's straight-through Gumbel-softmax
+    gradient equals autograd through the oracle's relaxed estimator (same
+    Philox noise on both sides)."""
+    w = _c3_small(n_side=10)
+    sysm = w.system
+    sysm.doe.emit = "sampled"
+    sysm.doe.n_ssr = 48
+    sysm.doe.seed = 99
+    sim = RW.Simulator(w, ctx=ctx)
+    psf = sim.forward()
+    tgt = torch.as_tensor(w.target, device=sim.dev)
+    gI = torch.empty_like(psf)
+    sim.loss(psf, tgt, gI)
+    dphi, _, dsurf = sim.backward(gI)
+    torch.cuda.synchronize()
+    prm = OP.params_of(sysm, requires_grad=True)
+    phi = torch.from_numpy(sysm.doe.phi.astype(np.float64)).requires_grad_(True)
+    img = OP.psf(w, params=prm, phi=phi)
+    assert rel_l2(psf.cpu().numpy(), img.detach().numpy()) < 1e-3
+    Lv, _ = OL.eq3_loss(img, torch.from_numpy(w.target.astype(np.float64)))
+    Lv.backward()
+    assert rel_l2(dphi.cpu().numpy(), phi.grad.numpy()) <= 1e-2, \
+        rel_l2(dphi.cpu().numpy(), phi.grad.numpy())
+    ds = dsurf.cpu().numpy()
+    for si in range(1, len(prm)):
+        ref = float(prm[si]["c"].grad)
+        assert abs(ds[si, 1] - ref) <= 1e-2 * abs(ref) + 1e-6, (si, ds[si, 1], ref)
+
+
+def test_batched_uneven_jobs_one_launch(RW, ctx):
+    """C5-shaped batch: 4 wavelengths x 4 fields with uneven ray counts
+    (log-uniform), six spherical surfaces, all jobs in one persistent launch."""
+    w = R.configs.c5(n_lams=4, n_fields=4, count_lo=30, count_hi=400, D=32, map_side=256,
+                     sensor_n=64)
+    w.system.doe.emit = "exhaustive"
+    w.system.sensor.pitch = 30e-3
+    counts = [j.n_rays for j in w.jobs]
+    assert len(set(counts)) > 4
+    sim = RW.Simulator(w, ctx=ctx)
+    launches0 = ctx.launches
+    psf = sim.forward().cpu().numpy()
+    assert ctx.launches - launches0 == 3          # prep maps, fused forward, finalize
+    ref = oracle_psf(w)
+    assert rel_l2(psf, ref) <= PSF_TOL, rel_l2(psf, ref)
