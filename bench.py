@@ -65,12 +65,14 @@ def flops_per_incident(D, n_post):
     return fft, fft + D * D * per_sec
 
 
-def flops_backward_per_incident(D, n_post):
-    """Adjoint: forward recomputation + reverse of every secondary ray
-    (emission 40, each surface 150, sensor 40) + conjugate FFT + map scatter (8/px)."""
+def flops_backward_per_incident(D, n_post, visible_frac=1.0):
+    """Adjoint: patch FFT recomputed, then for every secondary ray that reached
+    the sensor (the others carry no gradient) its re-trace (forward count) and
+    reverse (emission 40, each surface 150, sensor 40), the conjugate FFT and
+    the map scatter (8 per pixel)."""
     fft, fwd = flops_per_incident(D, n_post)
-    rev = D * D * (40.0 + 150.0 * n_post + 40.0)
-    return fwd + rev + fft + 8.0 * D * D
+    per_sec = (fwd - fft) / (D * D) + 40.0 + 150.0 * n_post + 40.0
+    return 2 * fft + visible_frac * D * D * per_sec + 8.0 * D * D
 
 
 # ------------------------------------------------------------------ clocks
@@ -206,6 +208,7 @@ def main():
     dphi = torch.zeros_like(sim.phi)
     dsurf = torch.zeros(len(sysm.surfaces), 8, dtype=torch.float64, device=dev)
     loss = torch.empty(3, dtype=torch.float64, device=dev)
+    vis = RW.alloc_vis(n_rays, sysm.doe.D, dev)      # 1 bit per secondary ray
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
 
@@ -214,13 +217,13 @@ def main():
         if ev: ev[0].record(stream)
         RW.rw_generate_rays(sim.ctx, w.z_start, sysm.n_object, sim.jobs, sim.rays)
         if ev: ev[1].record(stream)
-        RW.rw_forward(sim.ctx, s, sim.jobs, sim.rays, psf)
+        RW.rw_forward_vis(sim.ctx, s, sim.jobs, sim.rays, psf, vis)
         if ev: ev[2].record(stream)
         RW.rw_loss_eq3(sim.ctx, psf, tgt, loss, gI)
         dphi.zero_()
         dsurf.zero_()
         if ev: ev[3].record(stream)
-        RW.rw_backward(sim.ctx, s, sim.jobs, sim.rays, gI, dphi, None, dsurf)
+        RW.rw_backward_vis(sim.ctx, s, sim.jobs, sim.rays, gI, vis, dphi, None, dsurf)
         if ev: ev[4].record(stream)
 
     for _ in range(args.warmup):
@@ -279,12 +282,15 @@ def main():
 
     # ---- roofline of the dominant kernel (FP32 ALU bound)
     D = sysm.doe.D
+    lut = torch.tensor([bin(i).count("1") for i in range(256)], dtype=torch.int64, device=dev)
+    visible = int(lut[vis.view(torch.uint8).long()].sum().item())
+    vfrac = visible / float(n_rays * D * D)
     n_post = len(sysm.surfaces) - sysm.doe_index - 1
     fwd_ms = float(np.mean(t_fwd))
     bwd_ms = float(np.mean(t_bwd))
     peak = NUM_SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12      # TFLOP/s at max SM clock
     if bwd_ms >= fwd_ms:
-        name, tms, fl = "k_backward", bwd_ms, flops_backward_per_incident(D, n_post) * n_rays
+        name, tms, fl = "k_backward", bwd_ms, flops_backward_per_incident(D, n_post, vfrac) * n_rays
     else:
         name, tms, fl = "k_forward", fwd_ms, flops_per_incident(D, n_post)[1] * n_rays
     achieved = fl / (tms / 1e3) / 1e12
@@ -295,6 +301,7 @@ def main():
             "config": {"workload": w.name, "incident_rays": n_rays, "jobs": len(w.jobs),
                        "D": D, "secondary_rays_per_incident": D * D, "sensor": "512x512x9",
                        "surfaces_after_doe": n_post, "l2": "flushed between steps (256 MB)",
+                       "visible_secondary_fraction": vfrac,
                        "fwd_ms": fwd_ms, "bwd_ms": bwd_ms},
             "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,

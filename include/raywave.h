@@ -208,6 +208,15 @@ rw_status rw_doe_emit(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
 rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
                      int32_t njob, const rw_rays* rays, float* psf);
 
+/* rw_forward that also records which secondary rays reached the sensor:
+ * bit (f & 31) of vis[i * D*D/32 + f/32] is set when bin f of incident ray i
+ * (job order) hit the sensor plane with a bilinear tap on the sensor.  One
+ * bit per secondary ray (D = 64: 512 bytes per incident ray).  Needs the
+ * incoherent sensor and exhaustive emission.
+ * Errors: as rw_forward, RW_ECAPACITY (vis_words < n_rays * D*D / 32). */
+rw_status rw_forward_vis(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                         const rw_rays* rays, float* psf, uint32_t* vis, int64_t vis_words);
+
 /* ---- A3..A4: patch spectra only ----------------------------------------- */
 
 /* Trace every job's rays to the DOE and write the angular spectrum of each
@@ -265,6 +274,14 @@ rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
  * overlap on the GPU (different streams, no ordering) race on it. */
 rw_status rw_generate_rays_static(double z_start, double n_object, const rw_job* jobs,
                                   int32_t njob, rw_rays* rays, void* cuda_stream);
+
+/* rw_backward with the visibility mask written by rw_forward_vis for the
+ * SAME inputs: a secondary ray that deposited nothing on the sensor has zero
+ * gradient, so only the visible ones are re-traced and reversed (exact).
+ * Exhaustive emission; patch sizes above 64 ignore the mask. */
+rw_status rw_backward_vis(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                          const rw_rays* rays, const float* dl_dpsf, const uint32_t* vis,
+                          int64_t vis_words, float* dphi, float* damp, double* dsurf);
 
 #ifdef __cplusplus
 }

@@ -89,6 +89,11 @@ EXPORTS = {
     "rw_backward": (C.c_int, [C.c_void_p, C.POINTER(rw_system), C.POINTER(rw_job), C.c_int32,
                               C.POINTER(rw_rays), C.c_void_p, C.c_void_p, C.c_void_p,
                               C.c_void_p]),
+    "rw_forward_vis": (C.c_int, [C.c_void_p, C.POINTER(rw_system), C.POINTER(rw_job), C.c_int32,
+                                 C.POINTER(rw_rays), C.c_void_p, C.c_void_p, C.c_int64]),
+    "rw_backward_vis": (C.c_int, [C.c_void_p, C.POINTER(rw_system), C.POINTER(rw_job), C.c_int32,
+                                  C.POINTER(rw_rays), C.c_void_p, C.c_void_p, C.c_int64,
+                                  C.c_void_p, C.c_void_p, C.c_void_p]),
     "rw_patch_spectra": (C.c_int, [C.c_void_p, C.POINTER(rw_system), C.POINTER(rw_job), C.c_int32,
                                    C.POINTER(rw_rays), C.c_void_p, C.c_int64]),
     "rw_generate_rays_static": (C.c_int, [C.c_double, C.c_double, C.POINTER(rw_job), C.c_int32,

@@ -28,13 +28,25 @@ def surfaces_from_params(template, params):
     return out
 
 
+def _vis_ok(sim):
+    sysm = sim.w.system
+    return sysm.doe.emit == "exhaustive" and not sysm.sensor.coherent
+
+
 class RayWavePSF(torch.autograd.Function):
+    """Forward keeps the one-bit-per-secondary-ray visibility mask (exhaustive
+    emission) so the adjoint reverses only rays that reached the sensor."""
+
     @staticmethod
     def forward(ctx, sim, phi, params):
         surfs = surfaces_from_params(sim.w.system.surfaces, params)
-        psf = sim.forward(phi=phi.detach().contiguous(), surfaces=surfs)
+        vis = None
+        if _vis_ok(sim):
+            vis = RW.alloc_vis(sim.n_rays, sim.w.system.doe.D, sim.dev)
+        psf = sim.forward(phi=phi.detach().contiguous(), surfaces=surfs, vis=vis)
         ctx.sim = sim
         ctx.surfs = surfs
+        ctx.vis = vis
         ctx.save_for_backward(phi)
         return psf
 
@@ -42,7 +54,7 @@ class RayWavePSF(torch.autograd.Function):
     def backward(ctx, g):
         (phi,) = ctx.saved_tensors
         dphi, _, dsurf = ctx.sim.backward(g.contiguous(), phi=phi.detach().contiguous(),
-                                          surfaces=ctx.surfs)
+                                          surfaces=ctx.surfs, vis=ctx.vis)
         return None, dphi, dsurf
 
 

@@ -16,7 +16,7 @@ cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* job
                             const long long* prefix, int njob, long long total,
                             const RaysIn& rays, const float2* T, const float* amp,
                             const float* dl_dpsf, float* dphi, float* damp, double* dsurf,
-                            int scratch_slots, unsigned* status, int* launches);
+                            const unsigned* vis, unsigned* status, int* launches);
 size_t backward_smem_needed(const DSys& sys);
 cudaError_t launch_spectra(const LaunchCtx& L, const DSys& sys, int tc, const DJob* jobs,
                            const long long* prefix, int njob, long long total, const RaysIn& rays,
@@ -495,8 +495,9 @@ rw_status rw_doe_emit(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int
     return RW_OK;
 }
 
-rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
-                     const rw_rays* rays, float* psf) {
+static rw_status forward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
+                              int32_t njob, const rw_rays* rays, float* psf, uint32_t* vis,
+                              int64_t vis_words) {
     if (!ctx) return RW_EINVAL;
     ctx->err.clear();
     Packed P;
@@ -508,6 +509,13 @@ rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int3
     if ((st = check_rays(ctx, rays)) != RW_OK) return st;
     if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
     if (!psf) return fail(ctx, RW_EINVAL, "psf is NULL");
+    if (vis) {
+        if (P.sys.coherent || P.sys.emit != RW_EMIT_EXHAUSTIVE)
+            return fail(ctx, RW_EINVAL, "the visibility mask needs the incoherent sensor and "
+                                        "exhaustive emission");
+        if (vis_words < P.total * (int64_t)P.sys.D * P.sys.D / 32)
+            return fail(ctx, RW_ECAPACITY, "vis_words < n_rays * D * D / 32");
+    }
     const long long npx = (long long)P.sys.nx * P.sys.ny * njob;
     RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
     RW_CUDA(cudaMemsetAsync(psf, 0, npx * sizeof(float), ctx->stream), "psf clear");
@@ -534,13 +542,24 @@ rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int3
         RW_CUDA(cudaMemsetAsync(ctx->acc.p, 0, npx * sizeof(double), ctx->stream), "acc clear");
         RW_CUDA(launch_forward(lctx(ctx), MODE_SPLAT, P.sys, dj, dp, njob, P.total,
                                rays_in(rays), T, (double*)ctx->acc.p, nullptr, eo,
-                               status_word(ctx)),
+                               status_word(ctx), vis),
                 "forward kernel");
         ctx->launches++;
         RW_CUDA(launch_psf_finalize(lctx(ctx), (const double*)ctx->acc.p, psf, npx), "psf finalize");
         ctx->launches++;
     }
     return RW_OK;
+}
+
+rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                     const rw_rays* rays, float* psf) {
+    return forward_impl(ctx, sys, jobs, njob, rays, psf, nullptr, 0);
+}
+
+rw_status rw_forward_vis(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                         const rw_rays* rays, float* psf, uint32_t* vis, int64_t vis_words) {
+    if (!vis) return fail(ctx, RW_EINVAL, "vis is NULL");
+    return forward_impl(ctx, sys, jobs, njob, rays, psf, vis, vis_words);
 }
 
 rw_status rw_loss_eq3(rw_ctx* ctx, const float* psf, const float* target, int64_t n,
@@ -555,9 +574,10 @@ rw_status rw_loss_eq3(rw_ctx* ctx, const float* psf, const float* target, int64_
     return RW_OK;
 }
 
-rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
-                      const rw_rays* rays, const float* dl_dpsf, float* dphi, float* damp,
-                      double* dsurf) {
+static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
+                               int32_t njob, const rw_rays* rays, const float* dl_dpsf,
+                               const uint32_t* vis, int64_t vis_words, float* dphi, float* damp,
+                               double* dsurf) {
     if (!ctx) return RW_EINVAL;
     ctx->err.clear();
     Packed P;
@@ -577,15 +597,34 @@ rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int
             return fail(ctx, RW_EINVAL, "patch size / n_ssr too large for the adjoint's shared memory");
     }
     if (damp && !sys->doe.amp) return fail(ctx, RW_EINVAL, "damp requires doe.amp");
+    if (vis) {
+        if (P.sys.emit != RW_EMIT_EXHAUSTIVE)
+            return fail(ctx, RW_EINVAL, "the visibility mask needs exhaustive emission");
+        if (vis_words < P.total * (int64_t)P.sys.D * P.sys.D / 32)
+            return fail(ctx, RW_ECAPACITY, "vis_words < n_rays * D * D / 32");
+    }
     if (P.total == 0 || (!dphi && !damp && !dsurf)) return RW_OK;
     float2* T; DJob* dj; long long* dp;
     if ((st = prepare(ctx, sys, P, &T, &dj, &dp)) != RW_OK) return st;
     int nl = 0;
     RW_CUDA(launch_backward(lctx(ctx), P.sys, dj, dp, njob, P.total, rays_in(rays), T,
-                            sys->doe.amp, dl_dpsf, dphi, damp, dsurf, 0, status_word(ctx), &nl),
+                            sys->doe.amp, dl_dpsf, dphi, damp, dsurf, vis, status_word(ctx), &nl),
             "backward kernel");
     ctx->launches += nl;
     return RW_OK;
+}
+
+rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                      const rw_rays* rays, const float* dl_dpsf, float* dphi, float* damp,
+                      double* dsurf) {
+    return backward_impl(ctx, sys, jobs, njob, rays, dl_dpsf, nullptr, 0, dphi, damp, dsurf);
+}
+
+rw_status rw_backward_vis(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                          const rw_rays* rays, const float* dl_dpsf, const uint32_t* vis,
+                          int64_t vis_words, float* dphi, float* damp, double* dsurf) {
+    if (!vis) return fail(ctx, RW_EINVAL, "vis is NULL");
+    return backward_impl(ctx, sys, jobs, njob, rays, dl_dpsf, vis, vis_words, dphi, damp, dsurf);
 }
 
 rw_status rw_patch_spectra(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,

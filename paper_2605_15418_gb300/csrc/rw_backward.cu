@@ -55,16 +55,15 @@ __device__ __forceinline__ void bilinear_grad(const DSys& sys, float cx, float c
     gy = gfv * sys.inv_spitch;
 }
 
-// Per-thread accumulators of surface-parameter gradients.
+// Per-thread accumulators of surface-parameter gradients for the
+// specialised path: only constant indices, so they stay in registers.  The
+// generic path and the incident side use a separate per-thread array `gs`.
 template <int NS>
 struct SurfGrads {
     static constexpr int NR = NS > 0 ? NS : 1;
-    float gs[RW_MAXS * RW_NGRAD];    // generic path and incident side
-    float fz[NR], fc[NR], fn[NR];    // specialised path: z, c, n_after of post[i]
+    float fz[NR], fc[NR], fn[NR];    // z, c, n_after of post[i]
     float f_doe_n;                   // n_after of the DOE surface
     __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int i = 0; i < RW_MAXS * RW_NGRAD; ++i) gs[i] = 0.f;
 #pragma unroll
         for (int i = 0; i < NR; ++i) { fz[i] = 0.f; fc[i] = 0.f; fn[i] = 0.f; }
         f_doe_n = 0.f;
@@ -80,7 +79,7 @@ __device__ __forceinline__ bool secondary_adjoint(const DSys& sys, const RayAtDo
                                                   float dy, float dz, float w, float& gw,
                                                   float& gx, float& gy, float& gz, float& gdx,
                                                   float& gdy, float& gdz, SurfGrads<NS>& SG,
-                                                  unsigned* status) {
+                                                  float* gs, unsigned* status) {
     constexpr int NR = SurfGrads<NS>::NR;
     float x = R.px, y = R.py, zl = R.pz;
     float ex = dx, ey = dy, ez = dz;
@@ -144,8 +143,8 @@ __device__ __forceinline__ bool secondary_adjoint(const DSys& sys, const RayAtDo
         for (int s = sys.nsurf - 1; s > sys.doe_index; --s) {
             float gnb = 0.f;
             trace_one_adjoint(sys.s[s], st[s], gx, gy, gz, gdx, gdy, gdz,
-                              SG.gs + s * RW_NGRAD, &gnb);
-            SG.gs[(s - 1) * RW_NGRAD + 7] += gnb;
+                              gs + s * RW_NGRAD, &gnb);
+            gs[(s - 1) * RW_NGRAD + 7] += gnb;
         }
         return true;
     }
@@ -207,7 +206,8 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
                                                     const float2* phv,
                                                     const float* __restrict__ gimg, float2* G,
                                                     unsigned char* scr, float* acc,
-                                                    SurfGrads<NS>& SG, unsigned* status) {
+                                                    SurfGrads<NS>& SG, float* gs,
+                                                    unsigned* status) {
     constexpr int NB = D * D;
     const int N = sys.n_ssr;
     float* logp = reinterpret_cast<float*>(scr);
@@ -297,7 +297,7 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
                 const float w = a.x * a.x + a.y * a.y;
                 float gw, gx, gy, gz;
                 if (secondary_adjoint<NS>(sys, R, gimg, dx, dy, dz, w, gw, gx, gy, gz, gdx, gdy,
-                                          gdz, SG, status)) {
+                                          gdz, SG, gs, status)) {
                     emission_adjoint(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz, gx, gy, gz,
                                      gdx, gdy, gdz, acc);
                     g_a = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
@@ -388,9 +388,39 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
     }
 }
 
+// Reverse of exhaustive bin f of the current incident ray; writes its dL/dX.
+template <int D, int NS>
+__device__ __forceinline__ void exh_bin_adjoint(const DSys& sys, const RayAtDoe& R,
+                                                const float2* X, const float2* phu,
+                                                const float2* phv, const float* __restrict__ gimg,
+                                                float2* G, float2 ain, int f, float (&acc)[6],
+                                                SurfGrads<NS>& SG, float* gs, unsigned* status) {
+    const int jvi = f / D, jui = f - (f / D) * D;
+    int mu = jui + D / 2; if (mu >= D) mu -= D;
+    int mv = jvi + D / 2; if (mv >= D) mv -= D;
+    float2 gU = make_float2(0.f, 0.f);
+    float dx, dy, dz;
+    if (bin_direction<(NS >= 0)>(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
+        const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+        const float2 a = cmul(ain, U);
+        const float w = a.x * a.x + a.y * a.y;
+        float gw, gx, gy, gz, gdx, gdy, gdz;
+        if (secondary_adjoint<NS>(sys, R, gimg, dx, dy, dz, w, gw, gx, gy, gz, gdx, gdy, gdz, SG,
+                                  gs, status)) {
+            emission_adjoint(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz, gx, gy, gz, gdx, gdy,
+                             gdz, acc);
+            const float2 ga = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
+            gU = cmulc(ga, ain);          // conj(a_in) * dL/da
+        }
+    }
+    // dL/dX[m] = conj(phu phv) / D^2 * dL/dU~
+    const float2 ph = cmul(phu[jui], phv[jvi]);
+    G[mv * D + mu] = cscale(cmulc(gU, ph), 1.f / (float)(D * D));
+}
+
 // ------------------------------------------------------------------ kernel
 template <int D>
-struct BwdOcc { static constexpr int value = D == 64 ? 3 : (D == 96 ? 1 : 2); };
+struct BwdOcc { static constexpr int value = D == 96 ? 1 : 2; };
 
 template <int D, int NS>
 __global__ void __launch_bounds__(RW_THREADS, BwdOcc<D>::value)
@@ -398,7 +428,7 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
            int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
            const float* __restrict__ amp, const float* __restrict__ gpsf,
            float* __restrict__ dphi, float* __restrict__ damp, double* __restrict__ dsurf,
-           unsigned* status) {
+           unsigned* status, const unsigned* __restrict__ vis) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* X = reinterpret_cast<float2*>(smem);
     float2* tw = X + D * D;
@@ -412,6 +442,9 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
     fft_twiddles<D>(tw);
     SurfGrads<NS> SG;
     SG.zero();
+    float gs[RW_MAXS * RW_NGRAD];
+#pragma unroll
+    for (int i = 0; i < RW_MAXS * RW_NGRAD; ++i) gs[i] = 0.f;
     const long long npix_map = (long long)sys.H * sys.W;
     const long long npx = (long long)sys.nx * sys.ny;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
@@ -434,31 +467,48 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
             const float* gimg = gpsf + (long long)R.job * npx;
             float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
-                for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
-                    const int jvi = f / D, jui = f - (f / D) * D;
-                    int mu = jui + D / 2; if (mu >= D) mu -= D;
-                    int mv = jvi + D / 2; if (mv >= D) mv -= D;
-                    float2 gU = make_float2(0.f, 0.f);
-                    float dx, dy, dz;
-                    if (bin_direction<(NS >= 0)>(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
-                        const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
-                        const float2 a = cmul(ain, U);
-                        const float w = a.x * a.x + a.y * a.y;
-                        float gw, gx, gy, gz, gdx, gdy, gdz;
-                        if (secondary_adjoint<NS>(sys, R, gimg, dx, dy, dz, w, gw, gx, gy, gz,
-                                                  gdx, gdy, gdz, SG, status)) {
-                            emission_adjoint(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz, gx,
-                                             gy, gz, gdx, gdy, gdz, acc);
-                            const float2 ga = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
-                            gU = cmulc(ga, ain);          // conj(a_in) * dL/da
+                constexpr int KW = D * D / RW_THREADS;   // visibility words per warp and ray
+                if (vis && KW <= 32) {
+                    // Only secondary rays that reached the sensor carry gradient: zero
+                    // dL/dX, then compact this warp's visible bins (the forward's mask)
+                    // and reverse them in converged rounds of 32.
+                    for (int f = threadIdx.x; f < D * D; f += RW_THREADS)
+                        G[f] = make_float2(0.f, 0.f);
+                    __syncthreads();
+                    const unsigned* vw = vis + R.gid * (long long)(D * D / 32);
+                    const unsigned myw = lane < KW ? __ldg(vw + lane * (RW_THREADS / 32) + warp) : 0u;
+                    const int cnt = __popc(myw);
+                    int incl = cnt;
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int n = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += n;
+                    }
+                    const int total_w = __shfl_sync(0xffffffffu, incl, 31);
+                    const int excl = incl - cnt;
+                    for (int start = 0; start < total_w; start += 32) {
+                        const int idx = start + lane;
+                        int kk = -1, rank = 0;
+                        unsigned wsel = 0u;
+                        for (int k = 0; k < KW; ++k) {
+                            const int ek = __shfl_sync(0xffffffffu, excl, k);
+                            const int ck = __shfl_sync(0xffffffffu, cnt, k);
+                            const unsigned wk = __shfl_sync(0xffffffffu, myw, k);
+                            if (idx >= ek && idx < ek + ck) { kk = k; wsel = wk; rank = idx - ek; }
+                        }
+                        if (kk >= 0) {
+                            const int bit = (int)__fns(wsel, 0u, rank + 1);
+                            exh_bin_adjoint<D, NS>(sys, R, X, phu, phv, gimg, G, ain,
+                                                   kk * RW_THREADS + warp * 32 + bit, acc, SG,
+                                                   gs, status);
                         }
                     }
-                    // dL/dX[m] = conj(phu phv) / D^2 * dL/dU~
-                    const float2 ph = cmul(phu[jui], phv[jvi]);
-                    G[mv * D + mu] = cscale(cmulc(gU, ph), 1.f / (float)(D * D));
+                } else {
+                    for (int f = threadIdx.x; f < D * D; f += RW_THREADS)
+                        exh_bin_adjoint<D, NS>(sys, R, X, phu, phv, gimg, G, ain, f, acc, SG, gs,
+                                               status);
                 }
             } else {
-                sampled_ray_adjoint<D, NS>(sys, R, X, phu, phv, gimg, G, sscr, acc, SG, status);
+                sampled_ray_adjoint<D, NS>(sys, R, X, phu, phv, gimg, G, sscr, acc, SG, gs, status);
             }
             // ---- per-ray reduction of the geometric gradients
 #pragma unroll
@@ -545,8 +595,8 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                 trace_one<false>(sys.s[s], x, y, zl, dx, dy, dz, dummy, status);
             }
             // index gradients of the DOE emission
-            SG.gs[sys.doe_index * RW_NGRAD + 7] += B.gnout;
-            if (sys.doe_index > 0) SG.gs[(sys.doe_index - 1) * RW_NGRAD + 7] += B.gnin;
+            gs[sys.doe_index * RW_NGRAD + 7] += B.gnout;
+            if (sys.doe_index > 0) gs[(sys.doe_index - 1) * RW_NGRAD + 7] += B.gnin;
             float gx = B.gpx, gy = B.gpy, gz = B.gpz;
             float gdx = B.gdx, gdy = B.gdy, gdz = B.gdz;
             if (!sys.conformal) {
@@ -557,12 +607,12 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                 gdx += gx * t; gdy += gy * t; gdz += gz * t;
                 gz += -gt / dz;
                 gdz += -gt * t / dz;
-                SG.gs[sys.doe_index * RW_NGRAD + 0] += gt / dz;
+                gs[sys.doe_index * RW_NGRAD + 0] += gt / dz;
                 for (int s = sys.doe_index - 1; s >= 0; --s) {
                     float gnb = 0.f;
                     trace_one_adjoint(sys.s[s], st[s], gx, gy, gz, gdx, gdy, gdz,
-                                      SG.gs + s * RW_NGRAD, &gnb);
-                    if (s > 0) SG.gs[(s - 1) * RW_NGRAD + 7] += gnb;
+                                      gs + s * RW_NGRAD, &gnb);
+                    if (s > 0) gs[(s - 1) * RW_NGRAD + 7] += gnb;
                 }
             }
         }
@@ -573,17 +623,17 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
             const int si = sys.doe_index + 1 + i;
-            SG.gs[si * RW_NGRAD + 0] += SG.fz[i];
-            SG.gs[si * RW_NGRAD + 1] += SG.fc[i];
-            SG.gs[si * RW_NGRAD + 7] += SG.fn[i];
+            gs[si * RW_NGRAD + 0] += SG.fz[i];
+            gs[si * RW_NGRAD + 1] += SG.fc[i];
+            gs[si * RW_NGRAD + 7] += SG.fn[i];
         }
-        SG.gs[sys.doe_index * RW_NGRAD + 7] += SG.f_doe_n;
+        gs[sys.doe_index * RW_NGRAD + 7] += SG.f_doe_n;
     }
     __syncthreads();
     double* dred = reinterpret_cast<double*>(smem);
     for (int s = 0; s < sys.nsurf; ++s) {
         for (int k = 0; k < RW_NGRAD; ++k) {
-            float v = SG.gs[s * RW_NGRAD + k];
+            float v = gs[s * RW_NGRAD + k];
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
             if (lane == 0) dred[(s * RW_NGRAD + k) * (RW_THREADS / 32) + warp] = (double)v;
         }
@@ -611,7 +661,7 @@ static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const 
                                      const long long* prefix, int njob, long long total,
                                      const RaysIn& rays, const float2* T, const float* amp,
                                      const float* gpsf, float* dphi, float* damp, double* dsurf,
-                                     unsigned* status) {
+                                     unsigned* status, const unsigned* vis) {
     const size_t smem = backward_smem_bytes(D, sys.emit, sys.n_ssr);
     auto kern = k_backward<D, NS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -627,7 +677,8 @@ static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const 
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(sys, jobs, prefix, njob, total, rays, T,
-                                                          amp, gpsf, dphi, damp, dsurf, status);
+                                                          amp, gpsf, dphi, damp, dsurf, status,
+                                                          vis);
     return cudaGetLastError();
 }
 
@@ -635,11 +686,11 @@ cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* job
                             const long long* prefix, int njob, long long total,
                             const RaysIn& rays, const float2* T, const float* amp,
                             const float* dl_dpsf, float* dphi, float* damp, double* dsurf,
-                            int /*scratch_slots*/, unsigned* status, int* launches) {
+                            const unsigned* vis, unsigned* status, int* launches) {
     *launches = 1;
     const int ns = sys.fast_ok ? sys.n_post : -1;
 #define RW_BWD(DD, NN) \
-    launch_backward_d<DD, NN>(L, sys, jobs, prefix, njob, total, rays, T, amp, dl_dpsf, dphi, damp, dsurf, status)
+    launch_backward_d<DD, NN>(L, sys, jobs, prefix, njob, total, rays, T, amp, dl_dpsf, dphi, damp, dsurf, status, vis)
 #define RW_BWD_D(DD)                                      \
     case DD:                                              \
         switch (ns) {                                     \

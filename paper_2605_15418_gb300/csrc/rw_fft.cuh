@@ -1,6 +1,6 @@
 // Shared-memory 2D FFT of one D x D complex patch, FP32, whole CTA.
 //
-// Mixed-radix Stockham autosort (radix 2, 3, 4): stage with radix R after
+// Mixed-radix Stockham autosort (radix 2, 3, 4, 8): stage with radix R after
 // sub-transforms of length P reads x[i + q N/R], multiplies by
 // exp(-+2 pi i q (i mod P) / (P R)), does a length-R DFT and writes
 // y[(i / P) P R + (i mod P) + q P]; the output comes out in natural order.
@@ -10,8 +10,33 @@
 #include "rw_device.cuh"
 
 template <int R, bool INV>
+__device__ __forceinline__ void dft_small(float2* u);
+
+// 8-point DFT as two 4-point DFTs of the even and odd samples:
+// y_k = E_k + W^k O_k, y_{k+4} = E_k - W^k O_k, W = exp(-+2 pi i / 8).
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* u) {
+    float2 e[4] = {u[0], u[2], u[4], u[6]};
+    float2 o[4] = {u[1], u[3], u[5], u[7]};
+    dft_small<4, INV>(e);
+    dft_small<4, INV>(o);
+    const float h = 0.70710678118654752440f;
+    // W^1 o1, W^2 o2, W^3 o3 (forward W = (1 - i)/sqrt2; inverse conjugate)
+    const float sg = INV ? 1.f : -1.f;
+    const float2 w1 = make_float2(h * (o[1].x - sg * o[1].y), h * (o[1].y + sg * o[1].x));
+    const float2 w2 = make_float2(-sg * o[2].y, sg * o[2].x);
+    const float2 w3 = make_float2(h * (-o[3].x - sg * o[3].y), h * (-o[3].y + sg * o[3].x));
+    u[0] = cadd(e[0], o[0]); u[4] = csub(e[0], o[0]);
+    u[1] = cadd(e[1], w1);   u[5] = csub(e[1], w1);
+    u[2] = cadd(e[2], w2);   u[6] = csub(e[2], w2);
+    u[3] = cadd(e[3], w3);   u[7] = csub(e[3], w3);
+}
+
+template <int R, bool INV>
 __device__ __forceinline__ void dft_small(float2* u) {
-    if constexpr (R == 2) {
+    if constexpr (R == 8) {
+        dft8<INV>(u);
+    } else if constexpr (R == 2) {
         float2 a = u[0], b = u[1];
         u[0] = cadd(a, b);
         u[1] = csub(a, b);
@@ -94,16 +119,13 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
         fft_stage<16, 4, 4, INV, COLS>(buf, tw);
     } else if constexpr (N == 32) {
         fft_stage<32, 4, 1, INV, COLS>(buf, tw);
-        fft_stage<32, 4, 4, INV, COLS>(buf, tw);
-        fft_stage<32, 2, 16, INV, COLS>(buf, tw);
+        fft_stage<32, 8, 4, INV, COLS>(buf, tw);
     } else if constexpr (N == 64) {
-        fft_stage<64, 4, 1, INV, COLS>(buf, tw);
-        fft_stage<64, 4, 4, INV, COLS>(buf, tw);
-        fft_stage<64, 4, 16, INV, COLS>(buf, tw);
+        fft_stage<64, 8, 1, INV, COLS>(buf, tw);
+        fft_stage<64, 8, 8, INV, COLS>(buf, tw);
     } else if constexpr (N == 96) {
-        fft_stage<96, 4, 1, INV, COLS>(buf, tw);
-        fft_stage<96, 4, 4, INV, COLS>(buf, tw);
-        fft_stage<96, 2, 16, INV, COLS>(buf, tw);
+        fft_stage<96, 8, 1, INV, COLS>(buf, tw);
+        fft_stage<96, 4, 8, INV, COLS>(buf, tw);
         fft_stage<96, 3, 32, INV, COLS>(buf, tw);
     }
 }

@@ -64,7 +64,8 @@ template <int D, int MODE, int NS>
 __global__ void __launch_bounds__(RW_THREADS, FwdOcc<D>::value)
 k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
           int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
-          double* __restrict__ psf, float2* __restrict__ field, EmitOut eo, unsigned* status) {
+          double* __restrict__ psf, float2* __restrict__ field, EmitOut eo, unsigned* status,
+          unsigned* __restrict__ vis) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* X = reinterpret_cast<float2*>(smem);
     float2* tw = X + D * D;
@@ -84,6 +85,9 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             const RayAtDoe& R = info[r];
             if (!R.alive) {
                 if (MODE == MODE_EMIT) emit_dead<D>(sys, tile * RW_TILE + r, total, eo);
+                if (MODE == MODE_SPLAT && vis && tile * RW_TILE + r < total)
+                    for (int f = threadIdx.x; f < D * D / 32; f += RW_THREADS)
+                        vis[(tile * RW_TILE + r) * (long long)(D * D / 32) + f] = 0u;
                 continue;
             }
             const DJob& J = jobs[R.job];
@@ -92,7 +96,7 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             fft2d<D, false>(X, tw);
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
                 emit_exhaustive<D, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
-                                         tile * RW_TILE + r, status);
+                                             tile * RW_TILE + r, status, vis);
             } else {
                 emit_sampled<D, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                       tile * RW_TILE + r, status,
@@ -126,7 +130,8 @@ template <int D, int MODE, int NS>
 static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                     const long long* prefix, int njob, long long total,
                                     const RaysIn& rays, const float2* T, double* psf,
-                                    float2* field, const EmitOut& eo, unsigned* status) {
+                                    float2* field, const EmitOut& eo, unsigned* status,
+                                    unsigned* vis) {
     size_t smem = forward_smem_bytes(D, sys.emit, sys.n_ssr);
     auto kern = k_forward<D, MODE, NS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -142,7 +147,7 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(sys, jobs, prefix, njob, total, rays,
-                                                          T, psf, field, eo, status);
+                                                          T, psf, field, eo, status, vis);
     return cudaGetLastError();
 }
 
@@ -151,34 +156,35 @@ template <int D>
 static cudaError_t launch_splat(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                 const long long* prefix, int njob, long long total,
                                 const RaysIn& rays, const float2* T, double* psf,
-                                const EmitOut& eo, unsigned* status) {
+                                const EmitOut& eo, unsigned* status, unsigned* vis) {
     if (sys.fast_ok) {
         switch (sys.n_post) {
-            case 0: return launch_forward_d<D, MODE_SPLAT, 0>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status);
-            case 2: return launch_forward_d<D, MODE_SPLAT, 2>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status);
-            case 4: return launch_forward_d<D, MODE_SPLAT, 4>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status);
-            case 6: return launch_forward_d<D, MODE_SPLAT, 6>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status);
+            case 0: return launch_forward_d<D, MODE_SPLAT, 0>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
+            case 2: return launch_forward_d<D, MODE_SPLAT, 2>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
+            case 4: return launch_forward_d<D, MODE_SPLAT, 4>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
+            case 6: return launch_forward_d<D, MODE_SPLAT, 6>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
             default: break;
         }
     }
     return launch_forward_d<D, MODE_SPLAT, -1>(L, sys, jobs, prefix, njob, total, rays, T, psf,
-                                               nullptr, eo, status);
+                                               nullptr, eo, status, vis);
 }
 
 cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const DJob* jobs,
                            const long long* prefix, int njob, long long total,
                            const RaysIn& rays, const float2* T, double* psf, float2* field,
-                           const EmitOut& eo, unsigned* status) {
+                           const EmitOut& eo, unsigned* status, unsigned* vis) {
 #define RW_FWD_CASE(DD)                                                                       \
     case DD:                                                                                  \
         if (mode == MODE_SPLAT)                                                               \
             return launch_splat<DD>(L, sys, jobs, prefix, njob, total, rays, T, psf, eo,      \
-                                    status);                                                  \
+                                    status, vis);                                             \
         if (mode == MODE_COHERENT)                                                            \
             return launch_forward_d<DD, MODE_COHERENT, -1>(L, sys, jobs, prefix, njob, total, \
-                                                           rays, T, psf, field, eo, status);  \
+                                                           rays, T, psf, field, eo, status,   \
+                                                           nullptr);                          \
         return launch_forward_d<DD, MODE_EMIT, -1>(L, sys, jobs, prefix, njob, total, rays, T,\
-                                                   psf, field, eo, status);
+                                                   psf, field, eo, status, nullptr);
     switch (sys.D) {
         RW_FWD_CASE(16)
         RW_FWD_CASE(32)

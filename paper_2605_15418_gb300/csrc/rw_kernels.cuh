@@ -236,11 +236,11 @@ __device__ __forceinline__ bool trace_to_sensor(const DSys& sys, float& x, float
 // Bilinear |a|^2 deposit.  The image is accumulated in double: a focal
 // pixel can receive ~1e6 deposits, and float accumulation there would drop
 // small contributions.
-__device__ __forceinline__ void splat_bilinear(const DSys& sys, float cx, float cy, float x,
+__device__ __forceinline__ bool splat_bilinear(const DSys& sys, float cx, float cy, float x,
                                                float y, float w, double* __restrict__ img) {
     const float u = (x - cx) * sys.inv_spitch + 0.5f * sys.nx - 0.5f;
     const float v = (y - cy) * sys.inv_spitch + 0.5f * sys.ny - 0.5f;
-    if (!(u > -1.f && v > -1.f && u < (float)sys.nx && v < (float)sys.ny)) return;
+    if (!(u > -1.f && v > -1.f && u < (float)sys.nx && v < (float)sys.ny)) return false;
     const float fi = floorf(u), fj = floorf(v);
     const int i0 = (int)fi, j0 = (int)fj;
     const float fu = u - fi, fv = v - fj;
@@ -253,6 +253,7 @@ __device__ __forceinline__ void splat_bilinear(const DSys& sys, float cx, float 
         if (i0 >= 0) atomicAdd(img + (j0 + 1) * nx + i0, (double)(w * (1.f - fu) * fv));
         if (i0 + 1 < nx) atomicAdd(img + (j0 + 1) * nx + i0 + 1, (double)(w * fu * fv));
     }
+    return true;
 }
 
 // Eq. 2: add a exp(i k (OPL + n_s d_t.((X,Y) - r))) d_z over the window.
@@ -319,24 +320,28 @@ __device__ __forceinline__ float2 spectrum_at(const float2* X, const float2* phu
     return cscale(cmul(cmul(X[mv * D + mu], phu[jui]), phv[jvi]), invD2);
 }
 
+// Trace one secondary ray and deposit it; returns true if it reached the
+// sensor plane with any bilinear tap on the sensor (incoherent mode).
+// Incoherent: deposits w = |a|^2; coherent: sums the complex amplitude a.
 template <int MODE, int NS>
-__device__ __forceinline__ void deposit(const DSys& sys, const DJob& J, const RayAtDoe& R,
-                                        float dx, float dy, float dz, float2 a,
+__device__ __forceinline__ bool deposit(const DSys& sys, const DJob& J, const RayAtDoe& R,
+                                        float dx, float dy, float dz, float2 a, float w,
                                         double* __restrict__ psf, float2* __restrict__ field,
                                         unsigned* status) {
     float x = R.px, y = R.py, zl = R.pz;
     double opl = R.opl;
     const long long npx = (long long)sys.nx * sys.ny;
     if (MODE == MODE_SPLAT && NS >= 0) {
-        if (!fast_to_sensor<NS>(sys, x, y, zl, dx, dy, dz)) return;
-        splat_bilinear(sys, R.cx, R.cy, x, y, a.x * a.x + a.y * a.y, psf + (long long)R.job * npx);
+        if (!fast_to_sensor<NS>(sys, x, y, zl, dx, dy, dz)) return false;
+        return splat_bilinear(sys, R.cx, R.cy, x, y, w, psf + (long long)R.job * npx);
     } else if (MODE == MODE_SPLAT) {
-        if (!trace_to_sensor<false>(sys, x, y, zl, dx, dy, dz, opl, status)) return;
-        splat_bilinear(sys, R.cx, R.cy, x, y, a.x * a.x + a.y * a.y, psf + (long long)R.job * npx);
+        if (!trace_to_sensor<false>(sys, x, y, zl, dx, dy, dz, opl, status)) return false;
+        return splat_bilinear(sys, R.cx, R.cy, x, y, w, psf + (long long)R.job * npx);
     } else {
-        if (!trace_to_sensor<true>(sys, x, y, zl, dx, dy, dz, opl, status)) return;
+        if (!trace_to_sensor<true>(sys, x, y, zl, dx, dy, dz, opl, status)) return false;
         splat_coherent(sys, J.k0, R.cx, R.cy, x, y, opl, dx, dy, dz, a,
                        field + (long long)R.job * npx);
+        return true;
     }
 }
 
@@ -358,8 +363,11 @@ template <int D, int MODE, int NS>
 __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                                 const float2* X, const float2* phu,
                                                 const float2* phv, double* psf, float2* field,
-                                                const EmitOut& eo, long long g, unsigned* status) {
+                                                const EmitOut& eo, long long g, unsigned* status,
+                                                unsigned* __restrict__ vis) {
     const float2 ain = make_float2(R.a_re, R.a_im);
+    const float invD2 = 1.f / (float)(D * D);
+    const float ain2 = (ain.x * ain.x + ain.y * ain.y) * invD2 * invD2;
     if (MODE == MODE_EMIT && threadIdx.x == 0) {
         eo.hx[g] = R.px; eo.hy[g] = R.py; eo.hz[g] = (float)((double)R.pz + sys.s[sys.doe_index].z);
         eo.opl[g] = R.opl;
@@ -379,9 +387,26 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
             if (eo.bin) eo.bin[s] = f;
             continue;
         }
-        if (!prop) continue;
-        const float2 a = cmul(ain, spectrum_at<D>(X, phu, phv, jui, jvi));
-        deposit<MODE, NS>(sys, J, R, dx, dy, dz, a, psf, field, status);
+        bool landed = false;
+        if (prop) {
+            float2 a = make_float2(0.f, 0.f);
+            float w = 0.f;
+            if (MODE == MODE_SPLAT) {
+                // the incoherent deposit |a|^2 = |a_in|^2 |X_m|^2 / D^4 needs no phase factor
+                int mu = jui + D / 2; if (mu >= D) mu -= D;
+                int mv = jvi + D / 2; if (mv >= D) mv -= D;
+                const float2 xm = X[mv * D + mu];
+                w = ain2 * (xm.x * xm.x + xm.y * xm.y);
+            } else {
+                a = cmul(ain, spectrum_at<D>(X, phu, phv, jui, jvi));
+            }
+            landed = deposit<MODE, NS>(sys, J, R, dx, dy, dz, a, w, psf, field, status);
+        }
+        if (MODE == MODE_SPLAT && vis) {
+            // one visibility bit per secondary ray: bin f -> word g * D^2/32 + f/32
+            const unsigned word = __ballot_sync(0xffffffffu, landed);
+            if ((threadIdx.x & 31) == 0) vis[g * (long long)(D * D / 32) + (f >> 5)] = word;
+        }
     }
 }
 
@@ -483,7 +508,8 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
             if (eo.bin) eo.bin[s] = jb;
             continue;
         }
-        if (ok) deposit<MODE, NS>(sys, J, R, dx, dy, dz, a, psf, field, status);
+        if (ok) deposit<MODE, NS>(sys, J, R, dx, dy, dz, a, a.x * a.x + a.y * a.y, psf, field,
+                                  status);
     }
 }
 
@@ -496,7 +522,7 @@ cudaError_t launch_generate_rays(const LaunchCtx& L, const GenJob* jobs, const l
 cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const DJob* jobs,
                            const long long* prefix, int njob, long long total, const RaysIn& rays,
                            const float2* T, double* acc, float2* field, const EmitOut& eo,
-                           unsigned* status);
+                           unsigned* status, unsigned* vis = nullptr);
 cudaError_t launch_psf_finalize(const LaunchCtx& L, const double* acc, float* psf, long long n);
 cudaError_t launch_coherent_finalize(const LaunchCtx& L, const float2* field, float* psf,
                                      long long n);

@@ -207,6 +207,28 @@ def rw_forward(ctx, sys_struct, jobs_arr, rays, psf):
                                  C.byref(rs), _ptr(psf)), "rw_forward")
 
 
+def rw_forward_vis(ctx, sys_struct, jobs_arr, rays, psf, vis):
+    ctx._stream()
+    rs = rays_struct(rays)
+    ctx.check(ctx.lib.rw_forward_vis(ctx.h, C.byref(sys_struct), jobs_arr, len(jobs_arr),
+                                     C.byref(rs), _ptr(psf), _ptr(vis), int(vis.numel())),
+              "rw_forward_vis")
+
+
+def rw_backward_vis(ctx, sys_struct, jobs_arr, rays, dl_dpsf, vis, dphi=None, damp=None,
+                    dsurf=None):
+    ctx._stream()
+    rs = rays_struct(rays)
+    ctx.check(ctx.lib.rw_backward_vis(ctx.h, C.byref(sys_struct), jobs_arr, len(jobs_arr),
+                                      C.byref(rs), _ptr(dl_dpsf), _ptr(vis), int(vis.numel()),
+                                      _ptr(dphi), _ptr(damp), _ptr(dsurf)), "rw_backward_vis")
+
+
+def alloc_vis(n_rays, D, device):
+    """One visibility bit per secondary ray (int32 words, bit-exact uint32)."""
+    return torch.empty(n_rays * D * D // 32, dtype=torch.int32, device=device)
+
+
 def rw_patch_spectra(ctx, sys_struct, jobs_arr, rays, spectra):
     ctx._stream()
     rs = rays_struct(rays)
@@ -254,11 +276,15 @@ class Simulator:
         return system_struct(self.w.system, self.phi if phi is None else phi,
                              self.amp if amp is None else amp, self.dft, surfaces)
 
-    def forward(self, phi=None, surfaces=None, psf=None):
+    def forward(self, phi=None, surfaces=None, psf=None, vis=None):
+        """PSF [njob, ny, nx]; with `vis` (alloc_vis) also the visibility mask."""
         s, keep = self.sys_struct(phi, surfaces=surfaces)
         if psf is None:
             psf = torch.empty(self.psf_shape, dtype=torch.float32, device=self.dev)
-        rw_forward(self.ctx, s, self.jobs, self.rays, psf)
+        if vis is None:
+            rw_forward(self.ctx, s, self.jobs, self.rays, psf)
+        else:
+            rw_forward_vis(self.ctx, s, self.jobs, self.rays, psf, vis)
         return psf
 
     def emit(self, out=None):
@@ -279,12 +305,19 @@ class Simulator:
         rw_patch_spectra(self.ctx, s, self.jobs, self.rays, out)
         return torch.view_as_complex(out)
 
-    def backward(self, dl_dpsf, phi=None, surfaces=None, want_amp=False):
+    def backward(self, dl_dpsf, phi=None, surfaces=None, want_amp=False, vis=None):
+        """(dphi, damp, dsurf); `vis` from forward(vis=...) on the same inputs
+        restricts the adjoint to secondary rays that reached the sensor."""
         s, keep = self.sys_struct(phi, surfaces=surfaces)
         dphi = torch.zeros_like(self.phi)
         damp = torch.zeros_like(self.amp) if (want_amp and self.amp is not None) else None
         dsurf = torch.zeros(len(self.w.system.surfaces), 8, dtype=torch.float64, device=self.dev)
-        rw_backward(self.ctx, s, self.jobs, self.rays, dl_dpsf.contiguous(), dphi, damp, dsurf)
+        if vis is None:
+            rw_backward(self.ctx, s, self.jobs, self.rays, dl_dpsf.contiguous(), dphi, damp,
+                        dsurf)
+        else:
+            rw_backward_vis(self.ctx, s, self.jobs, self.rays, dl_dpsf.contiguous(), vis, dphi,
+                            damp, dsurf)
         return dphi, damp, dsurf
 
     def loss(self, psf, target, dl_dpsf=None):
