@@ -42,7 +42,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n-side", type=int, default=1024, help="rays per field = n_side^2")
-    ap.add_argument("--cpu-rays", type=int, default=96, help="oracle sample (incident rays)")
+    ap.add_argument("--cpu-rays", type=int, default=576,
+                    help="incident rays per oracle sample (cpu_baseline and the reference arm)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="CPU time the cpu_baseline leg keeps sampling for")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -142,13 +145,22 @@ def oracle_step_seconds(w, n_rays, seed=0):
     return time.perf_counter() - t0, per * len(w.jobs)
 
 
-def cpu_baseline(w, n_rays):
+def cpu_baseline(w, n_rays, budget_s):
+    """Oracle throughput on the host: independent seeded samples of n_rays
+    incident rays each (the autograd graph of one sample holds ~10 MB per
+    ray), repeated until budget_s seconds of CPU work have been timed."""
     import torch
-    secs, n = oracle_step_seconds(w, n_rays)
+    secs, n, k = 0.0, 0, 0
+    while k == 0 or secs < budget_s:
+        s, m = oracle_step_seconds(w, n_rays, seed=1000 + k)
+        secs += s
+        n += m
+        k += 1
     return {"value": n / secs, "unit": "rays/s", "cores": torch.get_num_threads(),
             "kind": "oracle",
-            "sample": f"{n} incident rays ({n // len(w.jobs)} per job, seeded) of the same "
-                      f"workload, forward + autograd backward in float64, {secs:.1f} s"}
+            "sample": f"{k} seeded samples of {n // k} incident rays ({n // k // len(w.jobs)} "
+                      f"per job) of the same workload, each a float64 forward + autograd "
+                      f"backward of Eq. 3, {secs:.1f} s in total"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -157,7 +169,7 @@ def run_reference(args, rank):
         return
     import torch
     w = workload(args.n_side)
-    per_step = max(len(w.jobs), args.cpu_rays // 3)
+    per_step = max(len(w.jobs), args.cpu_rays)
     for i in range(args.warmup):
         oracle_step_seconds(w, per_step, seed=100 + i)
     tot, nr = 0.0, 0
@@ -311,7 +323,7 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_rays)
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_rays, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librw.so")
-SOURCES = ["rw_api.cu", "rw_forward.cu", "rw_backward.cu", "rw_loss.cu", "rw_static.cu", "rw_spectra.cu"]
+SOURCES = ["rw_api.cu", "rw_forward.cu", "rw_backward.cu", "rw_loss.cu", "rw_static.cu", "rw_spectra.cu", "rw_bwd_split.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]

@@ -18,6 +18,26 @@ cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* job
                             const float* dl_dpsf, float* dphi, float* damp, double* dsurf,
                             const unsigned* vis, unsigned* status, int* launches);
 size_t backward_smem_needed(const DSys& sys);
+struct SplitBufs {
+    RayAtDoe* rinfo;
+    int* iray;
+    int* ibin;
+    float2* iU;
+    float2* igU;
+    long long* voff;
+    int* vcnt;
+    float* rsum;
+    unsigned long long* counter;
+    long long cap;
+};
+cudaError_t launch_bs_count(const LaunchCtx& L, const unsigned* vis, long long nwords,
+                            unsigned long long* total);
+cudaError_t launch_backward_split(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
+                                  const long long* prefix, int njob, long long total,
+                                  const RaysIn& rays, const float2* T, const float* amp,
+                                  const float* gpsf, const unsigned* vis, const SplitBufs& B,
+                                  long long nitems, float* dphi, float* damp, double* dsurf,
+                                  unsigned* status);
 cudaError_t launch_spectra(const LaunchCtx& L, const DSys& sys, int tc, const DJob* jobs,
                            const long long* prefix, int njob, long long total, const RaysIn& rays,
                            const float2* T, float2* out, unsigned* status);
@@ -50,6 +70,9 @@ struct rw_ctx {
     DevBuf tables;      // job tables, prefix sums, map scales
     DevBuf field;       // coherent field accumulator
     DevBuf acc;         // double PSF accumulator
+    DevBuf split_rays;  // split adjoint: per-ray state, offsets, sums
+    DevBuf split_items; // split adjoint: work list of visible secondary rays
+    unsigned long long* count_host = nullptr;   // pinned
     DevBuf misc;        // status word + loss sums
     void* staging = nullptr;       // pinned host copy source of `tables`
     size_t staging_bytes = 0;
@@ -372,6 +395,7 @@ rw_status rw_create(rw_ctx** out, int device, void* cuda_stream) {
         ctx->misc.ensure(256) != cudaSuccess ||
         cudaMemset(ctx->misc.p, 0, 256) != cudaSuccess ||
         cudaMallocHost(&ctx->cap_host, RW_CAPTURE_ARENA) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->count_host, 64) != cudaSuccess ||
         ctx->cap_dev.ensure(RW_CAPTURE_ARENA) != cudaSuccess) {
         delete ctx;
         return RW_ECUDA;
@@ -392,7 +416,10 @@ rw_status rw_destroy(rw_ctx* ctx) {
     ctx->acc.release();
     ctx->misc.release();
     ctx->cap_dev.release();
+    ctx->split_rays.release();
+    ctx->split_items.release();
     if (ctx->cap_host) cudaFreeHost(ctx->cap_host);
+    if (ctx->count_host) cudaFreeHost(ctx->count_host);
     if (ctx->staging) cudaFreeHost(ctx->staging);
     if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
     delete ctx;
@@ -606,6 +633,47 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
     if (P.total == 0 || (!dphi && !damp && !dsurf)) return RW_OK;
     float2* T; DJob* dj; long long* dp;
     if ((st = prepare(ctx, sys, P, &T, &dj, &dp)) != RW_OK) return st;
+    if (vis && P.sys.emit == RW_EMIT_EXHAUSTIVE && P.sys.D <= 64 && !capturing(ctx)) {
+        // Split adjoint: count the visible secondary rays (one host sync), size
+        // the work list, then spectra+list / trace+reverse / conjugate FFT+scatter.
+        const long long nwords = P.total * (long long)P.sys.D * P.sys.D / 32;
+        unsigned long long* dcount = reinterpret_cast<unsigned long long*>(
+            reinterpret_cast<char*>(ctx->misc.p) + 128);
+        RW_CUDA(launch_bs_count(lctx(ctx), vis, nwords, dcount), "visible count");
+        ctx->launches++;
+        RW_CUDA(cudaMemcpyAsync(ctx->count_host, dcount, sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, ctx->stream), "count read");
+        RW_CUDA(cudaStreamSynchronize(ctx->stream), "count sync");
+        const long long nitems = (long long)*ctx->count_host;
+        const size_t per_ray = sizeof(RayAtDoe) + sizeof(long long) + sizeof(int) + 6 * sizeof(float);
+        if ((st = ensure_buf(ctx, ctx->split_rays, P.total * per_ray + 256, "split adjoint rays")) != RW_OK)
+            return st;
+        const long long cap = nitems > 0 ? nitems : 1;
+        const size_t per_item = 2 * sizeof(int) + 2 * sizeof(float2);
+        if ((st = ensure_buf(ctx, ctx->split_items, (size_t)cap * per_item + 256, "split adjoint list")) != RW_OK)
+            return st;
+        char* rp = (char*)ctx->split_rays.p;
+        SplitBufs B;
+        B.rinfo = (RayAtDoe*)rp;                    rp += align16(P.total * sizeof(RayAtDoe));
+        B.voff = (long long*)rp;                    rp += align16(P.total * sizeof(long long));
+        B.vcnt = (int*)rp;                          rp += align16(P.total * sizeof(int));
+        B.rsum = (float*)rp;                        rp += align16(P.total * 6 * sizeof(float));
+        char* ip = (char*)ctx->split_items.p;
+        B.igU = (float2*)ip;                        ip += (size_t)cap * sizeof(float2);
+        B.iU = (float2*)ip;                         ip += (size_t)cap * sizeof(float2);
+        B.iray = (int*)ip;                          ip += (size_t)cap * sizeof(int);
+        B.ibin = (int*)ip;
+        B.counter = dcount;
+        B.cap = cap;
+        RW_CUDA(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), ctx->stream), "counter");
+        RW_CUDA(cudaMemsetAsync(B.rsum, 0, P.total * 6 * sizeof(float), ctx->stream), "sums");
+        RW_CUDA(launch_backward_split(lctx(ctx), P.sys, dj, dp, njob, P.total, rays_in(rays), T,
+                                      sys->doe.amp, dl_dpsf, vis, B, nitems, dphi, damp, dsurf,
+                                      status_word(ctx)),
+                "split adjoint");
+        ctx->launches += nitems > 0 ? 3 : 2;
+        return RW_OK;
+    }
     int nl = 0;
     RW_CUDA(launch_backward(lctx(ctx), P.sys, dj, dp, njob, P.total, rays_in(rays), T,
                             sys->doe.amp, dl_dpsf, dphi, damp, dsurf, vis, status_word(ctx), &nl),

@@ -20,156 +20,7 @@
 // FFT) to dL/dT on the D x D patch; dT/dphi = i (lambda0/lambda) T and
 // dT/dA = exp(i psi) give the map gradients, added with atomics.  Surface
 // gradients are kept per thread and reduced once per CTA into dsurf.
-#include "rw_kernels.cuh"
-
-struct BwdRay {
-    float gpx, gpy, gpz;      // dL/d(hit point)
-    float gdx, gdy, gdz;      // dL/d(incident direction at the DOE)
-    float gnin, gnout;        // dL/d(index before / after the DOE)
-};
-
-__device__ __forceinline__ void bilinear_grad(const DSys& sys, float cx, float cy, float x,
-                                              float y, const float* __restrict__ gimg,
-                                              float& gw, float& gx, float& gy) {
-    gw = 0.f; gx = 0.f; gy = 0.f;
-    const float u = (x - cx) * sys.inv_spitch + 0.5f * sys.nx - 0.5f;
-    const float v = (y - cy) * sys.inv_spitch + 0.5f * sys.ny - 0.5f;
-    if (!(u > -1.f && v > -1.f && u < (float)sys.nx && v < (float)sys.ny)) return;
-    const float fi = floorf(u), fj = floorf(v);
-    const int i0 = (int)fi, j0 = (int)fj;
-    const float fu = u - fi, fv = v - fj;
-    const int nx = sys.nx, ny = sys.ny;
-    float g00 = 0.f, g10 = 0.f, g01 = 0.f, g11 = 0.f;
-    if (j0 >= 0) {
-        if (i0 >= 0) g00 = __ldg(gimg + j0 * nx + i0);
-        if (i0 + 1 < nx) g10 = __ldg(gimg + j0 * nx + i0 + 1);
-    }
-    if (j0 + 1 < ny) {
-        if (i0 >= 0) g01 = __ldg(gimg + (j0 + 1) * nx + i0);
-        if (i0 + 1 < nx) g11 = __ldg(gimg + (j0 + 1) * nx + i0 + 1);
-    }
-    gw = (1.f - fu) * (1.f - fv) * g00 + fu * (1.f - fv) * g10 + (1.f - fu) * fv * g01 + fu * fv * g11;
-    const float gfu = (1.f - fv) * (g10 - g00) + fv * (g11 - g01);
-    const float gfv = (1.f - fu) * (g01 - g00) + fu * (g11 - g10);
-    gx = gfu * sys.inv_spitch;
-    gy = gfv * sys.inv_spitch;
-}
-
-// Per-thread accumulators of surface-parameter gradients for the
-// specialised path: only constant indices, so they stay in registers.  The
-// generic path and the incident side use a separate per-thread array `gs`.
-template <int NS>
-struct SurfGrads {
-    static constexpr int NR = NS > 0 ? NS : 1;
-    float fz[NR], fc[NR], fn[NR];    // z, c, n_after of post[i]
-    float f_doe_n;                   // n_after of the DOE surface
-    __device__ __forceinline__ void zero() {
-#pragma unroll
-        for (int i = 0; i < NR; ++i) { fz[i] = 0.f; fc[i] = 0.f; fn[i] = 0.f; }
-        f_doe_n = 0.f;
-    }
-};
-
-// Re-trace one secondary ray (origin = DOE hit of R, direction d, deposit
-// weight w = |a|^2) and reverse it.  On success returns dL/dw, dL/d(origin)
-// and dL/d(direction) and adds the surface-parameter gradients to SG.
-template <int NS>
-__device__ __forceinline__ bool secondary_adjoint(const DSys& sys, const RayAtDoe& R,
-                                                  const float* __restrict__ gimg, float dx,
-                                                  float dy, float dz, float w, float& gw,
-                                                  float& gx, float& gy, float& gz, float& gdx,
-                                                  float& gdy, float& gdz, SurfGrads<NS>& SG,
-                                                  float* gs, unsigned* status) {
-    constexpr int NR = SurfGrads<NS>::NR;
-    float x = R.px, y = R.py, zl = R.pz;
-    float ex = dx, ey = dy, ez = dz;
-    bool ok = true;
-    if constexpr (NS >= 0) {
-        SurfIn st[NR];
-#pragma unroll
-        for (int i = 0; i < NS; ++i) {
-            if (ok) {
-                st[i].x = x; st[i].y = y; st[i].zl = zl - sys.post[i].gap;
-                st[i].dx = ex; st[i].dy = ey; st[i].dz = ez;
-                ok = fast_step(sys.post[i], x, y, zl, ex, ey, ez);
-            }
-        }
-        if (!ok) return false;
-        const float zs = zl - sys.sensor_gap;
-        const float ts = -zs * rcp_fast(ez);
-        const float xs = fmaf(ts, ex, x), ys = fmaf(ts, ey, y);
-        float gxs, gys;
-        bilinear_grad(sys, R.cx, R.cy, xs, ys, gimg, gw, gxs, gys);
-        gxs *= w;   // the deposit is w times the tap weight
-        gys *= w;
-        if (gw == 0.f && gxs == 0.f && gys == 0.f) return false;
-        // sensor plane: xs = x + ts e, ts = -zs / ez
-        const float gts = gxs * ex + gys * ey;
-        gx = gxs; gy = gys;
-        gdx = gxs * ts; gdy = gys * ts;
-        const float iez = rcp_fast(ez);
-        gz = -gts * iez;
-        gdz = -gts * ts * iez;
-#pragma unroll
-        for (int i = NS - 1; i >= 0; --i) {
-            float gnb = 0.f;
-            fast_step_adjoint(sys.post[i], st[i], gx, gy, gz, gdx, gdy, gdz, SG.fz[i], SG.fc[i],
-                              SG.fn[i], gnb);
-            if (i > 0) SG.fn[i > 0 ? i - 1 : 0] += gnb; else SG.f_doe_n += gnb;
-        }
-        return true;
-    } else {
-        SurfIn st[RW_MAXS];
-        double dummy = 0.0;
-        for (int s = sys.doe_index + 1; s < sys.nsurf && ok; ++s) {
-            st[s].x = x; st[s].y = y; st[s].zl = zl - sys.s[s].gap;
-            st[s].dx = ex; st[s].dy = ey; st[s].dz = ez;
-            ok = trace_one<false>(sys.s[s], x, y, zl, ex, ey, ez, dummy, status);
-        }
-        if (!ok || ez == 0.f) return false;
-        const float zs = zl - sys.sensor_gap;
-        const float ts = -zs / ez;
-        const float xs = fmaf(ts, ex, x), ys = fmaf(ts, ey, y);
-        float gxs, gys;
-        bilinear_grad(sys, R.cx, R.cy, xs, ys, gimg, gw, gxs, gys);
-        gxs *= w;
-        gys *= w;
-        if (gw == 0.f && gxs == 0.f && gys == 0.f) return false;
-        const float gts = gxs * ex + gys * ey;
-        gx = gxs; gy = gys;
-        gdx = gxs * ts; gdy = gys * ts;
-        gz = -gts / ez;
-        gdz = -gts * ts / ez;
-        for (int s = sys.nsurf - 1; s > sys.doe_index; --s) {
-            float gnb = 0.f;
-            trace_one_adjoint(sys.s[s], st[s], gx, gy, gz, gdx, gdy, gdz,
-                              gs + s * RW_NGRAD, &gnb);
-            gs[(s - 1) * RW_NGRAD + 7] += gnb;
-        }
-        return true;
-    }
-}
-
-// Reverse of d = (ku u + kv v + kn n) / K for bin (ju, jv): adds dL/d(origin),
-// dL/dkappa_u, dL/dkappa_v and dL/dK to acc[0..5].
-__device__ __forceinline__ void emission_adjoint(const DSys& sys, const RayAtDoe& R, int ju,
-                                                 int jv, float dx, float dy, float dz,
-                                                 float gx, float gy, float gz, float gdx,
-                                                 float gdy, float gdz, float* acc) {
-    const float ku = R.kin_u + sys.kstep * (float)ju;
-    const float kv = R.kin_v + sys.kstep * (float)jv;
-    const float K = R.K;
-    const float kn2 = fmaxf(K * K - ku * ku - kv * kv, 0.f);
-    float ikn;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ikn) : "f"(kn2));
-    const float gdu = gdx * R.u[0] + gdy * R.u[1] + gdz * R.u[2];
-    const float gdv = gdx * R.v[0] + gdy * R.v[1] + gdz * R.v[2];
-    const float gdn = gdx * R.n[0] + gdy * R.n[1] + gdz * R.n[2];
-    acc[0] += gx; acc[1] += gy; acc[2] += gz;
-    acc[3] += (gdu - ku * ikn * gdn) * R.invK;
-    acc[4] += (gdv - kv * ikn * gdn) * R.invK;
-    acc[5] += gdn * ikn - (gdx * dx + gdy * dy + gdz * dz) * R.invK;
-}
+#include "rw_bwd_common.cuh"
 
 // ------------------------------------------------------------------ sampled
 // Shared scratch of the sampled adjoint (after the exhaustive layout).

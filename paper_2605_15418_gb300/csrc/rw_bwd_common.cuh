@@ -1,0 +1,289 @@
+// Pieces of the adjoint shared by the fused kernel (rw_backward.cu) and the
+// split kernels (rw_bwd_split.cu): reverse of one secondary ray, of its
+// emission, of the map gather, and of the incident side.
+#pragma once
+#include "rw_kernels.cuh"
+
+struct BwdRay {
+    float gpx, gpy, gpz;      // dL/d(hit point)
+    float gdx, gdy, gdz;      // dL/d(incident direction at the DOE)
+    float gnin, gnout;        // dL/d(index before / after the DOE)
+};
+
+__device__ __forceinline__ void bilinear_grad(const DSys& sys, float cx, float cy, float x,
+                                              float y, const float* __restrict__ gimg,
+                                              float& gw, float& gx, float& gy) {
+    gw = 0.f; gx = 0.f; gy = 0.f;
+    const float u = (x - cx) * sys.inv_spitch + 0.5f * sys.nx - 0.5f;
+    const float v = (y - cy) * sys.inv_spitch + 0.5f * sys.ny - 0.5f;
+    if (!(u > -1.f && v > -1.f && u < (float)sys.nx && v < (float)sys.ny)) return;
+    const float fi = floorf(u), fj = floorf(v);
+    const int i0 = (int)fi, j0 = (int)fj;
+    const float fu = u - fi, fv = v - fj;
+    const int nx = sys.nx, ny = sys.ny;
+    float g00 = 0.f, g10 = 0.f, g01 = 0.f, g11 = 0.f;
+    if (j0 >= 0) {
+        if (i0 >= 0) g00 = __ldg(gimg + j0 * nx + i0);
+        if (i0 + 1 < nx) g10 = __ldg(gimg + j0 * nx + i0 + 1);
+    }
+    if (j0 + 1 < ny) {
+        if (i0 >= 0) g01 = __ldg(gimg + (j0 + 1) * nx + i0);
+        if (i0 + 1 < nx) g11 = __ldg(gimg + (j0 + 1) * nx + i0 + 1);
+    }
+    gw = (1.f - fu) * (1.f - fv) * g00 + fu * (1.f - fv) * g10 + (1.f - fu) * fv * g01 + fu * fv * g11;
+    const float gfu = (1.f - fv) * (g10 - g00) + fv * (g11 - g01);
+    const float gfv = (1.f - fu) * (g01 - g00) + fu * (g11 - g10);
+    gx = gfu * sys.inv_spitch;
+    gy = gfv * sys.inv_spitch;
+}
+
+// Per-thread accumulators of surface-parameter gradients for the
+// specialised path: only constant indices, so they stay in registers.  The
+// generic path and the incident side use a separate per-thread array `gs`.
+template <int NS>
+struct SurfGrads {
+    static constexpr int NR = NS > 0 ? NS : 1;
+    float fz[NR], fc[NR], fn[NR];    // z, c, n_after of post[i]
+    float f_doe_n;                   // n_after of the DOE surface
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int i = 0; i < NR; ++i) { fz[i] = 0.f; fc[i] = 0.f; fn[i] = 0.f; }
+        f_doe_n = 0.f;
+    }
+};
+
+// Re-trace one secondary ray (origin = DOE hit of R, direction d, deposit
+// weight w = |a|^2) and reverse it.  On success returns dL/dw, dL/d(origin)
+// and dL/d(direction) and adds the surface-parameter gradients to SG.
+template <int NS>
+__device__ __forceinline__ bool secondary_adjoint(const DSys& sys, const RayAtDoe& R,
+                                                  const float* __restrict__ gimg, float dx,
+                                                  float dy, float dz, float w, float& gw,
+                                                  float& gx, float& gy, float& gz, float& gdx,
+                                                  float& gdy, float& gdz, SurfGrads<NS>& SG,
+                                                  float* gs, unsigned* status) {
+    constexpr int NR = SurfGrads<NS>::NR;
+    float x = R.px, y = R.py, zl = R.pz;
+    float ex = dx, ey = dy, ez = dz;
+    bool ok = true;
+    if constexpr (NS >= 0) {
+        SurfIn st[NR];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            if (ok) {
+                st[i].x = x; st[i].y = y; st[i].zl = zl - sys.post[i].gap;
+                st[i].dx = ex; st[i].dy = ey; st[i].dz = ez;
+                ok = fast_step(sys.post[i], x, y, zl, ex, ey, ez);
+            }
+        }
+        if (!ok) return false;
+        const float zs = zl - sys.sensor_gap;
+        const float ts = -zs * rcp_fast(ez);
+        const float xs = fmaf(ts, ex, x), ys = fmaf(ts, ey, y);
+        float gxs, gys;
+        bilinear_grad(sys, R.cx, R.cy, xs, ys, gimg, gw, gxs, gys);
+        gxs *= w;   // the deposit is w times the tap weight
+        gys *= w;
+        if (gw == 0.f && gxs == 0.f && gys == 0.f) return false;
+        // sensor plane: xs = x + ts e, ts = -zs / ez
+        const float gts = gxs * ex + gys * ey;
+        gx = gxs; gy = gys;
+        gdx = gxs * ts; gdy = gys * ts;
+        const float iez = rcp_fast(ez);
+        gz = -gts * iez;
+        gdz = -gts * ts * iez;
+#pragma unroll
+        for (int i = NS - 1; i >= 0; --i) {
+            float gnb = 0.f;
+            fast_step_adjoint(sys.post[i], st[i], gx, gy, gz, gdx, gdy, gdz, SG.fz[i], SG.fc[i],
+                              SG.fn[i], gnb);
+            if (i > 0) SG.fn[i > 0 ? i - 1 : 0] += gnb; else SG.f_doe_n += gnb;
+        }
+        return true;
+    } else {
+        SurfIn st[RW_MAXS];
+        double dummy = 0.0;
+        for (int s = sys.doe_index + 1; s < sys.nsurf && ok; ++s) {
+            st[s].x = x; st[s].y = y; st[s].zl = zl - sys.s[s].gap;
+            st[s].dx = ex; st[s].dy = ey; st[s].dz = ez;
+            ok = trace_one<false>(sys.s[s], x, y, zl, ex, ey, ez, dummy, status);
+        }
+        if (!ok || ez == 0.f) return false;
+        const float zs = zl - sys.sensor_gap;
+        const float ts = -zs / ez;
+        const float xs = fmaf(ts, ex, x), ys = fmaf(ts, ey, y);
+        float gxs, gys;
+        bilinear_grad(sys, R.cx, R.cy, xs, ys, gimg, gw, gxs, gys);
+        gxs *= w;
+        gys *= w;
+        if (gw == 0.f && gxs == 0.f && gys == 0.f) return false;
+        const float gts = gxs * ex + gys * ey;
+        gx = gxs; gy = gys;
+        gdx = gxs * ts; gdy = gys * ts;
+        gz = -gts / ez;
+        gdz = -gts * ts / ez;
+        for (int s = sys.nsurf - 1; s > sys.doe_index; --s) {
+            float gnb = 0.f;
+            trace_one_adjoint(sys.s[s], st[s], gx, gy, gz, gdx, gdy, gdz,
+                              gs + s * RW_NGRAD, &gnb);
+            gs[(s - 1) * RW_NGRAD + 7] += gnb;
+        }
+        return true;
+    }
+}
+
+// Reverse of d = (ku u + kv v + kn n) / K for bin (ju, jv): adds dL/d(origin),
+// dL/dkappa_u, dL/dkappa_v and dL/dK to acc[0..5].
+__device__ __forceinline__ void emission_adjoint(const DSys& sys, const RayAtDoe& R, int ju,
+                                                 int jv, float dx, float dy, float dz,
+                                                 float gx, float gy, float gz, float gdx,
+                                                 float gdy, float gdz, float* acc) {
+    const float ku = R.kin_u + sys.kstep * (float)ju;
+    const float kv = R.kin_v + sys.kstep * (float)jv;
+    const float K = R.K;
+    const float kn2 = fmaxf(K * K - ku * ku - kv * kv, 0.f);
+    float ikn;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(ikn) : "f"(kn2));
+    const float gdu = gdx * R.u[0] + gdy * R.u[1] + gdz * R.u[2];
+    const float gdv = gdx * R.v[0] + gdy * R.v[1] + gdz * R.v[2];
+    const float gdn = gdx * R.n[0] + gdy * R.n[1] + gdz * R.n[2];
+    acc[0] += gx; acc[1] += gy; acc[2] += gz;
+    acc[3] += (gdu - ku * ikn * gdn) * R.invK;
+    acc[4] += (gdv - kv * ikn * gdn) * R.invK;
+    acc[5] += gdn * ikn - (gdx * dx + gdy * dy + gdz * dz) * R.invK;
+}
+
+
+// Per-bin phase factors exp(-i k_j s_0) of the current ray (see gather_patch).
+template <int D>
+__device__ __forceinline__ void phase_factors(const DSys& sys, const RayAtDoe& R, float2* phu,
+                                              float2* phv) {
+    if (threadIdx.x < D) {
+        if (sys.gather == RW_GATHER_NEAREST) {
+            const float j = (float)((int)threadIdx.x - D / 2);
+            float s, c;
+            sincospif(-2.f * j * R.s0, &s, &c);
+            phu[threadIdx.x] = make_float2(c, s);
+            sincospif(-2.f * j * R.t0, &s, &c);
+            phv[threadIdx.x] = make_float2(c, s);
+        } else {
+            const float sg = ((((int)threadIdx.x - D / 2) & 1) ? -1.f : 1.f);
+            phu[threadIdx.x] = make_float2(sg, 0.f);
+            phv[threadIdx.x] = make_float2(sg, 0.f);
+        }
+    }
+}
+
+// Reverse of the patch gather: dL/dT on the D x D patch (G, natural order
+// after the conjugate FFT) -> dphi = (lambda0/lambda) Im(conj(T) g),
+// dA = Re(conj(T) g) / A, added to the maps with atomics.
+template <int D>
+__device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
+                                            const float2* __restrict__ T,
+                                            const float* __restrict__ amp, const float2* G,
+                                            float scale, float* __restrict__ dphi,
+                                            float* __restrict__ damp) {
+    const int H = sys.H, W = sys.W;
+    for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
+        const int b = f / D, a = f - (f / D) * D;
+        const float2 gT = G[f];
+        if (sys.gather == RW_GATHER_NEAREST) {
+            const int rr = R.r0 + b, cc = R.c0 + a;
+            if ((unsigned)rr < (unsigned)H && (unsigned)cc < (unsigned)W) {
+                const long long p = (long long)rr * W + cc;
+                const float2 t = __ldg(&T[p]);
+                if (dphi) atomicAdd(dphi + p, scale * (t.x * gT.y - t.y * gT.x));
+                if (damp) {
+                    const float A = __ldg(amp + p);
+                    if (A != 0.f) atomicAdd(damp + p, (t.x * gT.x + t.y * gT.y) / A);
+                }
+            }
+        } else {
+            const float oa = (float)(a - D / 2), ob = (float)(b - D / 2);
+            const float fu = R.s0 + oa * R.u[0] + ob * R.v[0];
+            const float fv = R.t0 + oa * R.u[1] + ob * R.v[1];
+            const float iuf = floorf(fu), ivf = floorf(fv);
+            const float wu = fu - iuf, wv = fv - ivf;
+            const int i0 = R.c0 + (int)iuf, j0 = R.r0 + (int)ivf;
+            const float wt[4] = {(1.f - wu) * (1.f - wv), wu * (1.f - wv), (1.f - wu) * wv, wu * wv};
+            const int di[4] = {0, 1, 0, 1}, dj[4] = {0, 0, 1, 1};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int rr = j0 + dj[q], cc = i0 + di[q];
+                if ((unsigned)rr < (unsigned)H && (unsigned)cc < (unsigned)W) {
+                    const long long p = (long long)rr * W + cc;
+                    const float2 t = __ldg(&T[p]);
+                    const float2 g = cscale(gT, wt[q]);
+                    if (dphi) atomicAdd(dphi + p, scale * (t.x * g.y - t.y * g.x));
+                    if (damp) {
+                        const float A = __ldg(amp + p);
+                        if (A != 0.f) atomicAdd(damp + p, (t.x * g.x + t.y * g.y) / A);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Incident side of one ray from its summed emission gradients
+// s = (dL/dP (3), dL/dkappa_u, dL/dkappa_v, dL/dK): reverse of the DOE hit and
+// of the pre-DOE surfaces; adds surface gradients to gs.
+__device__ __forceinline__ void incident_adjoint(const DSys& sys, const DJob* __restrict__ jobs,
+                                                 const long long* __restrict__ prefix,
+                                                 const RaysIn& rays, const RayAtDoe& R,
+                                                 const float* s, float* gs, unsigned* status) {
+    const DJob& J = jobs[R.job];
+    const float kn_in = J.k0 * sys.n_in;
+    float gx = s[0], gy = s[1], gz = s[2];
+    float gdx = kn_in * (s[3] * R.u[0] + s[4] * R.v[0]);
+    float gdy = kn_in * (s[3] * R.u[1] + s[4] * R.v[1]);
+    float gdz = kn_in * (s[3] * R.u[2] + s[4] * R.v[2]);
+    // index gradients of the emission: kappa_in = k0 n_in (d.u, d.v), K = k0 n_out
+    gs[sys.doe_index * RW_NGRAD + 7] += J.k0 * s[5];
+    if (sys.doe_index > 0)
+        gs[(sys.doe_index - 1) * RW_NGRAD + 7] += (R.kin_u * s[3] + R.kin_v * s[4]) / sys.n_in;
+    const long long ri = J.off + (R.gid - prefix[R.job]);
+    float x = rays.ox[ri], y = rays.oy[ri], zl = rays.oz[ri];
+    float dx = rays.dx[ri], dy = rays.dy[ri], dz = rays.dz[ri];
+    double dummy = 0.0;
+    SurfIn st[RW_MAXS];
+    for (int si = 0; si < sys.doe_index; ++si) {
+        st[si].x = x; st[si].y = y; st[si].zl = zl - sys.s[si].gap;
+        st[si].dx = dx; st[si].dy = dy; st[si].dz = dz;
+        trace_one<false>(sys.s[si], x, y, zl, dx, dy, dz, dummy, status);
+    }
+    if (sys.conformal) return;   // conformal frame / gather gradients are not propagated
+    // planar DOE hit: h = p + t d, t = (z_doe - p_z) / d_z
+    const float zld = zl - sys.s[sys.doe_index].gap;
+    const float t = -zld / dz;
+    const float gt = gx * dx + gy * dy + gz * dz;
+    gdx += gx * t; gdy += gy * t; gdz += gz * t;
+    gz += -gt / dz;
+    gdz += -gt * t / dz;
+    gs[sys.doe_index * RW_NGRAD + 0] += gt / dz;
+    for (int si = sys.doe_index - 1; si >= 0; --si) {
+        float gnb = 0.f;
+        trace_one_adjoint(sys.s[si], st[si], gx, gy, gz, gdx, gdy, gdz, gs + si * RW_NGRAD, &gnb);
+        if (si > 0) gs[(si - 1) * RW_NGRAD + 7] += gnb;
+    }
+}
+
+// CTA reduction of per-thread surface gradients gs into dsurf (double);
+// `dred` is shared scratch of RW_MAXS * RW_NGRAD * warps doubles.
+__device__ __forceinline__ void reduce_surface_grads(const DSys& sys, const float* gs,
+                                                     double* dred, double* __restrict__ dsurf) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    for (int si = 0; si < sys.nsurf; ++si)
+        for (int k = 0; k < RW_NGRAD; ++k) {
+            float v = gs[si * RW_NGRAD + k];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) dred[(si * RW_NGRAD + k) * (RW_THREADS / 32) + warp] = (double)v;
+        }
+    __syncthreads();
+    for (int i = threadIdx.x; i < sys.nsurf * RW_NGRAD; i += RW_THREADS) {
+        double v = 0.0;
+        for (int w = 0; w < RW_THREADS / 32; ++w) v += dred[i * (RW_THREADS / 32) + w];
+        if (v != 0.0) atomicAdd(dsurf + i, v);
+    }
+}

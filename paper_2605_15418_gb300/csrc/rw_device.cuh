@@ -160,7 +160,8 @@ __device__ __forceinline__ bool intersect_local(const DSurf& S, float x, float y
             if (gp == 0.f) return false;
             float step = g / gp;
             t1 -= step;
-            if (fabsf(step) <= 1e-7f * (fabsf(t1) + 1e-3f)) { conv = true; break; }
+            // a few FP32 ulps of t1: a one-ulp limit cycle must still count as converged
+            if (fabsf(step) <= 5e-7f * (fabsf(t1) + 1e-3f)) { conv = true; break; }
         }
         if (!conv) { if (status) atomicOr(status, RW_ST_NOTCONV); return false; }
     }

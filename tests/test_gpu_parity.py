@@ -133,11 +133,13 @@ def test_forward_conformal_asphere(RW, ctx):
     w = R.configs.c4(n_side=19, D=32, n_fields=3, max_field_deg=20.0, map_side=512,
                      lams=(550e-6, 656e-6))
     w.system.sensor.pitch = 20e-3
+    ctx.device_status()
     sim = RW.Simulator(w, ctx=ctx)
     psf = sim.forward().cpu().numpy()
     ref = oracle_psf(w)
     assert ref.sum() > 0
     assert rel_l2(psf, ref) <= PSF_TOL, rel_l2(psf, ref)
+    assert ctx.device_status() == 0        # every asphere Newton iteration converged
 
 
 def test_forward_coherent_window_and_full(RW, ctx):
@@ -367,6 +369,7 @@ def test_visibility_mask_backward_equals_full_backward(RW, ctx, D, n_side):
     """The adjoint restricted to rays the forward saw reach the sensor gives
     the same gradients (rays that deposit nothing have zero gradient)."""
     w = _c2_small(n_side=n_side, D=D, map_side=256)
+    ctx.device_status()                     # clear flags left by earlier calls
     sim = RW.Simulator(w, ctx=ctx)
     vis = RW.alloc_vis(sim.n_rays, D, sim.dev)
     psf_v = sim.forward(vis=vis)
@@ -381,6 +384,7 @@ def test_visibility_mask_backward_equals_full_backward(RW, ctx, D, n_side):
     torch.cuda.synchronize()
     assert rel_l2(culled[0].cpu().numpy(), full[0].cpu().numpy()) < 1e-5
     assert rel_l2(culled[2].cpu().numpy(), full[2].cpu().numpy()) < 1e-5
+    assert ctx.device_status() == 0        # no work-list overflow, no Newton failure
     # the mask agrees with the oracle's on-sensor set except at the sensor edge
     bits = np.unpackbits(vis.cpu().numpy().view(np.uint8), bitorder="little")
     frac = bits.mean()
