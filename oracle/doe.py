@@ -9,11 +9,17 @@ wavevectors by Gumbel-max with a softmax relaxation for gradients (third
 paragraph of the same section).
 
 Readings (the paper does not fix these):
-* spectrum: U~_j = (1/D^2) sum_{a,b} T_ab exp(-i (k_ju s_a + k_jv t_b)), with
+* spectrum: U~_j = c sum_{a,b} T_ab exp(-i (k_ju s_a + k_jv t_b)), with
   (s_a, t_b) the tangent-plane offsets of sample (a, b) from the hit point;
-  this is the Fourier-series coefficient of the patch referenced to the hit
-  point, and sum_j |U~_j|^2 = mean |T|^2 (Parseval);
-* k-grid: k_j = 2 pi j / (M p), j in [-M/2, M/2), M = D (no zero padding);
+  without padding c = 1/D^2: the Fourier-series coefficient of the patch
+  referenced to the hit point, and sum_j |U~_j|^2 = mean |T|^2 (Parseval);
+* zero padding (section "Benchmark and Inverse Design Demonstrations": patches
+  padded to a larger area for a finer angular spectrum): the D x D samples
+  are transformed on the grid of M = P D; a coherent sensor takes
+  c = 1/M^2 (the Fourier-series coefficient of the padded, M-periodic
+  patch, so the wavelet sum reproduces the padded field), an incoherent one
+  c = 1/(D M) (so that sum_j |U~_j|^2 = mean |T|^2 stays the ray's power);
+* k-grid: k_j = 2 pi j / (M p), j in [-M/2, M/2);
 * planar patch (gather 'nearest'): columns floor(x/p + W/2) - D/2 .. + D/2 - 1,
   rows likewise, offsets = pixel centres minus the hit point, so a binary map
   stays binary; conformal patch (gather 'bilinear'): samples at
@@ -120,16 +126,19 @@ def kgrid(M, pitch):
     return TWO_PI * j / (M * pitch)
 
 
-def spectrum(T, s, t, pitch):
-    """Direct separable DFT: U~[jv, ju] = (1/D^2) sum_b sum_a
-    exp(-i k_jv t_b) T[b, a] exp(-i k_ju s_a)."""
+def spectrum(T, s, t, pitch, M=None, coherent=False):
+    """Direct separable DFT on the k-grid of size M (default D, no padding):
+    U~[jv, ju] = c sum_b sum_a exp(-i k_jv t_b) T[b, a] exp(-i k_ju s_a),
+    c = 1/M^2 (coherent sensor) or 1/(D M) (incoherent); both 1/D^2 at M = D.
+    The zero samples of a padded patch add nothing to the sums."""
     D = T.shape[-1]
-    M = D
+    M = D if M is None else int(M)
     k = kgrid(M, pitch)
     Eu = torch.polar(torch.ones(1, dtype=torch.float64), -(k[None, :, None] * s[:, None, :]))
     Ev = torch.polar(torch.ones(1, dtype=torch.float64), -(k[None, :, None] * t[:, None, :]))
+    c = 1.0 / (M * M) if coherent else 1.0 / (D * M)
     # [N, M, D] @ [N, D, D] @ [N, D, M]
-    return (Ev @ T @ Eu.transpose(1, 2)) / float(D * D)
+    return (Ev @ T @ Eu.transpose(1, 2)) * c
 
 
 def outgoing(d_in, u, v, n, k0, n_in, n_out, M, pitch):
@@ -166,8 +175,8 @@ def doe_step(ray, doe_surface, doe, phi, amp, lam, n_in, n_out, ray_ids=None,
         T, s, t = gather_nearest(hit, phi, amp, lam, doe)
     else:
         T, s, t = gather_bilinear(hit, u, v, phi, amp, lam, doe)
-    U = spectrum(T, s, t, doe.pitch)
-    M = doe.D
+    M = doe.pad * doe.D
+    U = spectrum(T, s, t, doe.pitch, M=M, coherent=coherent)
     k0 = TWO_PI / lam
     dvec, prop = outgoing(d, u, v, nrm, k0, n_in, n_out, M, doe.pitch)
     alive_in = ray["alive"] & ok

@@ -46,6 +46,8 @@ class DOE:
     gather 'nearest' (planar default) or 'bilinear' (conformal default).
     emit 'exhaustive' (one secondary ray per propagating bin) or 'sampled'
     (n_ssr Gumbel-max draws from p ~ |U~|).
+    pad P >= 1: the D x D patch is zero-padded to M = P D samples before its
+    transform, so the spectrum is sampled on the finer k-grid 2 pi j / (M p).
     """
     phi: np.ndarray
     pitch: float
@@ -59,6 +61,11 @@ class DOE:
     n_ssr: int = 0
     seed: int = 0
     rng_offset: int = 0
+    pad: int = 1
+
+    @property
+    def M(self):
+        return int(self.pad) * int(self.D)
 
     @property
     def H(self):

@@ -19,6 +19,7 @@ from oracle import doe as DO
 from oracle import geometry as G
 from oracle import loss as L
 from oracle import pipeline as P
+from oracle import pipeline as P_
 from oracle import sensor as S
 from oracle.philox import philox4x32_10, sample_uniforms
 
@@ -417,3 +418,123 @@ def test_bilinear_splat_hand_computed_taps():
     ref[0, 7] += 1 * 0.5          # right neighbour (i = 8) is off the sensor
     ref[1, 0] += 5 * 0.5          # left neighbour (i = -1) is off the sensor
     assert torch.allclose(img, ref, atol=1e-12)
+
+
+# ------------------------------------------------------------------ zero padding (M = P D)
+def _random_patch(seed, N, D, p):
+    g = torch.Generator().manual_seed(seed)
+    T = torch.randn(N, D, D, dtype=F64, generator=g) + 1j * torch.randn(
+        N, D, D, dtype=F64, generator=g)
+    s0 = torch.rand(N, 1, dtype=F64, generator=g) * p - (D / 2) * p
+    t0 = torch.rand(N, 1, dtype=F64, generator=g) * p - (D / 2) * p
+    ar = torch.arange(D, dtype=F64)[None] * p
+    return T, s0 + ar, t0 + ar
+
+
+@pytest.mark.parametrize("P", [2, 4])
+@pytest.mark.parametrize("coherent", [False, True])
+def test_padded_spectrum_every_Pth_bin_is_the_unpadded_spectrum(P, coherent):
+    """k_{P m} on the grid of M = P D is k_m on the grid of D, and the zero
+    samples add nothing, so the padded transform restricted to every P-th
+    bin is the unpadded one times c_M / c_D = (D/M)^2 (coherent) or D/M."""
+    D, p = 16, 1e-3
+    M = P * D
+    T, s, t = _random_patch(11, 3, D, p)
+    U1 = DO.spectrum(T, s, t, p, M=D, coherent=coherent)
+    UP = DO.spectrum(T, s, t, p, M=M, coherent=coherent)
+    ratio = (D / M) ** 2 if coherent else D / M
+    sub = UP[:, M // 2 - P * (D // 2)::P, M // 2 - P * (D // 2)::P]
+    assert sub.shape == U1.shape
+    assert torch.allclose(sub, U1 * ratio, rtol=0, atol=1e-14 * float(U1.abs().max()))
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_padded_spectrum_parseval_both_normalisations(P):
+    """Parseval on the M-point grid: sum |X_j|^2 = M^2 sum |T|^2, so the
+    incoherent weights keep sum |U~|^2 = mean |T|^2 for every padding and the
+    coherent coefficients give sum |U~|^2 = sum |T|^2 / M^2."""
+    D, p = 16, 1e-3
+    M = P * D
+    T, s, t = _random_patch(12, 4, D, p)
+    Ui = DO.spectrum(T, s, t, p, M=M, coherent=False)
+    Uc = DO.spectrum(T, s, t, p, M=M, coherent=True)
+    e = (T.abs() ** 2).sum((1, 2))
+    assert torch.allclose((Ui.abs() ** 2).sum((1, 2)), e / (D * D), rtol=1e-12)
+    assert torch.allclose((Uc.abs() ** 2).sum((1, 2)), e / (M * M), rtol=1e-12)
+
+
+def test_padded_plane_wave_spectrum_is_the_dirichlet_kernel():
+    """A plane wave exp(i k_m x) cut to D samples: on the padded grid each
+    bin is a geometric series, sum_a exp(i delta x_a) with delta = k_m - k_j,
+    = exp(i delta x_0) (1 - exp(i delta D p)) / (1 - exp(i delta p)) (D when
+    delta = 0); the spectrum referred to the hit multiplies by exp(i k_j x_P)."""
+    D, P, p = 16, 2, 1e-3
+    M = P * D
+    m = 3
+    km = 2 * math.pi * m / (D * p)
+    xP, yP = 0.37 * p, -0.21 * p
+    xa = (np.arange(D) - D / 2 + 0.5) * p
+    T = torch.polar(torch.ones(D, dtype=F64), torch.from_numpy(km * xa))[None, :].expand(D, D)
+    U = DO.spectrum(T[None], torch.from_numpy(xa - xP)[None], torch.from_numpy(xa - yP)[None],
+                    p, M=M, coherent=True)[0].numpy()
+
+    def series(delta, x0):
+        if abs(delta) < 1e-9:
+            return D + 0j
+        return np.exp(1j * delta * x0) * (1 - np.exp(1j * delta * D * p)) / (1 - np.exp(1j * delta * p))
+
+    for jv in range(-M // 2, M // 2):
+        for ju in range(-M // 2, M // 2):
+            ku, kv = 2 * math.pi * ju / (M * p), 2 * math.pi * jv / (M * p)
+            fu = series(km - ku, xa[0]) * np.exp(1j * ku * xP)
+            fv = series(-kv, xa[0]) * np.exp(1j * kv * yP)
+            assert U[jv + M // 2, ju + M // 2] == pytest.approx(fu * fv / (M * M), abs=1e-14)
+
+
+def test_padded_coherent_full_patch_equals_padded_angular_spectrum():
+    """One patch covering the whole map, padded to M = 2D: the wavelet sum of
+    Eq. 2 is the angular-spectrum propagation of the zero-padded, M-periodic
+    field (NumPy FFT), seen on the original pixels."""
+    D, P, p, lam, zs = 32, 2, 1e-3, 0.8e-3, 0.03
+    M = P * D
+    rng = np.random.Generator(np.random.PCG64(6))
+    phi = rng.uniform(0, 2 * math.pi, (D, D)).astype(np.float32)
+    amp = rng.uniform(0.3, 1.0, (D, D)).astype(np.float32)
+    doe = R.DOE(phi=phi, amp=amp, pitch=p, D=D, lambda0=lam, pad=P)
+    sen = R.Sensor(z=zs, nx=D, ny=D, pitch=p, coherent=True)
+    sysm = R.System([R.Surface(R.PLANE, 0.0)], 0, doe, sen)
+    job = R.Job(lam=lam, grid_n=1, spacing=0.0, x0=0.31 * p, y0=0.77 * p)
+    img = P_.psf(R.systems.Workload("P5-pad", sysm, [job], z_start=-0.01))[0].numpy()
+    Tpad = np.zeros((M, M), np.complex128)
+    Tpad[:D, :D] = amp.astype(np.float64) * np.exp(1j * phi.astype(np.float64))
+    ref = np.abs(asm_propagate(Tpad, p, lam, zs)[:D, :D]) ** 2
+    assert np.allclose(img, ref, rtol=1e-9, atol=1e-12 * ref.max())
+    # the unpadded sum is the periodic (wrapped) field instead: a different image
+    img1 = P_.psf(R.systems.Workload("P5", R.System([R.Surface(R.PLANE, 0.0)], 0,
+                                                    R.DOE(phi=phi, amp=amp, pitch=p, D=D,
+                                                          lambda0=lam), sen),
+                                     [job], z_start=-0.01))[0].numpy()
+    assert np.abs(img1 - img).max() > 1e-3 * img.max()
+
+
+def test_padded_grating_orders_keep_their_angles_and_power():
+    """Binary grating, D = 32, P = 2: order m sits at bin 2 P m with
+    |U~|^2 = eta_m / P^2 (incoherent weights), directions still follow the
+    grating equation, and the whole spectrum keeps unit power."""
+    w = R.configs.c1(n_side=2, angles_deg=(0.0,))
+    sysm, job = w.system, w.jobs[0]
+    P = 2
+    sysm.doe.pad = P
+    em, _ = P_.emit_job(sysm, job, w.z_start, P_.params_of(sysm), *P_.map_tensors(sysm))
+    U = em["U"]
+    M = P * sysm.doe.D
+    c = M // 2
+    lam, period = job.lam, 16 * sysm.doe.pitch
+    eta = (U.abs() ** 2)
+    for r in range(U.shape[0]):
+        assert float(eta[r].sum()) == pytest.approx(1.0, abs=1e-12)
+        for m in range(-7, 8, 2):
+            assert float(eta[r, c, c + 2 * P * m]) == pytest.approx(
+                binary_grating_efficiency(m, 16) / P ** 2, abs=1e-12)
+            dvec = em["d"][r, c, c + 2 * P * m]
+            assert float(dvec[0]) == pytest.approx(m * lam / period, abs=1e-13)
