@@ -220,7 +220,7 @@ def main():
     dphi = torch.zeros_like(sim.phi)
     dsurf = torch.zeros(len(sysm.surfaces), 8, dtype=torch.float64, device=dev)
     loss = torch.empty(3, dtype=torch.float64, device=dev)
-    vis = RW.alloc_vis(n_rays, sysm.doe.D, dev)      # 1 bit per secondary ray
+    vis = RW.alloc_vis(n_rays, sysm.doe.M, dev)      # 1 bit per secondary ray
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
 

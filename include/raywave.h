@@ -11,7 +11,9 @@
  *   A2  DOE intersection and tangent frame (u, v, n)   [section "Ray-Wave
  *       Simulator Formalism", second paragraph]
  *   A3  D x D patch of the transmission U = A exp(i phi) centred on the hit
- *   A4  angular spectrum U~(k_u, k_v) of the patch (Fourier transform)
+ *   A4  angular spectrum U~(k_u, k_v) of the patch (Fourier transform), on
+ *       the grid of M = P D points when the patch is zero-padded by P
+ *       (section "Benchmark and Inverse Design Demonstrations")
  *   A5  secondary rays along the propagating wavevectors, weight U~ / p (Eq. 1);
  *       sampled mode draws wavevectors by Gumbel-max (same section, third
  *       paragraph)
@@ -101,7 +103,7 @@ typedef struct {
     double lambda0;        /* design wavelength of phi (HEIGHT model), mm */
     const float* phi;      /* device, [H][W] radians */
     const float* amp;      /* device, [H][W], or NULL for amplitude 1 */
-    int32_t D;             /* patch side: 16, 32, 64, 96 or 128 */
+    int32_t D;             /* patch side in pixels: 16, 32, 64 or 96 */
     int32_t gather;        /* RW_GATHER_* */
     int32_t emit;          /* RW_EMIT_* */
     int32_t n_ssr;         /* draws per incident ray in sampled mode */
@@ -109,6 +111,11 @@ typedef struct {
     int32_t dft;           /* RW_DFT_*: TC only in rw_patch_spectra (fused calls: FFT32) */
     uint64_t seed;         /* Philox key for sampled mode */
     uint64_t rng_offset;   /* Philox counter word 3 for sampled mode */
+    int32_t pad;           /* zero-padding factor P (0 or 1: none): the D x D patch is
+                            * transformed on M = P D points, M in {16, 32, 64, 96, 128};
+                            * bins are k_j = 2 pi j / (M pitch), and U~ is scaled by
+                            * 1/M^2 (coherent sensor) or 1/(D M) (incoherent) */
+    int32_t reserved_doe;  /* 0 */
 } rw_doe;
 
 /* Sensor plane z = const.  Pixel (i, j) of job J is centred at
@@ -154,8 +161,8 @@ typedef struct {
 } rw_rays;
 
 /* Secondary rays written by rw_doe_emit.  Slot s = i * S + b for incident
- * ray i and bin/draw b, S = D*D (exhaustive; b = (j_v + D/2) * D + (j_u + D/2))
- * or n_ssr (sampled).  Dropped rays (evanescent, missed DOE) have a = 0 and
+ * ray i and bin/draw b, S = M*M with M = pad * D (exhaustive;
+ * b = (j_v + M/2) * M + (j_u + M/2)) or n_ssr (sampled).  Dropped rays (evanescent, missed DOE) have a = 0 and
  * d = 0.  hit/opl are per incident ray. */
 typedef struct {
     int64_t capacity;                /* slots available: >= n_incident * S */
@@ -209,25 +216,26 @@ rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
                      int32_t njob, const rw_rays* rays, float* psf);
 
 /* rw_forward that also records which secondary rays reached the sensor:
- * bit (f & 31) of vis[i * D*D/32 + f/32] is set when bin f of incident ray i
+ * bit (f & 31) of vis[i * M*M/32 + f/32] is set when bin f of incident ray i
  * (job order) hit the sensor plane with a bilinear tap on the sensor.  One
- * bit per secondary ray (D = 64: 512 bytes per incident ray).  Needs the
+ * bit per secondary ray (M = 64: 512 bytes per incident ray).  Needs the
  * incoherent sensor and exhaustive emission.
- * Errors: as rw_forward, RW_ECAPACITY (vis_words < n_rays * D*D / 32). */
+ * Errors: as rw_forward, RW_ECAPACITY (vis_words < n_rays * M*M / 32). */
 rw_status rw_forward_vis(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
                          const rw_rays* rays, float* psf, uint32_t* vis, int64_t vis_words);
 
 /* ---- A3..A4: patch spectra only ----------------------------------------- */
 
 /* Trace every job's rays to the DOE and write the angular spectrum of each
- * patch, U~[j_v][j_u] referred to the hit point and normalised by 1/D^2
- * (section "Ray-Wave Simulator Formalism", second paragraph), as complex
- * float pairs: spectra[(i * D + (j_v + D/2)) * D + (j_u + D/2)] for incident
+ * patch, U~[j_v][j_u] referred to the hit point with the normalisation of
+ * doe.pad (1/D^2 without padding; section "Ray-Wave Simulator Formalism",
+ * second paragraph), as complex float pairs:
+ * spectra[(i * M + (j_v + M/2)) * M + (j_u + M/2)], M = pad * D, for incident
  * ray i in job order; rays that miss the DOE give zeros.  doe.dft selects the
- * implementation: RW_DFT_FFT32 (FP32 shared-memory FFT, any supported D) or
+ * implementation: RW_DFT_FFT32 (FP32 shared-memory FFT, any supported M) or
  * RW_DFT_TC (tensor-core contraction F X F^T with a BF16x3 split and FP32
- * accumulation, D = 64 only).  capacity counts complex entries.
- * Errors: RW_EINVAL, RW_ECAPACITY (capacity < n_rays * D * D). */
+ * accumulation, D = 64 without padding only).  capacity counts complex entries.
+ * Errors: RW_EINVAL, RW_ECAPACITY (capacity < n_rays * M * M). */
 rw_status rw_patch_spectra(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
                            const rw_rays* rays, float* spectra, int64_t capacity);
 
@@ -248,7 +256,8 @@ rw_status rw_loss_eq3(rw_ctx* ctx, const float* psf, const float* target, int64_
  *         (may be NULL).
  * Patches and spectra are recomputed, not stored.  Supported: incoherent
  * sensor, exhaustive or sampled emission (straight-through Gumbel-softmax
- * with temperature 1). */
+ * with temperature 1), M = pad * D <= 96 (M = 128 only through
+ * rw_backward_vis with exhaustive emission). */
 rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
                       int32_t njob, const rw_rays* rays, const float* dl_dpsf,
                       float* dphi, float* damp, double* dsurf);

@@ -35,7 +35,8 @@ class rw_doe(C.Structure):
                 ("lambda0", C.c_double), ("phi", C.c_void_p), ("amp", C.c_void_p),
                 ("D", C.c_int32), ("gather", C.c_int32), ("emit", C.c_int32),
                 ("n_ssr", C.c_int32), ("phase_model", C.c_int32), ("dft", C.c_int32),
-                ("seed", C.c_uint64), ("rng_offset", C.c_uint64)]
+                ("seed", C.c_uint64), ("rng_offset", C.c_uint64),
+                ("pad", C.c_int32), ("reserved_doe", C.c_int32)]
 
 
 class rw_sensor(C.Structure):

@@ -42,7 +42,7 @@ class RayWavePSF(torch.autograd.Function):
         surfs = surfaces_from_params(sim.w.system.surfaces, params)
         vis = None
         if _vis_ok(sim):
-            vis = RW.alloc_vis(sim.n_rays, sim.w.system.doe.D, sim.dev)
+            vis = RW.alloc_vis(sim.n_rays, sim.w.system.doe.M, sim.dev)
         psf = sim.forward(phi=phi.detach().contiguous(), surfaces=surfs, vis=vis)
         ctx.sim = sim
         ctx.surfs = surfs

@@ -188,6 +188,8 @@ struct Packed {
 };
 
 static bool supported_D(int D) { return D == 16 || D == 32 || D == 64 || D == 96; }
+// transform sizes with a compiled FFT plan (M = pad * D)
+static bool supported_M(int M) { return M == 16 || M == 32 || M == 64 || M == 96 || M == 128; }
 
 static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
     if (!sys) return fail(ctx, RW_EINVAL, "sys is NULL");
@@ -202,6 +204,9 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
     if (doe.H < 1 || doe.W < 1) return fail(ctx, RW_EINVAL, "doe map size must be positive");
     if (!(doe.pitch > 0)) return fail(ctx, RW_EINVAL, "doe.pitch must be > 0");
     if (!supported_D(doe.D)) return fail(ctx, RW_EINVAL, "doe.D must be 16, 32, 64 or 96");
+    const int pad = doe.pad > 0 ? doe.pad : 1;
+    if (pad > 8 || !supported_M(pad * doe.D))
+        return fail(ctx, RW_EINVAL, "doe.pad * doe.D must be 16, 32, 64, 96 or 128");
     if (doe.gather != RW_GATHER_NEAREST && doe.gather != RW_GATHER_BILINEAR)
         return fail(ctx, RW_EINVAL, "doe.gather invalid");
     if (doe.emit != RW_EMIT_EXHAUSTIVE && doe.emit != RW_EMIT_SAMPLED)
@@ -271,6 +276,10 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
         q.inv_n_after = (float)(1.0 / s.n_after);
     }
     d.H = doe.H; d.W = doe.W; d.D = doe.D;
+    d.M = pad * doe.D;
+    // coherent: Fourier-series coefficient of the padded patch; incoherent:
+    // keeps sum |U~|^2 = mean |T|^2 (both 1/D^2 without padding)
+    d.norm = sen.coherent ? (float)(1.0 / ((double)d.M * d.M)) : (float)(1.0 / ((double)d.D * d.M));
     d.gather = doe.gather; d.emit = doe.emit; d.n_ssr = doe.n_ssr;
     d.phase_model = doe.phase_model;
     d.pitch = doe.pitch;
@@ -278,7 +287,7 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
     d.inv_pitch = (float)(1.0 / doe.pitch);
     d.seed = doe.seed;
     d.rng_offset = doe.rng_offset;
-    d.kstep = (float)(2.0 * M_PI / (doe.D * doe.pitch));
+    d.kstep = (float)(2.0 * M_PI / (d.M * doe.pitch));
     d.sensor_z = sen.z;
     d.sensor_gap = (float)(sen.z - prev_z);
     d.nx = sen.nx; d.ny = sen.ny;
@@ -348,7 +357,7 @@ static RaysIn rays_in(const rw_rays* r) {
 static size_t shared_limit_ok(rw_ctx* ctx, const DSys& d) {
     int lim = 0;
     cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-    return forward_smem_bytes(d.D, d.emit, d.n_ssr) <= (size_t)lim;
+    return forward_smem_bytes(d.M, d.emit, d.n_ssr) <= (size_t)lim;
 }
 
 // Prepare the transmission maps and device tables.  Returns device pointers.
@@ -506,7 +515,7 @@ rw_status rw_doe_emit(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int
     if (!out || !out->dx || !out->dy || !out->dz || !out->a_re || !out->a_im || !out->hx ||
         !out->hy || !out->hz || !out->opl)
         return fail(ctx, RW_EINVAL, "an emitted-ray array is NULL");
-    const long long S = (P.sys.emit == RW_EMIT_EXHAUSTIVE) ? (long long)P.sys.D * P.sys.D
+    const long long S = (P.sys.emit == RW_EMIT_EXHAUSTIVE) ? (long long)P.sys.M * P.sys.M
                                                            : (long long)P.sys.n_ssr;
     if (out->capacity < P.total * S)
         return fail(ctx, RW_ECAPACITY, "emitted capacity < n_rays * slots per ray");
@@ -540,8 +549,8 @@ static rw_status forward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* j
         if (P.sys.coherent || P.sys.emit != RW_EMIT_EXHAUSTIVE)
             return fail(ctx, RW_EINVAL, "the visibility mask needs the incoherent sensor and "
                                         "exhaustive emission");
-        if (vis_words < P.total * (int64_t)P.sys.D * P.sys.D / 32)
-            return fail(ctx, RW_ECAPACITY, "vis_words < n_rays * D * D / 32");
+        if (vis_words < P.total * (int64_t)P.sys.M * P.sys.M / 32)
+            return fail(ctx, RW_ECAPACITY, "vis_words < n_rays * M * M / 32");
     }
     const long long npx = (long long)P.sys.nx * P.sys.ny * njob;
     RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
@@ -617,26 +626,31 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
     if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
     if (!dl_dpsf) return fail(ctx, RW_EINVAL, "dl_dpsf is NULL");
     if (P.sys.coherent) return fail(ctx, RW_EINVAL, "backward supports the incoherent sensor only");
-    {
+    // the split adjoint (three kernels) needs the mask and a host read-back of
+    // its count, so it runs eagerly; otherwise the fused kernel
+    const bool split = vis && P.sys.emit == RW_EMIT_EXHAUSTIVE && !capturing(ctx);
+    if (!split) {
         int lim = 0;
         cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
-        if (backward_smem_needed(P.sys) > (size_t)lim)
-            return fail(ctx, RW_EINVAL, "patch size / n_ssr too large for the adjoint's shared memory");
+        if (P.sys.M > 96 || backward_smem_needed(P.sys) > (size_t)lim)
+            return fail(ctx, RW_EINVAL, "patch size / n_ssr too large for the fused adjoint's "
+                                        "shared memory (M = 128 needs exhaustive emission with "
+                                        "a visibility mask, outside graph capture)");
     }
     if (damp && !sys->doe.amp) return fail(ctx, RW_EINVAL, "damp requires doe.amp");
     if (vis) {
         if (P.sys.emit != RW_EMIT_EXHAUSTIVE)
             return fail(ctx, RW_EINVAL, "the visibility mask needs exhaustive emission");
-        if (vis_words < P.total * (int64_t)P.sys.D * P.sys.D / 32)
-            return fail(ctx, RW_ECAPACITY, "vis_words < n_rays * D * D / 32");
+        if (vis_words < P.total * (int64_t)P.sys.M * P.sys.M / 32)
+            return fail(ctx, RW_ECAPACITY, "vis_words < n_rays * M * M / 32");
     }
     if (P.total == 0 || (!dphi && !damp && !dsurf)) return RW_OK;
     float2* T; DJob* dj; long long* dp;
     if ((st = prepare(ctx, sys, P, &T, &dj, &dp)) != RW_OK) return st;
-    if (vis && P.sys.emit == RW_EMIT_EXHAUSTIVE && P.sys.D <= 64 && !capturing(ctx)) {
+    if (split) {
         // Split adjoint: count the visible secondary rays (one host sync), size
         // the work list, then spectra+list / trace+reverse / conjugate FFT+scatter.
-        const long long nwords = P.total * (long long)P.sys.D * P.sys.D / 32;
+        const long long nwords = P.total * (long long)P.sys.M * P.sys.M / 32;
         unsigned long long* dcount = reinterpret_cast<unsigned long long*>(
             reinterpret_cast<char*>(ctx->misc.p) + 128);
         RW_CUDA(launch_bs_count(lctx(ctx), vis, nwords, dcount), "visible count");
@@ -706,10 +720,10 @@ rw_status rw_patch_spectra(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs
     if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
     if (!spectra) return fail(ctx, RW_EINVAL, "spectra is NULL");
     const int tc = sys->doe.dft == RW_DFT_TC;
-    if (tc && sys->doe.D != 64)
-        return fail(ctx, RW_EINVAL, "the tensor-core patch transform supports D = 64");
-    if (capacity < P.total * (int64_t)sys->doe.D * sys->doe.D)
-        return fail(ctx, RW_ECAPACITY, "spectra capacity < n_rays * D * D");
+    if (tc && (P.sys.D != 64 || P.sys.M != 64))
+        return fail(ctx, RW_EINVAL, "the tensor-core patch transform supports D = 64 without padding");
+    if (capacity < P.total * (int64_t)P.sys.M * P.sys.M)
+        return fail(ctx, RW_ECAPACITY, "spectra capacity < n_rays * M * M");
     if (P.total == 0) return RW_OK;
     float2* T; DJob* dj; long long* dp;
     if ((st = prepare(ctx, sys, P, &T, &dj, &dp)) != RW_OK) return st;

@@ -17,15 +17,16 @@
 // dL/dy_ij = Re(conj(dL/da_i) a_in w_j) + dL/dd_i . dir_j.
 //
 // dL/dU~ goes through the adjoint of the patch transform (the conjugate
-// FFT) to dL/dT on the D x D patch; dT/dphi = i (lambda0/lambda) T and
-// dT/dA = exp(i psi) give the map gradients, added with atomics.  Surface
+// FFT of the zero-padded M x M buffer) to dL/dT on the D x D patch;
+// dT/dphi = i (lambda0/lambda) T and dT/dA = exp(i psi) give the map
+// gradients, added with atomics.  Surface
 // gradients are kept per thread and reduced once per CTA into dsurf.
 #include "rw_bwd_common.cuh"
 
 // ------------------------------------------------------------------ sampled
 // Shared scratch of the sampled adjoint (after the exhaustive layout).
-__host__ __device__ inline size_t sampled_bwd_bytes(int D, int N) {
-    return (size_t)D * D * (4 + 8 + 4) + (size_t)N * (4 + 4 + 4 + 8 + 12 + 4) + 64 * 4;
+__host__ __device__ inline size_t sampled_bwd_bytes(int M, int N) {
+    return (size_t)M * M * (4 + 8 + 4) + (size_t)N * (4 + 4 + 4 + 8 + 12 + 4) + 64 * 4;
 }
 
 // Block-wide sum (all threads get the result); `red` holds >= 8 floats.
@@ -51,7 +52,7 @@ __device__ __forceinline__ void gumbel_group(const DSys& sys, long long gid, int
     g4[3] = -logf(-logf(u01(w.w)));
 }
 
-template <int D, int NS>
+template <int M, int NS>
 __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAtDoe& R,
                                                     const float2* X, const float2* phu,
                                                     const float2* phv,
@@ -59,8 +60,10 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
                                                     unsigned char* scr, float* acc,
                                                     SurfGrads<NS>& SG, float* gs,
                                                     unsigned* status) {
-    constexpr int NB = D * D;
+    constexpr int NB = M * M;
+    constexpr int S_ = Patch<M>::S;
     const int N = sys.n_ssr;
+    const float norm = sys.norm;
     float* logp = reinterpret_cast<float*>(scr);
     float2* gwb = reinterpret_cast<float2*>(logp + NB);
     float* glogp = reinterpret_cast<float*>(gwb + NB);
@@ -76,11 +79,11 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
     // ---- power weights m = |U~|^2 over propagating bins, p = m / S
     float part = 0.f;
     for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
-        const int jvi = f / D, jui = f - (f / D) * D;
+        const int jvi = f / M, jui = f - (f / M) * M;
         float dx, dy, dz;
         float m = 0.f;
-        if (bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
-            const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+        if (bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
+            const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
             m = U.x * U.x + U.y * U.y;
         }
         logp[f] = m;
@@ -139,17 +142,17 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
         float2 g_a = make_float2(0.f, 0.f);
         float gdx = 0.f, gdy = 0.f, gdz = 0.f;
         if (jb >= 0) {
-            const int jvi = jb / D, jui = jb - (jb / D) * D;
+            const int jvi = jb / M, jui = jb - (jb / M) * M;
             float dx, dy, dz;
-            if (bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
-                const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+            if (bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
+                const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
                 const float sc = __expf(-0.5f * logp[jb]) / sqN;     // 1 / sqrt(N p)
                 const float2 a = cscale(cmul(ain, U), sc);
                 const float w = a.x * a.x + a.y * a.y;
                 float gw, gx, gy, gz;
                 if (secondary_adjoint<NS>(sys, R, gimg, dx, dy, dz, w, gw, gx, gy, gz, gdx, gdy,
                                           gdz, SG, gs, status)) {
-                    emission_adjoint(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz, gx, gy, gz,
+                    emission_adjoint(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz, gx, gy, gz,
                                      gdx, gdy, gdz, acc);
                     g_a = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
                     // hard path: a = a_in w_jb  ->  dL/dw_jb += conj(a_in) dL/da
@@ -186,10 +189,10 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
                     const int jb = 4 * Gq + q;
                     if (jb >= NB || !(logp[jb] > -INFINITY)) continue;
                     const float soft = __expf(logp[jb] + g4[q] - mxi) * iz;
-                    const int jvi = jb / D, jui = jb - (jb / D) * D;
+                    const int jvi = jb / M, jui = jb - (jb / M) * M;
                     float dx, dy, dz;
-                    bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz);
-                    const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+                    bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz);
+                    const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
                     const float2 aw = cscale(cmul(ain, U), __expf(-0.5f * logp[jb]) / sqN);
                     const float gy = gai.x * aw.x + gai.y * aw.y + gdi0 * dx + gdi1 * dy + gdi2 * dz;
                     if (pass == 0) accd += soft * gy;
@@ -207,8 +210,8 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
     float sg = 0.f, sgp = 0.f;
     for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
         if (!(logp[f] > -INFINITY)) continue;
-        const int jvi = f / D, jui = f - (f / D) * D;
-        const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+        const int jvi = f / M, jui = f - (f / M) * M;
+        const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
         const float2 w = cscale(U, __expf(-0.5f * logp[f]) / sqN);
         const float2 gwv = gwb[f];
         // dL/dp from w (times p)
@@ -218,12 +221,12 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
     const float Sg = block_sum(sg, red);
     const float Sgp = block_sum(sgp, red);
     for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
-        const int jvi = f / D, jui = f - (f / D) * D;
-        int mu = jui + D / 2; if (mu >= D) mu -= D;
-        int mv = jvi + D / 2; if (mv >= D) mv -= D;
+        const int jvi = f / M, jui = f - (f / M) * M;
+        int mu = jui + M / 2; if (mu >= M) mu -= M;
+        int mv = jvi + M / 2; if (mv >= M) mv -= M;
         float2 gU = make_float2(0.f, 0.f);
         if (logp[f] > -INFINITY) {
-            const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+            const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
             const float p = __expf(logp[f]);
             const float m = p * S;
             const float isq = __expf(-0.5f * logp[f]) / sqN;
@@ -235,46 +238,47 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
             gU = make_float2(2.f * U.x * gm + gwv.x * isq, 2.f * U.y * gm + gwv.y * isq);
         }
         const float2 ph = cmul(phu[jui], phv[jvi]);
-        G[mv * D + mu] = cscale(cmulc(gU, ph), 1.f / (float)(D * D));
+        G[mv * S_ + mu] = cscale(cmulc(gU, ph), norm);
     }
 }
 
 // Reverse of exhaustive bin f of the current incident ray; writes its dL/dX.
-template <int D, int NS>
+template <int M, int NS>
 __device__ __forceinline__ void exh_bin_adjoint(const DSys& sys, const RayAtDoe& R,
                                                 const float2* X, const float2* phu,
                                                 const float2* phv, const float* __restrict__ gimg,
                                                 float2* G, float2 ain, int f, float (&acc)[6],
                                                 SurfGrads<NS>& SG, float* gs, unsigned* status) {
-    const int jvi = f / D, jui = f - (f / D) * D;
-    int mu = jui + D / 2; if (mu >= D) mu -= D;
-    int mv = jvi + D / 2; if (mv >= D) mv -= D;
+    const int jvi = f / M, jui = f - (f / M) * M;
+    int mu = jui + M / 2; if (mu >= M) mu -= M;
+    int mv = jvi + M / 2; if (mv >= M) mv -= M;
+    const float norm = sys.norm;
     float2 gU = make_float2(0.f, 0.f);
     float dx, dy, dz;
-    if (bin_direction<(NS >= 0)>(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
-        const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+    if (bin_direction<(NS >= 0)>(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
+        const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
         const float2 a = cmul(ain, U);
         const float w = a.x * a.x + a.y * a.y;
         float gw, gx, gy, gz, gdx, gdy, gdz;
         if (secondary_adjoint<NS>(sys, R, gimg, dx, dy, dz, w, gw, gx, gy, gz, gdx, gdy, gdz, SG,
                                   gs, status)) {
-            emission_adjoint(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz, gx, gy, gz, gdx, gdy,
+            emission_adjoint(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz, gx, gy, gz, gdx, gdy,
                              gdz, acc);
             const float2 ga = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
             gU = cmulc(ga, ain);          // conj(a_in) * dL/da
         }
     }
-    // dL/dX[m] = conj(phu phv) / D^2 * dL/dU~
+    // dL/dX[m] = conj(phu phv) norm dL/dU~
     const float2 ph = cmul(phu[jui], phv[jvi]);
-    G[mv * D + mu] = cscale(cmulc(gU, ph), 1.f / (float)(D * D));
+    G[mv * Patch<M>::S + mu] = cscale(cmulc(gU, ph), norm);
 }
 
 // ------------------------------------------------------------------ kernel
-template <int D>
-struct BwdOcc { static constexpr int value = D == 96 ? 1 : 2; };
+template <int M>
+struct BwdOcc { static constexpr int value = M >= 96 ? 1 : 2; };
 
-template <int D, int NS>
-__global__ void __launch_bounds__(RW_THREADS, BwdOcc<D>::value)
+template <int M, int NS>
+__global__ void __launch_bounds__(RW_THREADS, BwdOcc<M>::value)
 k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
            int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
            const float* __restrict__ amp, const float* __restrict__ gpsf,
@@ -282,15 +286,15 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
            unsigned* status, const unsigned* __restrict__ vis) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* X = reinterpret_cast<float2*>(smem);
-    float2* tw = X + D * D;
-    float2* phu = tw + D;
-    float2* phv = phu + D;
-    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + D);
-    float2* G = reinterpret_cast<float2*>(smem + sampled_scratch_offset(D));
-    BwdRay* bray = reinterpret_cast<BwdRay*>(G + D * D);
+    float2* tw = X + Patch<M>::ELEMS;
+    float2* phu = tw + M;
+    float2* phv = phu + M;
+    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + M);
+    float2* G = reinterpret_cast<float2*>(smem + sampled_scratch_offset(M));
+    BwdRay* bray = reinterpret_cast<BwdRay*>(G + Patch<M>::ELEMS);
     float* red = reinterpret_cast<float*>(bray + RW_TILE);   // [8 warps][9]
     unsigned char* sscr = reinterpret_cast<unsigned char*>(red + 9 * (RW_THREADS / 32));
-    fft_twiddles<D>(tw);
+    fft_twiddles<M>(tw);
     SurfGrads<NS> SG;
     SG.zero();
     float gs[RW_MAXS * RW_NGRAD];
@@ -311,22 +315,22 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
             if (!R.alive) continue;
             const DJob& J = jobs[R.job];
             const float2* T = Tmaps + (long long)J.slot * npix_map;
-            gather_patch<D>(sys, R, T, X, phu, phv);
+            gather_patch<M>(sys, R, T, X, phu, phv);
             __syncthreads();
-            fft2d<D, false>(X, tw);
+            fft2d<M, false>(X, tw);
             const float2 ain = make_float2(R.a_re, R.a_im);
             const float* gimg = gpsf + (long long)R.job * npx;
             float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
-                constexpr int KW = D * D / RW_THREADS;   // visibility words per warp and ray
+                constexpr int KW = M * M / RW_THREADS;   // visibility words per warp and ray
                 if (vis && KW <= 32) {
                     // Only secondary rays that reached the sensor carry gradient: zero
                     // dL/dX, then compact this warp's visible bins (the forward's mask)
                     // and reverse them in converged rounds of 32.
-                    for (int f = threadIdx.x; f < D * D; f += RW_THREADS)
+                    for (int f = threadIdx.x; f < Patch<M>::ELEMS; f += RW_THREADS)
                         G[f] = make_float2(0.f, 0.f);
                     __syncthreads();
-                    const unsigned* vw = vis + R.gid * (long long)(D * D / 32);
+                    const unsigned* vw = vis + R.gid * (long long)(M * M / 32);
                     const unsigned myw = lane < KW ? __ldg(vw + lane * (RW_THREADS / 32) + warp) : 0u;
                     const int cnt = __popc(myw);
                     int incl = cnt;
@@ -348,18 +352,18 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                         }
                         if (kk >= 0) {
                             const int bit = (int)__fns(wsel, 0u, rank + 1);
-                            exh_bin_adjoint<D, NS>(sys, R, X, phu, phv, gimg, G, ain,
+                            exh_bin_adjoint<M, NS>(sys, R, X, phu, phv, gimg, G, ain,
                                                    kk * RW_THREADS + warp * 32 + bit, acc, SG,
                                                    gs, status);
                         }
                     }
                 } else {
-                    for (int f = threadIdx.x; f < D * D; f += RW_THREADS)
-                        exh_bin_adjoint<D, NS>(sys, R, X, phu, phv, gimg, G, ain, f, acc, SG, gs,
+                    for (int f = threadIdx.x; f < M * M; f += RW_THREADS)
+                        exh_bin_adjoint<M, NS>(sys, R, X, phu, phv, gimg, G, ain, f, acc, SG, gs,
                                                status);
                 }
             } else {
-                sampled_ray_adjoint<D, NS>(sys, R, X, phu, phv, gimg, G, sscr, acc, SG, gs, status);
+                sampled_ray_adjoint<M, NS>(sys, R, X, phu, phv, gimg, G, sscr, acc, SG, gs, status);
             }
             // ---- per-ray reduction of the geometric gradients
 #pragma unroll
@@ -385,49 +389,8 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                 B.gnout = J.k0 * s[5];
             }
             // ---- adjoint patch transform and map scatter
-            fft2d<D, true>(G, tw);
-            const float scale = J.phase_scale;
-            const int H = sys.H, W = sys.W;
-            for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
-                const int b = f / D, a = f - (f / D) * D;
-                const float2 gT = G[f];
-                if (sys.gather == RW_GATHER_NEAREST) {
-                    const int rr = R.r0 + b, cc = R.c0 + a;
-                    if ((unsigned)rr < (unsigned)H && (unsigned)cc < (unsigned)W) {
-                        const long long p = (long long)rr * W + cc;
-                        const float2 t = __ldg(&T[p]);
-                        if (dphi) atomicAdd(dphi + p, scale * (t.x * gT.y - t.y * gT.x));
-                        if (damp) {
-                            const float A = __ldg(amp + p);
-                            if (A != 0.f) atomicAdd(damp + p, (t.x * gT.x + t.y * gT.y) / A);
-                        }
-                    }
-                } else {
-                    const float oa = (float)(a - D / 2), ob = (float)(b - D / 2);
-                    const float fu = R.s0 + oa * R.u[0] + ob * R.v[0];
-                    const float fv = R.t0 + oa * R.u[1] + ob * R.v[1];
-                    const float iuf = floorf(fu), ivf = floorf(fv);
-                    const float wu = fu - iuf, wv = fv - ivf;
-                    const int i0 = R.c0 + (int)iuf, j0 = R.r0 + (int)ivf;
-                    const float wt[4] = {(1.f - wu) * (1.f - wv), wu * (1.f - wv),
-                                         (1.f - wu) * wv, wu * wv};
-                    const int di[4] = {0, 1, 0, 1}, dj[4] = {0, 0, 1, 1};
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int rr = j0 + dj[q], cc = i0 + di[q];
-                        if ((unsigned)rr < (unsigned)H && (unsigned)cc < (unsigned)W) {
-                            const long long p = (long long)rr * W + cc;
-                            const float2 t = __ldg(&T[p]);
-                            const float2 g = cscale(gT, wt[q]);
-                            if (dphi) atomicAdd(dphi + p, scale * (t.x * g.y - t.y * g.x));
-                            if (damp) {
-                                const float A = __ldg(amp + p);
-                                if (A != 0.f) atomicAdd(damp + p, (t.x * g.x + t.y * g.y) / A);
-                            }
-                        }
-                    }
-                }
-            }
+            fft2d<M, true>(G, tw);
+            map_scatter<M>(sys, R, T, amp, G, J.phase_scale, dphi, damp);
             __syncthreads();
         }
         // ---- incident side: DOE hit and pre-DOE surfaces, one lane per ray
@@ -497,24 +460,24 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
     }
 }
 
-inline size_t backward_smem_bytes(int D, int emit, int n_ssr) {
-    size_t b = sampled_scratch_offset(D) + sizeof(float2) * (size_t)D * D +
+inline size_t backward_smem_bytes(int M, int emit, int n_ssr) {
+    size_t b = sampled_scratch_offset(M) + sizeof(float2) * (size_t)M * (M + 1) +
                sizeof(BwdRay) * RW_TILE + sizeof(float) * 9 * (RW_THREADS / 32);
-    if (emit == RW_EMIT_SAMPLED) b += sampled_bwd_bytes(D, n_ssr);
+    if (emit == RW_EMIT_SAMPLED) b += sampled_bwd_bytes(M, n_ssr);
     size_t red = sizeof(double) * RW_MAXS * RW_NGRAD * (RW_THREADS / 32);
     return b > red ? b : red;
 }
 
-size_t backward_smem_needed(const DSys& sys) { return backward_smem_bytes(sys.D, sys.emit, sys.n_ssr); }
+size_t backward_smem_needed(const DSys& sys) { return backward_smem_bytes(sys.M, sys.emit, sys.n_ssr); }
 
-template <int D, int NS>
+template <int M, int NS>
 static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                      const long long* prefix, int njob, long long total,
                                      const RaysIn& rays, const float2* T, const float* amp,
                                      const float* gpsf, float* dphi, float* damp, double* dsurf,
                                      unsigned* status, const unsigned* vis) {
-    const size_t smem = backward_smem_bytes(D, sys.emit, sys.n_ssr);
-    auto kern = k_backward<D, NS>;
+    const size_t smem = backward_smem_bytes(M, sys.emit, sys.n_ssr);
+    auto kern = k_backward<M, NS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -551,7 +514,7 @@ cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* job
             case 6: return RW_BWD(DD, 6);                 \
             default: return RW_BWD(DD, -1);               \
         }
-    switch (sys.D) {
+    switch (sys.M) {
         RW_BWD_D(16)
         RW_BWD_D(32)
         RW_BWD_D(64)

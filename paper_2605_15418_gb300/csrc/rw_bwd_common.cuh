@@ -154,39 +154,20 @@ __device__ __forceinline__ void emission_adjoint(const DSys& sys, const RayAtDoe
 }
 
 
-// Per-bin phase factors exp(-i k_j s_0) of the current ray (see gather_patch).
-template <int D>
-__device__ __forceinline__ void phase_factors(const DSys& sys, const RayAtDoe& R, float2* phu,
-                                              float2* phv) {
-    if (threadIdx.x < D) {
-        if (sys.gather == RW_GATHER_NEAREST) {
-            const float j = (float)((int)threadIdx.x - D / 2);
-            float s, c;
-            sincospif(-2.f * j * R.s0, &s, &c);
-            phu[threadIdx.x] = make_float2(c, s);
-            sincospif(-2.f * j * R.t0, &s, &c);
-            phv[threadIdx.x] = make_float2(c, s);
-        } else {
-            const float sg = ((((int)threadIdx.x - D / 2) & 1) ? -1.f : 1.f);
-            phu[threadIdx.x] = make_float2(sg, 0.f);
-            phv[threadIdx.x] = make_float2(sg, 0.f);
-        }
-    }
-}
-
-// Reverse of the patch gather: dL/dT on the D x D patch (G, natural order
-// after the conjugate FFT) -> dphi = (lambda0/lambda) Im(conj(T) g),
+// Reverse of the patch gather: dL/dT on the D x D patch (the top-left
+// corner of the M x M buffer G, natural order after the conjugate FFT; the
+// padding carries no map samples) -> dphi = (lambda0/lambda) Im(conj(T) g),
 // dA = Re(conj(T) g) / A, added to the maps with atomics.
-template <int D>
+template <int M>
 __device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
                                             const float2* __restrict__ T,
                                             const float* __restrict__ amp, const float2* G,
                                             float scale, float* __restrict__ dphi,
                                             float* __restrict__ damp) {
-    const int H = sys.H, W = sys.W;
+    const int H = sys.H, W = sys.W, D = sys.D;
     for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
         const int b = f / D, a = f - (f / D) * D;
-        const float2 gT = G[f];
+        const float2 gT = G[b * Patch<M>::S + a];
         if (sys.gather == RW_GATHER_NEAREST) {
             const int rr = R.r0 + b, cc = R.c0 + a;
             if ((unsigned)rr < (unsigned)H && (unsigned)cc < (unsigned)W) {

@@ -42,20 +42,22 @@ __global__ void k_bs_count(const unsigned* __restrict__ vis, long long nwords,
 }
 
 // ------------------------------------------------------------------ 1: spectra + list
-template <int D>
-__global__ void __launch_bounds__(RW_THREADS, D <= 64 ? 4 : 1)
+template <int M>
+__global__ void __launch_bounds__(RW_THREADS, M <= 64 ? 4 : 1)
 k_bs_spectra(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
              int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
              const unsigned* __restrict__ vis, SplitBufs B, unsigned* status) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* X = reinterpret_cast<float2*>(smem);
-    float2* tw = X + D * D;
-    float2* phu = tw + D;
-    float2* phv = phu + D;
-    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + D);
-    int* wsum = reinterpret_cast<int*>(smem + sampled_scratch_offset(D));   // [8 warps + 2]
-    fft_twiddles<D>(tw);
-    constexpr int NW = D * D / 32;          // visibility words per ray
+    float2* tw = X + Patch<M>::ELEMS;
+    float2* phu = tw + M;
+    float2* phv = phu + M;
+    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + M);
+    int* wsum = reinterpret_cast<int*>(smem + sampled_scratch_offset(M));   // [8 warps + 3]
+    fft_twiddles<M>(tw);
+    constexpr int NW = M * M / 32;                               // visibility words per ray
+    constexpr int KW = (NW + RW_THREADS - 1) / RW_THREADS;       // words per thread
+    const float norm = sys.norm;
     const long long npix_map = (long long)sys.H * sys.W;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -71,10 +73,16 @@ k_bs_spectra(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
             const long long g = tile * RW_TILE + r;
             if (g >= total) break;
             const RayAtDoe& R = info[r];
-            // visible bins of this ray: thread t < NW owns word t (bins 32t .. 32t+31)
-            unsigned word = 0u;
-            if (R.alive && threadIdx.x < NW) word = __ldg(vis + g * (long long)NW + threadIdx.x);
-            const int cnt = __popc(word);
+            // visible bins of this ray: thread t owns words t KW .. t KW + KW - 1
+            // (word w holds bins 32w .. 32w + 31), so items come out in bin order
+            unsigned word[KW];
+            int cnt = 0;
+#pragma unroll
+            for (int k = 0; k < KW; ++k) {
+                const int wi = threadIdx.x * KW + k;
+                word[k] = (R.alive && wi < NW) ? __ldg(vis + g * (long long)NW + wi) : 0u;
+                cnt += __popc(word[k]);
+            }
             int incl = cnt;
             for (int o = 1; o < 32; o <<= 1) {
                 const int v = __shfl_up_sync(0xffffffffu, incl, o);
@@ -99,19 +107,23 @@ k_bs_spectra(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
             if (ntot == 0) continue;
             const long long base = (long long)wsum[RW_THREADS / 32] +
                                    ((long long)wsum[RW_THREADS / 32 + 1] << 31);
-            gather_patch<D>(sys, R, Tmaps + (long long)jobs[R.job].slot * npix_map, X, phu, phv);
+            gather_patch<M>(sys, R, Tmaps + (long long)jobs[R.job].slot * npix_map, X, phu, phv);
             __syncthreads();
-            fft2d<D, false>(X, tw);
+            fft2d<M, false>(X, tw);
             long long pos = base + wsum[warp] + (incl - cnt);
-            while (word) {
-                const int b = __ffs(word) - 1;
-                word &= word - 1u;
-                const int f = threadIdx.x * 32 + b;
-                const int jvi = f / D, jui = f - (f / D) * D;
-                B.iray[pos] = (int)g;
-                B.ibin[pos] = f;
-                B.iU[pos] = spectrum_at<D>(X, phu, phv, jui, jvi);
-                ++pos;
+#pragma unroll
+            for (int k = 0; k < KW; ++k) {
+                unsigned wk = word[k];
+                while (wk) {
+                    const int b = __ffs(wk) - 1;
+                    wk &= wk - 1u;
+                    const int f = (threadIdx.x * KW + k) * 32 + b;
+                    const int jvi = f / M, jui = f - (f / M) * M;
+                    B.iray[pos] = (int)g;
+                    B.ibin[pos] = f;
+                    B.iU[pos] = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
+                    ++pos;
+                }
             }
             __syncthreads();
         }
@@ -119,7 +131,7 @@ k_bs_spectra(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
 }
 
 // ------------------------------------------------------------------ 2: trace + reverse
-template <int D, int NS>
+template <int M, int NS>
 __global__ void __launch_bounds__(RW_THREADS, 2)
 k_bs_trace(const DSys sys, const float* __restrict__ gpsf, SplitBufs B, long long nitems,
            double* __restrict__ dsurf, unsigned* status) {
@@ -143,17 +155,17 @@ k_bs_trace(const DSys sys, const float* __restrict__ gpsf, SplitBufs B, long lon
             const int f = __ldg(B.ibin + t);
             const float2 U = B.iU[t];
             const RayAtDoe& R = B.rinfo[g];
-            const int jvi = f / D, jui = f - (f / D) * D;
+            const int jvi = f / M, jui = f - (f / M) * M;
             float2 gU = make_float2(0.f, 0.f);
             float dx, dy, dz;
             const float2 ain = make_float2(R.a_re, R.a_im);
-            if (bin_direction<(NS >= 0)>(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
+            if (bin_direction<(NS >= 0)>(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
                 const float2 a = cmul(ain, U);
                 const float w = a.x * a.x + a.y * a.y;
                 float gw, gx, gy, gz, gdx, gdy, gdz;
                 if (secondary_adjoint<NS>(sys, R, gpsf + (long long)R.job * npx, dx, dy, dz, w,
                                           gw, gx, gy, gz, gdx, gdy, gdz, SG, gs, status)) {
-                    emission_adjoint(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz, gx, gy, gz,
+                    emission_adjoint(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz, gx, gy, gz,
                                      gdx, gdy, gdz, acc);
                     const float2 ga = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
                     gU = cmulc(ga, ain);
@@ -216,19 +228,20 @@ k_bs_trace(const DSys sys, const float* __restrict__ gpsf, SplitBufs B, long lon
 }
 
 // ------------------------------------------------------------------ 3: conjugate FFT + scatter
-template <int D>
-__global__ void __launch_bounds__(RW_THREADS, D <= 64 ? 4 : 1)
+template <int M>
+__global__ void __launch_bounds__(RW_THREADS, M <= 64 ? 4 : 1)
 k_bs_scatter(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
              int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
              const float* __restrict__ amp, SplitBufs B, float* __restrict__ dphi,
              float* __restrict__ damp, double* __restrict__ dsurf, unsigned* status) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* G = reinterpret_cast<float2*>(smem);
-    float2* tw = G + D * D;
-    float2* phu = tw + D;
-    float2* phv = phu + D;
-    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + D);
-    fft_twiddles<D>(tw);
+    float2* tw = G + Patch<M>::ELEMS;
+    float2* phu = tw + M;
+    float2* phv = phu + M;
+    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + M);
+    fft_twiddles<M>(tw);
+    const float norm = sys.norm;
     float gs[RW_MAXS * RW_NGRAD];
     for (int i = 0; i < RW_MAXS * RW_NGRAD; ++i) gs[i] = 0.f;
     const long long npix_map = (long long)sys.H * sys.W;
@@ -247,21 +260,22 @@ k_bs_scatter(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
             const int n = R.alive ? B.vcnt[g] : 0;
             if (n == 0) continue;
             const long long off = B.voff[g];
-            for (int f = threadIdx.x; f < D * D; f += RW_THREADS) G[f] = make_float2(0.f, 0.f);
-            phase_factors<D>(sys, R, phu, phv);
+            for (int f = threadIdx.x; f < Patch<M>::ELEMS; f += RW_THREADS)
+                G[f] = make_float2(0.f, 0.f);
+            phase_factors<M>(sys, R, phu, phv);
             __syncthreads();
             for (int i = threadIdx.x; i < n; i += RW_THREADS) {
                 const int f = __ldg(B.ibin + off + i);
                 const float2 gU = B.igU[off + i];
-                const int jvi = f / D, jui = f - (f / D) * D;
-                int mu = jui + D / 2; if (mu >= D) mu -= D;
-                int mv = jvi + D / 2; if (mv >= D) mv -= D;
+                const int jvi = f / M, jui = f - (f / M) * M;
+                int mu = jui + M / 2; if (mu >= M) mu -= M;
+                int mv = jvi + M / 2; if (mv >= M) mv -= M;
                 const float2 ph = cmul(phu[jui], phv[jvi]);
-                G[mv * D + mu] = cscale(cmulc(gU, ph), 1.f / (float)(D * D));
+                G[mv * Patch<M>::S + mu] = cscale(cmulc(gU, ph), norm);
             }
             __syncthreads();
-            fft2d<D, true>(G, tw);
-            map_scatter<D>(sys, R, Tmaps + (long long)jobs[R.job].slot * npix_map, amp, G,
+            fft2d<M, true>(G, tw);
+            map_scatter<M>(sys, R, Tmaps + (long long)jobs[R.job].slot * npix_map, amp, G,
                            jobs[R.job].phase_scale, dphi, damp);
             __syncthreads();
         }
@@ -307,7 +321,7 @@ static cudaError_t persistent_launch_cfg(K kern, size_t smem, int num_sms, long 
     return cudaSuccess;
 }
 
-template <int D, int NS>
+template <int M, int NS>
 static cudaError_t launch_split_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                   const long long* prefix, int njob, long long total,
                                   const RaysIn& rays, const float2* T, const float* amp,
@@ -316,29 +330,29 @@ static cudaError_t launch_split_d(const LaunchCtx& L, const DSys& sys, const DJo
                                   unsigned* status) {
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     long long grid;
-    size_t smem1 = sampled_scratch_offset(D) + 64;
-    cudaError_t e = persistent_launch_cfg(k_bs_spectra<D>, smem1, L.num_sms, ntiles, L.grid_override, &grid);
+    size_t smem1 = sampled_scratch_offset(M) + 64;
+    cudaError_t e = persistent_launch_cfg(k_bs_spectra<M>, smem1, L.num_sms, ntiles, L.grid_override, &grid);
     if (e != cudaSuccess) return e;
-    k_bs_spectra<D><<<(unsigned)grid, RW_THREADS, smem1, L.stream>>>(sys, jobs, prefix, njob,
+    k_bs_spectra<M><<<(unsigned)grid, RW_THREADS, smem1, L.stream>>>(sys, jobs, prefix, njob,
                                                                      total, rays, T, vis, B, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (nitems > 0) {
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bs_trace<D, NS>, RW_THREADS, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bs_trace<M, NS>, RW_THREADS, 0);
         if (e != cudaSuccess) return e;
         long long g2 = (long long)L.num_sms * (per_sm > 0 ? per_sm : 1) * 4;
         const long long need = (nitems + RW_THREADS - 1) / RW_THREADS;
         if (g2 > need) g2 = need;
-        k_bs_trace<D, NS><<<(unsigned)g2, RW_THREADS, 0, L.stream>>>(sys, gpsf, B, nitems, dsurf,
+        k_bs_trace<M, NS><<<(unsigned)g2, RW_THREADS, 0, L.stream>>>(sys, gpsf, B, nitems, dsurf,
                                                                       status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    size_t smem3 = sampled_scratch_offset(D);
+    size_t smem3 = sampled_scratch_offset(M);
     const size_t red = sizeof(double) * RW_MAXS * RW_NGRAD * (RW_THREADS / 32);
     if (smem3 < red) smem3 = red;
-    e = persistent_launch_cfg(k_bs_scatter<D>, smem3, L.num_sms, ntiles, L.grid_override, &grid);
+    e = persistent_launch_cfg(k_bs_scatter<M>, smem3, L.num_sms, ntiles, L.grid_override, &grid);
     if (e != cudaSuccess) return e;
-    k_bs_scatter<D><<<(unsigned)grid, RW_THREADS, smem3, L.stream>>>(
+    k_bs_scatter<M><<<(unsigned)grid, RW_THREADS, smem3, L.stream>>>(
         sys, jobs, prefix, njob, total, rays, T, amp, B, dphi, damp, dsurf, status);
     return cudaGetLastError();
 }
@@ -361,10 +375,12 @@ cudaError_t launch_backward_split(const LaunchCtx& L, const DSys& sys, const DJo
             case 6: return RW_BS(DD, 6);     \
             default: return RW_BS(DD, -1);   \
         }
-    switch (sys.D) {
+    switch (sys.M) {
         RW_BS_D(16)
         RW_BS_D(32)
         RW_BS_D(64)
+        RW_BS_D(96)
+        RW_BS_D(128)
         default: return cudaErrorInvalidValue;
     }
 #undef RW_BS_D

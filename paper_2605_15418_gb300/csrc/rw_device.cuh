@@ -48,12 +48,14 @@ struct DSys {
     double n_object;
     // DOE
     int H, W, D, gather, emit, n_ssr, phase_model, conformal;
+    int M;             // transform size P D (zero-padded patch)
+    float norm;        // spectrum scale: 1/M^2 (coherent sensor) or 1/(D M)
     double pitch;
     float pitchf, inv_pitch;
     unsigned long long seed, rng_offset;
     float n_in, n_out;
     double n_in_d;
-    float kstep;       // 2 pi / (D p): wavevector step of the patch spectrum
+    float kstep;       // 2 pi / (M p): wavevector step of the patch spectrum
     // sensor
     double sensor_z;
     float sensor_gap;  // z_sensor - z of the last surface
@@ -84,7 +86,7 @@ struct RayAtDoe {
     double opl;
     double pxd, pyd;        // hit in double (patch indexing)
     int c0, r0;             // nearest: window origin; bilinear: pixel of the hit
-    float s0, t0;           // nearest: offset of sample 0 from the hit / (D p);
+    float s0, t0;           // nearest: offset of sample 0 from the hit / (M p);
                             // bilinear: fractional pixel coordinate of the hit
     float cx, cy;           // sensor window centre of the job
     long long gid;          // global incident ray id (sampling stream)

@@ -6,8 +6,19 @@
 // y[(i / P) P R + (i mod P) + q P]; the output comes out in natural order.
 // Each stage is done in place: all butterflies of the CTA are loaded into
 // registers, the CTA synchronises, then they are stored.
+//
+// Layout: an N x N patch buffer keeps row b at X + b (N + 1).  With the odd
+// row stride, and consecutive threads on consecutive rows (row pass) or
+// columns (column pass), every load and store of a stage touches 16
+// different bank pairs per half-warp: no shared-memory bank conflicts.
 #pragma once
 #include "rw_device.cuh"
+
+template <int N>
+struct Patch {
+    static constexpr int S = N + 1;          // row stride (complex elements)
+    static constexpr int ELEMS = N * (N + 1);
+};
 
 template <int R, bool INV>
 __device__ __forceinline__ void dft_small(float2* u);
@@ -63,23 +74,48 @@ __device__ __forceinline__ void dft_small(float2* u) {
     }
 }
 
-// One Stockham stage over all D rows (COLS = false) or all D columns.
+// Line b and butterfly i of the k-th butterfly a thread owns in a stage.
+// Row passes that divide evenly keep one butterfly index i per thread (its
+// twiddles are loaded once) over PER rows BL apart, BL >= 16 consecutive
+// threads on consecutive rows; otherwise (and in column passes, where this
+// costs fewer registers overall) thread f works on line f % N, butterfly f / N.
+template <int N, int NB, int PER, bool COLS>
+struct StageMap {
+    static constexpr int TOT = N * NB;
+    static constexpr int BL = N / PER;
+    static constexpr bool BLOCKED = (TOT % RW_THREADS == 0) && (N % PER == 0) &&
+                                    (BL * NB == RW_THREADS) && (BL >= 16) && !COLS;
+    __device__ static __forceinline__ void at(int k, int& b, int& i) {
+        if constexpr (BLOCKED) {
+            b = (int)threadIdx.x % BL + k * BL;
+            i = (int)threadIdx.x / BL;
+        } else {
+            const int f = (int)threadIdx.x + k * RW_THREADS;
+            b = f % N;
+            i = f / N;
+        }
+    }
+};
+
+// One Stockham stage over all N rows (COLS = false) or all N columns.
 template <int N, int R, int P, bool INV, bool COLS>
 __device__ __forceinline__ void fft_stage(float2* buf, const float2* tw) {
+    constexpr int S = Patch<N>::S;
     constexpr int NB = N / R;
     constexpr int TOT = N * NB;
     constexpr int PER = (TOT + RW_THREADS - 1) / RW_THREADS;
+    using Map = StageMap<N, NB, PER, COLS>;
     float2 v[PER][R];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int f = threadIdx.x + k * RW_THREADS;
         if ((TOT % RW_THREADS == 0) || f < TOT) {
-            const int b = COLS ? (f % N) : (f / NB);
-            const int i = COLS ? (f / N) : (f % NB);
+            int b, i;
+            Map::at(k, b, i);
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int e = i + q * NB;
-                v[k][q] = COLS ? buf[e * N + b] : buf[b * N + e];
+                v[k][q] = COLS ? buf[e * S + b] : buf[b * S + e];
             }
             if constexpr (P > 1) {
                 const int kk = i % P;
@@ -98,14 +134,14 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* tw) {
     for (int k = 0; k < PER; ++k) {
         const int f = threadIdx.x + k * RW_THREADS;
         if ((TOT % RW_THREADS == 0) || f < TOT) {
-            const int b = COLS ? (f % N) : (f / NB);
-            const int i = COLS ? (f / N) : (f % NB);
+            int b, i;
+            Map::at(k, b, i);
             const int kk = i % P;
             const int j = (i / P) * P * R + kk;
 #pragma unroll
             for (int q = 0; q < R; ++q) {
                 const int e = j + q * P;
-                if (COLS) buf[e * N + b] = v[k][q]; else buf[b * N + e] = v[k][q];
+                if (COLS) buf[e * S + b] = v[k][q]; else buf[b * S + e] = v[k][q];
             }
         }
     }
@@ -127,10 +163,15 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
         fft_stage<96, 8, 1, INV, COLS>(buf, tw);
         fft_stage<96, 4, 8, INV, COLS>(buf, tw);
         fft_stage<96, 3, 32, INV, COLS>(buf, tw);
+    } else if constexpr (N == 128) {
+        fft_stage<128, 8, 1, INV, COLS>(buf, tw);
+        fft_stage<128, 4, 8, INV, COLS>(buf, tw);
+        fft_stage<128, 4, 32, INV, COLS>(buf, tw);
     }
 }
 
-// X[b][a] -> sum_{a,b} X[b][a] exp(-+2 pi i (m_u a + m_v b) / N), natural order.
+// X[b][a] -> sum_{a,b} X[b][a] exp(-+2 pi i (m_u a + m_v b) / N), natural
+// order, X[b][a] at buf[b (N + 1) + a].
 template <int N, bool INV>
 __device__ __forceinline__ void fft2d(float2* buf, const float2* tw) {
     fft_pass<N, INV, false>(buf, tw);

@@ -6,7 +6,8 @@
 //
 // One CTA of 256 threads owns one incident ray at a time: warp 0 first
 // traces a tile of 32 incident rays to the DOE, then the CTA walks the tile,
-// each thread handling D^2/256 spectral bins of the current ray.
+// each thread handling M^2/256 spectral bins of the current ray (M = P D,
+// the zero-padded transform size; the template parameter).
 #include "rw_kernels.cuh"
 
 // ------------------------------------------------------------- A3 input
@@ -55,24 +56,24 @@ __global__ void k_generate_rays(const GenJob* __restrict__ jobs, const long long
 }
 
 // ------------------------------------------------------------- fused forward
-// Resident CTAs per SM the register allocation is sized for (D = 96 needs
+// Resident CTAs per SM the register allocation is sized for (M >= 96 needs
 // more registers for its FFT stages and more shared memory per CTA).
-template <int D>
-struct FwdOcc { static constexpr int value = D <= 64 ? 4 : 1; };
+template <int M>
+struct FwdOcc { static constexpr int value = M <= 64 ? 4 : 1; };
 
-template <int D, int MODE, int NS>
-__global__ void __launch_bounds__(RW_THREADS, FwdOcc<D>::value)
+template <int M, int MODE, int NS>
+__global__ void __launch_bounds__(RW_THREADS, FwdOcc<M>::value)
 k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
           int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
           double* __restrict__ psf, float2* __restrict__ field, EmitOut eo, unsigned* status,
           unsigned* __restrict__ vis) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* X = reinterpret_cast<float2*>(smem);
-    float2* tw = X + D * D;
-    float2* phu = tw + D;
-    float2* phv = phu + D;
-    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + D);
-    fft_twiddles<D>(tw);
+    float2* tw = X + Patch<M>::ELEMS;
+    float2* phu = tw + M;
+    float2* phv = phu + M;
+    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + M);
+    fft_twiddles<M>(tw);
     const long long npix_map = (long long)sys.H * sys.W;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -84,23 +85,23 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
         for (int r = 0; r < RW_TILE; ++r) {
             const RayAtDoe& R = info[r];
             if (!R.alive) {
-                if (MODE == MODE_EMIT) emit_dead<D>(sys, tile * RW_TILE + r, total, eo);
+                if (MODE == MODE_EMIT) emit_dead<M>(sys, tile * RW_TILE + r, total, eo);
                 if (MODE == MODE_SPLAT && vis && tile * RW_TILE + r < total)
-                    for (int f = threadIdx.x; f < D * D / 32; f += RW_THREADS)
-                        vis[(tile * RW_TILE + r) * (long long)(D * D / 32) + f] = 0u;
+                    for (int f = threadIdx.x; f < M * M / 32; f += RW_THREADS)
+                        vis[(tile * RW_TILE + r) * (long long)(M * M / 32) + f] = 0u;
                 continue;
             }
             const DJob& J = jobs[R.job];
-            gather_patch<D>(sys, R, Tmaps + (long long)J.slot * npix_map, X, phu, phv);
+            gather_patch<M>(sys, R, Tmaps + (long long)J.slot * npix_map, X, phu, phv);
             __syncthreads();
-            fft2d<D, false>(X, tw);
+            fft2d<M, false>(X, tw);
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
-                emit_exhaustive<D, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
+                emit_exhaustive<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                              tile * RW_TILE + r, status, vis);
             } else {
-                emit_sampled<D, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
-                                      tile * RW_TILE + r, status,
-                                      smem + sampled_scratch_offset(D));
+                emit_sampled<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
+                                          tile * RW_TILE + r, status,
+                                          smem + sampled_scratch_offset(M));
             }
             __syncthreads();
         }
@@ -126,14 +127,14 @@ __global__ void k_coherent_finalize(const float2* __restrict__ field, float* __r
 }
 
 // ------------------------------------------------------------- launchers
-template <int D, int MODE, int NS>
+template <int M, int MODE, int NS>
 static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                     const long long* prefix, int njob, long long total,
                                     const RaysIn& rays, const float2* T, double* psf,
                                     float2* field, const EmitOut& eo, unsigned* status,
                                     unsigned* vis) {
-    size_t smem = forward_smem_bytes(D, sys.emit, sys.n_ssr);
-    auto kern = k_forward<D, MODE, NS>;
+    size_t smem = forward_smem_bytes(M, sys.emit, sys.n_ssr);
+    auto kern = k_forward<M, MODE, NS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -152,21 +153,21 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
 }
 
 // Post-DOE surface counts with a specialised (unrolled plane/sphere) trace.
-template <int D>
+template <int M>
 static cudaError_t launch_splat(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                 const long long* prefix, int njob, long long total,
                                 const RaysIn& rays, const float2* T, double* psf,
                                 const EmitOut& eo, unsigned* status, unsigned* vis) {
     if (sys.fast_ok) {
         switch (sys.n_post) {
-            case 0: return launch_forward_d<D, MODE_SPLAT, 0>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
-            case 2: return launch_forward_d<D, MODE_SPLAT, 2>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
-            case 4: return launch_forward_d<D, MODE_SPLAT, 4>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
-            case 6: return launch_forward_d<D, MODE_SPLAT, 6>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
+            case 0: return launch_forward_d<M, MODE_SPLAT, 0>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
+            case 2: return launch_forward_d<M, MODE_SPLAT, 2>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
+            case 4: return launch_forward_d<M, MODE_SPLAT, 4>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
+            case 6: return launch_forward_d<M, MODE_SPLAT, 6>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
             default: break;
         }
     }
-    return launch_forward_d<D, MODE_SPLAT, -1>(L, sys, jobs, prefix, njob, total, rays, T, psf,
+    return launch_forward_d<M, MODE_SPLAT, -1>(L, sys, jobs, prefix, njob, total, rays, T, psf,
                                                nullptr, eo, status, vis);
 }
 
@@ -185,11 +186,12 @@ cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const 
                                                            nullptr);                          \
         return launch_forward_d<DD, MODE_EMIT, -1>(L, sys, jobs, prefix, njob, total, rays, T,\
                                                    psf, field, eo, status, nullptr);
-    switch (sys.D) {
+    switch (sys.M) {
         RW_FWD_CASE(16)
         RW_FWD_CASE(32)
         RW_FWD_CASE(64)
         RW_FWD_CASE(96)
+        RW_FWD_CASE(128)
         default: return cudaErrorInvalidValue;
     }
 #undef RW_FWD_CASE

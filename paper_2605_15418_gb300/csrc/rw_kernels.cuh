@@ -33,13 +33,14 @@ struct EmitOut {
 
 // ------------------------------------------------------------------ sizes
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-// patch X, twiddles, two phase vectors, the tile's incident states
-__host__ __device__ inline size_t sampled_scratch_offset(int D) {
-    return align16(sizeof(float2) * (size_t)(D * D + 3 * D) + sizeof(RayAtDoe) * RW_TILE);
+// patch X (M rows of stride M + 1), twiddles, two phase vectors, the tile's
+// incident states
+__host__ __device__ inline size_t sampled_scratch_offset(int M) {
+    return align16(sizeof(float2) * (size_t)(M * (M + 1) + 3 * M) + sizeof(RayAtDoe) * RW_TILE);
 }
-inline size_t forward_smem_bytes(int D, int emit = RW_EMIT_EXHAUSTIVE, int n_ssr = 0) {
-    size_t b = sampled_scratch_offset(D);
-    if (emit == RW_EMIT_SAMPLED) b += sizeof(float) * (size_t)D * D + sizeof(int) * n_ssr + 128;
+inline size_t forward_smem_bytes(int M, int emit = RW_EMIT_EXHAUSTIVE, int n_ssr = 0) {
+    size_t b = sampled_scratch_offset(M);
+    if (emit == RW_EMIT_SAMPLED) b += sizeof(float) * (size_t)M * M + sizeof(int) * n_ssr + 128;
     return b;
 }
 
@@ -152,8 +153,8 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
         const double rs = floor(pyd / p + (double)sys.H / 2.0);
         R.c0 = (int)cs - sys.D / 2;
         R.r0 = (int)rs - sys.D / 2;
-        R.s0 = (float)((((double)R.c0 - (double)sys.W / 2.0 + 0.5) * p - pxd) / (sys.D * p));
-        R.t0 = (float)((((double)R.r0 - (double)sys.H / 2.0 + 0.5) * p - pyd) / (sys.D * p));
+        R.s0 = (float)((((double)R.c0 - (double)sys.W / 2.0 + 0.5) * p - pxd) / (sys.M * p));
+        R.t0 = (float)((((double)R.r0 - (double)sys.H / 2.0 + 0.5) * p - pyd) / (sys.M * p));
     } else {
         const double uc = pxd / p + (double)sys.W / 2.0 - 0.5;
         const double vc = pyd / p + (double)sys.H / 2.0 - 0.5;
@@ -170,29 +171,47 @@ __device__ __forceinline__ float2 tmap(const float2* __restrict__ T, int H, int 
     return make_float2(0.f, 0.f);
 }
 
-// Fill X[b][a] with the patch and phu/phv with the per-bin phase factors
-// exp(-i k_j s_0) that refer the spectrum to the hit point.
-template <int D>
-__device__ __forceinline__ void gather_patch(const DSys& sys, const RayAtDoe& R,
-                                             const float2* __restrict__ T, float2* X,
-                                             float2* phu, float2* phv) {
-    const int H = sys.H, W = sys.W;
-    if (sys.gather == RW_GATHER_NEAREST) {
-        for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
-            const int b = f / D, a = f - (f / D) * D;
-            X[f] = tmap(T, H, W, R.r0 + b, R.c0 + a);
-        }
-        if (threadIdx.x < D) {
-            const float j = (float)((int)threadIdx.x - D / 2);
-            float s, c;
+// Per-bin phase factors exp(-i k_j s_0), j in [-M/2, M/2), that refer the
+// spectrum to the hit point.  Bilinear patches start at s_0 = -(D/2) p, so
+// the factor is exp(i pi j D / M).
+template <int M>
+__device__ __forceinline__ void phase_factors(const DSys& sys, const RayAtDoe& R, float2* phu,
+                                              float2* phv) {
+    if (threadIdx.x < M) {
+        const float j = (float)((int)threadIdx.x - M / 2);
+        float s, c;
+        if (sys.gather == RW_GATHER_NEAREST) {
             sincospif(-2.f * j * R.s0, &s, &c);
             phu[threadIdx.x] = make_float2(c, s);
             sincospif(-2.f * j * R.t0, &s, &c);
             phv[threadIdx.x] = make_float2(c, s);
+        } else {
+            sincospif(j / (float)(M / sys.D), &s, &c);
+            phu[threadIdx.x] = make_float2(c, s);
+            phv[threadIdx.x] = make_float2(c, s);
+        }
+    }
+}
+
+// Fill the M x M buffer X (row stride M + 1) with the D x D patch in its
+// top-left corner and zeros elsewhere (the padding), and phu/phv with the
+// phase factors.
+template <int M>
+__device__ __forceinline__ void gather_patch(const DSys& sys, const RayAtDoe& R,
+                                             const float2* __restrict__ T, float2* X,
+                                             float2* phu, float2* phv) {
+    constexpr int S = Patch<M>::S;
+    const int H = sys.H, W = sys.W, D = sys.D;
+    if (sys.gather == RW_GATHER_NEAREST) {
+        for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
+            const int b = f / M, a = f - (f / M) * M;
+            X[b * S + a] = (a < D && b < D) ? tmap(T, H, W, R.r0 + b, R.c0 + a)
+                                            : make_float2(0.f, 0.f);
         }
     } else {
-        for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
-            const int b = f / D, a = f - (f / D) * D;
+        for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
+            const int b = f / M, a = f - (f / M) * M;
+            if (a >= D || b >= D) { X[b * S + a] = make_float2(0.f, 0.f); continue; }
             const float oa = (float)(a - D / 2), ob = (float)(b - D / 2);
             const float fu = R.s0 + oa * R.u[0] + ob * R.v[0];
             const float fv = R.t0 + oa * R.u[1] + ob * R.v[1];
@@ -203,16 +222,11 @@ __device__ __forceinline__ void gather_patch(const DSys& sys, const RayAtDoe& R,
             float2 t01 = tmap(T, H, W, j0 + 1, i0), t11 = tmap(T, H, W, j0 + 1, i0 + 1);
             const float w00 = (1.f - wu) * (1.f - wv), w10 = wu * (1.f - wv);
             const float w01 = (1.f - wu) * wv, w11 = wu * wv;
-            X[f] = make_float2(w00 * t00.x + w10 * t10.x + w01 * t01.x + w11 * t11.x,
-                               w00 * t00.y + w10 * t10.y + w01 * t01.y + w11 * t11.y);
-        }
-        if (threadIdx.x < D) {
-            // s_0 = -(D/2) p  ->  exp(-i k_j s_0) = (-1)^j
-            const float sg = ((((int)threadIdx.x - D / 2) & 1) ? -1.f : 1.f);
-            phu[threadIdx.x] = make_float2(sg, 0.f);
-            phv[threadIdx.x] = make_float2(sg, 0.f);
+            X[b * S + a] = make_float2(w00 * t00.x + w10 * t10.x + w01 * t01.x + w11 * t11.x,
+                                       w00 * t00.y + w10 * t10.y + w01 * t01.y + w11 * t11.y);
         }
     }
+    phase_factors<M>(sys, R, phu, phv);
 }
 
 // ------------------------------------------------------------------ A6 + A7
@@ -305,19 +319,27 @@ __device__ __forceinline__ bool bin_direction(const DSys& sys, const RayAtDoe& R
     if (FAST) asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(kn) : "f"(K2 - kt2));
     else kn = sqrtf(K2 - kt2);
     const float invK = R.invK;
+    if (FAST && !sys.conformal) {
+        // planar DOE: u = x, n = (0, 0, s), v = n x u = (0, s, 0) with s = +-1
+        const float sgn = R.n[2];
+        dx = ku * invK;
+        dy = (kv * sgn) * invK;
+        dz = (kn * sgn) * invK;
+        return true;
+    }
     dx = (ku * R.u[0] + kv * R.v[0] + kn * R.n[0]) * invK;
     dy = (ku * R.u[1] + kv * R.v[1] + kn * R.n[1]) * invK;
     dz = (ku * R.u[2] + kv * R.v[2] + kn * R.n[2]) * invK;
     return true;
 }
 
-template <int D>
+// U~ of bin (jui - M/2, jvi - M/2) from the FFT output X (row stride S).
+template <int M, int S = Patch<M>::S>
 __device__ __forceinline__ float2 spectrum_at(const float2* X, const float2* phu, const float2* phv,
-                                              int jui, int jvi) {
-    int mu = jui + D / 2; if (mu >= D) mu -= D;
-    int mv = jvi + D / 2; if (mv >= D) mv -= D;
-    const float invD2 = 1.f / (float)(D * D);
-    return cscale(cmul(cmul(X[mv * D + mu], phu[jui]), phv[jvi]), invD2);
+                                              int jui, int jvi, float norm) {
+    int mu = jui + M / 2; if (mu >= M) mu -= M;
+    int mv = jvi + M / 2; if (mv >= M) mv -= M;
+    return cscale(cmul(cmul(X[mv * S + mu], phu[jui]), phv[jvi]), norm);
 }
 
 // Trace one secondary ray and deposit it; returns true if it reached the
@@ -345,11 +367,11 @@ __device__ __forceinline__ bool deposit(const DSys& sys, const DJob& J, const Ra
     }
 }
 
-template <int D>
+template <int M>
 __device__ __forceinline__ void emit_dead(const DSys& sys, long long g, long long total,
                                           const EmitOut& eo) {
     if (g >= total) return;
-    const long long S = (sys.emit == RW_EMIT_EXHAUSTIVE) ? (long long)D * D : sys.n_ssr;
+    const long long S = (sys.emit == RW_EMIT_EXHAUSTIVE) ? (long long)M * M : sys.n_ssr;
     for (long long b = threadIdx.x; b < S; b += RW_THREADS) {
         const long long s = g * S + b;
         eo.dx[s] = 0.f; eo.dy[s] = 0.f; eo.dz[s] = 0.f; eo.are[s] = 0.f; eo.aim[s] = 0.f;
@@ -359,29 +381,30 @@ __device__ __forceinline__ void emit_dead(const DSys& sys, long long g, long lon
 }
 
 // ------------------------------------------------------------------ A5 exhaustive
-template <int D, int MODE, int NS>
+template <int M, int MODE, int NS>
 __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                                 const float2* X, const float2* phu,
                                                 const float2* phv, double* psf, float2* field,
                                                 const EmitOut& eo, long long g, unsigned* status,
                                                 unsigned* __restrict__ vis) {
+    constexpr int S = Patch<M>::S;
     const float2 ain = make_float2(R.a_re, R.a_im);
-    const float invD2 = 1.f / (float)(D * D);
-    const float ain2 = (ain.x * ain.x + ain.y * ain.y) * invD2 * invD2;
+    const float norm = sys.norm;
+    const float ain2 = (ain.x * ain.x + ain.y * ain.y) * norm * norm;
     if (MODE == MODE_EMIT && threadIdx.x == 0) {
         eo.hx[g] = R.px; eo.hy[g] = R.py; eo.hz[g] = (float)((double)R.pz + sys.s[sys.doe_index].z);
         eo.opl[g] = R.opl;
     }
-    for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
-        const int jvi = f / D, jui = f - (f / D) * D;
+    for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
+        const int jvi = f / M, jui = f - (f / M) * M;
         float dx, dy, dz;
-        const bool prop = bin_direction<(NS >= 0)>(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz);
+        const bool prop = bin_direction<(NS >= 0)>(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz);
         if (MODE == MODE_EMIT) {
-            const long long s = g * (long long)(D * D) + f;
+            const long long s = g * (long long)(M * M) + f;
             if (!prop) {
                 eo.dx[s] = 0.f; eo.dy[s] = 0.f; eo.dz[s] = 0.f; eo.are[s] = 0.f; eo.aim[s] = 0.f;
             } else {
-                const float2 a = cmul(ain, spectrum_at<D>(X, phu, phv, jui, jvi));
+                const float2 a = cmul(ain, spectrum_at<M>(X, phu, phv, jui, jvi, norm));
                 eo.dx[s] = dx; eo.dy[s] = dy; eo.dz[s] = dz; eo.are[s] = a.x; eo.aim[s] = a.y;
             }
             if (eo.bin) eo.bin[s] = f;
@@ -392,20 +415,20 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
             float2 a = make_float2(0.f, 0.f);
             float w = 0.f;
             if (MODE == MODE_SPLAT) {
-                // the incoherent deposit |a|^2 = |a_in|^2 |X_m|^2 / D^4 needs no phase factor
-                int mu = jui + D / 2; if (mu >= D) mu -= D;
-                int mv = jvi + D / 2; if (mv >= D) mv -= D;
-                const float2 xm = X[mv * D + mu];
+                // the incoherent deposit |a|^2 = |a_in|^2 |X_m|^2 norm^2 needs no phase factor
+                int mu = jui + M / 2; if (mu >= M) mu -= M;
+                int mv = jvi + M / 2; if (mv >= M) mv -= M;
+                const float2 xm = X[mv * S + mu];
                 w = ain2 * (xm.x * xm.x + xm.y * xm.y);
             } else {
-                a = cmul(ain, spectrum_at<D>(X, phu, phv, jui, jvi));
+                a = cmul(ain, spectrum_at<M>(X, phu, phv, jui, jvi, norm));
             }
             landed = deposit<MODE, NS>(sys, J, R, dx, dy, dz, a, w, psf, field, status);
         }
         if (MODE == MODE_SPLAT && vis) {
-            // one visibility bit per secondary ray: bin f -> word g * D^2/32 + f/32
+            // one visibility bit per secondary ray: bin f -> word g * M^2/32 + f/32
             const unsigned word = __ballot_sync(0xffffffffu, landed);
-            if ((threadIdx.x & 31) == 0) vis[g * (long long)(D * D / 32) + (f >> 5)] = word;
+            if ((threadIdx.x & 31) == 0) vis[g * (long long)(M * M / 32) + (f >> 5)] = word;
         }
     }
 }
@@ -415,25 +438,26 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
 // g = -log(-log u), u from Philox (counter (j>>2, i, ray, offset), word j&3).
 // Coherent sensor: p ~ |U~|, a = a_in U~ / (N p).  Incoherent: p ~ |U~|^2,
 // a = a_in U~ / sqrt(N p) so that |a|^2 is the unbiased power weight.
-// Shared scratch after the patch: logp[D*D] floats, sel[n_ssr] ints, red[32].
-template <int D, int MODE, int NS>
+// Shared scratch after the patch: logp[M*M] floats, sel[n_ssr] ints, red[32].
+template <int M, int MODE, int NS>
 __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                              const float2* X, const float2* phu, const float2* phv,
                                              double* psf, float2* field, const EmitOut& eo,
                                              long long g, unsigned* status,
                                              unsigned char* scratch) {
     float* logp = reinterpret_cast<float*>(scratch);
-    int* sel = reinterpret_cast<int*>(logp + D * D);
+    int* sel = reinterpret_cast<int*>(logp + M * M);
     float* red = reinterpret_cast<float*>(sel + sys.n_ssr);
     const bool coh = sys.coherent != 0;
+    const float norm = sys.norm;
     // magnitudes and their sum
     float part = 0.f;
-    for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
-        const int jvi = f / D, jui = f - (f / D) * D;
+    for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
+        const int jvi = f / M, jui = f - (f / M) * M;
         float dx, dy, dz;
         float m = 0.f;
-        if (bin_direction(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz)) {
-            const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+        if (bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
+            const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
             const float p2 = U.x * U.x + U.y * U.y;
             m = coh ? sqrtf(p2) : p2;
         }
@@ -446,7 +470,7 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
     float tot = 0.f;
     for (int w = 0; w < RW_THREADS / 32; ++w) tot += red[w];
     const float inv_tot = tot > 0.f ? 1.f / tot : 0.f;
-    for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
+    for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
         const float pj = logp[f] * inv_tot;
         logp[f] = pj > 0.f ? logf(pj) : -INFINITY;
     }
@@ -457,14 +481,14 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
     for (int i = warp; i < sys.n_ssr; i += RW_THREADS / 32) {
         float best = -INFINITY;
         int bj = 0x7fffffff;
-        for (int G = lane; G * 4 < D * D; G += 32) {
+        for (int G = lane; G * 4 < M * M; G += 32) {
             const uint4 w = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)i, (uint32_t)R.gid,
                                                      (uint32_t)sys.rng_offset), k0, k1);
             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int jb = 4 * G + q;
-                if (jb < D * D) {
+                if (jb < M * M) {
                     const float lp = logp[jb];
                     if (lp > -INFINITY) {
                         const float gmb = -logf(-logf(u01(ws[q])));
@@ -494,9 +518,9 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
         float2 a = make_float2(0.f, 0.f);
         bool ok = false;
         if (jb >= 0) {
-            const int jvi = jb / D, jui = jb - (jb / D) * D;
-            ok = bin_direction<(NS >= 0)>(sys, R, jui - D / 2, jvi - D / 2, dx, dy, dz);
-            const float2 U = spectrum_at<D>(X, phu, phv, jui, jvi);
+            const int jvi = jb / M, jui = jb - (jb / M) * M;
+            ok = bin_direction<(NS >= 0)>(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz);
+            const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
             const float pj = expf(logp[jb]);
             const float sc = coh ? 1.f / (N * pj) : rsqrtf(N * pj);
             a = cscale(cmul(ain, U), sc);

@@ -1,11 +1,12 @@
 // A3 + A4 on their own: the angular spectrum U~ of every incident ray's
 // patch, written to HBM.  Two implementations with identical output:
 //
-//   k_spectra_fft<D>  FP32 mixed-radix Stockham FFT in shared memory (the
-//                     per-ray CUDA-core form used inside the fused kernels);
+//   k_spectra_fft<M>  FP32 mixed-radix Stockham FFT in shared memory (the
+//                     per-ray CUDA-core form used inside the fused kernels),
+//                     any supported padded size M = P D;
 //   k_spectra_tc      the dense contraction U = F X F^T on the tensor cores
-//                     (tcgen05, D = 64), BF16x3 split with FP32 accumulation
-//                     in tensor memory.
+//                     (tcgen05, D = 64 without padding), BF16x3 split with
+//                     FP32 accumulation in tensor memory.
 //
 // Tensor-core form.  A complex product C = A B is one real product
 //   [C_re; C_im] = [[A_re, -A_im], [A_im, A_re]] [B_re; B_im],
@@ -19,23 +20,25 @@
 // is read back (tcgen05.ld), re-split and stored transposed as stage 2's B
 // operand; stage 2's accumulator is staged through shared memory so the
 // spectrum is written coalesced, with the phase factors that refer it to
-// the hit point and the 1/D^2 normalisation applied on the way out.
+// the hit point and the normalisation (1/D^2 without padding) applied on the
+// way out.
 #include "rw_kernels.cuh"
 #include "rw_tc.cuh"
 
 // ------------------------------------------------------------------ FFT form
-template <int D>
-__global__ void __launch_bounds__(RW_THREADS, 2)
+template <int M>
+__global__ void __launch_bounds__(RW_THREADS, M <= 64 ? 2 : 1)
 k_spectra_fft(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
               int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
               float2* __restrict__ out, unsigned* status) {
     extern __shared__ __align__(1024) unsigned char smem[];
     float2* X = reinterpret_cast<float2*>(smem);
-    float2* tw = X + D * D;
-    float2* phu = tw + D;
-    float2* phv = phu + D;
-    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + D);
-    fft_twiddles<D>(tw);
+    float2* tw = X + Patch<M>::ELEMS;
+    float2* phu = tw + M;
+    float2* phv = phu + M;
+    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + M);
+    fft_twiddles<M>(tw);
+    const float norm = sys.norm;
     const long long npix_map = (long long)sys.H * sys.W;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -48,17 +51,17 @@ k_spectra_fft(const DSys sys, const DJob* __restrict__ jobs, const long long* __
             const long long g = tile * RW_TILE + r;
             if (g >= total) break;
             const RayAtDoe& R = info[r];
-            float2* o = out + g * (long long)(D * D);
+            float2* o = out + g * (long long)(M * M);
             if (!R.alive) {
-                for (int f = threadIdx.x; f < D * D; f += RW_THREADS) o[f] = make_float2(0.f, 0.f);
+                for (int f = threadIdx.x; f < M * M; f += RW_THREADS) o[f] = make_float2(0.f, 0.f);
                 continue;
             }
-            gather_patch<D>(sys, R, Tmaps + (long long)jobs[R.job].slot * npix_map, X, phu, phv);
+            gather_patch<M>(sys, R, Tmaps + (long long)jobs[R.job].slot * npix_map, X, phu, phv);
             __syncthreads();
-            fft2d<D, false>(X, tw);
-            for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
-                const int jvi = f / D, jui = f - (f / D) * D;
-                o[f] = spectrum_at<D>(X, phu, phv, jui, jvi);
+            fft2d<M, false>(X, tw);
+            for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
+                const int jvi = f / M, jui = f - (f / M) * M;
+                o[f] = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
             }
             __syncthreads();
         }
@@ -266,7 +269,7 @@ k_spectra_tc(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
             // ---- U~ = Z (natural order) * phases / D^2, coalesced
             for (int f = tid; f < D * D; f += RW_THREADS) {
                 const int jvi = f / D, jui = f - (f / D) * D;
-                o[f] = spectrum_at<D>(S, phu, phv, jui, jvi);
+                o[f] = spectrum_at<D, D>(S, phu, phv, jui, jvi, sys.norm);
             }
             __syncthreads();
         }
@@ -282,13 +285,13 @@ k_spectra_tc(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
 }
 
 // ------------------------------------------------------------------ launchers
-template <int D>
+template <int M>
 static cudaError_t launch_spectra_fft_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                         const long long* prefix, int njob, long long total,
                                         const RaysIn& rays, const float2* T, float2* out,
                                         unsigned* status) {
-    const size_t smem = forward_smem_bytes(D);
-    auto kern = k_spectra_fft<D>;
+    const size_t smem = forward_smem_bytes(M);
+    auto kern = k_spectra_fft<M>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -307,7 +310,7 @@ cudaError_t launch_spectra(const LaunchCtx& L, const DSys& sys, int tc, const DJ
                            const long long* prefix, int njob, long long total, const RaysIn& rays,
                            const float2* T, float2* out, unsigned* status) {
     if (tc) {
-        if (sys.D != tcdft::D) return cudaErrorInvalidValue;
+        if (sys.D != tcdft::D || sys.M != tcdft::D) return cudaErrorInvalidValue;
         cudaError_t e = cudaFuncSetAttribute(k_spectra_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)tcdft::SMEM);
         if (e != cudaSuccess) return e;
@@ -319,11 +322,12 @@ cudaError_t launch_spectra(const LaunchCtx& L, const DSys& sys, int tc, const DJ
             sys, jobs, prefix, njob, total, rays, T, out, status);
         return cudaGetLastError();
     }
-    switch (sys.D) {
+    switch (sys.M) {
         case 16: return launch_spectra_fft_d<16>(L, sys, jobs, prefix, njob, total, rays, T, out, status);
         case 32: return launch_spectra_fft_d<32>(L, sys, jobs, prefix, njob, total, rays, T, out, status);
         case 64: return launch_spectra_fft_d<64>(L, sys, jobs, prefix, njob, total, rays, T, out, status);
         case 96: return launch_spectra_fft_d<96>(L, sys, jobs, prefix, njob, total, rays, T, out, status);
+        case 128: return launch_spectra_fft_d<128>(L, sys, jobs, prefix, njob, total, rays, T, out, status);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -115,6 +115,7 @@ def system_struct(system, phi, amp=None, dft="fft32", surfaces=None):
     s.doe.dft = _DFT[dft]
     s.doe.seed = int(doe.seed)
     s.doe.rng_offset = int(doe.rng_offset)
+    s.doe.pad = int(getattr(doe, "pad", 1))
     sen = system.sensor
     s.sensor.z = float(sen.z)
     s.sensor.nx, s.sensor.ny = int(sen.nx), int(sen.ny)
@@ -224,9 +225,10 @@ def rw_backward_vis(ctx, sys_struct, jobs_arr, rays, dl_dpsf, vis, dphi=None, da
                                       _ptr(dphi), _ptr(damp), _ptr(dsurf)), "rw_backward_vis")
 
 
-def alloc_vis(n_rays, D, device):
-    """One visibility bit per secondary ray (int32 words, bit-exact uint32)."""
-    return torch.empty(n_rays * D * D // 32, dtype=torch.int32, device=device)
+def alloc_vis(n_rays, M, device):
+    """One visibility bit per secondary ray, M x M bins per incident ray
+    (M = pad * D; int32 words, bit-exact uint32)."""
+    return torch.empty(n_rays * M * M // 32, dtype=torch.int32, device=device)
 
 
 def rw_patch_spectra(ctx, sys_struct, jobs_arr, rays, spectra):
@@ -289,7 +291,7 @@ class Simulator:
 
     def emit(self, out=None):
         sysm = self.w.system
-        slots = sysm.doe.D ** 2 if sysm.doe.emit == "exhaustive" else sysm.doe.n_ssr
+        slots = sysm.doe.M ** 2 if sysm.doe.emit == "exhaustive" else sysm.doe.n_ssr
         if out is None:
             out = alloc_emitted(self.n_rays, slots, self.dev)
         s, keep = self.sys_struct()
@@ -297,10 +299,10 @@ class Simulator:
         return out
 
     def spectra(self, dft=None, out=None):
-        """Patch spectra U~ [n_rays, D, D] (complex64) with the FFT or tensor cores."""
-        D = self.w.system.doe.D
+        """Patch spectra U~ [n_rays, M, M] (complex64) with the FFT or tensor cores."""
+        M = self.w.system.doe.M
         if out is None:
-            out = torch.empty(self.n_rays, D, D, 2, dtype=torch.float32, device=self.dev)
+            out = torch.empty(self.n_rays, M, M, 2, dtype=torch.float32, device=self.dev)
         s, keep = system_struct(self.w.system, self.phi, self.amp, dft or self.dft)
         rw_patch_spectra(self.ctx, s, self.jobs, self.rays, out)
         return torch.view_as_complex(out)
