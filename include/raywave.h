@@ -74,6 +74,9 @@ enum { RW_EMIT_EXHAUSTIVE = 0, RW_EMIT_SAMPLED = 1 };
 enum { RW_PHASE_HEIGHT = 0, RW_PHASE_FIXED = 1 };
 /* patch transform implementation */
 enum { RW_DFT_FFT32 = 0, RW_DFT_TC = 1 };
+/* rw_doe.flags: trace every secondary ray (no block culling; the results are
+ * the same, only slower -- for verification) */
+enum { RW_DOE_TRACE_ALL = 1 };
 
 #define RW_MAX_SURFACES 16
 
@@ -115,7 +118,11 @@ typedef struct {
                             * transformed on M = P D points, M in {16, 32, 64, 96, 128};
                             * bins are k_j = 2 pi j / (M pitch), and U~ is scaled by
                             * 1/M^2 (coherent sensor) or 1/(D M) (incoherent) */
-    int32_t reserved_doe;  /* 0 */
+    int32_t flags;         /* RW_DOE_* bits, 0 by default.  Without RW_DOE_TRACE_ALL
+                            * the exhaustive incoherent forward over plane/sphere
+                            * surfaces skips blocks of bins whose affine-arithmetic
+                            * enclosure of the sensor hit lies two pixels or more
+                            * outside the sensor window (they cannot deposit) */
 } rw_doe;
 
 /* Sensor plane z = const.  Pixel (i, j) of job J is centred at
@@ -189,6 +196,21 @@ rw_status rw_device_status(rw_ctx* ctx, uint32_t* status_out);
 const char* rw_version(void);
 /* Number of kernels this context has launched so far (for benchmarks). */
 int64_t rw_launch_count(const rw_ctx* ctx);
+/* Per-launch timing (library extension for benchmarks; the paper has no
+ * counterpart).  rw_profile(ctx, 1) synchronises the stream, clears the
+ * totals and from then on records a CUDA event on the context's stream just
+ * before and just after every kernel launch (not while the stream is being
+ * captured into a graph); rw_profile(ctx, 0) stops recording.
+ * rw_profile_read synchronises the stream, folds the recorded launches into
+ * per-kernel totals (since the last rw_profile call) and returns how many
+ * kernels there are; rw_profile_entry(i) gives kernel i's name (owned by the
+ * context, valid until the next rw_profile / rw_profile_read), its summed
+ * launch durations in ms and its launch count.  Errors: RW_EINVAL (null
+ * argument, index out of range), RW_ECUDA. */
+rw_status rw_profile(rw_ctx* ctx, int32_t enable);
+rw_status rw_profile_read(rw_ctx* ctx, int32_t* n_kernels);
+rw_status rw_profile_entry(rw_ctx* ctx, int32_t i, const char** kernel, double* total_ms,
+                           int64_t* launches);
 
 /* ---- A0: ray generation ------------------------------------------------ */
 

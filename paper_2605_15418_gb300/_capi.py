@@ -17,6 +17,7 @@ RW_GATHER_NEAREST, RW_GATHER_BILINEAR = 0, 1
 RW_EMIT_EXHAUSTIVE, RW_EMIT_SAMPLED = 0, 1
 RW_PHASE_HEIGHT, RW_PHASE_FIXED = 0, 1
 RW_DFT_FFT32, RW_DFT_TC = 0, 1
+RW_DOE_TRACE_ALL = 1
 RW_MAX_SURFACES = 16
 FP = C.POINTER(C.c_float)
 DP = C.POINTER(C.c_double)
@@ -36,7 +37,7 @@ class rw_doe(C.Structure):
                 ("D", C.c_int32), ("gather", C.c_int32), ("emit", C.c_int32),
                 ("n_ssr", C.c_int32), ("phase_model", C.c_int32), ("dft", C.c_int32),
                 ("seed", C.c_uint64), ("rng_offset", C.c_uint64),
-                ("pad", C.c_int32), ("reserved_doe", C.c_int32)]
+                ("pad", C.c_int32), ("flags", C.c_int32)]
 
 
 class rw_sensor(C.Structure):
@@ -79,6 +80,10 @@ EXPORTS = {
     "rw_device_status": (C.c_int, [C.c_void_p, C.POINTER(C.c_uint32)]),
     "rw_version": (C.c_char_p, []),
     "rw_launch_count": (C.c_int64, [C.c_void_p]),
+    "rw_profile": (C.c_int, [C.c_void_p, C.c_int32]),
+    "rw_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
+    "rw_profile_entry": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_char_p),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
     "rw_generate_rays": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(rw_job),
                                    C.c_int32, C.POINTER(rw_rays)]),
     "rw_doe_emit": (C.c_int, [C.c_void_p, C.POINTER(rw_system), C.POINTER(rw_job), C.c_int32,

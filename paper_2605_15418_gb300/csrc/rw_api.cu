@@ -72,6 +72,7 @@ struct rw_ctx {
     DevBuf acc;         // double PSF accumulator
     DevBuf split_rays;  // split adjoint: per-ray state, offsets, sums
     DevBuf split_items; // split adjoint: work list of visible secondary rays
+    DevBuf keep;        // block culling: kept 8 x 8 bin blocks per incident ray
     unsigned long long* count_host = nullptr;   // pinned
     DevBuf misc;        // status word + loss sums
     void* staging = nullptr;       // pinned host copy source of `tables`
@@ -84,6 +85,15 @@ struct rw_ctx {
     size_t cap_used = 0;
     int64_t launches = 0;
     long long grid_override = 0;
+    // per-launch timing (rw_profile): events around every kernel launch
+    bool prof_on = false;
+    ProfHook prof_hook{};
+    std::vector<cudaEvent_t> prof_pool;       // created on demand, reused
+    std::vector<const char*> prof_names;      // name per recorded event (null: end)
+    size_t prof_used = 0;
+    std::vector<std::string> prof_kernels;    // results of the last rw_profile_read
+    std::vector<double> prof_ms;
+    std::vector<int64_t> prof_count;
 };
 
 static rw_status fail(rw_ctx* c, rw_status s, const std::string& m) {
@@ -170,11 +180,31 @@ static rw_status upload(rw_ctx* ctx, const std::vector<std::pair<const void*, si
     return RW_OK;
 }
 
+static bool capturing(rw_ctx* ctx);
+
+static void prof_mark(void* user, const char* kernel) {
+    rw_ctx* ctx = static_cast<rw_ctx*>(user);
+    if (ctx->prof_used == ctx->prof_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        ctx->prof_pool.push_back(e);
+        ctx->prof_names.push_back(nullptr);
+    }
+    if (cudaEventRecord(ctx->prof_pool[ctx->prof_used], ctx->stream) != cudaSuccess) return;
+    ctx->prof_names[ctx->prof_used++] = kernel;
+}
+
 static LaunchCtx lctx(rw_ctx* ctx) {
     LaunchCtx L;
     L.stream = ctx->stream;
     L.num_sms = ctx->num_sms;
     L.grid_override = ctx->grid_override;
+    L.prof = nullptr;
+    if (ctx->prof_on && !capturing(ctx)) {
+        ctx->prof_hook.user = ctx;
+        ctx->prof_hook.mark = prof_mark;
+        L.prof = &ctx->prof_hook;
+    }
     return L;
 }
 
@@ -288,6 +318,7 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
     d.seed = doe.seed;
     d.rng_offset = doe.rng_offset;
     d.kstep = (float)(2.0 * M_PI / (d.M * doe.pitch));
+    d.cull = (doe.flags & RW_DOE_TRACE_ALL) ? 0 : 1;
     d.sensor_z = sen.z;
     d.sensor_gap = (float)(sen.z - prev_z);
     d.nx = sen.nx; d.ny = sen.ny;
@@ -427,11 +458,62 @@ rw_status rw_destroy(rw_ctx* ctx) {
     ctx->cap_dev.release();
     ctx->split_rays.release();
     ctx->split_items.release();
+    ctx->keep.release();
     if (ctx->cap_host) cudaFreeHost(ctx->cap_host);
     if (ctx->count_host) cudaFreeHost(ctx->count_host);
     if (ctx->staging) cudaFreeHost(ctx->staging);
     if (ctx->staging_done) cudaEventDestroy(ctx->staging_done);
+    for (cudaEvent_t e : ctx->prof_pool) cudaEventDestroy(e);
     delete ctx;
+    return RW_OK;
+}
+
+rw_status rw_profile(rw_ctx* ctx, int32_t enable) {
+    if (!ctx) return RW_EINVAL;
+    ctx->err.clear();
+    RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    RW_CUDA(cudaStreamSynchronize(ctx->stream), "profile sync");
+    ctx->prof_on = enable != 0;
+    ctx->prof_used = 0;
+    ctx->prof_kernels.clear();
+    ctx->prof_ms.clear();
+    ctx->prof_count.clear();
+    return RW_OK;
+}
+
+rw_status rw_profile_read(rw_ctx* ctx, int32_t* n_kernels) {
+    if (!ctx || !n_kernels) return fail(ctx, RW_EINVAL, "null argument");
+    ctx->err.clear();
+    RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    RW_CUDA(cudaStreamSynchronize(ctx->stream), "profile sync");
+    for (size_t i = 0; i + 1 < ctx->prof_used; ++i) {
+        const char* name = ctx->prof_names[i];
+        if (!name || ctx->prof_names[i + 1]) continue;     // a start mark followed by its end
+        float ms = 0.f;
+        RW_CUDA(cudaEventElapsedTime(&ms, ctx->prof_pool[i], ctx->prof_pool[i + 1]), "elapsed");
+        size_t k = 0;
+        while (k < ctx->prof_kernels.size() && ctx->prof_kernels[k] != name) ++k;
+        if (k == ctx->prof_kernels.size()) {
+            ctx->prof_kernels.push_back(name);
+            ctx->prof_ms.push_back(0.0);
+            ctx->prof_count.push_back(0);
+        }
+        ctx->prof_ms[k] += ms;
+        ctx->prof_count[k] += 1;
+    }
+    ctx->prof_used = 0;
+    *n_kernels = (int32_t)ctx->prof_kernels.size();
+    return RW_OK;
+}
+
+rw_status rw_profile_entry(rw_ctx* ctx, int32_t i, const char** kernel, double* total_ms,
+                           int64_t* launches) {
+    if (!ctx || !kernel || !total_ms || !launches) return fail(ctx, RW_EINVAL, "null argument");
+    if (i < 0 || i >= (int32_t)ctx->prof_kernels.size())
+        return fail(ctx, RW_EINVAL, "profile entry out of range");
+    *kernel = ctx->prof_kernels[i].c_str();
+    *total_ms = ctx->prof_ms[i];
+    *launches = ctx->prof_count[i];
     return RW_OK;
 }
 
@@ -576,9 +658,16 @@ static rw_status forward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* j
             RW_OK)
             return st;
         RW_CUDA(cudaMemsetAsync(ctx->acc.p, 0, npx * sizeof(double), ctx->stream), "acc clear");
+        unsigned* keep = nullptr;
+        if (forward_culls(P.sys)) {
+            const size_t kb = (size_t)P.total * cull_keep_words(P.sys.M) * sizeof(unsigned);
+            if ((st = ensure_buf(ctx, ctx->keep, kb, "block-culling scratch")) != RW_OK) return st;
+            keep = (unsigned*)ctx->keep.p;
+            ctx->launches++;          // k_cull
+        }
         RW_CUDA(launch_forward(lctx(ctx), MODE_SPLAT, P.sys, dj, dp, njob, P.total,
                                rays_in(rays), T, (double*)ctx->acc.p, nullptr, eo,
-                               status_word(ctx), vis),
+                               status_word(ctx), vis, keep),
                 "forward kernel");
         ctx->launches++;
         RW_CUDA(launch_psf_finalize(lctx(ctx), (const double*)ctx->acc.p, psf, npx), "psf finalize");

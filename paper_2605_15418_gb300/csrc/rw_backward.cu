@@ -490,9 +490,11 @@ static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const 
     if (L.grid_override > 0) grid = L.grid_override;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
+    RW_MARK(L, "k_backward");
     kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(sys, jobs, prefix, njob, total, rays, T,
                                                           amp, gpsf, dphi, damp, dsurf, status,
                                                           vis);
+    RW_MARK(L, nullptr);
     return cudaGetLastError();
 }
 

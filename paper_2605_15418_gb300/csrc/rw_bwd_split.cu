@@ -302,7 +302,9 @@ cudaError_t launch_bs_count(const LaunchCtx& L, const unsigned* vis, long long n
     long long grid = (nwords + 255) / 256;
     if (grid > (long long)L.num_sms * 8) grid = (long long)L.num_sms * 8;
     if (grid < 1) grid = 1;
+    RW_MARK(L, "k_bs_count");
     k_bs_count<<<(unsigned)grid, 256, 0, L.stream>>>(vis, nwords, total);
+    RW_MARK(L, nullptr);
     return cudaGetLastError();
 }
 
@@ -333,8 +335,10 @@ static cudaError_t launch_split_d(const LaunchCtx& L, const DSys& sys, const DJo
     size_t smem1 = sampled_scratch_offset(M) + 64;
     cudaError_t e = persistent_launch_cfg(k_bs_spectra<M>, smem1, L.num_sms, ntiles, L.grid_override, &grid);
     if (e != cudaSuccess) return e;
+    RW_MARK(L, "k_bs_spectra");
     k_bs_spectra<M><<<(unsigned)grid, RW_THREADS, smem1, L.stream>>>(sys, jobs, prefix, njob,
                                                                      total, rays, T, vis, B, status);
+    RW_MARK(L, nullptr);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (nitems > 0) {
         int per_sm = 0;
@@ -343,8 +347,10 @@ static cudaError_t launch_split_d(const LaunchCtx& L, const DSys& sys, const DJo
         long long g2 = (long long)L.num_sms * (per_sm > 0 ? per_sm : 1) * 4;
         const long long need = (nitems + RW_THREADS - 1) / RW_THREADS;
         if (g2 > need) g2 = need;
+        RW_MARK(L, "k_bs_trace");
         k_bs_trace<M, NS><<<(unsigned)g2, RW_THREADS, 0, L.stream>>>(sys, gpsf, B, nitems, dsurf,
                                                                       status);
+        RW_MARK(L, nullptr);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     size_t smem3 = sampled_scratch_offset(M);
@@ -352,8 +358,10 @@ static cudaError_t launch_split_d(const LaunchCtx& L, const DSys& sys, const DJo
     if (smem3 < red) smem3 = red;
     e = persistent_launch_cfg(k_bs_scatter<M>, smem3, L.num_sms, ntiles, L.grid_override, &grid);
     if (e != cudaSuccess) return e;
+    RW_MARK(L, "k_bs_scatter");
     k_bs_scatter<M><<<(unsigned)grid, RW_THREADS, smem3, L.stream>>>(
         sys, jobs, prefix, njob, total, rays, T, amp, B, dphi, damp, dsurf, status);
+    RW_MARK(L, nullptr);
     return cudaGetLastError();
 }
 

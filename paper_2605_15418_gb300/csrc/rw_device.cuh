@@ -49,6 +49,7 @@ struct DSys {
     // DOE
     int H, W, D, gather, emit, n_ssr, phase_model, conformal;
     int M;             // transform size P D (zero-padded patch)
+    int cull;          // 1: exhaustive incoherent forward drops blocks that miss the sensor
     float norm;        // spectrum scale: 1/M^2 (coherent sensor) or 1/(D M)
     double pitch;
     float pitchf, inv_pitch;

@@ -66,13 +66,15 @@ __global__ void __launch_bounds__(RW_THREADS, FwdOcc<M>::value)
 k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
           int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
           double* __restrict__ psf, float2* __restrict__ field, EmitOut eo, unsigned* status,
-          unsigned* __restrict__ vis) {
+          unsigned* __restrict__ vis, const unsigned* __restrict__ keep) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* X = reinterpret_cast<float2*>(smem);
     float2* tw = X + Patch<M>::ELEMS;
     float2* phu = tw + M;
     float2* phv = phu + M;
     RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + M);
+    // exhaustive emission with block culling: visibility words of the ray
+    unsigned* vw = reinterpret_cast<unsigned*>(smem + sampled_scratch_offset(M));
     fft_twiddles<M>(tw);
     const long long npix_map = (long long)sys.H * sys.W;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
@@ -97,7 +99,8 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             fft2d<M, false>(X, tw);
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
                 emit_exhaustive<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
-                                             tile * RW_TILE + r, status, vis);
+                                             tile * RW_TILE + r, status, vis,
+                                             keep, vw);
             } else {
                 emit_sampled<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                           tile * RW_TILE + r, status,
@@ -105,6 +108,44 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             }
             __syncthreads();
         }
+    }
+}
+
+// ------------------------------------------------------------- block culling
+// keep[g * KW + w] bit b: 8 x 8 bin block 32 w + b of incident ray g may reach
+// the sensor (its affine enclosure does not miss the sensor window).  One
+// thread per (ray, block) pair of a 32-ray tile; rays that miss the DOE keep
+// nothing.
+template <int M, int NS>
+__global__ void __launch_bounds__(RW_THREADS, 2)
+k_cull(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
+       int njob, long long total, RaysIn rays, unsigned* __restrict__ keep, unsigned* status) {
+    constexpr int B8 = M / 8, NB = B8 * B8, KW = cull_keep_words(M);
+    __shared__ RayAtDoe info[RW_TILE];
+    __shared__ unsigned kw[RW_TILE * KW];
+    const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
+    const float ks = sys.kstep;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x < RW_TILE)
+            incident_to_doe(sys, jobs, prefix, njob, total, rays, tile * RW_TILE + threadIdx.x,
+                            info[threadIdx.x], status);
+        for (int i = threadIdx.x; i < RW_TILE * KW; i += RW_THREADS) kw[i] = 0u;
+        __syncthreads();
+        for (int t = threadIdx.x; t < RW_TILE * NB; t += RW_THREADS) {
+            const int r = t / NB, bi = t - r * NB;
+            const RayAtDoe& R = info[r];
+            if (!R.alive) continue;
+            const float ju_c = (float)((bi % B8) * 8 - M / 2) + 3.5f;
+            const float jv_c = (float)((bi / B8) * 8 - M / 2) + 3.5f;
+            if (!af_block_misses_sensor<NS>(sys, R, fmaf(ks, ju_c, R.kin_u), 3.5f * ks,
+                                            fmaf(ks, jv_c, R.kin_v), 3.5f * ks))
+                atomicOr(&kw[r * KW + (bi >> 5)], 1u << (bi & 31));
+        }
+        __syncthreads();
+        const long long g0 = tile * RW_TILE;
+        for (int i = threadIdx.x; i < RW_TILE * KW; i += RW_THREADS)
+            if (g0 + i / KW < total) keep[g0 * KW + i] = kw[i];
     }
 }
 
@@ -132,7 +173,27 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
                                     const long long* prefix, int njob, long long total,
                                     const RaysIn& rays, const float2* T, double* psf,
                                     float2* field, const EmitOut& eo, unsigned* status,
-                                    unsigned* vis) {
+                                    unsigned* vis, unsigned* keep) {
+    if constexpr (MODE == MODE_SPLAT && NS >= 0) {
+        if (keep) {
+            // block culling: kept-block bits for every incident ray first
+            int per_sm = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cull<M, NS>,
+                                                                          RW_THREADS, 0);
+            if (e != cudaSuccess) return e;
+            long long ntiles = (total + RW_TILE - 1) / RW_TILE;
+            long long grid = (long long)L.num_sms * (per_sm > 0 ? per_sm : 1);
+            if (grid > ntiles) grid = ntiles;
+            if (grid < 1) grid = 1;
+            RW_MARK(L, "k_cull");
+            k_cull<M, NS><<<(unsigned)grid, RW_THREADS, 0, L.stream>>>(sys, jobs, prefix, njob,
+                                                                      total, rays, keep, status);
+            RW_MARK(L, nullptr);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    } else {
+        keep = nullptr;
+    }
     size_t smem = forward_smem_bytes(M, sys.emit, sys.n_ssr);
     auto kern = k_forward<M, MODE, NS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -147,8 +208,10 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
     if (L.grid_override > 0) grid = L.grid_override;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
+    RW_MARK(L, "k_forward");
     kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(sys, jobs, prefix, njob, total, rays,
-                                                          T, psf, field, eo, status, vis);
+                                                          T, psf, field, eo, status, vis, keep);
+    RW_MARK(L, nullptr);
     return cudaGetLastError();
 }
 
@@ -157,35 +220,43 @@ template <int M>
 static cudaError_t launch_splat(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                 const long long* prefix, int njob, long long total,
                                 const RaysIn& rays, const float2* T, double* psf,
-                                const EmitOut& eo, unsigned* status, unsigned* vis) {
+                                const EmitOut& eo, unsigned* status, unsigned* vis,
+                                unsigned* keep) {
+#define RW_SPLAT(NN) \
+    launch_forward_d<M, MODE_SPLAT, NN>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis, keep)
     if (sys.fast_ok) {
         switch (sys.n_post) {
-            case 0: return launch_forward_d<M, MODE_SPLAT, 0>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
-            case 2: return launch_forward_d<M, MODE_SPLAT, 2>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
-            case 4: return launch_forward_d<M, MODE_SPLAT, 4>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
-            case 6: return launch_forward_d<M, MODE_SPLAT, 6>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis);
+            case 0: return RW_SPLAT(0);
+            case 2: return RW_SPLAT(2);
+            case 4: return RW_SPLAT(4);
+            case 6: return RW_SPLAT(6);
             default: break;
         }
     }
-    return launch_forward_d<M, MODE_SPLAT, -1>(L, sys, jobs, prefix, njob, total, rays, T, psf,
-                                               nullptr, eo, status, vis);
+    return RW_SPLAT(-1);
+#undef RW_SPLAT
+}
+
+bool forward_culls(const DSys& sys) {
+    return sys.cull && sys.emit == RW_EMIT_EXHAUSTIVE && !sys.coherent && sys.fast_ok &&
+           (sys.n_post == 0 || sys.n_post == 2 || sys.n_post == 4 || sys.n_post == 6);
 }
 
 cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const DJob* jobs,
                            const long long* prefix, int njob, long long total,
                            const RaysIn& rays, const float2* T, double* psf, float2* field,
-                           const EmitOut& eo, unsigned* status, unsigned* vis) {
+                           const EmitOut& eo, unsigned* status, unsigned* vis, unsigned* keep) {
 #define RW_FWD_CASE(DD)                                                                       \
     case DD:                                                                                  \
         if (mode == MODE_SPLAT)                                                               \
             return launch_splat<DD>(L, sys, jobs, prefix, njob, total, rays, T, psf, eo,      \
-                                    status, vis);                                             \
+                                    status, vis, forward_culls(sys) ? keep : nullptr);        \
         if (mode == MODE_COHERENT)                                                            \
             return launch_forward_d<DD, MODE_COHERENT, -1>(L, sys, jobs, prefix, njob, total, \
                                                            rays, T, psf, field, eo, status,   \
-                                                           nullptr);                          \
+                                                           nullptr, nullptr);                 \
         return launch_forward_d<DD, MODE_EMIT, -1>(L, sys, jobs, prefix, njob, total, rays, T,\
-                                                   psf, field, eo, status, nullptr);
+                                                   psf, field, eo, status, nullptr, nullptr);
     switch (sys.M) {
         RW_FWD_CASE(16)
         RW_FWD_CASE(32)
@@ -203,7 +274,9 @@ cudaError_t launch_prep_maps(const LaunchCtx& L, const float* phi, const float* 
     long long grid = (n + 255) / 256;
     long long cap = (long long)L.num_sms * 8;
     if (grid > cap) grid = cap;
+    RW_MARK(L, "k_prep_maps");
     k_prep_maps<<<(unsigned)grid, 256, 0, L.stream>>>(phi, amp, npix, scales_dev, nslot, T);
+    RW_MARK(L, nullptr);
     return cudaGetLastError();
 }
 
@@ -214,8 +287,10 @@ cudaError_t launch_generate_rays(const LaunchCtx& L, const GenJob* jobs, const l
     long long cap = (long long)L.num_sms * 16;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
+    RW_MARK(L, "k_generate_rays");
     k_generate_rays<<<(unsigned)grid, 256, 0, L.stream>>>(jobs, prefix, njob, total, z_start,
                                                           n_object, out);
+    RW_MARK(L, nullptr);
     return cudaGetLastError();
 }
 
@@ -225,7 +300,9 @@ cudaError_t launch_coherent_finalize(const LaunchCtx& L, const float2* field, fl
     long long cap = (long long)L.num_sms * 8;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
+    RW_MARK(L, "k_coherent_finalize");
     k_coherent_finalize<<<(unsigned)grid, 256, 0, L.stream>>>(field, psf, n);
+    RW_MARK(L, nullptr);
     return cudaGetLastError();
 }
 
@@ -234,6 +311,8 @@ cudaError_t launch_psf_finalize(const LaunchCtx& L, const double* acc, float* ps
     long long cap = (long long)L.num_sms * 8;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
+    RW_MARK(L, "k_psf_finalize");
     k_psf_finalize<<<(unsigned)grid, 256, 0, L.stream>>>(acc, psf, n);
+    RW_MARK(L, nullptr);
     return cudaGetLastError();
 }

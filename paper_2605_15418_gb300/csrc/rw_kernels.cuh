@@ -4,14 +4,29 @@
 #include "rw_device.cuh"
 #include "rw_fast.cuh"
 #include "rw_fft.cuh"
+#include "rw_cull.cuh"
 
 enum { MODE_SPLAT = 0, MODE_COHERENT = 1, MODE_EMIT = 2 };
+
+// Optional per-launch timing: mark(user, name) is called just before kernel
+// `name` is launched on the stream and mark(user, nullptr) just after, so the
+// caller can record CUDA events around every launch.
+struct ProfHook {
+    void* user;
+    void (*mark)(void* user, const char* kernel);
+};
 
 struct LaunchCtx {
     cudaStream_t stream;
     int num_sms;
     long long grid_override;   // > 0 forces the persistent grid size
+    const ProfHook* prof;      // may be null
 };
+
+#define RW_MARK(L, name)                                          \
+    do {                                                          \
+        if ((L).prof) (L).prof->mark((L).prof->user, (name));     \
+    } while (0)
 
 struct GenJob {
     long long off, n;          // first ray, grid side
@@ -38,9 +53,17 @@ __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(
 __host__ __device__ inline size_t sampled_scratch_offset(int M) {
     return align16(sizeof(float2) * (size_t)(M * (M + 1) + 3 * M) + sizeof(RayAtDoe) * RW_TILE);
 }
+// block culling (exhaustive emission): one bit per 8 x 8 block of bins and
+// incident ray (set: the block is kept); the forward stages the current
+// ray's visibility words in shared memory
+__host__ __device__ constexpr int cull_keep_words(int M) { return ((M / 8) * (M / 8) + 31) / 32; }
+__host__ __device__ inline size_t cull_scratch_bytes(int M) {
+    return align16(sizeof(unsigned) * (size_t)(M * M / 32));
+}
 inline size_t forward_smem_bytes(int M, int emit = RW_EMIT_EXHAUSTIVE, int n_ssr = 0) {
     size_t b = sampled_scratch_offset(M);
     if (emit == RW_EMIT_SAMPLED) b += sizeof(float) * (size_t)M * M + sizeof(int) * n_ssr + 128;
+    else b += cull_scratch_bytes(M);
     return b;
 }
 
@@ -381,12 +404,73 @@ __device__ __forceinline__ void emit_dead(const DSys& sys, long long g, long lon
 }
 
 // ------------------------------------------------------------------ A5 exhaustive
+// Ray phase: trace only the bins of kept blocks, packed over the CTA's
+// threads (converged warps).  Dropped bins cannot deposit, so the image and
+// the visibility mask equal those of tracing every bin.
+template <int M, int NS>
+__device__ __forceinline__ void emit_culled(const DSys& sys, const DJob& J, const RayAtDoe& R,
+                                            const float2* X, double* psf, long long g,
+                                            unsigned* status, unsigned* __restrict__ vis,
+                                            const unsigned* __restrict__ keepg, unsigned* vw) {
+    constexpr int S = Patch<M>::S;
+    constexpr int NW = M * M / 32, B8 = M / 8, KW = cull_keep_words(M);
+    unsigned keep[KW];
+    int nkept = 0;
+#pragma unroll
+    for (int w = 0; w < KW; ++w) {
+        keep[w] = __ldg(keepg + g * KW + w);
+        nkept += __popc(keep[w]);
+    }
+    if (vis) {
+        for (int i = threadIdx.x; i < NW; i += RW_THREADS) vw[i] = 0u;
+        __syncthreads();
+    }
+    const float2 ain = make_float2(R.a_re, R.a_im);
+    const float norm = sys.norm;
+    const float ain2 = (ain.x * ain.x + ain.y * ain.y) * norm * norm;
+    for (int i = threadIdx.x; i < 64 * nkept; i += RW_THREADS) {
+        // block of the (i / 64)-th set bit, bin i % 64 inside it
+        int k = i >> 6, bi = 0;
+#pragma unroll
+        for (int w = 0; w < KW; ++w) {
+            const int c = __popc(keep[w]);
+            if (k >= 0 && k < c) bi = w * 32 + (int)__fns(keep[w], 0u, k + 1);
+            k -= c;
+        }
+        const int q = i & 63;
+        const int jui = (bi % B8) * 8 + (q & 7), jvi = (bi / B8) * 8 + (q >> 3);
+        float dx, dy, dz;
+        if (!bin_direction<true>(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) continue;
+        int mu = jui + M / 2; if (mu >= M) mu -= M;
+        int mv = jvi + M / 2; if (mv >= M) mv -= M;
+        const float2 xm = X[mv * S + mu];
+        const float w2 = ain2 * (xm.x * xm.x + xm.y * xm.y);
+        if (deposit<MODE_SPLAT, NS>(sys, J, R, dx, dy, dz, make_float2(0.f, 0.f), w2, psf,
+                                    nullptr, status) && vis) {
+            const int f = jvi * M + jui;
+            atomicOr(&vw[f >> 5], 1u << (f & 31));
+        }
+    }
+    if (vis) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < NW; i += RW_THREADS) vis[g * (long long)NW + i] = vw[i];
+    }
+}
+
 template <int M, int MODE, int NS>
 __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                                 const float2* X, const float2* phu,
                                                 const float2* phv, double* psf, float2* field,
                                                 const EmitOut& eo, long long g, unsigned* status,
-                                                unsigned* __restrict__ vis) {
+                                                unsigned* __restrict__ vis,
+                                                const unsigned* __restrict__ keepg,
+                                                unsigned* vw) {
+    if constexpr (MODE == MODE_SPLAT && NS >= 0) {
+        if (keepg) {
+            emit_culled<M, NS>(sys, J, R, X, psf, g, status, vis, keepg, vw);
+            return;
+        }
+    }
     constexpr int S = Patch<M>::S;
     const float2 ain = make_float2(R.a_re, R.a_im);
     const float norm = sys.norm;
@@ -543,10 +627,15 @@ cudaError_t launch_prep_maps(const LaunchCtx& L, const float* phi, const float* 
 cudaError_t launch_generate_rays(const LaunchCtx& L, const GenJob* jobs, const long long* prefix,
                                  int njob, long long total, double z_start, double n_object,
                                  const RaysOut& out);
+// Block culling applies (exhaustive incoherent splat over plane/sphere
+// surfaces without RW_DOE_TRACE_ALL); `keep` then needs cull_keep_words(M)
+// words per incident ray.
+bool forward_culls(const DSys& sys);
 cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const DJob* jobs,
-                           const long long* prefix, int njob, long long total, const RaysIn& rays,
-                           const float2* T, double* acc, float2* field, const EmitOut& eo,
-                           unsigned* status, unsigned* vis = nullptr);
+                           const long long* prefix, int njob, long long total,
+                           const RaysIn& rays, const float2* T, double* psf, float2* field,
+                           const EmitOut& eo, unsigned* status, unsigned* vis = nullptr,
+                           unsigned* keep = nullptr);
 cudaError_t launch_psf_finalize(const LaunchCtx& L, const double* acc, float* psf, long long n);
 cudaError_t launch_coherent_finalize(const LaunchCtx& L, const float2* field, float* psf,
                                      long long n);

@@ -53,9 +53,13 @@ cudaError_t launch_loss_eq3(const LaunchCtx& L, const float* I, const float* T, 
     long long cap = (long long)L.num_sms * 4;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
+    RW_MARK(L, "k_loss_sums");
     k_loss_sums<<<(unsigned)grid, 256, 0, L.stream>>>(I, T, n, acc);
+    RW_MARK(L, nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    RW_MARK(L, "k_loss_grad");
     k_loss_grad<<<(unsigned)grid, 256, 0, L.stream>>>(I, T, n, acc, out, g);
+    RW_MARK(L, nullptr);
     return cudaGetLastError();
 }

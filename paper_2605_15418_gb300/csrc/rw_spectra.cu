@@ -301,8 +301,10 @@ static cudaError_t launch_spectra_fft_d(const LaunchCtx& L, const DSys& sys, con
     long long grid = (long long)L.num_sms * (per_sm > 0 ? per_sm : 1);
     if (L.grid_override > 0) grid = L.grid_override;
     if (grid > ntiles) grid = ntiles;
+    RW_MARK(L, "k_spectra_fft");
     kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(sys, jobs, prefix, njob, total, rays, T,
                                                           out, status);
+    RW_MARK(L, nullptr);
     return cudaGetLastError();
 }
 
@@ -318,8 +320,10 @@ cudaError_t launch_spectra(const LaunchCtx& L, const DSys& sys, int tc, const DJ
         long long grid = (long long)L.num_sms * 2;
         if (L.grid_override > 0) grid = L.grid_override;
         if (grid > ntiles) grid = ntiles;
+        RW_MARK(L, "k_spectra_tc");
         k_spectra_tc<<<(unsigned)grid, RW_THREADS, tcdft::SMEM, L.stream>>>(
             sys, jobs, prefix, njob, total, rays, T, out, status);
+        RW_MARK(L, nullptr);
         return cudaGetLastError();
     }
     switch (sys.M) {

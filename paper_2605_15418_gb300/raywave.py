@@ -59,6 +59,24 @@ class Context:
     def launches(self):
         return int(self.lib.rw_launch_count(self.h))
 
+    def profile(self, enable=True):
+        """Start (clearing the totals) or stop per-launch CUDA-event timing."""
+        self._stream()
+        self.check(self.lib.rw_profile(self.h, 1 if enable else 0), "rw_profile")
+
+    def profile_read(self):
+        """{kernel: (total ms, launches)} since profile() was last called."""
+        self._stream()
+        n = C.c_int32(0)
+        self.check(self.lib.rw_profile_read(self.h, C.byref(n)), "rw_profile_read")
+        out = {}
+        for i in range(n.value):
+            name, ms, cnt = C.c_char_p(), C.c_double(), C.c_int64()
+            self.check(self.lib.rw_profile_entry(self.h, i, C.byref(name), C.byref(ms),
+                                                 C.byref(cnt)), "rw_profile_entry")
+            out[name.value.decode()] = (ms.value, cnt.value)
+        return out
+
     def device_status(self):
         self._stream()
         v = C.c_uint32(0)
@@ -91,7 +109,7 @@ def surfaces_struct(surfaces):
     return arr
 
 
-def system_struct(system, phi, amp=None, dft="fft32", surfaces=None):
+def system_struct(system, phi, amp=None, dft="fft32", surfaces=None, trace_all=False):
     """rw_system for `system` with device maps phi (and amp).  Returns
     (struct, keepalive)."""
     doe = system.doe
@@ -116,6 +134,7 @@ def system_struct(system, phi, amp=None, dft="fft32", surfaces=None):
     s.doe.seed = int(doe.seed)
     s.doe.rng_offset = int(doe.rng_offset)
     s.doe.pad = int(getattr(doe, "pad", 1))
+    s.doe.flags = A.RW_DOE_TRACE_ALL if trace_all else 0
     sen = system.sensor
     s.sensor.z = float(sen.z)
     s.sensor.nx, s.sensor.ny = int(sen.nx), int(sen.ny)
@@ -257,8 +276,9 @@ def rw_backward(ctx, sys_struct, jobs_arr, rays, dl_dpsf, dphi=None, damp=None, 
 class Simulator:
     """A workload bound to a context: device maps, jobs and generated rays."""
 
-    def __init__(self, workload, ctx=None, device=0, dft="fft32", rays=None):
+    def __init__(self, workload, ctx=None, device=0, dft="fft32", rays=None, trace_all=False):
         self.ctx = ctx or Context(device)
+        self.trace_all = trace_all
         self.w = workload
         self.dev = self.ctx.device
         sysm = workload.system
@@ -276,7 +296,8 @@ class Simulator:
 
     def sys_struct(self, phi=None, amp=None, surfaces=None):
         return system_struct(self.w.system, self.phi if phi is None else phi,
-                             self.amp if amp is None else amp, self.dft, surfaces)
+                             self.amp if amp is None else amp, self.dft, surfaces,
+                             self.trace_all)
 
     def forward(self, phi=None, surfaces=None, psf=None, vis=None):
         """PSF [njob, ny, nx]; with `vis` (alloc_vis) also the visibility mask."""

@@ -359,7 +359,8 @@ def test_batched_uneven_jobs_one_launch(RW, ctx):
     sim = RW.Simulator(w, ctx=ctx)
     launches0 = ctx.launches
     psf = sim.forward().cpu().numpy()
-    assert ctx.launches - launches0 == 3          # prep maps, fused forward, finalize
+    # prep maps, block culling, fused forward, finalize
+    assert ctx.launches - launches0 == 4
     ref = oracle_psf(w)
     assert rel_l2(psf, ref) <= PSF_TOL, rel_l2(psf, ref)
 
