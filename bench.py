@@ -32,6 +32,11 @@ sys.path.insert(0, ROOT)
 METRIC = ("rays/s fwd+bwd through DOE ray–wave step at PSF err≤1e-4 vs FP64; "
           "% HBM/TC peak")
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) per launch at the default workload, from one ncu
+# capture of the current kernel at n-side 256 scaled by the incident-ray
+# count (16x): see the profiles/ summaries.  A kernel missing here has no
+# capture of its current code.
+TRAFFIC = {}
 NUM_SMS = 152
 
 
@@ -56,26 +61,47 @@ def workload(n_side):
 
 
 # ------------------------------------------------------------------ algorithmic work
-def flops_per_incident(D, n_post):
-    """Algorithmic FP32 operations per incident ray (each add, multiply,
-    divide, square root and compare counted once; an FMA counts 2).
+# FP32 operations (each add, multiply, divide, square root and compare
+# counted once, an FMA twice) of the kernels of one step.
+def fft_flops(M):
+    """Radix FFT count of one M x M patch transform: 5 N log2 N, N = M^2."""
+    return 5.0 * M * M * math.log2(M * M)
 
-    patch spectrum (radix FFT count): 5 N log2 N with N = D^2
-    per secondary ray: emission 45, each spherical surface 65, sensor +
+
+def bin_fwd_flops(S):
+    """One traced secondary ray: emission 45, each spherical surface 65
+    (intersection 20 + 3 sqrt/div, hit 6, normal 15, Snell 20), sensor +
     bilinear splat 20."""
-    fft = 5.0 * D * D * math.log2(D * D)
-    per_sec = 45.0 + 65.0 * n_post + 20.0
-    return fft, fft + D * D * per_sec
+    return 45.0 + 65.0 * S + 20.0
 
 
-def flops_backward_per_incident(D, n_post, visible_frac=1.0):
-    """Adjoint: patch FFT recomputed, then for every secondary ray that reached
-    the sensor (the others carry no gradient) its re-trace (forward count) and
-    reverse (emission 40, each surface 150, sensor 40), the conjugate FFT and
-    the map scatter (8 per pixel)."""
-    fft, fwd = flops_per_incident(D, n_post)
-    per_sec = (fwd - fft) / (D * D) + 40.0 + 150.0 * n_post + 40.0
-    return 2 * fft + visible_frac * D * D * per_sec + 8.0 * D * D
+def bin_bwd_flops(S):
+    """Re-trace of one visible secondary ray plus its reverse (emission 40,
+    each surface 150, sensor 40)."""
+    return bin_fwd_flops(S) + 40.0 + 150.0 * S + 40.0
+
+
+def block_test_flops(S):
+    """Affine-arithmetic test of one 8 x 8 block of bins: direction setup 130,
+    each sphere ~970 (21 affine products at 22, 25 sums/scalings at 10, five
+    square roots / reciprocals at 38), sensor plane 150."""
+    return 280.0 + 970.0 * S
+
+
+def kernel_flops(name, M, D, S, n_rays, rays_with_items, items, blocks, kept):
+    """Algorithmic work of one launch of `name` in the benchmark step."""
+    if name == "k_forward":
+        traced = 64.0 * kept if blocks else float(n_rays) * M * M
+        return n_rays * fft_flops(M) + traced * bin_fwd_flops(S)
+    if name == "k_cull":
+        return blocks * block_test_flops(S)
+    if name == "k_bs_spectra":
+        return rays_with_items * fft_flops(M) + items * 30.0
+    if name == "k_bs_trace":
+        return items * bin_bwd_flops(S)
+    if name == "k_bs_scatter":
+        return rays_with_items * (fft_flops(M) + 8.0 * D * D) + items * 20.0
+    return None
 
 
 # ------------------------------------------------------------------ clocks
@@ -247,12 +273,15 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = sim.ctx.launches
+    sim.ctx.profile(True)
     clk.start()
     for k in range(args.steps):
         flush.zero_()
         step(evs[k])
     torch.cuda.synchronize()
     clocks = clk.stop()
+    prof = sim.ctx.profile_read()
+    sim.ctx.profile(False)
     launches = sim.ctx.launches - launches0
     if dist:
         dist.barrier()
@@ -292,20 +321,25 @@ def main():
     h2d = phi_h.numel() * 4 + tgt_h.numel() * 4
     d2h = psf_h.numel() * 4 + dphi_h.numel() * 4 + dsurf_h.numel() * 8 + 24
 
-    # ---- roofline of the dominant kernel (FP32 ALU bound)
-    D = sysm.doe.D
+    # ---- roofline of the dominant kernel (FP32 ALU bound), per-launch times
+    # from the library's CUDA events around every launch of the timed steps
+    D, M = sysm.doe.D, sysm.doe.M
     lut = torch.tensor([bin(i).count("1") for i in range(256)], dtype=torch.int64, device=dev)
-    visible = int(lut[vis.view(torch.uint8).long()].sum().item())
-    vfrac = visible / float(n_rays * D * D)
+    vrow = vis.view(n_rays, M * M // 32)
+    items = int(lut[vrow.view(torch.uint8).long()].sum().item())
+    rays_with_items = int((vrow != 0).any(1).sum().item())
+    vfrac = items / float(n_rays * M * M)
+    blocks, kept = sim.ctx.cull_stats()
     n_post = len(sysm.surfaces) - sysm.doe_index - 1
     fwd_ms = float(np.mean(t_fwd))
     bwd_ms = float(np.mean(t_bwd))
     peak = NUM_SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12      # TFLOP/s at max SM clock
-    if bwd_ms >= fwd_ms:
-        name, tms, fl = "k_backward", bwd_ms, flops_backward_per_incident(D, n_post, vfrac) * n_rays
-    else:
-        name, tms, fl = "k_forward", fwd_ms, flops_per_incident(D, n_post)[1] * n_rays
-    achieved = fl / (tms / 1e3) / 1e12
+    kernel_ms = {k: v[0] / v[1] for k, v in prof.items() if v[1] > 0}
+    modelled = {k: kernel_flops(k, M, D, n_post, n_rays, rays_with_items, items, blocks, kept)
+                for k in kernel_ms}
+    name = max((k for k in kernel_ms if modelled[k] is not None), key=lambda k: prof[k][0])
+    tms = kernel_ms[name]
+    achieved = modelled[name] / (tms / 1e3) / 1e12
     line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -314,9 +348,13 @@ def main():
                        "D": D, "secondary_rays_per_incident": D * D, "sensor": "512x512x9",
                        "surfaces_after_doe": n_post, "l2": "flushed between steps (256 MB)",
                        "visible_secondary_fraction": vfrac,
-                       "fwd_ms": fwd_ms, "bwd_ms": bwd_ms},
+                       "traced_secondary_fraction": (64.0 * kept / (n_rays * M * M)
+                                                     if blocks else 1.0),
+                       "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
+                       "kernel_ms": {k: round(v, 4) for k, v in kernel_ms.items()}},
             "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": TRAFFIC.get(name),
                          "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal)"},
             "e2e": {"value": world * n_rays / (e2e_ms / 1e3), "unit": "rays/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

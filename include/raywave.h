@@ -211,6 +211,12 @@ rw_status rw_profile(rw_ctx* ctx, int32_t enable);
 rw_status rw_profile_read(rw_ctx* ctx, int32_t* n_kernels);
 rw_status rw_profile_entry(rw_ctx* ctx, int32_t i, const char** kernel, double* total_ms,
                            int64_t* launches);
+/* Block-culling statistics of the most recent forward call on this context
+ * that culled (library extension; the paper has no counterpart): the number
+ * of 8 x 8 bin blocks (n_rays * (M/8)^2) and how many of them were kept and
+ * traced (64 bins each).  Synchronises the stream; (0, 0) if no forward has
+ * culled yet.  Errors: RW_EINVAL, RW_ECUDA. */
+rw_status rw_cull_stats(rw_ctx* ctx, int64_t* blocks, int64_t* kept);
 
 /* ---- A0: ray generation ------------------------------------------------ */
 

@@ -81,6 +81,7 @@ EXPORTS = {
     "rw_version": (C.c_char_p, []),
     "rw_launch_count": (C.c_int64, [C.c_void_p]),
     "rw_profile": (C.c_int, [C.c_void_p, C.c_int32]),
+    "rw_cull_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "rw_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "rw_profile_entry": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_char_p),
                                    C.POINTER(C.c_double), C.POINTER(C.c_int64)]),

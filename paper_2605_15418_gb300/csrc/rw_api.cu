@@ -1,6 +1,7 @@
 // Host side of the C ABI declared in include/raywave.h: argument checks,
 // packing of the host descriptors into device-side structs, per-context
 // scratch, and kernel launches on the context's stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -18,26 +19,14 @@ cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* job
                             const float* dl_dpsf, float* dphi, float* damp, double* dsurf,
                             const unsigned* vis, unsigned* status, int* launches);
 size_t backward_smem_needed(const DSys& sys);
-struct SplitBufs {
-    RayAtDoe* rinfo;
-    int* iray;
-    int* ibin;
-    float2* iU;
-    float2* igU;
-    long long* voff;
-    int* vcnt;
-    float* rsum;
-    unsigned long long* counter;
-    long long cap;
-};
 cudaError_t launch_bs_count(const LaunchCtx& L, const unsigned* vis, long long nwords,
                             unsigned long long* total);
 cudaError_t launch_backward_split(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                   const long long* prefix, int njob, long long total,
                                   const RaysIn& rays, const float2* T, const float* amp,
                                   const float* gpsf, const unsigned* vis, const SplitBufs& B,
-                                  long long nitems, float* dphi, float* damp, double* dsurf,
-                                  unsigned* status);
+                                  long long nitems, int have_list, float* dphi, float* damp,
+                                  double* dsurf, unsigned* status);
 cudaError_t launch_spectra(const LaunchCtx& L, const DSys& sys, int tc, const DJob* jobs,
                            const long long* prefix, int njob, long long total, const RaysIn& rays,
                            const float2* T, float2* out, unsigned* status);
@@ -73,6 +62,13 @@ struct rw_ctx {
     DevBuf split_rays;  // split adjoint: per-ray state, offsets, sums
     DevBuf split_items; // split adjoint: work list of visible secondary rays
     DevBuf keep;        // block culling: kept 8 x 8 bin blocks per incident ray
+    long long keep_words = 0, keep_blocks = 0;   // of the last culled forward
+    // tape of the last rw_forward_vis: its visible secondary rays already in
+    // split_rays / split_items, valid for the adjoint with the same mask
+    bool tape_valid = false;
+    const void* tape_vis = nullptr;
+    long long tape_total = 0, tape_cap = 0, tape_hint = 0;
+    int tape_M = 0;
     unsigned long long* count_host = nullptr;   // pinned
     DevBuf misc;        // status word + loss sums
     void* staging = nullptr;       // pinned host copy source of `tables`
@@ -220,6 +216,34 @@ struct Packed {
 static bool supported_D(int D) { return D == 16 || D == 32 || D == 64 || D == 96; }
 // transform sizes with a compiled FFT plan (M = pad * D)
 static bool supported_M(int M) { return M == 16 || M == 32 || M == 64 || M == 96 || M == 128; }
+
+// Split-adjoint buffers for n incident rays and cap work items (the forward's
+// tape uses the same layout).
+static rw_status split_buffers(rw_ctx* ctx, long long n, long long cap, SplitBufs& B) {
+    const size_t per_ray = sizeof(RayAtDoe) + sizeof(long long) + sizeof(int) + 6 * sizeof(float);
+    rw_status st = ensure_buf(ctx, ctx->split_rays, n * per_ray + 256, "split adjoint rays");
+    if (st != RW_OK) return st;
+    if (cap < 1) cap = 1;
+    const size_t per_item = 2 * sizeof(int) + 2 * sizeof(float2);
+    st = ensure_buf(ctx, ctx->split_items, (size_t)cap * per_item + 256, "split adjoint list");
+    if (st != RW_OK) return st;
+    char* rp = (char*)ctx->split_rays.p;
+    B.rinfo = (RayAtDoe*)rp;                    rp += align16(n * sizeof(RayAtDoe));
+    B.voff = (long long*)rp;                    rp += align16(n * sizeof(long long));
+    B.vcnt = (int*)rp;                          rp += align16(n * sizeof(int));
+    B.rsum = (float*)rp;
+    char* ip = (char*)ctx->split_items.p;
+    B.igU = (float2*)ip;                        ip += (size_t)cap * sizeof(float2);
+    B.iU = (float2*)ip;                         ip += (size_t)cap * sizeof(float2);
+    B.iray = (int*)ip;                          ip += (size_t)cap * sizeof(int);
+    B.ibin = (int*)ip;
+    B.cap = cap;
+    return RW_OK;
+}
+// tape counter, forward-with-mask epoch, epoch of the tape: three adjacent words
+static unsigned long long* tape_counter(rw_ctx* ctx) {
+    return reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctx->misc.p) + 192);
+}
 
 static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
     if (!sys) return fail(ctx, RW_EINVAL, "sys is NULL");
@@ -517,6 +541,25 @@ rw_status rw_profile_entry(rw_ctx* ctx, int32_t i, const char** kernel, double* 
     return RW_OK;
 }
 
+rw_status rw_cull_stats(rw_ctx* ctx, int64_t* blocks, int64_t* kept) {
+    if (!ctx || !blocks || !kept) return fail(ctx, RW_EINVAL, "null argument");
+    ctx->err.clear();
+    *blocks = ctx->keep_blocks;
+    *kept = 0;
+    if (ctx->keep_words == 0) return RW_OK;
+    RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    unsigned long long* dcount = reinterpret_cast<unsigned long long*>(
+        reinterpret_cast<char*>(ctx->misc.p) + 128);
+    RW_CUDA(launch_bs_count(lctx(ctx), (const unsigned*)ctx->keep.p, ctx->keep_words, dcount),
+            "kept-block count");
+    ctx->launches++;
+    RW_CUDA(cudaMemcpyAsync(ctx->count_host, dcount, sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, ctx->stream), "count read");
+    RW_CUDA(cudaStreamSynchronize(ctx->stream), "count sync");
+    *kept = (int64_t)*ctx->count_host;
+    return RW_OK;
+}
+
 rw_status rw_set_stream(rw_ctx* ctx, void* cuda_stream) {
     if (!ctx) return RW_EINVAL;
     ctx->stream = (cudaStream_t)cuda_stream;
@@ -659,15 +702,37 @@ static rw_status forward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* j
             return st;
         RW_CUDA(cudaMemsetAsync(ctx->acc.p, 0, npx * sizeof(double), ctx->stream), "acc clear");
         unsigned* keep = nullptr;
+        SplitBufs tape;
+        std::memset(&tape, 0, sizeof(tape));
+        if (vis) {
+            ctx->tape_valid = false;
+            tape.epoch = tape_counter(ctx) + 1;
+        }
         if (forward_culls(P.sys)) {
             const size_t kb = (size_t)P.total * cull_keep_words(P.sys.M) * sizeof(unsigned);
             if ((st = ensure_buf(ctx, ctx->keep, kb, "block-culling scratch")) != RW_OK) return st;
             keep = (unsigned*)ctx->keep.p;
+            ctx->keep_words = (long long)P.total * cull_keep_words(P.sys.M);
+            ctx->keep_blocks = (long long)P.total * (P.sys.M / 8) * (P.sys.M / 8);
             ctx->launches++;          // k_cull
+            if (vis && !capturing(ctx)) {
+                // tape the visible secondary rays for the adjoint
+                long long cap = ctx->tape_hint;
+                if (cap <= 0) cap = std::max<long long>(1 << 20, P.total * P.sys.M * P.sys.M / 64);
+                if ((st = split_buffers(ctx, P.total, cap, tape)) != RW_OK) return st;
+                tape.counter = tape_counter(ctx);
+                RW_CUDA(cudaMemsetAsync(tape.counter, 0, sizeof(unsigned long long), ctx->stream),
+                        "tape counter");
+                ctx->tape_valid = true;
+                ctx->tape_vis = vis;
+                ctx->tape_total = P.total;
+                ctx->tape_M = P.sys.M;
+                ctx->tape_cap = cap;
+            }
         }
         RW_CUDA(launch_forward(lctx(ctx), MODE_SPLAT, P.sys, dj, dp, njob, P.total,
                                rays_in(rays), T, (double*)ctx->acc.p, nullptr, eo,
-                               status_word(ctx), vis, keep),
+                               status_word(ctx), vis, keep, vis ? &tape : nullptr),
                 "forward kernel");
         ctx->launches++;
         RW_CUDA(launch_psf_finalize(lctx(ctx), (const double*)ctx->acc.p, psf, npx), "psf finalize");
@@ -737,44 +802,55 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
     float2* T; DJob* dj; long long* dp;
     if ((st = prepare(ctx, sys, P, &T, &dj, &dp)) != RW_OK) return st;
     if (split) {
-        // Split adjoint: count the visible secondary rays (one host sync), size
-        // the work list, then spectra+list / trace+reverse / conjugate FFT+scatter.
-        const long long nwords = P.total * (long long)P.sys.M * P.sys.M / 32;
-        unsigned long long* dcount = reinterpret_cast<unsigned long long*>(
-            reinterpret_cast<char*>(ctx->misc.p) + 128);
-        RW_CUDA(launch_bs_count(lctx(ctx), vis, nwords, dcount), "visible count");
-        ctx->launches++;
-        RW_CUDA(cudaMemcpyAsync(ctx->count_host, dcount, sizeof(unsigned long long),
-                                cudaMemcpyDeviceToHost, ctx->stream), "count read");
-        RW_CUDA(cudaStreamSynchronize(ctx->stream), "count sync");
-        const long long nitems = (long long)*ctx->count_host;
-        const size_t per_ray = sizeof(RayAtDoe) + sizeof(long long) + sizeof(int) + 6 * sizeof(float);
-        if ((st = ensure_buf(ctx, ctx->split_rays, P.total * per_ray + 256, "split adjoint rays")) != RW_OK)
-            return st;
-        const long long cap = nitems > 0 ? nitems : 1;
-        const size_t per_item = 2 * sizeof(int) + 2 * sizeof(float2);
-        if ((st = ensure_buf(ctx, ctx->split_items, (size_t)cap * per_item + 256, "split adjoint list")) != RW_OK)
-            return st;
-        char* rp = (char*)ctx->split_rays.p;
+        // Split adjoint over the mask's visible secondary rays: with the
+        // forward's tape for this mask, trace+reverse / conjugate FFT+scatter
+        // of the taped work list; otherwise count them (one host sync), size the
+        // work list and run spectra+list / trace+reverse / conjugate FFT+scatter.
         SplitBufs B;
-        B.rinfo = (RayAtDoe*)rp;                    rp += align16(P.total * sizeof(RayAtDoe));
-        B.voff = (long long*)rp;                    rp += align16(P.total * sizeof(long long));
-        B.vcnt = (int*)rp;                          rp += align16(P.total * sizeof(int));
-        B.rsum = (float*)rp;                        rp += align16(P.total * 6 * sizeof(float));
-        char* ip = (char*)ctx->split_items.p;
-        B.igU = (float2*)ip;                        ip += (size_t)cap * sizeof(float2);
-        B.iU = (float2*)ip;                         ip += (size_t)cap * sizeof(float2);
-        B.iray = (int*)ip;                          ip += (size_t)cap * sizeof(int);
-        B.ibin = (int*)ip;
-        B.counter = dcount;
-        B.cap = cap;
-        RW_CUDA(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), ctx->stream), "counter");
+        std::memset(&B, 0, sizeof(B));
+        long long nitems = 0;
+        bool taped = ctx->tape_valid && ctx->tape_vis == (const void*)vis &&
+                     ctx->tape_total == P.total && ctx->tape_M == P.sys.M;
+        if (taped) {
+            // counter, epoch, tape epoch: a forward with a mask replayed from a
+            // graph since the tape was written has moved the epoch on
+            RW_CUDA(cudaMemcpyAsync(ctx->count_host, tape_counter(ctx),
+                                    3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                    ctx->stream), "tape count read");
+            RW_CUDA(cudaStreamSynchronize(ctx->stream), "tape count sync");
+            nitems = (long long)ctx->count_host[0];
+            if (ctx->count_host[1] != ctx->count_host[2]) {
+                taped = false;
+            } else if (nitems > ctx->tape_cap) {
+                // the tape overflowed: size the next one, recompute this time
+                ctx->tape_hint = nitems + nitems / 8 + 1024;
+                taped = false;
+            } else {
+                if ((st = split_buffers(ctx, P.total, ctx->tape_cap, B)) != RW_OK) return st;
+                B.counter = tape_counter(ctx);
+            }
+        }
+        if (!taped) {
+            ctx->tape_valid = false;          // the buffers are reused below
+            const long long nwords = P.total * (long long)P.sys.M * P.sys.M / 32;
+            unsigned long long* dcount = reinterpret_cast<unsigned long long*>(
+                reinterpret_cast<char*>(ctx->misc.p) + 128);
+            RW_CUDA(launch_bs_count(lctx(ctx), vis, nwords, dcount), "visible count");
+            ctx->launches++;
+            RW_CUDA(cudaMemcpyAsync(ctx->count_host, dcount, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, ctx->stream), "count read");
+            RW_CUDA(cudaStreamSynchronize(ctx->stream), "count sync");
+            nitems = (long long)*ctx->count_host;
+            if ((st = split_buffers(ctx, P.total, nitems, B)) != RW_OK) return st;
+            B.counter = dcount;
+            RW_CUDA(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), ctx->stream), "counter");
+        }
         RW_CUDA(cudaMemsetAsync(B.rsum, 0, P.total * 6 * sizeof(float), ctx->stream), "sums");
         RW_CUDA(launch_backward_split(lctx(ctx), P.sys, dj, dp, njob, P.total, rays_in(rays), T,
-                                      sys->doe.amp, dl_dpsf, vis, B, nitems, dphi, damp, dsurf,
-                                      status_word(ctx)),
+                                      sys->doe.amp, dl_dpsf, vis, B, nitems, taped ? 1 : 0, dphi,
+                                      damp, dsurf, status_word(ctx)),
                 "split adjoint");
-        ctx->launches += nitems > 0 ? 3 : 2;
+        ctx->launches += (taped ? 1 : 2) + (nitems > 0 ? 1 : 0);
         return RW_OK;
     }
     int nl = 0;

@@ -17,19 +17,6 @@
 // (rw_backward.cu); only the schedule differs.
 #include "rw_bwd_common.cuh"
 
-struct SplitBufs {
-    RayAtDoe* rinfo;             // [n] incident state at the DOE
-    int* iray;                   // [cap] work list: incident ray
-    int* ibin;                   // [cap] bin
-    float2* iU;                  // [cap] U~ of that bin
-    float2* igU;                 // [cap] dL/dU~
-    long long* voff;             // [n] first work item of ray
-    int* vcnt;                   // [n] number of work items of ray
-    float* rsum;                 // [n][6] per-ray geometric sums
-    unsigned long long* counter; // work-list allocator
-    long long cap;
-};
-
 // ------------------------------------------------------------------ count
 __global__ void k_bs_count(const unsigned* __restrict__ vis, long long nwords,
                            unsigned long long* __restrict__ total) {
@@ -328,18 +315,23 @@ static cudaError_t launch_split_d(const LaunchCtx& L, const DSys& sys, const DJo
                                   const long long* prefix, int njob, long long total,
                                   const RaysIn& rays, const float2* T, const float* amp,
                                   const float* gpsf, const unsigned* vis, const SplitBufs& B,
-                                  long long nitems, float* dphi, float* damp, double* dsurf,
-                                  unsigned* status) {
+                                  long long nitems, int have_list, float* dphi, float* damp,
+                                  double* dsurf, unsigned* status) {
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     long long grid;
-    size_t smem1 = sampled_scratch_offset(M) + 64;
-    cudaError_t e = persistent_launch_cfg(k_bs_spectra<M>, smem1, L.num_sms, ntiles, L.grid_override, &grid);
-    if (e != cudaSuccess) return e;
-    RW_MARK(L, "k_bs_spectra");
-    k_bs_spectra<M><<<(unsigned)grid, RW_THREADS, smem1, L.stream>>>(sys, jobs, prefix, njob,
-                                                                     total, rays, T, vis, B, status);
-    RW_MARK(L, nullptr);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (!have_list) {
+        // patch spectra and the work list (otherwise the forward taped both)
+        size_t smem1 = sampled_scratch_offset(M) + 64;
+        e = persistent_launch_cfg(k_bs_spectra<M>, smem1, L.num_sms, ntiles, L.grid_override,
+                                  &grid);
+        if (e != cudaSuccess) return e;
+        RW_MARK(L, "k_bs_spectra");
+        k_bs_spectra<M><<<(unsigned)grid, RW_THREADS, smem1, L.stream>>>(sys, jobs, prefix, njob,
+                                                                         total, rays, T, vis, B, status);
+        RW_MARK(L, nullptr);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (nitems > 0) {
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bs_trace<M, NS>, RW_THREADS, 0);
@@ -369,11 +361,11 @@ cudaError_t launch_backward_split(const LaunchCtx& L, const DSys& sys, const DJo
                                   const long long* prefix, int njob, long long total,
                                   const RaysIn& rays, const float2* T, const float* amp,
                                   const float* gpsf, const unsigned* vis, const SplitBufs& B,
-                                  long long nitems, float* dphi, float* damp, double* dsurf,
-                                  unsigned* status) {
+                                  long long nitems, int have_list, float* dphi, float* damp,
+                                  double* dsurf, unsigned* status) {
     const int ns = sys.fast_ok ? sys.n_post : -1;
 #define RW_BS(DD, NN) \
-    launch_split_d<DD, NN>(L, sys, jobs, prefix, njob, total, rays, T, amp, gpsf, vis, B, nitems, dphi, damp, dsurf, status)
+    launch_split_d<DD, NN>(L, sys, jobs, prefix, njob, total, rays, T, amp, gpsf, vis, B, nitems, have_list, dphi, damp, dsurf, status)
 #define RW_BS_D(DD)                          \
     case DD:                                 \
         switch (ns) {                        \

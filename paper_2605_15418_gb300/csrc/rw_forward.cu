@@ -8,6 +8,8 @@
 // traces a tile of 32 incident rays to the DOE, then the CTA walks the tile,
 // each thread handling M^2/256 spectral bins of the current ray (M = P D,
 // the zero-padded transform size; the template parameter).
+#include <cstring>
+
 #include "rw_kernels.cuh"
 
 // ------------------------------------------------------------- A3 input
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(RW_THREADS, FwdOcc<M>::value)
 k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
           int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
           double* __restrict__ psf, float2* __restrict__ field, EmitOut eo, unsigned* status,
-          unsigned* __restrict__ vis, const unsigned* __restrict__ keep) {
+          unsigned* __restrict__ vis, const unsigned* __restrict__ keep, SplitBufs tape) {
     extern __shared__ __align__(16) unsigned char smem[];
     float2* X = reinterpret_cast<float2*>(smem);
     float2* tw = X + Patch<M>::ELEMS;
@@ -75,14 +77,20 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
     RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + M);
     // exhaustive emission with block culling: visibility words of the ray
     unsigned* vw = reinterpret_cast<unsigned*>(smem + sampled_scratch_offset(M));
+    if (tape.epoch && blockIdx.x == 0 && threadIdx.x == 0) {
+        const unsigned long long e = atomicAdd(tape.epoch, 1ull) + 1ull;
+        if (tape.iray) tape.epoch[1] = e;
+    }
     fft_twiddles<M>(tw);
     const long long npix_map = (long long)sys.H * sys.W;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();
-        if (threadIdx.x < RW_TILE)
-            incident_to_doe(sys, jobs, prefix, njob, total, rays, tile * RW_TILE + threadIdx.x,
-                            info[threadIdx.x], status);
+        if (threadIdx.x < RW_TILE) {
+            const long long g = tile * RW_TILE + threadIdx.x;
+            incident_to_doe(sys, jobs, prefix, njob, total, rays, g, info[threadIdx.x], status);
+            if (tape.rinfo && g < total) tape.rinfo[g] = info[threadIdx.x];
+        }
         __syncthreads();
         for (int r = 0; r < RW_TILE; ++r) {
             const RayAtDoe& R = info[r];
@@ -100,7 +108,7 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
                 emit_exhaustive<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                              tile * RW_TILE + r, status, vis,
-                                             keep, vw);
+                                             keep, vw, tape);
             } else {
                 emit_sampled<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                           tile * RW_TILE + r, status,
@@ -173,7 +181,9 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
                                     const long long* prefix, int njob, long long total,
                                     const RaysIn& rays, const float2* T, double* psf,
                                     float2* field, const EmitOut& eo, unsigned* status,
-                                    unsigned* vis, unsigned* keep) {
+                                    unsigned* vis, unsigned* keep, const SplitBufs* tapep) {
+    SplitBufs tape;
+    std::memset(&tape, 0, sizeof(tape));
     if constexpr (MODE == MODE_SPLAT && NS >= 0) {
         if (keep) {
             // block culling: kept-block bits for every incident ray first
@@ -190,6 +200,10 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
                                                                       total, rays, keep, status);
             RW_MARK(L, nullptr);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        if (tapep && vis) {
+            tape = *tapep;
+            if (!keep) tape.iray = nullptr;     // only the culled path tapes
         }
     } else {
         keep = nullptr;
@@ -210,7 +224,8 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
     if (grid < 1) grid = 1;
     RW_MARK(L, "k_forward");
     kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(sys, jobs, prefix, njob, total, rays,
-                                                          T, psf, field, eo, status, vis, keep);
+                                                          T, psf, field, eo, status, vis, keep,
+                                                          tape);
     RW_MARK(L, nullptr);
     return cudaGetLastError();
 }
@@ -221,9 +236,9 @@ static cudaError_t launch_splat(const LaunchCtx& L, const DSys& sys, const DJob*
                                 const long long* prefix, int njob, long long total,
                                 const RaysIn& rays, const float2* T, double* psf,
                                 const EmitOut& eo, unsigned* status, unsigned* vis,
-                                unsigned* keep) {
+                                unsigned* keep, const SplitBufs* tape) {
 #define RW_SPLAT(NN) \
-    launch_forward_d<M, MODE_SPLAT, NN>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis, keep)
+    launch_forward_d<M, MODE_SPLAT, NN>(L, sys, jobs, prefix, njob, total, rays, T, psf, nullptr, eo, status, vis, keep, tape)
     if (sys.fast_ok) {
         switch (sys.n_post) {
             case 0: return RW_SPLAT(0);
@@ -245,18 +260,20 @@ bool forward_culls(const DSys& sys) {
 cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const DJob* jobs,
                            const long long* prefix, int njob, long long total,
                            const RaysIn& rays, const float2* T, double* psf, float2* field,
-                           const EmitOut& eo, unsigned* status, unsigned* vis, unsigned* keep) {
+                           const EmitOut& eo, unsigned* status, unsigned* vis, unsigned* keep,
+                           const SplitBufs* tape) {
 #define RW_FWD_CASE(DD)                                                                       \
     case DD:                                                                                  \
         if (mode == MODE_SPLAT)                                                               \
             return launch_splat<DD>(L, sys, jobs, prefix, njob, total, rays, T, psf, eo,      \
-                                    status, vis, forward_culls(sys) ? keep : nullptr);        \
+                                    status, vis, forward_culls(sys) ? keep : nullptr, tape);  \
         if (mode == MODE_COHERENT)                                                            \
             return launch_forward_d<DD, MODE_COHERENT, -1>(L, sys, jobs, prefix, njob, total, \
                                                            rays, T, psf, field, eo, status,   \
-                                                           nullptr, nullptr);                 \
+                                                           nullptr, nullptr, nullptr);        \
         return launch_forward_d<DD, MODE_EMIT, -1>(L, sys, jobs, prefix, njob, total, rays, T,\
-                                                   psf, field, eo, status, nullptr, nullptr);
+                                                   psf, field, eo, status, nullptr, nullptr,  \
+                                                   nullptr);
     switch (sys.M) {
         RW_FWD_CASE(16)
         RW_FWD_CASE(32)

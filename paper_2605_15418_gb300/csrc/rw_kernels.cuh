@@ -34,6 +34,25 @@ struct GenJob {
     float dx, dy, dz, pad;
 };
 
+// Work list of visible secondary rays of the split adjoint (and the forward's
+// tape of it): per incident ray its state at the DOE and its items, each item
+// one secondary ray that reached the sensor (ray, bin, U~), in bin order.
+struct SplitBufs {
+    RayAtDoe* rinfo;             // [n] incident state at the DOE
+    int* iray;                   // [cap] work list: incident ray
+    int* ibin;                   // [cap] bin
+    float2* iU;                  // [cap] U~ of that bin
+    float2* igU;                 // [cap] dL/dU~
+    long long* voff;             // [n] first work item of ray
+    int* vcnt;                   // [n] number of work items of ray
+    float* rsum;                 // [n][6] per-ray geometric sums
+    unsigned long long* counter; // work-list allocator (may exceed cap: overflow)
+    long long cap;
+    // forward with a mask: epoch[0] counts such launches (graph replays
+    // included), epoch[1] is the count at the launch that wrote the tape
+    unsigned long long* epoch;
+};
+
 struct RaysOut {
     float *ox, *oy, *oz, *dx, *dy, *dz, *are, *aim;
     double* opl;
@@ -55,10 +74,10 @@ __host__ __device__ inline size_t sampled_scratch_offset(int M) {
 }
 // block culling (exhaustive emission): one bit per 8 x 8 block of bins and
 // incident ray (set: the block is kept); the forward stages the current
-// ray's visibility words in shared memory
+// ray's visibility words and the tape's per-warp counts in shared memory
 __host__ __device__ constexpr int cull_keep_words(int M) { return ((M / 8) * (M / 8) + 31) / 32; }
 __host__ __device__ inline size_t cull_scratch_bytes(int M) {
-    return align16(sizeof(unsigned) * (size_t)(M * M / 32));
+    return align16(sizeof(unsigned) * (size_t)(M * M / 32 + RW_THREADS / 32 + 4));
 }
 inline size_t forward_smem_bytes(int M, int emit = RW_EMIT_EXHAUSTIVE, int n_ssr = 0) {
     size_t b = sampled_scratch_offset(M);
@@ -407,11 +426,19 @@ __device__ __forceinline__ void emit_dead(const DSys& sys, long long g, long lon
 // Ray phase: trace only the bins of kept blocks, packed over the CTA's
 // threads (converged warps).  Dropped bins cannot deposit, so the image and
 // the visibility mask equal those of tracing every bin.
+//
+// With a tape (tape.iray != null, needs vis), the secondary rays that
+// reached the sensor are also appended to the adjoint's work list: one
+// allocation per incident ray, items (ray, bin, U~) in bin order, so the
+// adjoint need not recompute the patch and its spectrum.  An allocation past
+// tape.cap writes nothing; the counter still grows, which tells the host.
 template <int M, int NS>
 __device__ __forceinline__ void emit_culled(const DSys& sys, const DJob& J, const RayAtDoe& R,
-                                            const float2* X, double* psf, long long g,
+                                            const float2* X, const float2* phu,
+                                            const float2* phv, double* psf, long long g,
                                             unsigned* status, unsigned* __restrict__ vis,
-                                            const unsigned* __restrict__ keepg, unsigned* vw) {
+                                            const unsigned* __restrict__ keepg, unsigned* vw,
+                                            const SplitBufs& tape) {
     constexpr int S = Patch<M>::S;
     constexpr int NW = M * M / 32, B8 = M / 8, KW = cull_keep_words(M);
     unsigned keep[KW];
@@ -455,6 +482,59 @@ __device__ __forceinline__ void emit_culled(const DSys& sys, const DJob& J, cons
         __syncthreads();
         for (int i = threadIdx.x; i < NW; i += RW_THREADS) vis[g * (long long)NW + i] = vw[i];
     }
+    if (vis && tape.iray) {
+        constexpr int KV = (NW + RW_THREADS - 1) / RW_THREADS;   // words per thread
+        constexpr int NWARP = RW_THREADS / 32;
+        int* wsum = reinterpret_cast<int*>(vw + NW);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        unsigned word[KV];
+        int cnt = 0;
+#pragma unroll
+        for (int k = 0; k < KV; ++k) {
+            const int wi = threadIdx.x * KV + k;
+            word[k] = wi < NW ? vw[wi] : 0u;
+            cnt += __popc(word[k]);
+        }
+        int incl = cnt;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t = 0;
+            for (int w = 0; w < NWARP; ++w) { const int v = wsum[w]; wsum[w] = t; t += v; }
+            long long base = 0;
+            if (t > 0) base = (long long)atomicAdd(tape.counter, (unsigned long long)t);
+            if (base + t > tape.cap) t = 0;
+            tape.voff[g] = base;
+            tape.vcnt[g] = t;
+            wsum[NWARP] = (int)(base & 0x7fffffff);
+            wsum[NWARP + 1] = (int)(base >> 31);
+            wsum[NWARP + 2] = t;
+        }
+        __syncthreads();
+        if (wsum[NWARP + 2] > 0) {
+            long long pos = (long long)wsum[NWARP] + ((long long)wsum[NWARP + 1] << 31) +
+                            wsum[warp] + (incl - cnt);
+            const float norm = sys.norm;
+#pragma unroll
+            for (int k = 0; k < KV; ++k) {
+                unsigned wk = word[k];
+                while (wk) {
+                    const int b = __ffs(wk) - 1;
+                    wk &= wk - 1u;
+                    const int f = (threadIdx.x * KV + k) * 32 + b;
+                    const int jvi = f / M, jui = f - (f / M) * M;
+                    tape.iray[pos] = (int)g;
+                    tape.ibin[pos] = f;
+                    tape.iU[pos] = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
+                    ++pos;
+                }
+            }
+        }
+    }
 }
 
 template <int M, int MODE, int NS>
@@ -464,10 +544,10 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
                                                 const EmitOut& eo, long long g, unsigned* status,
                                                 unsigned* __restrict__ vis,
                                                 const unsigned* __restrict__ keepg,
-                                                unsigned* vw) {
+                                                unsigned* vw, const SplitBufs& tape) {
     if constexpr (MODE == MODE_SPLAT && NS >= 0) {
         if (keepg) {
-            emit_culled<M, NS>(sys, J, R, X, psf, g, status, vis, keepg, vw);
+            emit_culled<M, NS>(sys, J, R, X, phu, phv, psf, g, status, vis, keepg, vw, tape);
             return;
         }
     }
@@ -635,7 +715,7 @@ cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const 
                            const long long* prefix, int njob, long long total,
                            const RaysIn& rays, const float2* T, double* psf, float2* field,
                            const EmitOut& eo, unsigned* status, unsigned* vis = nullptr,
-                           unsigned* keep = nullptr);
+                           unsigned* keep = nullptr, const SplitBufs* tape = nullptr);
 cudaError_t launch_psf_finalize(const LaunchCtx& L, const double* acc, float* psf, long long n);
 cudaError_t launch_coherent_finalize(const LaunchCtx& L, const float2* field, float* psf,
                                      long long n);

@@ -77,6 +77,13 @@ class Context:
             out[name.value.decode()] = (ms.value, cnt.value)
         return out
 
+    def cull_stats(self):
+        """(8 x 8 bin blocks, blocks kept) of the last culled forward."""
+        self._stream()
+        b, k = C.c_int64(), C.c_int64()
+        self.check(self.lib.rw_cull_stats(self.h, C.byref(b), C.byref(k)), "rw_cull_stats")
+        return int(b.value), int(k.value)
+
     def device_status(self):
         self._stream()
         v = C.c_uint32(0)

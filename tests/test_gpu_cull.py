@@ -94,3 +94,37 @@ def test_culling_at_full_c2_size_keeps_every_visible_ray(RW, ctx):
     torch.cuda.synchronize()
     assert torch.equal(vis_c, vis_f)
     assert rel_l2(psf_c.cpu().numpy(), psf_f.cpu().numpy()) < 1e-6
+
+
+def test_taped_adjoint_equals_recomputed_adjoint(RW, ctx):
+    """The forward with a mask tapes its visible secondary rays; the adjoint
+    over that tape equals the adjoint that recomputes patches and spectra
+    (forced here by a newer forward on another mask, which retires the tape
+    of the first)."""
+    w = _c2(23, 64)
+    M = w.system.doe.M
+    sim = RW.Simulator(w, ctx=ctx)
+    vis1 = RW.alloc_vis(sim.n_rays, M, sim.dev)
+    vis2 = RW.alloc_vis(sim.n_rays, M, sim.dev)
+    ctx.device_status()
+    psf = sim.forward(vis=vis1)
+    tgt = torch.as_tensor(R.gaussian_spots_target(len(w.jobs), 96, 96, seed=3), device=sim.dev)
+    gI = torch.empty_like(psf)
+    sim.loss(psf, tgt, gI)
+    n0 = ctx.launches
+    taped = sim.backward(gI, vis=vis1)                 # tape: no spectra kernel
+    n_taped = ctx.launches - n0
+    sim.forward(vis=vis2)                              # same inputs, new tape for vis2
+    n0 = ctx.launches
+    recomputed = sim.backward(gI, vis=vis1)            # vis1 has no tape now
+    n_recomputed = ctx.launches - n0
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 0
+    # maps + trace + scatter; maps + count + spectra + trace + scatter
+    assert n_taped == 3 and n_recomputed == 5, (n_taped, n_recomputed)
+    assert rel_l2(taped[0].cpu().numpy(), recomputed[0].cpu().numpy()) < 1e-6
+    assert rel_l2(taped[2].cpu().numpy(), recomputed[2].cpu().numpy()) < 1e-6
+    # and the taped adjoint matches the fused adjoint over every bin
+    full = sim.backward(gI)
+    torch.cuda.synchronize()
+    assert rel_l2(taped[0].cpu().numpy(), full[0].cpu().numpy()) < 1e-5
