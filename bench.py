@@ -36,7 +36,9 @@ FP32_LANES_PER_SM = 128
 # capture of the current kernel at n-side 256 scaled by the incident-ray
 # count (16x): see the profiles/ summaries.  A kernel missing here has no
 # capture of its current code.
-TRAFFIC = {}
+TRAFFIC = {"k_bs_scatter": 16 * (1.397035e9 + 0.193390e9),
+           "k_bs_trace": 16 * (1.378204e9 + 0.734588e9),
+           "k_cull": 16 * 0.023702e9}
 NUM_SMS = 152
 
 
