@@ -220,6 +220,22 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest x over all ranks (the job's time is its slowest rank)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(rays_per_rank, world, ms_per_step):
+    """Whole-job incident rays/s: every rank runs its own replica."""
+    return world * rays_per_rank / (ms_per_step / 1e3)
+
+
 # ------------------------------------------------------------------ our arm
 def main():
     args = parse()
@@ -290,13 +306,9 @@ def main():
     t_step = [evs[k][0].elapsed_time(evs[k][4]) for k in range(args.steps)]
     t_fwd = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
     t_bwd = [evs[k][3].elapsed_time(evs[k][4]) for k in range(args.steps)]
-    ms = float(np.sum(t_step))
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.sum(t_step)), dist, dev)
     ms_per_step = ms / args.steps
-    value = world * n_rays / (ms_per_step / 1e3)
+    value = weak_scaling_value(n_rays, world, ms_per_step)
 
     # ---- end to end through the public API with host buffers
     phi_h = torch.from_numpy(np.ascontiguousarray(sysm.doe.phi)).pin_memory()
