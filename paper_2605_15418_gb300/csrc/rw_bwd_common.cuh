@@ -165,8 +165,10 @@ __device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
                                             float scale, float* __restrict__ dphi,
                                             float* __restrict__ damp) {
     const int H = sys.H, W = sys.W, D = sys.D;
-    for (int f = threadIdx.x; f < D * D; f += RW_THREADS) {
-        const int b = f / D, a = f - (f / D) * D;
+    // walk the M x M grid (compile-time shifts) and skip the padding
+    for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
+        const int b = f / M, a = f - (f / M) * M;
+        if (a >= D || b >= D) continue;
         const float2 gT = G[b * Patch<M>::S + a];
         if (sys.gather == RW_GATHER_NEAREST) {
             const int rr = R.r0 + b, cc = R.c0 + a;

@@ -3,8 +3,11 @@
 // The bins of one incident ray form a regular grid in the tangential
 // wavevector (k_u, k_v).  For a rectangular block of bins we trace the whole
 // block at once in affine arithmetic: every quantity is held as
-//     c + a e1 + b e2 + [-r, r],   e1, e2 in [-1, 1],
-// where k_u = k_u,c + h_u e1 and k_v = k_v,c + h_v e2 span the block, and r
+//     c + a e1 + b e2 + p e3 + q e4 + [-r, r],   e1..e4 in [-1, 1],
+// where k_u = k_u,c + h_u e1 and k_v = k_v,c + h_v e2 span the block and
+// x = x_c + h_x e3, y = y_c + h_y e4 span the DOE hit points of a group of
+// neighbouring incident rays of one job (planar DOE; a single ray has
+// h_x = h_y = 0), so one test covers the block for the whole group, and r
 // bounds everything nonlinear (products of the noise terms, linearisation
 // remainders of sqrt and 1/x, and the FP32 rounding of each operation, which
 // is absorbed by widening r by a relative 1e-6 per operation -- far above
@@ -21,46 +24,49 @@
 #include "rw_fast.cuh"
 
 struct AF {
-    float c, a, b, r;
+    float c, a, b, p, q, r;
 };
 
 #define RW_AF_REL 1e-6f
 
-__device__ __forceinline__ float af_rad(const AF& x) { return fabsf(x.a) + fabsf(x.b) + x.r; }
+__device__ __forceinline__ float af_lin_sum(const AF& x) {
+    return fabsf(x.a) + fabsf(x.b) + fabsf(x.p) + fabsf(x.q);
+}
+__device__ __forceinline__ float af_rad(const AF& x) { return af_lin_sum(x) + x.r; }
 __device__ __forceinline__ float af_lo(const AF& x) { return x.c - af_rad(x) * (1.f + 4.f * RW_AF_REL); }
 __device__ __forceinline__ float af_hi(const AF& x) { return x.c + af_rad(x) * (1.f + 4.f * RW_AF_REL); }
 
 // widen r to cover the rounding of the operation that produced x
 __device__ __forceinline__ AF af_fix(AF x) {
-    x.r = x.r * (1.f + 4.f * RW_AF_REL) + RW_AF_REL * (fabsf(x.c) + fabsf(x.a) + fabsf(x.b)) +
-          1e-30f;
+    x.r = x.r * (1.f + 4.f * RW_AF_REL) + RW_AF_REL * (fabsf(x.c) + af_lin_sum(x)) + 1e-30f;
     return x;
 }
-__device__ __forceinline__ AF af_pt(float v) { return AF{v, 0.f, 0.f, 0.f}; }
+__device__ __forceinline__ AF af_pt(float v) { return AF{v, 0.f, 0.f, 0.f, 0.f, 0.f}; }
 __device__ __forceinline__ AF af_add(const AF& x, const AF& y) {
-    return af_fix(AF{x.c + y.c, x.a + y.a, x.b + y.b, x.r + y.r});
+    return af_fix(AF{x.c + y.c, x.a + y.a, x.b + y.b, x.p + y.p, x.q + y.q, x.r + y.r});
 }
 __device__ __forceinline__ AF af_sub(const AF& x, const AF& y) {
-    return af_fix(AF{x.c - y.c, x.a - y.a, x.b - y.b, x.r + y.r});
+    return af_fix(AF{x.c - y.c, x.a - y.a, x.b - y.b, x.p - y.p, x.q - y.q, x.r + y.r});
 }
-__device__ __forceinline__ AF af_neg(const AF& x) { return AF{-x.c, -x.a, -x.b, x.r}; }
+__device__ __forceinline__ AF af_neg(const AF& x) { return AF{-x.c, -x.a, -x.b, -x.p, -x.q, x.r}; }
 __device__ __forceinline__ AF af_addc(const AF& x, float s) {
-    return af_fix(AF{x.c + s, x.a, x.b, x.r});
+    return af_fix(AF{x.c + s, x.a, x.b, x.p, x.q, x.r});
 }
 __device__ __forceinline__ AF af_scale(const AF& x, float s) {
-    return af_fix(AF{x.c * s, x.a * s, x.b * s, x.r * fabsf(s)});
+    return af_fix(AF{x.c * s, x.a * s, x.b * s, x.p * s, x.q * s, x.r * fabsf(s)});
 }
 __device__ __forceinline__ AF af_mul(const AF& x, const AF& y) {
     const float rx = af_rad(x), ry = af_rad(y);
     return af_fix(AF{x.c * y.c, fmaf(x.c, y.a, y.c * x.a), fmaf(x.c, y.b, y.c * x.b),
+                     fmaf(x.c, y.p, y.c * x.p), fmaf(x.c, y.q, y.c * x.q),
                      fmaf(fabsf(x.c), y.r, fmaf(fabsf(y.c), x.r, rx * ry))});
 }
 // alpha x + zeta +- delta, with alpha applied to the affine part
 __device__ __forceinline__ AF af_lin(const AF& x, float alpha, float g_lo, float g_hi) {
     const float zeta = 0.5f * (g_lo + g_hi);
     const float delta = 0.5f * fabsf(g_hi - g_lo) + RW_AF_REL * (fabsf(g_lo) + fabsf(g_hi));
-    return af_fix(AF{fmaf(alpha, x.c, zeta), alpha * x.a, alpha * x.b,
-                     fmaf(fabsf(alpha), x.r, delta)});
+    return af_fix(AF{fmaf(alpha, x.c, zeta), alpha * x.a, alpha * x.b, alpha * x.p,
+                     alpha * x.q, fmaf(fabsf(alpha), x.r, delta)});
 }
 // sqrt on [lo, hi], lo > 0: slope just below f'(hi) keeps g = f - alpha x
 // increasing, so its range is [g(lo), g(hi)].
@@ -138,13 +144,16 @@ __device__ __forceinline__ bool af_step(const PSurf& S, AF& x, AF& y, AF& zl, AF
     return true;
 }
 
-// True when no secondary ray of R whose tangential wavevector lies in
-// [ku_c - hu, ku_c + hu] x [kv_c - hv, kv_c + hv] can deposit on the sensor
-// window of R's job (incoherent bilinear splat, margin of two pixels).
+// True when no secondary ray with tangential wavevector in
+// [ku_c - hu, ku_c + hu] x [kv_c - hv, kv_c + hv] leaving the DOE at a point
+// of [xc - hx, xc + hx] x [yc - hy, yc + hy] (z, frame, K and the sensor
+// window from R) can deposit on the sensor (incoherent bilinear splat,
+// margin of two pixels).  hx, hy > 0 only for a planar DOE.
 template <int NS>
 __device__ __noinline__ bool af_block_misses_sensor(const DSys& sys, const RayAtDoe& R, float ku_c,
-                                                    float hu, float kv_c, float hv) {
-    const AF ku = AF{ku_c, hu, 0.f, 0.f}, kv = AF{kv_c, 0.f, hv, 0.f};
+                                                    float hu, float kv_c, float hv, float xc,
+                                                    float hx, float yc, float hy) {
+    const AF ku = AF{ku_c, hu, 0.f, 0.f, 0.f, 0.f}, kv = AF{kv_c, 0.f, hv, 0.f, 0.f, 0.f};
     AF kn;
     const AF kt2 = af_add(af_mul(ku, ku), af_mul(kv, kv));
     if (!af_sqrt(af_addc(af_neg(kt2), R.K * R.K), kn)) return false;
@@ -163,7 +172,8 @@ __device__ __noinline__ bool af_block_misses_sensor(const DSys& sys, const RayAt
         dz = af_scale(af_add(af_add(af_scale(ku, R.u[2]), af_scale(kv, R.v[2])),
                              af_scale(kn, R.n[2])), iK);
     }
-    AF x = af_pt(R.px), y = af_pt(R.py), zl = af_pt(R.pz);
+    AF x = AF{xc, 0.f, 0.f, hx, 0.f, 0.f}, y = AF{yc, 0.f, 0.f, 0.f, hy, 0.f};
+    AF zl = af_pt(R.pz);
 #pragma unroll
     for (int i = 0; i < NS; ++i)
         if (!af_step(sys.post[i], x, y, zl, dx, dy, dz)) return false;

@@ -121,18 +121,25 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
 
 // ------------------------------------------------------------- block culling
 // keep[g * KW + w] bit b: 8 x 8 bin block 32 w + b of incident ray g may reach
-// the sensor (its affine enclosure does not miss the sensor window).  One
-// thread per (ray, block) pair of a 32-ray tile; rays that miss the DOE keep
-// nothing.
+// the sensor (its affine enclosure does not miss the sensor window).  With a
+// planar DOE, the rays of a tile are tested in groups of 8 of one job: one
+// test per (group, block) spans the group's DOE hit points and incident
+// tangential wavevectors, and a kept block is kept for every ray of the
+// group.  Other groups (mixed jobs, conformal DOE) are tested ray by ray.
+// Rays that miss the DOE keep nothing.
 template <int M, int NS>
 __global__ void __launch_bounds__(RW_THREADS, 2)
 k_cull(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
        int njob, long long total, RaysIn rays, unsigned* __restrict__ keep, unsigned* status) {
     constexpr int B8 = M / 8, NB = B8 * B8, KW = cull_keep_words(M);
+    constexpr int G = 8, NG = RW_TILE / G;
     __shared__ RayAtDoe info[RW_TILE];
     __shared__ unsigned kw[RW_TILE * KW];
+    __shared__ float gbox[NG][8];     // x, y, k_u, k_v ranges of the group's rays
+    __shared__ int grep[NG];          // group's first live ray; -1: ray by ray; -2: none
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     const float ks = sys.kstep;
+    const int lane = threadIdx.x & 31;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();
         if (threadIdx.x < RW_TILE)
@@ -140,14 +147,64 @@ k_cull(const DSys sys, const DJob* __restrict__ jobs, const long long* __restric
                             info[threadIdx.x], status);
         for (int i = threadIdx.x; i < RW_TILE * KW; i += RW_THREADS) kw[i] = 0u;
         __syncthreads();
+        if (threadIdx.x < RW_TILE) {
+            const RayAtDoe& R = info[lane];
+            const bool live = R.alive != 0;
+            // minima of (x, -x, y, -y, k_u, -k_u, k_v, -k_v) over each group of 8 lanes
+            float v[8] = {live ? R.px : INFINITY, live ? -R.px : INFINITY,
+                          live ? R.py : INFINITY, live ? -R.py : INFINITY,
+                          live ? R.kin_u : INFINITY, live ? -R.kin_u : INFINITY,
+                          live ? R.kin_v : INFINITY, live ? -R.kin_v : INFINITY};
+            int jlo = live ? R.job : 0x7fffffff, jhi = live ? R.job : -1;
+            int first = live ? lane : 0x7fffffff;
+            for (int o = 1; o < G; o <<= 1) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) v[k] = fminf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+                jlo = min(jlo, __shfl_xor_sync(0xffffffffu, jlo, o));
+                jhi = max(jhi, __shfl_xor_sync(0xffffffffu, jhi, o));
+                first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+            }
+            if ((lane & (G - 1)) == 0) {
+                const int g = lane / G;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    gbox[g][2 * k] = v[2 * k];
+                    gbox[g][2 * k + 1] = -v[2 * k + 1];
+                }
+                grep[g] = (jhi < 0) ? -2 : ((jlo == jhi && !sys.conformal) ? first : -1);
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < NG * NB; t += RW_THREADS) {
+            const int g = t / NB, bi = t - g * NB;
+            const int rep = grep[g];
+            if (rep < 0) continue;
+            const float* b = gbox[g];
+            const float ju_c = (float)((bi % B8) * 8 - M / 2) + 3.5f;
+            const float jv_c = (float)((bi / B8) * 8 - M / 2) + 3.5f;
+            // centre and half-width of each range, widened by a relative 1e-6
+            const float hu = (3.5f * ks + 0.5f * (b[5] - b[4])) * (1.f + 1e-6f);
+            const float hv = (3.5f * ks + 0.5f * (b[7] - b[6])) * (1.f + 1e-6f);
+            const float hx = 0.5f * (b[1] - b[0]) * (1.f + 1e-6f);
+            const float hy = 0.5f * (b[3] - b[2]) * (1.f + 1e-6f);
+            if (!af_block_misses_sensor<NS>(sys, info[rep], fmaf(ks, ju_c, 0.5f * (b[4] + b[5])),
+                                            hu, fmaf(ks, jv_c, 0.5f * (b[6] + b[7])), hv,
+                                            0.5f * (b[0] + b[1]), hx, 0.5f * (b[2] + b[3]), hy)) {
+                for (int i = 0; i < G; ++i)
+                    if (info[g * G + i].alive)
+                        atomicOr(&kw[(g * G + i) * KW + (bi >> 5)], 1u << (bi & 31));
+            }
+        }
         for (int t = threadIdx.x; t < RW_TILE * NB; t += RW_THREADS) {
             const int r = t / NB, bi = t - r * NB;
+            if (grep[r / G] != -1) continue;
             const RayAtDoe& R = info[r];
             if (!R.alive) continue;
             const float ju_c = (float)((bi % B8) * 8 - M / 2) + 3.5f;
             const float jv_c = (float)((bi / B8) * 8 - M / 2) + 3.5f;
             if (!af_block_misses_sensor<NS>(sys, R, fmaf(ks, ju_c, R.kin_u), 3.5f * ks,
-                                            fmaf(ks, jv_c, R.kin_v), 3.5f * ks))
+                                            fmaf(ks, jv_c, R.kin_v), 3.5f * ks, R.px, 0.f, R.py,
+                                            0.f))
                 atomicOr(&kw[r * KW + (bi >> 5)], 1u << (bi & 31));
         }
         __syncthreads();
