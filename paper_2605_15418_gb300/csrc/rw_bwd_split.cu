@@ -227,10 +227,6 @@ k_bs_scatter(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
     float2* phu = tw + M;
     float2* phv = phu + M;
     RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + M);
-    // rows m_v of the sparse dL/dU~ that hold a nonzero, their count and list
-    unsigned* rmask = reinterpret_cast<unsigned*>(smem + sampled_scratch_offset(M));
-    int* nsel = reinterpret_cast<int*>(rmask + 4);
-    unsigned char* sel = reinterpret_cast<unsigned char*>(nsel + 1);
     fft_twiddles<M>(tw);
     const float norm = sys.norm;
     float gs[RW_MAXS * RW_NGRAD];
@@ -253,7 +249,6 @@ k_bs_scatter(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
             const long long off = B.voff[g];
             for (int f = threadIdx.x; f < Patch<M>::ELEMS; f += RW_THREADS)
                 G[f] = make_float2(0.f, 0.f);
-            if (threadIdx.x < 4) rmask[threadIdx.x] = 0u;
             phase_factors<M>(sys, R, phu, phv);
             __syncthreads();
             for (int i = threadIdx.x; i < n; i += RW_THREADS) {
@@ -264,26 +259,9 @@ k_bs_scatter(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
                 int mv = jvi + M / 2; if (mv >= M) mv -= M;
                 const float2 ph = cmul(phu[jui], phv[jvi]);
                 G[mv * Patch<M>::S + mu] = cscale(cmulc(gU, ph), norm);
-                atomicOr(&rmask[mv >> 5], 1u << (mv & 31));
             }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                int k = 0;
-                for (int w = 0; w < (M + 31) / 32; ++w) {
-                    unsigned wd = rmask[w];
-                    while (wd) {
-                        const int b = __ffs(wd) - 1;
-                        wd &= wd - 1u;
-                        sel[k++] = (unsigned char)(w * 32 + b);
-                    }
-                }
-                if (k > 0) pad_lines<M>(sel, k);
-                *nsel = k;
-            }
-            __syncthreads();
-            // all-zero rows stay zero: the row pass runs on the listed rows only
-            fft_pass_sel<M, true, false>(G, tw, sel, *nsel);
-            fft_pass<M, true, true>(G, tw);
+            fft2d<M, true>(G, tw);
             map_scatter<M>(sys, R, Tmaps + (long long)jobs[R.job].slot * npix_map, amp, G,
                            jobs[R.job].phase_scale, dphi, damp);
             __syncthreads();
@@ -367,7 +345,7 @@ static cudaError_t launch_split_d(const LaunchCtx& L, const DSys& sys, const DJo
         RW_MARK(L, nullptr);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    size_t smem3 = sampled_scratch_offset(M) + 32 + M + 32;
+    size_t smem3 = sampled_scratch_offset(M);
     const size_t red = sizeof(double) * RW_MAXS * RW_NGRAD * (RW_THREADS / 32);
     if (smem3 < red) smem3 = red;
     e = persistent_launch_cfg(k_bs_scatter<M>, smem3, L.num_sms, ntiles, L.grid_override, &grid);

@@ -170,104 +170,6 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
     }
 }
 
-// Lines per chunk of a pass on listed lines: N <= 32 all of them; N = 64
-// 32 (one butterfly per thread and stage); larger N all of them.
-template <int N>
-__host__ __device__ constexpr int sel_chunk() { return N == 64 ? 32 : N; }
-
-// A stage on L listed lines only (rows, or columns with COLS): sel[0..L)
-// line indices, a line possibly listed twice (both threads then compute and
-// store the same values).  Lines left out are neither read nor written --
-// for an all-zero input line (the output is zero) or a line whose output
-// nobody reads.  Thread f takes butterfly f % NB of line sel[f / NB]; with
-// the odd row stride both passes stay free of bank conflicts.
-template <int N, int R, int P, bool INV, bool COLS, int L>
-__device__ __forceinline__ void fft_stage_sel(float2* buf, const float2* tw,
-                                              const unsigned char* sel) {
-    constexpr int S = Patch<N>::S;
-    constexpr int NB = N / R;
-    constexpr int TOT = L * NB;
-    constexpr int PER = (TOT + RW_THREADS - 1) / RW_THREADS;
-    float2 v[PER][R];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int f = threadIdx.x + k * RW_THREADS;
-        if ((TOT % RW_THREADS == 0) || f < TOT) {
-            const int b = sel[f / NB], i = f % NB;
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const int e = i + q * NB;
-                v[k][q] = COLS ? buf[e * S + b] : buf[b * S + e];
-            }
-            if constexpr (P > 1) {
-                const int kk = i % P;
-#pragma unroll
-                for (int q = 1; q < R; ++q) {
-                    float2 w = tw[q * kk * (N / (P * R))];
-                    if (INV) w.y = -w.y;
-                    v[k][q] = cmul(v[k][q], w);
-                }
-            }
-            dft_small<R, INV>(v[k]);
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int f = threadIdx.x + k * RW_THREADS;
-        if ((TOT % RW_THREADS == 0) || f < TOT) {
-            const int b = sel[f / NB], i = f % NB;
-            const int kk = i % P;
-            const int j = (i / P) * P * R + kk;
-#pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const int e = j + q * P;
-                if (COLS) buf[e * S + b] = v[k][q]; else buf[b * S + e] = v[k][q];
-            }
-        }
-    }
-    __syncthreads();
-}
-
-// All stages of a pass on the listed lines, chunk by chunk (lines are
-// independent within a pass).  sel holds nsel lines padded to a multiple of
-// sel_chunk<N>() with repeats of its last line (pad_lines).
-template <int N, bool INV, bool COLS>
-__device__ __forceinline__ void fft_pass_sel(float2* buf, const float2* tw,
-                                             const unsigned char* sel, int nsel) {
-    constexpr int L = sel_chunk<N>();
-    for (int c = 0; c < nsel; c += L) {
-        const unsigned char* s = sel + c;
-        if constexpr (N == 16) {
-            fft_stage_sel<16, 4, 1, INV, COLS, L>(buf, tw, s);
-            fft_stage_sel<16, 4, 4, INV, COLS, L>(buf, tw, s);
-        } else if constexpr (N == 32) {
-            fft_stage_sel<32, 4, 1, INV, COLS, L>(buf, tw, s);
-            fft_stage_sel<32, 8, 4, INV, COLS, L>(buf, tw, s);
-        } else if constexpr (N == 64) {
-            fft_stage_sel<64, 8, 1, INV, COLS, L>(buf, tw, s);
-            fft_stage_sel<64, 8, 8, INV, COLS, L>(buf, tw, s);
-        } else if constexpr (N == 96) {
-            fft_stage_sel<96, 8, 1, INV, COLS, L>(buf, tw, s);
-            fft_stage_sel<96, 4, 8, INV, COLS, L>(buf, tw, s);
-            fft_stage_sel<96, 3, 32, INV, COLS, L>(buf, tw, s);
-        } else if constexpr (N == 128) {
-            fft_stage_sel<128, 8, 1, INV, COLS, L>(buf, tw, s);
-            fft_stage_sel<128, 4, 8, INV, COLS, L>(buf, tw, s);
-            fft_stage_sel<128, 4, 32, INV, COLS, L>(buf, tw, s);
-        }
-    }
-}
-
-// Pad a list of n > 0 lines to a multiple of sel_chunk<N>() with its last line.
-template <int N>
-__device__ __forceinline__ int pad_lines(unsigned char* sel, int n) {
-    constexpr int L = sel_chunk<N>();
-    const int m = (n + L - 1) / L * L;
-    for (int k = n; k < m; ++k) sel[k] = sel[n - 1];
-    return n;
-}
-
 // X[b][a] -> sum_{a,b} X[b][a] exp(-+2 pi i (m_u a + m_v b) / N), natural
 // order, X[b][a] at buf[b (N + 1) + a].
 template <int N, bool INV>

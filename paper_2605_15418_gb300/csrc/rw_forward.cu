@@ -102,53 +102,9 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
                 continue;
             }
             const DJob& J = jobs[R.job];
-            bool dense = true;
-            if constexpr (MODE == MODE_SPLAT && NS >= 0 && M <= 64) {
-                if (keep) {
-                    // block culling: only the spectrum columns m_u = (j_u + M/2) mod M of
-                    // kept blocks are needed (block column c holds j_u in [8c, 8c + 8)),
-                    // so the column pass runs on those; a ray with no kept block needs
-                    // no patch at all
-                    constexpr int B8 = M / 8, KW = cull_keep_words(M);
-                    int* nsel = reinterpret_cast<int*>(vw + M * M / 32 + RW_THREADS / 32 + 3);
-                    unsigned char* sel = reinterpret_cast<unsigned char*>(nsel + 1);
-                    if (threadIdx.x == 0) {
-                        const long long g = tile * RW_TILE + r;
-                        unsigned cols = 0u;
-                        for (int w = 0; w < KW; ++w) {
-                            unsigned wd = __ldg(keep + g * KW + w);
-                            while (wd) {
-                                const int b = __ffs(wd) - 1;
-                                wd &= wd - 1u;
-                                cols |= 1u << ((w * 32 + b) % B8);
-                            }
-                        }
-                        int n = 0;
-                        for (int mu = 0; mu < M; ++mu)
-                            if ((cols >> (((mu + M / 2) % M) / 8)) & 1u) sel[n++] = (unsigned char)mu;
-                        if (n > 0) pad_lines<M>(sel, n);
-                        *nsel = n;
-                    }
-                    __syncthreads();
-                    const int ncol = *nsel;
-                    if (ncol > 0) {
-                        gather_patch<M>(sys, R, Tmaps + (long long)J.slot * npix_map, X, phu, phv);
-                        __syncthreads();
-                        if constexpr (M == 64) {
-                            fft_pass<M, false, false>(X, tw);
-                            fft_pass_sel<M, false, true>(X, tw, sel, ncol);
-                        } else {
-                            fft2d<M, false>(X, tw);      // fewer registers at these sizes
-                        }
-                    }
-                    dense = false;
-                }
-            }
-            if (dense) {
-                gather_patch<M>(sys, R, Tmaps + (long long)J.slot * npix_map, X, phu, phv);
-                __syncthreads();
-                fft2d<M, false>(X, tw);
-            }
+            gather_patch<M>(sys, R, Tmaps + (long long)J.slot * npix_map, X, phu, phv);
+            __syncthreads();
+            fft2d<M, false>(X, tw);
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
                 emit_exhaustive<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                              tile * RW_TILE + r, status, vis,

@@ -74,11 +74,10 @@ __host__ __device__ inline size_t sampled_scratch_offset(int M) {
 }
 // block culling (exhaustive emission): one bit per 8 x 8 block of bins and
 // incident ray (set: the block is kept); the forward stages the current
-// ray's visibility words, the tape's per-warp counts, the number of spectrum
-// columns the kept bins need and their list in shared memory
+// ray's visibility words and the tape's per-warp counts in shared memory
 __host__ __device__ constexpr int cull_keep_words(int M) { return ((M / 8) * (M / 8) + 31) / 32; }
 __host__ __device__ inline size_t cull_scratch_bytes(int M) {
-    return align16(sizeof(unsigned) * (size_t)(M * M / 32 + RW_THREADS / 32 + 4) + M + 32);
+    return align16(sizeof(unsigned) * (size_t)(M * M / 32 + RW_THREADS / 32 + 4));
 }
 inline size_t forward_smem_bytes(int M, int emit = RW_EMIT_EXHAUSTIVE, int n_ssr = 0) {
     size_t b = sampled_scratch_offset(M);
