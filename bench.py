@@ -36,9 +36,10 @@ FP32_LANES_PER_SM = 128
 # capture of the current kernel at n-side 256 scaled by the incident-ray
 # count (16x): see the profiles/ summaries.  A kernel missing here has no
 # capture of its current code.
-TRAFFIC = {"k_bs_scatter": 16 * (1.397035e9 + 0.193390e9),
+TRAFFIC = {"k_bs_scatter": 16 * (1.391148e9 + 0.193961e9),
            "k_bs_trace": 16 * (1.378204e9 + 0.734588e9),
-           "k_cull": 16 * 0.023702e9}
+           "k_cull": 16 * 0.023728e9,
+           "k_forward": 16 * (0.304082e9 + 1.473253e9)}
 NUM_SMS = 152
 
 
@@ -84,10 +85,11 @@ def bin_bwd_flops(S):
 
 
 def block_test_flops(S):
-    """Affine-arithmetic test of one 8 x 8 block of bins: direction setup 130,
-    each sphere ~970 (21 affine products at 22, 25 sums/scalings at 10, five
-    square roots / reciprocals at 38), sensor plane 150."""
-    return 280.0 + 970.0 * S
+    """Affine-arithmetic test of one 8 x 8 block of bins for a group of rays
+    (affine forms with four noise terms): direction setup ~200, each sphere
+    ~1,290 (21 affine products at 34, 25 sums/scalings at 14, five square
+    roots / reciprocals at 45), sensor plane ~200."""
+    return 400.0 + 1290.0 * S
 
 
 def kernel_flops(name, M, D, S, n_rays, rays_with_items, items, blocks, kept):
@@ -96,7 +98,8 @@ def kernel_flops(name, M, D, S, n_rays, rays_with_items, items, blocks, kept):
         traced = 64.0 * kept if blocks else float(n_rays) * M * M
         return n_rays * fft_flops(M) + traced * bin_fwd_flops(S)
     if name == "k_cull":
-        return blocks * block_test_flops(S)
+        # planar DOE: one test per block covers a group of 8 rays of one job
+        return blocks / 8.0 * block_test_flops(S)
     if name == "k_bs_spectra":
         return rays_with_items * fft_flops(M) + items * 30.0
     if name == "k_bs_trace":
