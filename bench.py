@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU time the cpu_baseline leg keeps sampling for")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the occupancy-default persistent grids (no rw_autotune)")
     return ap.parse_args()
 
 
@@ -285,6 +287,11 @@ def main():
         RW.rw_backward_vis(sim.ctx, s, sim.jobs, sim.rays, gI, vis, dphi, None, dsurf)
         if ev: ev[4].record(stream)
 
+    tuned = None
+    if not args.no_autotune:
+        # one step to size every buffer, then the library's launch tuning (A10)
+        step()
+        tuned = sim.ctx.autotune(sim, gI, vis)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -368,7 +375,8 @@ def main():
                        "traced_secondary_fraction": (64.0 * kept / (n_rays * M * M)
                                                      if blocks else 1.0),
                        "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
-                       "kernel_ms": {k: round(v, 4) for k, v in kernel_ms.items()}},
+                       "kernel_ms": {k: round(v, 4) for k, v in kernel_ms.items()},
+                       "tuned_grids": tuned},
             "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": TRAFFIC.get(name),

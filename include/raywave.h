@@ -218,6 +218,31 @@ rw_status rw_profile_entry(rw_ctx* ctx, int32_t i, const char** kernel, double* 
  * culled yet.  Errors: RW_EINVAL, RW_ECUDA. */
 rw_status rw_cull_stats(rw_ctx* ctx, int64_t* blocks, int64_t* kept);
 
+/* ---- A10: launch tuning ------------------------------------------------- */
+
+/* Kernels whose persistent grid (CTAs of the launch) can be tuned; indices of
+ * the grids arrays below. */
+enum { RW_K_FORWARD = 0, RW_K_CULL, RW_K_BS_SPECTRA, RW_K_BS_TRACE, RW_K_BS_SCATTER,
+       RW_K_BACKWARD, RW_K_SPECTRA, RW_NK };
+
+/* Tune the persistent grid of every kernel on this workload (batching and
+ * scheduling of the method's per-ray work; the paper names no GPU and has no
+ * counterpart): runs one warm-up step, then one step -- rw_forward_vis (or
+ * rw_forward when vis is NULL) and, when dl_dpsf is not NULL, the adjoint
+ * with the same mask -- for each candidate grid (the occupancy default and
+ * 1, 2, 3, 4, 6, 8 CTAs per SM), times every launch with CUDA events and
+ * keeps, per kernel, the fastest.  The context then launches with those
+ * grids; grids_out receives them (RW_NK entries, 0 = occupancy default).
+ * psf, dphi, dsurf are used as scratch: their contents afterwards are
+ * unspecified.  Synchronises the stream; not during graph capture.
+ * Errors: as rw_forward / rw_backward_vis, RW_EINVAL. */
+rw_status rw_autotune(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                      const rw_rays* rays, float* psf, const float* dl_dpsf, uint32_t* vis,
+                      int64_t vis_words, float* dphi, double* dsurf, int64_t* grids_out);
+/* Set the per-kernel grids directly (RW_NK entries, <= 0 = occupancy default),
+ * e.g. to reuse an earlier rw_autotune result.  Errors: RW_EINVAL. */
+rw_status rw_set_grids(rw_ctx* ctx, const int64_t* grids);
+
 /* ---- A0: ray generation ------------------------------------------------ */
 
 /* Fill rays[ray_offset ..) of every job with its collimated grid launched

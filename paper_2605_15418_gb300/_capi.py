@@ -18,6 +18,8 @@ RW_EMIT_EXHAUSTIVE, RW_EMIT_SAMPLED = 0, 1
 RW_PHASE_HEIGHT, RW_PHASE_FIXED = 0, 1
 RW_DFT_FFT32, RW_DFT_TC = 0, 1
 RW_DOE_TRACE_ALL = 1
+KERNEL_KINDS = ("k_forward", "k_cull", "k_bs_spectra", "k_bs_trace", "k_bs_scatter",
+                "k_backward", "k_spectra")
 RW_MAX_SURFACES = 16
 FP = C.POINTER(C.c_float)
 DP = C.POINTER(C.c_double)
@@ -82,6 +84,10 @@ EXPORTS = {
     "rw_launch_count": (C.c_int64, [C.c_void_p]),
     "rw_profile": (C.c_int, [C.c_void_p, C.c_int32]),
     "rw_cull_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "rw_autotune": (C.c_int, [C.c_void_p, C.POINTER(rw_system), C.POINTER(rw_job), C.c_int32,
+                              C.POINTER(rw_rays), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                              C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
+    "rw_set_grids": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
     "rw_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "rw_profile_entry": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_char_p),
                                    C.POINTER(C.c_double), C.POINTER(C.c_int64)]),

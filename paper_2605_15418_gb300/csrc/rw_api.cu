@@ -81,6 +81,7 @@ struct rw_ctx {
     size_t cap_used = 0;
     int64_t launches = 0;
     long long grid_override = 0;
+    long long grid[RW_NK] = {0, 0, 0, 0, 0, 0, 0};    // tuned persistent grids (rw_autotune)
     // per-launch timing (rw_profile): events around every kernel launch
     bool prof_on = false;
     ProfHook prof_hook{};
@@ -195,6 +196,7 @@ static LaunchCtx lctx(rw_ctx* ctx) {
     L.stream = ctx->stream;
     L.num_sms = ctx->num_sms;
     L.grid_override = ctx->grid_override;
+    for (int k = 0; k < RW_NK; ++k) L.grid[k] = ctx->grid[k];
     L.prof = nullptr;
     if (ctx->prof_on && !capturing(ctx)) {
         ctx->prof_hook.user = ctx;
@@ -872,6 +874,67 @@ rw_status rw_backward_vis(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
                           int64_t vis_words, float* dphi, float* damp, double* dsurf) {
     if (!vis) return fail(ctx, RW_EINVAL, "vis is NULL");
     return backward_impl(ctx, sys, jobs, njob, rays, dl_dpsf, vis, vis_words, dphi, damp, dsurf);
+}
+
+// ---------------------------------------------------------------- autotuning (A10)
+static int kernel_kind(const std::string& name) {
+    if (name == "k_forward") return RW_K_FORWARD;
+    if (name == "k_cull") return RW_K_CULL;
+    if (name == "k_bs_spectra") return RW_K_BS_SPECTRA;
+    if (name == "k_bs_trace") return RW_K_BS_TRACE;
+    if (name == "k_bs_scatter") return RW_K_BS_SCATTER;
+    if (name == "k_backward") return RW_K_BACKWARD;
+    if (name == "k_spectra_fft" || name == "k_spectra_tc") return RW_K_SPECTRA;
+    return -1;
+}
+
+rw_status rw_autotune(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
+                      const rw_rays* rays, float* psf, const float* dl_dpsf, uint32_t* vis,
+                      int64_t vis_words, float* dphi, double* dsurf, int64_t* grids_out) {
+    if (!ctx) return RW_EINVAL;
+    if (!grids_out) return fail(ctx, RW_EINVAL, "grids_out is NULL");
+    if (capturing(ctx)) return fail(ctx, RW_EINVAL, "rw_autotune cannot run during capture");
+    const bool prof_was = ctx->prof_on;
+    auto step = [&]() -> rw_status {
+        rw_status st = forward_impl(ctx, sys, jobs, njob, rays, psf, vis, vis_words);
+        if (st != RW_OK || !dl_dpsf) return st;
+        return backward_impl(ctx, sys, jobs, njob, rays, dl_dpsf, vis, vis_words, dphi, nullptr,
+                             dsurf);
+    };
+    for (int k = 0; k < RW_NK; ++k) ctx->grid[k] = 0;
+    rw_status st = step();                                   // warm-up: sizes every buffer
+    if (st != RW_OK) return st;
+    // candidates: the occupancy default (0), then 1, 2, 3, 4, 6, 8 CTAs per SM
+    const int mult[7] = {0, 1, 2, 3, 4, 6, 8};
+    double best_ms[RW_NK];
+    long long best[RW_NK];
+    for (int k = 0; k < RW_NK; ++k) { best_ms[k] = -1.0; best[k] = 0; }
+    for (int c = 0; c < 7; ++c) {
+        for (int k = 0; k < RW_NK; ++k) ctx->grid[k] = (long long)mult[c] * ctx->num_sms;
+        if ((st = rw_profile(ctx, 1)) != RW_OK) break;
+        if ((st = step()) != RW_OK) break;
+        int32_t n = 0;
+        if ((st = rw_profile_read(ctx, &n)) != RW_OK) break;
+        for (int i = 0; i < n; ++i) {
+            const int k = kernel_kind(ctx->prof_kernels[i]);
+            if (k < 0 || ctx->prof_count[i] == 0) continue;
+            const double ms = ctx->prof_ms[i] / (double)ctx->prof_count[i];
+            if (best_ms[k] < 0.0 || ms < best_ms[k]) { best_ms[k] = ms; best[k] = ctx->grid[k]; }
+        }
+    }
+    ctx->prof_on = prof_was;
+    ctx->prof_used = 0;
+    for (int k = 0; k < RW_NK; ++k) {
+        ctx->grid[k] = (st == RW_OK) ? best[k] : 0;
+        grids_out[k] = ctx->grid[k];
+    }
+    return st;
+}
+
+rw_status rw_set_grids(rw_ctx* ctx, const int64_t* grids) {
+    if (!ctx || !grids) return fail(ctx, RW_EINVAL, "null argument");
+    for (int k = 0; k < RW_NK; ++k) ctx->grid[k] = grids[k] > 0 ? grids[k] : 0;
+    return RW_OK;
 }
 
 rw_status rw_patch_spectra(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,

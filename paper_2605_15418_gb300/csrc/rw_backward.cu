@@ -487,7 +487,7 @@ static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const 
     if (per_sm < 1) per_sm = 1;
     long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     long long grid = (long long)L.num_sms * per_sm;
-    if (L.grid_override > 0) grid = L.grid_override;
+    grid = pick_grid(L, RW_K_BACKWARD, grid);
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     RW_MARK(L, "k_backward");

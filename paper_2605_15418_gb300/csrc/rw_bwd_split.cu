@@ -323,8 +323,8 @@ static cudaError_t launch_split_d(const LaunchCtx& L, const DSys& sys, const DJo
     if (!have_list) {
         // patch spectra and the work list (otherwise the forward taped both)
         size_t smem1 = sampled_scratch_offset(M) + 64;
-        e = persistent_launch_cfg(k_bs_spectra<M>, smem1, L.num_sms, ntiles, L.grid_override,
-                                  &grid);
+        e = persistent_launch_cfg(k_bs_spectra<M>, smem1, L.num_sms, ntiles,
+                                  pick_grid(L, RW_K_BS_SPECTRA, 0), &grid);
         if (e != cudaSuccess) return e;
         RW_MARK(L, "k_bs_spectra");
         k_bs_spectra<M><<<(unsigned)grid, RW_THREADS, smem1, L.stream>>>(sys, jobs, prefix, njob,
@@ -336,7 +336,7 @@ static cudaError_t launch_split_d(const LaunchCtx& L, const DSys& sys, const DJo
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bs_trace<M, NS>, RW_THREADS, 0);
         if (e != cudaSuccess) return e;
-        long long g2 = (long long)L.num_sms * (per_sm > 0 ? per_sm : 1) * 4;
+        long long g2 = pick_grid(L, RW_K_BS_TRACE, (long long)L.num_sms * (per_sm > 0 ? per_sm : 1) * 4);
         const long long need = (nitems + RW_THREADS - 1) / RW_THREADS;
         if (g2 > need) g2 = need;
         RW_MARK(L, "k_bs_trace");
@@ -348,7 +348,8 @@ static cudaError_t launch_split_d(const LaunchCtx& L, const DSys& sys, const DJo
     size_t smem3 = sampled_scratch_offset(M);
     const size_t red = sizeof(double) * RW_MAXS * RW_NGRAD * (RW_THREADS / 32);
     if (smem3 < red) smem3 = red;
-    e = persistent_launch_cfg(k_bs_scatter<M>, smem3, L.num_sms, ntiles, L.grid_override, &grid);
+    e = persistent_launch_cfg(k_bs_scatter<M>, smem3, L.num_sms, ntiles,
+                              pick_grid(L, RW_K_BS_SCATTER, 0), &grid);
     if (e != cudaSuccess) return e;
     RW_MARK(L, "k_bs_scatter");
     k_bs_scatter<M><<<(unsigned)grid, RW_THREADS, smem3, L.stream>>>(

@@ -249,7 +249,7 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
                                                                           RW_THREADS, 0);
             if (e != cudaSuccess) return e;
             long long ntiles = (total + RW_TILE - 1) / RW_TILE;
-            long long grid = (long long)L.num_sms * (per_sm > 0 ? per_sm : 1);
+            long long grid = pick_grid(L, RW_K_CULL, (long long)L.num_sms * (per_sm > 0 ? per_sm : 1));
             if (grid > ntiles) grid = ntiles;
             if (grid < 1) grid = 1;
             RW_MARK(L, "k_cull");
@@ -275,8 +275,7 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     long long ntiles = (total + RW_TILE - 1) / RW_TILE;
-    long long grid = (long long)L.num_sms * per_sm;
-    if (L.grid_override > 0) grid = L.grid_override;
+    long long grid = pick_grid(L, RW_K_FORWARD, (long long)L.num_sms * per_sm);
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
     RW_MARK(L, "k_forward");

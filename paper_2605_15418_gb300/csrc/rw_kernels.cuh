@@ -19,9 +19,17 @@ struct ProfHook {
 struct LaunchCtx {
     cudaStream_t stream;
     int num_sms;
-    long long grid_override;   // > 0 forces the persistent grid size
+    long long grid_override;   // > 0 forces the persistent grid size of every kernel
+    long long grid[RW_NK];     // > 0: tuned grid size of kernel RW_K_* (wins over the above)
     const ProfHook* prof;      // may be null
 };
+
+// Grid of kernel `kind`: tuned size, else the forced size, else `dflt`.
+inline long long pick_grid(const LaunchCtx& L, int kind, long long dflt) {
+    if (L.grid[kind] > 0) return L.grid[kind];
+    if (L.grid_override > 0) return L.grid_override;
+    return dflt;
+}
 
 #define RW_MARK(L, name)                                          \
     do {                                                          \

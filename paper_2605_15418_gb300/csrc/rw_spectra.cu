@@ -299,7 +299,7 @@ static cudaError_t launch_spectra_fft_d(const LaunchCtx& L, const DSys& sys, con
     if (e != cudaSuccess) return e;
     long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     long long grid = (long long)L.num_sms * (per_sm > 0 ? per_sm : 1);
-    if (L.grid_override > 0) grid = L.grid_override;
+    grid = pick_grid(L, RW_K_SPECTRA, grid);
     if (grid > ntiles) grid = ntiles;
     RW_MARK(L, "k_spectra_fft");
     kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(sys, jobs, prefix, njob, total, rays, T,
@@ -318,7 +318,7 @@ cudaError_t launch_spectra(const LaunchCtx& L, const DSys& sys, int tc, const DJ
         if (e != cudaSuccess) return e;
         long long ntiles = (total + RW_TILE - 1) / RW_TILE;
         long long grid = (long long)L.num_sms * 2;
-        if (L.grid_override > 0) grid = L.grid_override;
+        grid = pick_grid(L, RW_K_SPECTRA, grid);
         if (grid > ntiles) grid = ntiles;
         RW_MARK(L, "k_spectra_tc");
         k_spectra_tc<<<(unsigned)grid, RW_THREADS, tcdft::SMEM, L.stream>>>(

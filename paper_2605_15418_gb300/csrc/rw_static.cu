@@ -95,6 +95,7 @@ extern "C" rw_status rw_generate_rays_static(double z_start, double n_object,
     L.stream = st;
     L.num_sms = sms > 0 ? sms : 1;
     L.grid_override = 0;
+    for (int k = 0; k < RW_NK; ++k) L.grid[k] = 0;
     L.prof = nullptr;
     RaysOut o;
     o.ox = rays->ox; o.oy = rays->oy; o.oz = rays->oz; o.dx = rays->dx; o.dy = rays->dy;

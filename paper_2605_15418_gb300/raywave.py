@@ -77,6 +77,28 @@ class Context:
             out[name.value.decode()] = (ms.value, cnt.value)
         return out
 
+    def autotune(self, sim, dl_dpsf=None, vis=None):
+        """Tune the persistent grid of every kernel on `sim`'s workload (one
+        forward with `vis`, plus the adjoint when dl_dpsf is given, per
+        candidate grid); returns {kernel: grid} (0 = occupancy default)."""
+        self._stream()
+        s, keep = sim.sys_struct()
+        rs = rays_struct(sim.rays)
+        psf = torch.empty(sim.psf_shape, dtype=torch.float32, device=sim.dev)
+        dphi = torch.zeros_like(sim.phi)
+        dsurf = torch.zeros(len(sim.w.system.surfaces), 8, dtype=torch.float64, device=sim.dev)
+        out = (C.c_int64 * len(A.KERNEL_KINDS))()
+        self.check(self.lib.rw_autotune(self.h, C.byref(s), sim.jobs, len(sim.jobs), C.byref(rs),
+                                        _ptr(psf), _ptr(dl_dpsf), _ptr(vis),
+                                        0 if vis is None else vis.numel(), _ptr(dphi),
+                                        _ptr(dsurf), out), "rw_autotune")
+        return dict(zip(A.KERNEL_KINDS, [int(v) for v in out]))
+
+    def set_grids(self, grids):
+        """Per-kernel grids ({kernel: grid}, missing or 0 = occupancy default)."""
+        arr = (C.c_int64 * len(A.KERNEL_KINDS))(*[int(grids.get(k, 0)) for k in A.KERNEL_KINDS])
+        self.check(self.lib.rw_set_grids(self.h, arr), "rw_set_grids")
+
     def cull_stats(self):
         """(8 x 8 bin blocks, blocks kept) of the last culled forward."""
         self._stream()
