@@ -461,7 +461,7 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
 }
 
 inline size_t backward_smem_bytes(int M, int emit, int n_ssr) {
-    size_t b = sampled_scratch_offset(M) + sizeof(float2) * (size_t)M * (M + 1) +
+    size_t b = sampled_scratch_offset(M) + sizeof(float2) * (size_t)M * (M + 2) +
                sizeof(BwdRay) * RW_TILE + sizeof(float) * 9 * (RW_THREADS / 32);
     if (emit == RW_EMIT_SAMPLED) b += sampled_bwd_bytes(M, n_ssr);
     size_t red = sizeof(double) * RW_MAXS * RW_NGRAD * (RW_THREADS / 32);

@@ -17,7 +17,8 @@
 template <int N>
 struct Patch {
     static constexpr int S = N + 1;          // row stride (complex elements)
-    static constexpr int ELEMS = N * (N + 1);
+    // buffer size: also holds N rows of N + 2 samples staged by bulk copies
+    static constexpr int ELEMS = N * (N + 2);
 };
 
 template <int R, bool INV>
@@ -168,6 +169,52 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
         fft_stage<128, 4, 8, INV, COLS>(buf, tw);
         fft_stage<128, 4, 32, INV, COLS>(buf, tw);
     }
+}
+
+// First row stage (radix R, no twiddles) reading rows staged with stride
+// N + 2 at column offset `off` and writing the usual stride N + 1 layout in
+// place: every load of the stage happens before its barrier.
+template <int N, int R, bool INV>
+__device__ __forceinline__ void fft_stage_from_staged(float2* buf, int off) {
+    constexpr int S = Patch<N>::S, SS = N + 2;
+    constexpr int NB = N / R;
+    constexpr int TOT = N * NB;
+    constexpr int PER = (TOT + RW_THREADS - 1) / RW_THREADS;
+    using Map = StageMap<N, NB, PER, false>;
+    float2 v[PER][R];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int f = threadIdx.x + k * RW_THREADS;
+        if ((TOT % RW_THREADS == 0) || f < TOT) {
+            int b, i;
+            Map::at(k, b, i);
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[k][q] = buf[b * SS + off + i + q * NB];
+            dft_small<R, INV>(v[k]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int f = threadIdx.x + k * RW_THREADS;
+        if ((TOT % RW_THREADS == 0) || f < TOT) {
+            int b, i;
+            Map::at(k, b, i);
+#pragma unroll
+            for (int q = 0; q < R; ++q) buf[b * S + i * R + q] = v[k][q];
+        }
+    }
+    __syncthreads();
+}
+
+// 2D FFT of an N = 64 patch staged as rows of N + 2 samples (bulk copies),
+// the patch starting at column `off` of each staged row.
+template <int N, bool INV>
+__device__ __forceinline__ void fft2d_staged(float2* buf, const float2* tw, int off) {
+    static_assert(N == 64, "staged patches are 64 x 64");
+    fft_stage_from_staged<64, 8, INV>(buf, off);
+    fft_stage<64, 8, 8, INV, false>(buf, tw);
+    fft_pass<64, INV, true>(buf, tw);
 }
 
 // X[b][a] -> sum_{a,b} X[b][a] exp(-+2 pi i (m_u a + m_v b) / N), natural

@@ -81,6 +81,9 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
         const unsigned long long e = atomicAdd(tape.epoch, 1ull) + 1ull;
         if (tape.iray) tape.epoch[1] = e;
     }
+    __shared__ __align__(8) uint64_t bulk_bar;     // completion of the patch row copies
+    uint32_t bulk_phase = 0;
+    if (M == 64 && threadIdx.x == 0) mbar_init(&bulk_bar, 1);
     fft_twiddles<M>(tw);
     const long long npix_map = (long long)sys.H * sys.W;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
@@ -102,9 +105,24 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
                 continue;
             }
             const DJob& J = jobs[R.job];
-            gather_patch<M>(sys, R, Tmaps + (long long)J.slot * npix_map, X, phu, phv);
-            __syncthreads();
-            fft2d<M, false>(X, tw);
+            const float2* Tj = Tmaps + (long long)J.slot * npix_map;
+            bool staged = false;
+            if constexpr (M == 64) {
+                if (bulk_patch_ok<M>(sys, R)) {
+                    if (threadIdx.x < 32) bulk_patch_issue<M>(sys, R, Tj, X, &bulk_bar);
+                    phase_factors<M>(sys, R, phu, phv);
+                    if (!mbar_wait_bounded(&bulk_bar, bulk_phase, RW_BULK_WAIT) && threadIdx.x == 0)
+                        atomicOr(status, RW_ST_TIMEOUT);
+                    bulk_phase ^= 1u;
+                    fft2d_staged<M, false>(X, tw, R.c0 & 1);
+                    staged = true;
+                }
+            }
+            if (!staged) {
+                gather_patch<M>(sys, R, Tj, X, phu, phv);
+                __syncthreads();
+                fft2d<M, false>(X, tw);
+            }
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
                 emit_exhaustive<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                              tile * RW_TILE + r, status, vis,
@@ -114,6 +132,8 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
                                           tile * RW_TILE + r, status,
                                           smem + sampled_scratch_offset(M));
             }
+            // the next patch's bulk copies write X through the async proxy
+            if (M == 64) fence_async_smem();
             __syncthreads();
         }
     }

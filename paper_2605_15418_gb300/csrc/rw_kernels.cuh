@@ -5,6 +5,7 @@
 #include "rw_fast.cuh"
 #include "rw_fft.cuh"
 #include "rw_cull.cuh"
+#include "rw_tc.cuh"
 
 enum { MODE_SPLAT = 0, MODE_COHERENT = 1, MODE_EMIT = 2 };
 
@@ -75,10 +76,10 @@ struct EmitOut {
 
 // ------------------------------------------------------------------ sizes
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-// patch X (M rows of stride M + 1), twiddles, two phase vectors, the tile's
-// incident states
+// patch X (M rows of stride M + 1, room for M rows of M + 2 staged samples),
+// twiddles, two phase vectors, the tile's incident states
 __host__ __device__ inline size_t sampled_scratch_offset(int M) {
-    return align16(sizeof(float2) * (size_t)(M * (M + 1) + 3 * M) + sizeof(RayAtDoe) * RW_TILE);
+    return align16(sizeof(float2) * (size_t)(M * (M + 2) + 3 * M) + sizeof(RayAtDoe) * RW_TILE);
 }
 // block culling (exhaustive emission): one bit per 8 x 8 block of bins and
 // incident ray (set: the block is kept); the forward stages the current
@@ -277,6 +278,46 @@ __device__ __forceinline__ void gather_patch(const DSys& sys, const RayAtDoe& R,
         }
     }
     phase_factors<M>(sys, R, phu, phv);
+}
+
+// ------------------------------------------------------------------ A3 by bulk copies
+// A nearest-pixel patch without padding (D = M = 64) whose rows r0 .. r0+63
+// and columns c0 .. c0+63 lie inside a map of even width: row b is fetched
+// as the M + 2 samples from column c0 & ~1 (a 16-byte aligned source) by one
+// asynchronous bulk copy to stage + b (M + 2); the first FFT stage reads the
+// patch at column offset c0 & 1 (fft2d_staged).
+#define RW_BULK_WAIT (1ll << 26)   // polls of the copy barrier before giving up
+
+template <int M>
+__device__ __forceinline__ bool bulk_patch_ok(const DSys& sys, const RayAtDoe& R) {
+    return M == 64 && sys.gather == RW_GATHER_NEAREST && sys.D == M && (sys.W & 1) == 0 &&
+           R.r0 >= 0 && R.r0 + M <= sys.H && R.c0 >= 0 && (R.c0 & ~1) + M + 2 <= sys.W;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                 "[%0], [%1], %2, [%3];"
+                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+// Warp 0 issues the M row copies (lane 0 first posts the byte count).
+template <int M>
+__device__ __forceinline__ void bulk_patch_issue(const DSys& sys, const RayAtDoe& R,
+                                                 const float2* __restrict__ T, float2* stage,
+                                                 uint64_t* bar) {
+    constexpr uint32_t ROW = (M + 2) * sizeof(float2);
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) mbar_expect_tx(bar, ROW * M);
+    __syncwarp();
+    const int ca = R.c0 & ~1;
+    for (int b = lane; b < M; b += 32)
+        bulk_g2s(stage + b * (M + 2), T + (long long)(R.r0 + b) * sys.W + ca, ROW, bar);
 }
 
 // ------------------------------------------------------------------ A6 + A7
