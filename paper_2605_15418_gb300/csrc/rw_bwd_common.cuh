@@ -165,6 +165,32 @@ __device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
                                             float scale, float* __restrict__ dphi,
                                             float* __restrict__ damp) {
     const int H = sys.H, W = sys.W, D = sys.D;
+    if (sys.gather == RW_GATHER_NEAREST && dphi && !damp && D == M && R.r0 >= 0 &&
+        R.r0 + M <= H && R.c0 >= 0 && R.c0 + M <= W) {
+        // interior patch: loads of T in batches of 4 ahead of their atomics
+        constexpr int PER = M * M / RW_THREADS, B = PER < 4 ? PER : 4;
+        const float2* Tb = T + (long long)R.r0 * W + R.c0;
+        float* Db = dphi + (long long)R.r0 * W + R.c0;
+#pragma unroll
+        for (int k0 = 0; k0 < PER; k0 += B) {
+            float2 t[B];
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                const int f = threadIdx.x + (k0 + k) * RW_THREADS;
+                if (k0 + k < PER) t[k] = __ldg(Tb + (long long)(f / M) * W + (f % M));
+            }
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                const int f = threadIdx.x + (k0 + k) * RW_THREADS;
+                if (k0 + k < PER) {
+                    const int b = f / M, a = f % M;
+                    const float2 gT = G[b * Patch<M>::S + a];
+                    atomicAdd(Db + (long long)b * W + a, scale * (t[k].x * gT.y - t[k].y * gT.x));
+                }
+            }
+        }
+        return;
+    }
     // walk the M x M grid (compile-time shifts) and skip the padding
     for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
         const int b = f / M, a = f - (f / M) * M;
