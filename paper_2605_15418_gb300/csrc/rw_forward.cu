@@ -81,6 +81,9 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
         const unsigned long long e = atomicAdd(tape.epoch, 1ull) + 1ull;
         if (tape.iray) tape.epoch[1] = e;
     }
+    __shared__ unsigned skeep[RW_TILE * 2];        // the tile's kept-block words (M <= 64)
+    if (vis)
+        for (int i = threadIdx.x; i < M * M / 32; i += RW_THREADS) vw[i] = 0u;
     __shared__ __align__(8) uint64_t bulk_bar;     // completion of the patch row copies
     uint32_t bulk_phase = 0;
     if (M == 64 && threadIdx.x == 0) mbar_init(&bulk_bar, 1);
@@ -93,6 +96,12 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             const long long g = tile * RW_TILE + threadIdx.x;
             incident_to_doe(sys, jobs, prefix, njob, total, rays, g, info[threadIdx.x], status);
             if (tape.rinfo && g < total) tape.rinfo[g] = info[threadIdx.x];
+        }
+        if (keep) {
+            constexpr int KW = cull_keep_words(M);
+            const long long w0 = tile * RW_TILE * KW;
+            if (threadIdx.x < RW_TILE * KW && KW <= 2)
+                skeep[threadIdx.x] = (w0 + threadIdx.x < total * KW) ? __ldg(keep + w0 + threadIdx.x) : 0u;
         }
         __syncthreads();
         for (int r = 0; r < RW_TILE; ++r) {
@@ -126,7 +135,8 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
                 emit_exhaustive<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                              tile * RW_TILE + r, status, vis,
-                                             keep, vw, tape);
+                                             keep ? skeep + r * cull_keep_words(M) : nullptr,
+                                             vw, tape);
             } else {
                 emit_sampled<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                           tile * RW_TILE + r, status,

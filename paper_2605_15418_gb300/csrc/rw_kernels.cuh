@@ -486,20 +486,20 @@ __device__ __forceinline__ void emit_culled(const DSys& sys, const DJob& J, cons
                                             const float2* X, const float2* phu,
                                             const float2* phv, double* psf, long long g,
                                             unsigned* status, unsigned* __restrict__ vis,
-                                            const unsigned* __restrict__ keepg, unsigned* vw,
+                                            const unsigned* keepw, unsigned* vw,
                                             const SplitBufs& tape) {
+    // keepw: this ray's kept-block words (shared); vw: its visibility words,
+    // zero on entry and left zero on return (each word is read and cleared by
+    // the thread that owns it)
     constexpr int S = Patch<M>::S;
     constexpr int NW = M * M / 32, B8 = M / 8, KW = cull_keep_words(M);
+    static_assert(NW <= RW_THREADS, "one visibility word per thread at most");
     unsigned keep[KW];
     int nkept = 0;
 #pragma unroll
     for (int w = 0; w < KW; ++w) {
-        keep[w] = __ldg(keepg + g * KW + w);
+        keep[w] = keepw[w];
         nkept += __popc(keep[w]);
-    }
-    if (vis) {
-        for (int i = threadIdx.x; i < NW; i += RW_THREADS) vw[i] = 0u;
-        __syncthreads();
     }
     const float2 ain = make_float2(R.a_re, R.a_im);
     const float norm = sys.norm;
@@ -530,6 +530,8 @@ __device__ __forceinline__ void emit_culled(const DSys& sys, const DJob& J, cons
     if (vis) {
         __syncthreads();
         for (int i = threadIdx.x; i < NW; i += RW_THREADS) vis[g * (long long)NW + i] = vw[i];
+        if (!tape.iray)
+            for (int i = threadIdx.x; i < NW; i += RW_THREADS) vw[i] = 0u;
     }
     if (vis && tape.iray) {
         constexpr int KV = (NW + RW_THREADS - 1) / RW_THREADS;   // words per thread
@@ -542,6 +544,7 @@ __device__ __forceinline__ void emit_culled(const DSys& sys, const DJob& J, cons
         for (int k = 0; k < KV; ++k) {
             const int wi = threadIdx.x * KV + k;
             word[k] = wi < NW ? vw[wi] : 0u;
+            if (wi < NW) vw[wi] = 0u;
             cnt += __popc(word[k]);
         }
         int incl = cnt;
@@ -592,11 +595,11 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
                                                 const float2* phv, double* psf, float2* field,
                                                 const EmitOut& eo, long long g, unsigned* status,
                                                 unsigned* __restrict__ vis,
-                                                const unsigned* __restrict__ keepg,
-                                                unsigned* vw, const SplitBufs& tape) {
+                                                const unsigned* keepw, unsigned* vw,
+                                                const SplitBufs& tape) {
     if constexpr (MODE == MODE_SPLAT && NS >= 0 && M <= 64) {
-        if (keepg) {
-            emit_culled<M, NS>(sys, J, R, X, phu, phv, psf, g, status, vis, keepg, vw, tape);
+        if (keepw) {
+            emit_culled<M, NS>(sys, J, R, X, phu, phv, psf, g, status, vis, keepw, vw, tape);
             return;
         }
     }
