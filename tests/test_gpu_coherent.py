@@ -5,7 +5,10 @@
    the angular-spectrum propagation of the zero-padded field (NumPy FFT), the
    same identity the oracle is pinned to.
 2. Many overlapping patches (64 rays, D = 32, P = 2: 4,096 secondary rays
-   each, windowed sum) against the FP64 oracle.
+   each) summed over the whole sensor, against the FP64 oracle.  (A windowed
+   sum decides each ray's window from its rounded hit pixel; near a pixel
+   boundary FP32 and FP64 can round differently and move a whole
+   contribution, so parity at scale is checked on the full sum.)
 """
 import math
 
@@ -50,7 +53,7 @@ def test_coherent_overlapping_patches_padded_against_oracle():
     w.system.sensor.z = 0.2
     w.system.sensor.pitch = 2e-3
     w.system.sensor.coherent = True
-    w.system.sensor.window = 6
+    w.system.sensor.window = 0
     sim = RW.Simulator(w)
     psf = sim.forward().cpu().numpy()
     ref = oracle_psf(w)
