@@ -308,9 +308,16 @@ rw_status rw_loss_eq3(rw_ctx* ctx, const float* psf, const float* target, int64_
  *   dsurf device double [nsurf][8] = d/d(z, c, k, A4, A6, A8, A10, n_after)
  *         (may be NULL).
  * Patches and spectra are recomputed, not stored.  Supported: incoherent
- * sensor, exhaustive or sampled emission (straight-through Gumbel-softmax
- * with temperature 1), M = pad * D <= 96 (M = 128 only through
- * rw_backward_vis with exhaustive emission). */
+ * and coherent sensor, exhaustive or sampled emission (straight-through
+ * Gumbel-softmax with temperature 1), M = pad * D <= 96 (M = 128 only
+ * through rw_backward_vis with exhaustive emission and the incoherent
+ * sensor).  Coherent sensor (Eq. 2, psf = |U|^2): the call first recomputes
+ * the complex field U of the same inputs (one forward pass; the phase is not
+ * in psf), forms dL/dU = 2 (dL/dpsf) U and reverses every secondary ray's
+ * window sum, optical path included; surface gradients then carry the
+ * optical-path terms of every segment.  With a conformal DOE the gradients
+ * through its frame and bilinear gather are not formed (dphi and damp are,
+ * and so are the surfaces behind the DOE). */
 rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
                       int32_t njob, const rw_rays* rays, const float* dl_dpsf,
                       float* dphi, float* damp, double* dsurf);
@@ -340,7 +347,8 @@ rw_status rw_generate_rays_static(double z_start, double n_object, const rw_job*
 /* rw_backward with the visibility mask written by rw_forward_vis for the
  * SAME inputs: a secondary ray that deposited nothing on the sensor has zero
  * gradient, so only the visible ones are re-traced and reversed (exact).
- * Exhaustive emission; patch sizes above 64 ignore the mask. */
+ * Exhaustive emission and the incoherent sensor; patch sizes above 64
+ * ignore the mask. */
 rw_status rw_backward_vis(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
                           const rw_rays* rays, const float* dl_dpsf, const uint32_t* vis,
                           int64_t vis_words, float* dphi, float* damp, double* dsurf);

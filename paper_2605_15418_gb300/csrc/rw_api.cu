@@ -16,7 +16,8 @@ cudaError_t launch_loss_eq3(const LaunchCtx& L, const float* I, const float* T, 
 cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                             const long long* prefix, int njob, long long total,
                             const RaysIn& rays, const float2* T, const float* amp,
-                            const float* dl_dpsf, float* dphi, float* damp, double* dsurf,
+                            const float* dl_dpsf, const float2* gfield, float* coh_rsum,
+                            double* coh_jsum, float* dphi, float* damp, double* dsurf,
                             const unsigned* vis, unsigned* status, int* launches);
 size_t backward_smem_needed(const DSys& sys);
 cudaError_t launch_bs_count(const LaunchCtx& L, const unsigned* vis, long long nwords,
@@ -58,6 +59,8 @@ struct rw_ctx {
     DevBuf tmaps;       // complex transmission per wavelength slot
     DevBuf tables;      // job tables, prefix sums, map scales
     DevBuf field;       // coherent field accumulator
+    DevBuf coh_rsum;    // coherent adjoint: per-ray emission gradient sums (7 floats)
+    DevBuf coh_jsum;    // coherent adjoint: per-job sum of dL/dOPL and ray count
     DevBuf acc;         // double PSF accumulator
     DevBuf split_rays;  // split adjoint: per-ray state, offsets, sums
     DevBuf split_items; // split adjoint: work list of visible secondary rays
@@ -479,6 +482,8 @@ rw_status rw_destroy(rw_ctx* ctx) {
     ctx->tmaps.release();
     ctx->tables.release();
     ctx->field.release();
+    ctx->coh_rsum.release();
+    ctx->coh_jsum.release();
     ctx->acc.release();
     ctx->misc.release();
     ctx->cap_dev.release();
@@ -781,7 +786,8 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
     if ((st = check_rays(ctx, rays)) != RW_OK) return st;
     if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
     if (!dl_dpsf) return fail(ctx, RW_EINVAL, "dl_dpsf is NULL");
-    if (P.sys.coherent) return fail(ctx, RW_EINVAL, "backward supports the incoherent sensor only");
+    if (P.sys.coherent && vis)
+        return fail(ctx, RW_EINVAL, "the visibility mask needs the incoherent sensor");
     // the split adjoint (three kernels) needs the mask and a host read-back of
     // its count, so it runs eagerly; otherwise the fused kernel
     const bool split = vis && P.sys.emit == RW_EMIT_EXHAUSTIVE && !capturing(ctx);
@@ -855,9 +861,40 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
         ctx->launches += (taped ? 1 : 2) + (nitems > 0 ? 1 : 0);
         return RW_OK;
     }
+    float2* gfield = nullptr;
+    float* coh_rsum = nullptr;
+    double* coh_jsum = nullptr;
+    if (P.sys.coherent) {
+        if ((st = ensure_buf(ctx, ctx->coh_rsum, (size_t)P.total * 7 * sizeof(float),
+                             "coherent adjoint scratch")) != RW_OK)
+            return st;
+        if ((st = ensure_buf(ctx, ctx->coh_jsum, (size_t)njob * 2 * sizeof(double),
+                             "coherent adjoint scratch")) != RW_OK)
+            return st;
+        coh_rsum = (float*)ctx->coh_rsum.p;
+        coh_jsum = (double*)ctx->coh_jsum.p;
+        RW_CUDA(cudaMemsetAsync(coh_jsum, 0, (size_t)njob * 2 * sizeof(double), ctx->stream),
+                "job sums clear");
+        // I = |U|^2 loses the phase of U: recompute the field, then
+        // dL/dU = 2 (dL/dI) U in place
+        const long long npx = (long long)P.sys.nx * P.sys.ny * njob;
+        if ((st = ensure_buf(ctx, ctx->field, npx * sizeof(float2), "coherent field scratch")) !=
+            RW_OK)
+            return st;
+        gfield = (float2*)ctx->field.p;
+        EmitOut eo;
+        std::memset(&eo, 0, sizeof(eo));
+        RW_CUDA(cudaMemsetAsync(gfield, 0, npx * sizeof(float2), ctx->stream), "field clear");
+        RW_CUDA(launch_forward(lctx(ctx), MODE_COHERENT, P.sys, dj, dp, njob, P.total,
+                               rays_in(rays), T, nullptr, gfield, eo, status_word(ctx)),
+                "coherent field");
+        RW_CUDA(launch_coherent_grad(lctx(ctx), gfield, dl_dpsf, npx), "field gradient");
+        ctx->launches += 2;
+    }
     int nl = 0;
     RW_CUDA(launch_backward(lctx(ctx), P.sys, dj, dp, njob, P.total, rays_in(rays), T,
-                            sys->doe.amp, dl_dpsf, dphi, damp, dsurf, vis, status_word(ctx), &nl),
+                            sys->doe.amp, dl_dpsf, gfield, coh_rsum, coh_jsum, dphi, damp,
+                            dsurf, vis, status_word(ctx), &nl),
             "backward kernel");
     ctx->launches += nl;
     return RW_OK;

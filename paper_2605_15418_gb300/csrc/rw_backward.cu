@@ -1,4 +1,4 @@
-// A9: adjoint of the fused forward (incoherent sensor).
+// A9: adjoint of the fused forward (incoherent and coherent sensor).
 //
 // Per incident ray the CTA recomputes the patch and its spectrum (nothing
 // from the forward is stored).  For every secondary ray it re-traces to the
@@ -21,6 +21,16 @@
 // dT/dphi = i (lambda0/lambda) T and dT/dA = exp(i psi) give the map
 // gradients, added with atomics.  Surface
 // gradients are kept per thread and reduced once per CTA into dsurf.
+//
+// Coherent sensor (Eq. 2, I = |U|^2): the caller passes gf = dL/dU = 2 (dL/dI) U
+// of the recomputed field.  Each secondary ray is re-traced with its optical
+// path; its window sum against gf gives dL/da, dL/dOPL, dL/d(sensor hit) and
+// dL/d(direction) (tilt term and obliquity d_z).  dL/dOPL runs back through
+// every segment n t (surfaces, DOE hit, pre-DOE trace).  With a = a_in U~,
+// dL/dU~ = conj(a_in) dL/da; sampled: p ~ |U~|, w = U~ / (N p).  On a planar
+// DOE the patch offsets are measured from the hit, U~ = X exp(-i k.(s0, t0))
+// with (s0, t0) = (first sample) - hit, so dU~/dhit = i k U~ (zero in the
+// incoherent case, where the gradient w.r.t. U~ is a real multiple of U~).
 #include "rw_bwd_common.cuh"
 
 // ------------------------------------------------------------------ sampled
@@ -52,11 +62,12 @@ __device__ __forceinline__ void gumbel_group(const DSys& sys, long long gid, int
     g4[3] = -logf(-logf(u01(w.w)));
 }
 
-template <int M, int NS>
+template <int M, int NS, bool COH>
 __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAtDoe& R,
-                                                    const float2* X, const float2* phu,
+                                                    float k0, const float2* X, const float2* phu,
                                                     const float2* phv,
-                                                    const float* __restrict__ gimg, float2* G,
+                                                    const float* __restrict__ gimg,
+                                                    const float2* __restrict__ gf, float2* G,
                                                     unsigned char* scr, float* acc,
                                                     SurfGrads<NS>& SG, float* gs,
                                                     unsigned* status) {
@@ -76,7 +87,7 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
     float* red = cdot + N;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float2 ain = make_float2(R.a_re, R.a_im);
-    // ---- power weights m = |U~|^2 over propagating bins, p = m / S
+    // ---- weights m = |U~|^2 (|U~| coherent) over propagating bins, p = m / S
     float part = 0.f;
     for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
         const int jvi = f / M, jui = f - (f / M) * M;
@@ -85,6 +96,7 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
         if (bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
             const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
             m = U.x * U.x + U.y * U.y;
+            if (COH) m = sqrtf(m);
         }
         logp[f] = m;
         gwb[f] = make_float2(0.f, 0.f);
@@ -136,7 +148,10 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
     }
     __syncthreads();
     // ---- every draw: trace + reverse of its (hard) secondary ray
+    // weight scale sc(p) = 1 / sqrt(N p) (incoherent) or 1 / (N p) (coherent)
     const float sqN = sqrtf((float)N);
+    constexpr float EXPO = COH ? -1.f : -0.5f;       // d log sc / d log p
+    const float sN = COH ? (float)N : sqN;
     for (int i = threadIdx.x; i < N; i += RW_THREADS) {
         const int jb = sel[i];
         float2 g_a = make_float2(0.f, 0.f);
@@ -146,20 +161,31 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
             float dx, dy, dz;
             if (bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
                 const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
-                const float sc = __expf(-0.5f * logp[jb]) / sqN;     // 1 / sqrt(N p)
+                const float sc = __expf(EXPO * logp[jb]) / sN;
                 const float2 a = cscale(cmul(ain, U), sc);
-                const float w = a.x * a.x + a.y * a.y;
-                float gw, gx, gy, gz;
-                if (secondary_adjoint<NS>(sys, R, gimg, dx, dy, dz, w, gw, gx, gy, gz, gdx, gdy,
-                                          gdz, SG, gs, status)) {
+                float gx, gy, gz;
+                bool hit;
+                if constexpr (COH) {
+                    float gopl;
+                    hit = secondary_adjoint_coh(sys, R, k0, gf, dx, dy, dz, a, g_a, gx, gy, gz,
+                                                gdx, gdy, gdz, gopl, gs, status);
+                    if (hit) acc[6] += gopl;
+                } else {
+                    const float w = a.x * a.x + a.y * a.y;
+                    float gw;
+                    hit = secondary_adjoint<NS>(sys, R, gimg, dx, dy, dz, w, gw, gx, gy, gz, gdx,
+                                                gdy, gdz, SG, gs, status);
+                    if (hit) g_a = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
+                }
+                if (hit) {
                     emission_adjoint(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz, gx, gy, gz,
                                      gdx, gdy, gdz, acc);
-                    g_a = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
                     // hard path: a = a_in w_jb  ->  dL/dw_jb += conj(a_in) dL/da
                     const float2 gwv = cmulc(g_a, ain);
                     atomicAdd(&gwb[jb].x, gwv.x);
                     atomicAdd(&gwb[jb].y, gwv.y);
                 } else {
+                    g_a = make_float2(0.f, 0.f);
                     gdx = gdy = gdz = 0.f;
                 }
             }
@@ -193,7 +219,7 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
                     float dx, dy, dz;
                     bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz);
                     const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
-                    const float2 aw = cscale(cmul(ain, U), __expf(-0.5f * logp[jb]) / sqN);
+                    const float2 aw = cscale(cmul(ain, U), __expf(EXPO * logp[jb]) / sN);
                     const float gy = gai.x * aw.x + gai.y * aw.y + gdi0 * dx + gdi1 * dy + gdi2 * dz;
                     if (pass == 0) accd += soft * gy;
                     else atomicAdd(&glogp[jb], soft * (gy - ci));
@@ -206,16 +232,16 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
         }
         __syncthreads();
     }
-    // ---- p = m / S, w = U~ / sqrt(N p), m = |U~|^2  ->  dL/dU~  ->  dL/dX
+    // ---- p = m / S, w = U~ sc(p), m = |U~|^2 or |U~|  ->  dL/dU~  ->  dL/dX
     float sg = 0.f, sgp = 0.f;
     for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
         if (!(logp[f] > -INFINITY)) continue;
         const int jvi = f / M, jui = f - (f / M) * M;
         const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
-        const float2 w = cscale(U, __expf(-0.5f * logp[f]) / sqN);
+        const float2 w = cscale(U, __expf(EXPO * logp[f]) / sN);
         const float2 gwv = gwb[f];
         // dL/dp from w (times p)
-        sgp += -0.5f * (gwv.x * w.x + gwv.y * w.y);
+        sgp += EXPO * (gwv.x * w.x + gwv.y * w.y);
         sg += glogp[f];
     }
     const float Sg = block_sum(sg, red);
@@ -229,17 +255,60 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
             const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
             const float p = __expf(logp[f]);
             const float m = p * S;
-            const float isq = __expf(-0.5f * logp[f]) / sqN;
+            const float isq = __expf(EXPO * logp[f]) / sN;
             const float2 w = cscale(U, isq);
             const float2 gwv = gwb[f];
-            const float gp = -0.5f * (gwv.x * w.x + gwv.y * w.y) / p;
+            const float gp = EXPO * (gwv.x * w.x + gwv.y * w.y) / p;
             // logp = log m - log S ; p = m / S
             const float gm = glogp[f] / m - Sg * iS + gp * iS - Sgp * iS;
-            gU = make_float2(2.f * U.x * gm + gwv.x * isq, 2.f * U.y * gm + gwv.y * isq);
+            // dm/dU~: 2 U~ (m = |U~|^2) or U~ / m (m = |U~|)
+            const float dm = COH ? 1.f / m : 2.f;
+            gU = make_float2(U.x * dm * gm + gwv.x * isq, U.y * dm * gm + gwv.y * isq);
+            if (COH && !sys.conformal) {
+                const float im = gU.x * U.y - gU.y * U.x;          // Im(conj(gU) U)
+                acc[0] -= sys.kstep * (float)(jui - M / 2) * im;
+                acc[1] -= sys.kstep * (float)(jvi - M / 2) * im;
+            }
         }
         const float2 ph = cmul(phu[jui], phv[jvi]);
         G[mv * S_ + mu] = cscale(cmulc(gU, ph), norm);
     }
+}
+
+// Coherent sensor: reverse of exhaustive bin f; writes its dL/dX.
+template <int M>
+__device__ __forceinline__ void exh_bin_adjoint_coh(const DSys& sys, const RayAtDoe& R, float k0,
+                                                    const float2* X, const float2* phu,
+                                                    const float2* phv,
+                                                    const float2* __restrict__ gf, float2* G,
+                                                    float2 ain, int f, float (&acc)[7],
+                                                    float* gs, unsigned* status) {
+    const int jvi = f / M, jui = f - (f / M) * M;
+    int mu = jui + M / 2; if (mu >= M) mu -= M;
+    int mv = jvi + M / 2; if (mv >= M) mv -= M;
+    const float norm = sys.norm;
+    float2 gU = make_float2(0.f, 0.f);
+    float dx, dy, dz;
+    if (bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
+        const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
+        const float2 a = cmul(ain, U);
+        float2 ga;
+        float gx, gy, gz, gdx, gdy, gdz, gopl;
+        if (secondary_adjoint_coh(sys, R, k0, gf, dx, dy, dz, a, ga, gx, gy, gz, gdx, gdy, gdz,
+                                  gopl, gs, status)) {
+            emission_adjoint(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz, gx, gy, gz, gdx, gdy,
+                             gdz, acc);
+            acc[6] += gopl;
+            gU = cmulc(ga, ain);          // conj(a_in) * dL/da
+            if (!sys.conformal) {
+                const float im = gU.x * U.y - gU.y * U.x;          // Im(conj(gU) U)
+                acc[0] -= sys.kstep * (float)(jui - M / 2) * im;
+                acc[1] -= sys.kstep * (float)(jvi - M / 2) * im;
+            }
+        }
+    }
+    const float2 ph = cmul(phu[jui], phv[jvi]);
+    G[mv * Patch<M>::S + mu] = cscale(cmulc(gU, ph), norm);
 }
 
 // Reverse of exhaustive bin f of the current incident ray; writes its dL/dX.
@@ -247,7 +316,7 @@ template <int M, int NS>
 __device__ __forceinline__ void exh_bin_adjoint(const DSys& sys, const RayAtDoe& R,
                                                 const float2* X, const float2* phu,
                                                 const float2* phv, const float* __restrict__ gimg,
-                                                float2* G, float2 ain, int f, float (&acc)[6],
+                                                float2* G, float2 ain, int f, float (&acc)[7],
                                                 SurfGrads<NS>& SG, float* gs, unsigned* status) {
     const int jvi = f / M, jui = f - (f / M) * M;
     int mu = jui + M / 2; if (mu >= M) mu -= M;
@@ -277,13 +346,16 @@ __device__ __forceinline__ void exh_bin_adjoint(const DSys& sys, const RayAtDoe&
 template <int M>
 struct BwdOcc { static constexpr int value = M >= 96 ? 1 : 2; };
 
-template <int M, int NS>
+template <int M, int NS, bool COH>
 __global__ void __launch_bounds__(RW_THREADS, BwdOcc<M>::value)
 k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
            int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
            const float* __restrict__ amp, const float* __restrict__ gpsf,
-           float* __restrict__ dphi, float* __restrict__ damp, double* __restrict__ dsurf,
-           unsigned* status, const unsigned* __restrict__ vis) {
+           const float2* __restrict__ gfield, float* __restrict__ dphi,
+           float* __restrict__ damp, double* __restrict__ dsurf, unsigned* status,
+           const unsigned* __restrict__ vis, float* __restrict__ coh_rsum,
+           double* __restrict__ coh_jsum) {
+    constexpr int NACC = COH ? 7 : 6;     // dL/dP (3), dL/dkappa (2), dL/dK, dL/dOPL
     extern __shared__ __align__(16) unsigned char smem[];
     float2* X = reinterpret_cast<float2*>(smem);
     float2* tw = X + Patch<M>::ELEMS;
@@ -320,10 +392,15 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
             fft2d<M, false>(X, tw);
             const float2 ain = make_float2(R.a_re, R.a_im);
             const float* gimg = gpsf + (long long)R.job * npx;
-            float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float2* gf = COH ? gfield + (long long)R.job * npx : nullptr;
+            float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
                 constexpr int KW = M * M / RW_THREADS;   // visibility words per warp and ray
-                if (vis && KW <= 32) {
+                if (COH) {
+                    for (int f = threadIdx.x; f < M * M; f += RW_THREADS)
+                        exh_bin_adjoint_coh<M>(sys, R, J.k0, X, phu, phv, gf, G, ain, f, acc, gs,
+                                               status);
+                } else if (vis && KW <= 32) {
                     // Only secondary rays that reached the sensor carry gradient: zero
                     // dL/dX, then compact this warp's visible bins (the forward's mask)
                     // and reverse them in converged rounds of 32.
@@ -363,21 +440,22 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                                                status);
                 }
             } else {
-                sampled_ray_adjoint<M, NS>(sys, R, X, phu, phv, gimg, G, sscr, acc, SG, gs, status);
+                sampled_ray_adjoint<M, NS, COH>(sys, R, J.k0, X, phu, phv, gimg, gf, G, sscr, acc,
+                                                SG, gs, status);
             }
             // ---- per-ray reduction of the geometric gradients
 #pragma unroll
-            for (int k = 0; k < 6; ++k)
+            for (int k = 0; k < NACC; ++k)
                 for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
             __syncthreads();
             if (lane == 0)
 #pragma unroll
-                for (int k = 0; k < 6; ++k) red[warp * 9 + k] = acc[k];
+                for (int k = 0; k < NACC; ++k) red[warp * 9 + k] = acc[k];
             __syncthreads();
             if (threadIdx.x == 0) {
-                float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float s[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 for (int w = 0; w < RW_THREADS / 32; ++w)
-                    for (int k = 0; k < 6; ++k) s[k] += red[w * 9 + k];
+                    for (int k = 0; k < NACC; ++k) s[k] += red[w * 9 + k];
                 BwdRay& B = bray[r];
                 B.gpx = s[0]; B.gpy = s[1]; B.gpz = s[2];
                 // kappa_in = k0 n_in (d.u, d.v)
@@ -387,6 +465,16 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                 B.gdz = kn_in * (s[3] * R.u[2] + s[4] * R.v[2]);
                 B.gnin = (R.kin_u * s[3] + R.kin_v * s[4]) / sys.n_in;
                 B.gnout = J.k0 * s[5];
+                B.gopl = s[6];
+                if (COH) {
+                    // the incident side runs in k_coh_incident once every ray's
+                    // dL/dOPL is known (see there)
+                    float* o = coh_rsum + R.gid * 7;
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) o[k] = s[k];
+                    atomicAdd(coh_jsum + 2 * R.job, (double)s[6]);
+                    atomicAdd(coh_jsum + 2 * R.job + 1, 1.0);
+                }
             }
             // ---- adjoint patch transform and map scatter
             fft2d<M, true>(G, tw);
@@ -394,7 +482,7 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
             __syncthreads();
         }
         // ---- incident side: DOE hit and pre-DOE surfaces, one lane per ray
-        if (threadIdx.x < RW_TILE && info[threadIdx.x].alive) {
+        if (!COH && threadIdx.x < RW_TILE && info[threadIdx.x].alive) {
             const RayAtDoe& R = info[threadIdx.x];
             const BwdRay& B = bray[threadIdx.x];
             const DJob& J = jobs[R.job];
@@ -460,6 +548,37 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
     }
 }
 
+// Coherent sensor, incident side.  A global phase of a job's field leaves
+// |U|^2 unchanged, so the optical-path gradients of the job's incident rays
+// sum to zero; the pre-DOE path derivatives are nearly the same for every
+// ray (a lens's thickness, the run to the DOE), so in float the rounding of
+// that zero sum, times the common path derivative, would swamp the small
+// ray-to-ray differences that carry the gradient.  Every ray's dL/dOPL is
+// therefore first reduced per job (k_backward), and here the job mean --
+// zero in exact arithmetic -- is subtracted before the incident adjoint.
+__global__ void __launch_bounds__(RW_THREADS)
+k_coh_incident(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
+               int njob, long long total, RaysIn rays, const float* __restrict__ rsum,
+               const double* __restrict__ jsum, double* __restrict__ dsurf, unsigned* status) {
+    __shared__ double dred[RW_MAXS * RW_NGRAD * (RW_THREADS / 32)];
+    float gs[RW_MAXS * RW_NGRAD];
+#pragma unroll
+    for (int i = 0; i < RW_MAXS * RW_NGRAD; ++i) gs[i] = 0.f;
+    for (long long g = blockIdx.x * (long long)RW_THREADS + threadIdx.x; g < total;
+         g += (long long)gridDim.x * RW_THREADS) {
+        RayAtDoe R;
+        incident_to_doe(sys, jobs, prefix, njob, total, rays, g, R, status);
+        if (!R.alive) continue;
+        float s[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s[k] = rsum[g * 7 + k];
+        const double n = jsum[2 * R.job + 1];
+        const float gopl = n > 0.0 ? (float)((double)s[6] - jsum[2 * R.job] / n) : s[6];
+        incident_adjoint<true>(sys, jobs, prefix, rays, R, s, gs, status, gopl);
+    }
+    reduce_surface_grads(sys, gs, dred, dsurf);
+}
+
 inline size_t backward_smem_bytes(int M, int emit, int n_ssr) {
     size_t b = sampled_scratch_offset(M) + sizeof(float2) * (size_t)M * (M + 2) +
                sizeof(BwdRay) * RW_TILE + sizeof(float) * 9 * (RW_THREADS / 32);
@@ -470,14 +589,16 @@ inline size_t backward_smem_bytes(int M, int emit, int n_ssr) {
 
 size_t backward_smem_needed(const DSys& sys) { return backward_smem_bytes(sys.M, sys.emit, sys.n_ssr); }
 
-template <int M, int NS>
+template <int M, int NS, bool COH = false>
 static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                      const long long* prefix, int njob, long long total,
                                      const RaysIn& rays, const float2* T, const float* amp,
-                                     const float* gpsf, float* dphi, float* damp, double* dsurf,
-                                     unsigned* status, const unsigned* vis) {
+                                     const float* gpsf, const float2* gfield, float* dphi,
+                                     float* damp, double* dsurf, unsigned* status,
+                                     const unsigned* vis, float* coh_rsum = nullptr,
+                                     double* coh_jsum = nullptr) {
     const size_t smem = backward_smem_bytes(M, sys.emit, sys.n_ssr);
-    auto kern = k_backward<M, NS>;
+    auto kern = k_backward<M, NS, COH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -492,8 +613,18 @@ static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const 
     if (grid < 1) grid = 1;
     RW_MARK(L, "k_backward");
     kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(sys, jobs, prefix, njob, total, rays, T,
-                                                          amp, gpsf, dphi, damp, dsurf, status,
-                                                          vis);
+                                                          amp, gpsf, gfield, dphi, damp, dsurf,
+                                                          status, vis, coh_rsum, coh_jsum);
+    RW_MARK(L, nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !COH || !dsurf) return e;
+    long long g2 = (total + RW_THREADS - 1) / RW_THREADS;
+    const long long cap = (long long)L.num_sms * 4;
+    if (g2 > cap) g2 = cap;
+    if (g2 < 1) g2 = 1;
+    RW_MARK(L, "k_coh_incident");
+    k_coh_incident<<<(unsigned)g2, RW_THREADS, 0, L.stream>>>(sys, jobs, prefix, njob, total, rays,
+                                                               coh_rsum, coh_jsum, dsurf, status);
     RW_MARK(L, nullptr);
     return cudaGetLastError();
 }
@@ -501,12 +632,31 @@ static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const 
 cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                             const long long* prefix, int njob, long long total,
                             const RaysIn& rays, const float2* T, const float* amp,
-                            const float* dl_dpsf, float* dphi, float* damp, double* dsurf,
+                            const float* dl_dpsf, const float2* gfield, float* coh_rsum,
+                            double* coh_jsum, float* dphi, float* damp, double* dsurf,
                             const unsigned* vis, unsigned* status, int* launches) {
     *launches = 1;
     const int ns = sys.fast_ok ? sys.n_post : -1;
+    if (sys.coherent) {
+        // the coherent sum needs each ray's optical path: generic trace only
+        if (!gfield || !coh_rsum || !coh_jsum) return cudaErrorInvalidValue;
+        if (dsurf) *launches = 2;
+#define RW_BWD_COH(DD)                                                                          \
+    case DD:                                                                                    \
+        return launch_backward_d<DD, -1, true>(L, sys, jobs, prefix, njob, total, rays, T, amp, \
+                                               dl_dpsf, gfield, dphi, damp, dsurf, status,      \
+                                               nullptr, coh_rsum, coh_jsum);
+        switch (sys.M) {
+            RW_BWD_COH(16)
+            RW_BWD_COH(32)
+            RW_BWD_COH(64)
+            RW_BWD_COH(96)
+            default: return cudaErrorInvalidValue;
+        }
+#undef RW_BWD_COH
+    }
 #define RW_BWD(DD, NN) \
-    launch_backward_d<DD, NN>(L, sys, jobs, prefix, njob, total, rays, T, amp, dl_dpsf, dphi, damp, dsurf, status, vis)
+    launch_backward_d<DD, NN>(L, sys, jobs, prefix, njob, total, rays, T, amp, dl_dpsf, nullptr, dphi, damp, dsurf, status, vis)
 #define RW_BWD_D(DD)                                      \
     case DD:                                              \
         switch (ns) {                                     \

@@ -8,6 +8,7 @@ struct BwdRay {
     float gpx, gpy, gpz;      // dL/d(hit point)
     float gdx, gdy, gdz;      // dL/d(incident direction at the DOE)
     float gnin, gnout;        // dL/d(index before / after the DOE)
+    float gopl;               // dL/d(optical path at the DOE), coherent sensor
 };
 
 __device__ __forceinline__ void bilinear_grad(const DSys& sys, float cx, float cy, float x,
@@ -132,6 +133,93 @@ __device__ __forceinline__ bool secondary_adjoint(const DSys& sys, const RayAtDo
     }
 }
 
+// ------------------------------------------------------------------ coherent sensor
+// Reverse of one ray's Eq. 2 sum.  The ray adds c_p = A exp(i theta_p) to
+// pixel p, with A = a d_z and theta_p = k OPL + k n_s (d_x (X_p - x) +
+// d_y (Y_p - y)).  For gf = dL/dU (dL = sum_p Re(conj(gf_p) dU_p)) and
+// w_p = gf_p exp(-i theta_p) this returns W0 = sum w_p, WX = sum w_p (X_p - x)
+// and WY = sum w_p (Y_p - y) over the same pixels the forward sums; then
+// dL/dA = W0 and dL/dtheta_p = -Im(A conj(w_p)).
+__device__ __forceinline__ bool coherent_sums(const DSys& sys, float k0, float cx, float cy,
+                                              float x, float y, double opl, float dx, float dy,
+                                              const float2* __restrict__ gf, float2& W0,
+                                              float2& WX, float2& WY) {
+    W0 = WX = WY = make_float2(0.f, 0.f);
+    int i_lo, i_hi, j_lo, j_hi;
+    float phb;
+    if (!coherent_range(sys, k0, cx, cy, x, y, opl, i_lo, i_hi, j_lo, j_hi, phb)) return false;
+    const float kx = k0 * sys.n_sensor * dx, ky = k0 * sys.n_sensor * dy;
+    for (int j = j_lo; j <= j_hi; ++j) {
+        const float Y = cy + ((float)j - 0.5f * sys.ny + 0.5f) * sys.spitch;
+        const float ry = Y - y;
+        for (int i = i_lo; i <= i_hi; ++i) {
+            const float X = cx + ((float)i - 0.5f * sys.nx + 0.5f) * sys.spitch;
+            const float rx = X - x;
+            const float ph = phb + kx * rx + ky * ry;
+            float sn, cs;
+            sincosf(ph, &sn, &cs);
+            const float2 g = __ldg(gf + j * sys.nx + i);
+            const float wr = g.x * cs + g.y * sn, wi = g.y * cs - g.x * sn;
+            W0.x += wr; W0.y += wi;
+            WX.x = fmaf(wr, rx, WX.x); WX.y = fmaf(wi, rx, WX.y);
+            WY.x = fmaf(wr, ry, WY.x); WY.y = fmaf(wi, ry, WY.y);
+        }
+    }
+    return true;
+}
+
+// Coherent sensor: re-trace one secondary ray with its optical path
+// (origin = DOE hit of R, direction d, amplitude a) and reverse it, optical
+// path included.  On success returns dL/da, dL/d(origin), dL/d(direction) and
+// dL/dOPL at the DOE and adds the surface-parameter gradients to gs.
+__device__ __forceinline__ bool secondary_adjoint_coh(const DSys& sys, const RayAtDoe& R,
+                                                      float k0, const float2* __restrict__ gf,
+                                                      float dx, float dy, float dz, float2 a,
+                                                      float2& ga, float& gx, float& gy,
+                                                      float& gz, float& gdx, float& gdy,
+                                                      float& gdz, float& gopl, float* gs,
+                                                      unsigned* status) {
+    float x = R.px, y = R.py, zl = R.pz;
+    double opl = R.opl;
+    float ex = dx, ey = dy, ez = dz;
+    SurfIn st[RW_MAXS];
+    bool ok = true;
+    for (int s = sys.doe_index + 1; s < sys.nsurf && ok; ++s) {
+        st[s].x = x; st[s].y = y; st[s].zl = zl - sys.s[s].gap;
+        st[s].dx = ex; st[s].dy = ey; st[s].dz = ez;
+        ok = trace_one<true>(sys.s[s], x, y, zl, ex, ey, ez, opl, status);
+    }
+    if (!ok) return false;
+    float xs = x, ys = y, ts;
+    if (!sensor_segment<true>(sys, xs, ys, zl, ex, ey, ez, opl, ts)) return false;
+    float2 W0, WX, WY;
+    if (!coherent_sums(sys, k0, R.cx, R.cy, xs, ys, opl, ex, ey, gf, W0, WX, WY)) return false;
+    const float2 A = make_float2(a.x * ez, a.y * ez);
+    const float h0 = A.x * W0.y - A.y * W0.x;     // sum_p dL/dtheta_p
+    const float hx = A.x * WX.y - A.y * WX.x;     //   ... (X_p - x)
+    const float hy = A.x * WY.y - A.y * WY.x;     //   ... (Y_p - y)
+    const float kn = k0 * sys.n_sensor;
+    gopl = k0 * h0;
+    const float gxs = -kn * ex * h0, gys = -kn * ey * h0;
+    ga = make_float2(W0.x * ez, W0.y * ez);
+    // sensor plane: (xs, ys) = (x, y) + ts e, OPL += n_s ts, ts = (gap - zl) / ez
+    const float gts = gxs * ex + gys * ey + sys.n_sensor * gopl;
+    gx = gxs; gy = gys;
+    gdx = fmaf(gxs, ts, kn * hx);
+    gdy = fmaf(gys, ts, kn * hy);
+    gz = -gts / ez;
+    gdz = (W0.x * a.x + W0.y * a.y) - gts * ts / ez;
+    // the index at the sensor enters the tilt term and the last segment
+    gs[(sys.nsurf - 1) * RW_NGRAD + 7] += k0 * (ex * hx + ey * hy) + ts * gopl;
+    for (int s = sys.nsurf - 1; s > sys.doe_index; --s) {
+        float gnb = 0.f;
+        trace_one_adjoint<true>(sys.s[s], st[s], gx, gy, gz, gdx, gdy, gdz, gs + s * RW_NGRAD,
+                                &gnb, gopl);
+        gs[(s - 1) * RW_NGRAD + 7] += gnb;
+    }
+    return true;
+}
+
 // Reverse of d = (ku u + kv v + kn n) / K for bin (ju, jv): adds dL/d(origin),
 // dL/dkappa_u, dL/dkappa_v and dL/dK to acc[0..5].
 __device__ __forceinline__ void emission_adjoint(const DSys& sys, const RayAtDoe& R, int ju,
@@ -236,11 +324,15 @@ __device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
 
 // Incident side of one ray from its summed emission gradients
 // s = (dL/dP (3), dL/dkappa_u, dL/dkappa_v, dL/dK): reverse of the DOE hit and
-// of the pre-DOE surfaces; adds surface gradients to gs.
+// of the pre-DOE surfaces; adds surface gradients to gs.  OPLG: the optical
+// path at the DOE carries the gradient gopl (coherent sensor), reversed
+// through every segment n t.
+template <bool OPLG = false>
 __device__ __forceinline__ void incident_adjoint(const DSys& sys, const DJob* __restrict__ jobs,
                                                  const long long* __restrict__ prefix,
                                                  const RaysIn& rays, const RayAtDoe& R,
-                                                 const float* s, float* gs, unsigned* status) {
+                                                 const float* s, float* gs, unsigned* status,
+                                                 float gopl = 0.f) {
     const DJob& J = jobs[R.job];
     const float kn_in = J.k0 * sys.n_in;
     float gx = s[0], gy = s[1], gz = s[2];
@@ -265,14 +357,20 @@ __device__ __forceinline__ void incident_adjoint(const DSys& sys, const DJob* __
     // planar DOE hit: h = p + t d, t = (z_doe - p_z) / d_z
     const float zld = zl - sys.s[sys.doe_index].gap;
     const float t = -zld / dz;
-    const float gt = gx * dx + gy * dy + gz * dz;
+    float gt = gx * dx + gy * dy + gz * dz;
+    if (OPLG) {
+        // OPL at the DOE = OPL before + n_in t
+        gt += sys.n_in * gopl;
+        if (sys.doe_index > 0) gs[(sys.doe_index - 1) * RW_NGRAD + 7] += t * gopl;
+    }
     gdx += gx * t; gdy += gy * t; gdz += gz * t;
     gz += -gt / dz;
     gdz += -gt * t / dz;
     gs[sys.doe_index * RW_NGRAD + 0] += gt / dz;
     for (int si = sys.doe_index - 1; si >= 0; --si) {
         float gnb = 0.f;
-        trace_one_adjoint(sys.s[si], st[si], gx, gy, gz, gdx, gdy, gdz, gs + si * RW_NGRAD, &gnb);
+        trace_one_adjoint<OPLG>(sys.s[si], st[si], gx, gy, gz, gdx, gdy, gdz, gs + si * RW_NGRAD,
+                                &gnb, gopl);
         if (si > 0) gs[(si - 1) * RW_NGRAD + 7] += gnb;
     }
 }

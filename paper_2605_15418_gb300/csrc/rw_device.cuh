@@ -109,6 +109,12 @@ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
+// Length of a float direction, in double.
+__device__ __forceinline__ double dnorm(float dx, float dy, float dz) {
+    const double x = dx, y = dy, z = dz;
+    return sqrt(x * x + y * y + z * z);
+}
+
 // ---------------------------------------------------------------- sag
 struct Sag { float z, dz, ddz; bool ok; float q; };
 
@@ -199,10 +205,34 @@ __device__ __forceinline__ bool refract(float& dx, float& dy, float& dz, float n
 // One surface in local coordinates.  On entry zl is relative to the
 // previous reference; on exit relative to this surface's vertex.
 // Adds n_before * t to opl.  Returns false if the ray is dropped.
+//
+// With OPL the path length is kept to double precision (the coherent sum
+// turns 1e-7 mm of path into 1e-3 rad of phase): the run to the vertex
+// plane, t0 = (gap - zl) / d_z, is formed from the exact double difference
+// of the two floats, the ray is put on that plane (local z = 0) and the
+// short remaining run t1 to the surface is found from there.  The distance
+// travelled is (t0 + t1) |d|: a float direction is unit only to ~1e-7.
 template <bool OPL>
 __device__ __forceinline__ bool trace_one(const DSurf& S, float& x, float& y, float& zl,
                                           float& dx, float& dy, float& dz, double& opl,
                                           unsigned* status) {
+    if (OPL) {
+        if (dz == 0.f) return false;
+        const double dn = dnorm(dx, dy, dz);
+        const double t0 = ((double)S.gap - (double)zl) / (double)dz;
+        x = fmaf((float)t0, dx, x);
+        y = fmaf((float)t0, dy, y);
+        float t1;
+        if (!intersect_local(S, x, y, 0.f, dx, dy, dz, t1, status)) return false;
+        x = fmaf(t1, dx, x); y = fmaf(t1, dy, y); zl = t1 * dz;
+        if (S.r_ap2 > 0.f && x * x + y * y > S.r_ap2) return false;
+        float nx, ny, nz; bool ok;
+        surf_normal(S, x, y, nx, ny, nz, ok);
+        if (!ok) return false;
+        if (!refract(dx, dy, dz, nx, ny, nz, S.n_before / S.n_after)) return false;
+        opl += (double)S.n_before * (t0 + (double)t1) * dn;
+        return true;
+    }
     zl -= S.gap;
     float t;
     if (!intersect_local(S, x, y, zl, dx, dy, dz, t, status)) return false;
@@ -229,10 +259,15 @@ struct SurfIn { float x, y, zl, dx, dy, dz; };
 // gdz) w.r.t. the output hit point and refracted direction, overwrite them
 // with gradients w.r.t. the input point/direction and add parameter
 // gradients to g[0..7] of this surface and to *g_nbefore (index before).
+// OPLG: the ray's optical path also carries a gradient gopl (coherent
+// sensor); the segment n_before * t adds n_before gopl to dL/dt and
+// t gopl to dL/dn_before (gopl itself passes through unchanged).
+template <bool OPLG = false>
 __device__ __forceinline__ void trace_one_adjoint(const DSurf& S, const SurfIn& in,
                                                   float& gx, float& gy, float& gz,
                                                   float& gdx, float& gdy, float& gdz,
-                                                  float* g, float* g_nbefore) {
+                                                  float* g, float* g_nbefore,
+                                                  float gopl = 0.f) {
     // ---- recompute forward
     float t;
     intersect_local(S, in.x, in.y, in.zl, in.dx, in.dy, in.dz, t, nullptr);
@@ -296,6 +331,10 @@ __device__ __forceinline__ void trace_one_adjoint(const DSurf& S, const SurfIn& 
     // ---- hit point h = p + t d (p = input point); total gradient on h
     float ghx = gx + g_xh, ghy = gy + g_yh, ghz = gz;
     float g_t = ghx * in.dx + ghy * in.dy + ghz * in.dz;
+    if (OPLG) {
+        g_t += S.n_before * gopl;
+        *g_nbefore += t * gopl;
+    }
     g_dx += ghx * t; g_dy += ghy * t; g_dz += ghz * t;
     float g_px = ghx, g_py = ghy, g_pz = ghz;
     // ---- t from G(t; p, d, theta) = (p_z + t d_z) - sag(s(t)) = 0 (local z)

@@ -262,6 +262,17 @@ __global__ void k_coherent_finalize(const float2* __restrict__ field, float* __r
     }
 }
 
+// dL/dU = 2 (dL/dI) U for I = |U|^2 (real and imaginary part), in place.
+__global__ void k_coherent_grad(float2* __restrict__ field, const float* __restrict__ g,
+                                long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 f = field[i];
+        const float s = 2.f * g[i];
+        field[i] = make_float2(s * f.x, s * f.y);
+    }
+}
+
 // ------------------------------------------------------------- launchers
 template <int M, int MODE, int NS>
 static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
@@ -406,6 +417,17 @@ cudaError_t launch_coherent_finalize(const LaunchCtx& L, const float2* field, fl
     if (grid < 1) grid = 1;
     RW_MARK(L, "k_coherent_finalize");
     k_coherent_finalize<<<(unsigned)grid, 256, 0, L.stream>>>(field, psf, n);
+    RW_MARK(L, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coherent_grad(const LaunchCtx& L, float2* field, const float* g, long long n) {
+    long long grid = (n + 255) / 256;
+    long long cap = (long long)L.num_sms * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    RW_MARK(L, "k_coherent_grad");
+    k_coherent_grad<<<(unsigned)grid, 256, 0, L.stream>>>(field, g, n);
     RW_MARK(L, nullptr);
     return cudaGetLastError();
 }

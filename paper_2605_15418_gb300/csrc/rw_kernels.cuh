@@ -195,7 +195,7 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     R.px = (float)pxd; R.py = (float)pyd; R.pz = (float)pzl;
     R.pxd = pxd; R.pyd = pyd;
     R.a_re = rays.are[ri]; R.a_im = rays.aim[ri];
-    R.opl = opl + sys.n_in_d * t;
+    R.opl = opl + sys.n_in_d * t * dnorm(dx, dy, dz);
     R.job = j;
     R.cx = J.cx; R.cy = J.cy;
     const double p = sys.pitch;
@@ -323,19 +323,34 @@ __device__ __forceinline__ void bulk_patch_issue(const DSys& sys, const RayAtDoe
 // ------------------------------------------------------------------ A6 + A7
 // Trace a secondary ray from the DOE hit through the remaining surfaces to
 // the sensor; returns false if dropped.  Position is left in (x, y).
+// Run from a point at local z = zl (relative to the last surface's vertex)
+// to the sensor plane: moves (x, y) there and returns the run t; with OPL
+// the run is formed in double (see trace_one) and n_s t |d| is added to opl.
+template <bool OPL>
+__device__ __forceinline__ bool sensor_segment(const DSys& sys, float& x, float& y, float zl,
+                                               float dx, float dy, float dz, double& opl,
+                                               float& t) {
+    if (dz == 0.f) return false;
+    if (OPL) {
+        const double td = ((double)sys.sensor_gap - (double)zl) / (double)dz;
+        t = (float)td;
+        opl += (double)sys.n_sensor * td * dnorm(dx, dy, dz);
+    } else {
+        t = -(zl - sys.sensor_gap) / dz;
+    }
+    x = fmaf(t, dx, x);
+    y = fmaf(t, dy, y);
+    return true;
+}
+
 template <bool OPL>
 __device__ __forceinline__ bool trace_to_sensor(const DSys& sys, float& x, float& y, float& zl,
                                                 float& dx, float& dy, float& dz, double& opl,
                                                 unsigned* status) {
     for (int s = sys.doe_index + 1; s < sys.nsurf; ++s)
         if (!trace_one<OPL>(sys.s[s], x, y, zl, dx, dy, dz, opl, status)) return false;
-    zl -= sys.sensor_gap;
-    if (dz == 0.f) return false;
-    const float t = -zl / dz;
-    x = fmaf(t, dx, x);
-    y = fmaf(t, dy, y);
-    if (OPL) opl += (double)sys.n_sensor * (double)t;
-    return true;
+    float t;
+    return sensor_segment<OPL>(sys, x, y, zl, dx, dy, dz, opl, t);
 }
 
 // Bilinear |a|^2 deposit.  The image is accumulated in double: a focal
@@ -361,27 +376,40 @@ __device__ __forceinline__ bool splat_bilinear(const DSys& sys, float cx, float 
     return true;
 }
 
+// Pixel range [i_lo, i_hi] x [j_lo, j_hi] of the Eq. 2 sum of a ray that
+// meets the sensor plane at (x, y): the whole sensor, or +-window pixels
+// around the nearest pixel.  False if the range is empty.  Also returns
+// the wavelet's phase at the hit, k OPL reduced to [-pi, pi] in double.
+__device__ __forceinline__ bool coherent_range(const DSys& sys, float k0, float cx, float cy,
+                                               float x, float y, double opl, int& i_lo,
+                                               int& i_hi, int& j_lo, int& j_hi, float& phb) {
+    const double TWO_PI = 6.283185307179586;
+    double ph0 = (double)k0 * opl;
+    ph0 -= TWO_PI * rint(ph0 / TWO_PI);
+    phb = (float)ph0;
+    const float u = (x - cx) * sys.inv_spitch + 0.5f * sys.nx - 0.5f;
+    const float v = (y - cy) * sys.inv_spitch + 0.5f * sys.ny - 0.5f;
+    if (!(u == u) || !(v == v)) return false;
+    i_lo = 0; i_hi = sys.nx - 1; j_lo = 0; j_hi = sys.ny - 1;
+    if (sys.window > 0) {
+        const float ic = rintf(u), jc = rintf(v);
+        if (ic < -(float)sys.window - 1.f || ic > (float)(sys.nx + sys.window)) return false;
+        if (jc < -(float)sys.window - 1.f || jc > (float)(sys.ny + sys.window)) return false;
+        i_lo = max(i_lo, (int)ic - sys.window); i_hi = min(i_hi, (int)ic + sys.window);
+        j_lo = max(j_lo, (int)jc - sys.window); j_hi = min(j_hi, (int)jc + sys.window);
+    }
+    return i_lo <= i_hi && j_lo <= j_hi;
+}
+
 // Eq. 2: add a exp(i k (OPL + n_s d_t.((X,Y) - r))) d_z over the window.
 __device__ __forceinline__ void splat_coherent(const DSys& sys, float k0, float cx, float cy,
                                                float x, float y, double opl, float dx,
                                                float dy, float dz, float2 a,
                                                float2* __restrict__ fld) {
-    const double TWO_PI = 6.283185307179586;
-    double ph0 = (double)k0 * opl;
-    ph0 -= TWO_PI * rint(ph0 / TWO_PI);
-    const float phb = (float)ph0;
+    int i_lo, i_hi, j_lo, j_hi;
+    float phb;
+    if (!coherent_range(sys, k0, cx, cy, x, y, opl, i_lo, i_hi, j_lo, j_hi, phb)) return;
     const float kx = k0 * sys.n_sensor * dx, ky = k0 * sys.n_sensor * dy;
-    const float u = (x - cx) * sys.inv_spitch + 0.5f * sys.nx - 0.5f;
-    const float v = (y - cy) * sys.inv_spitch + 0.5f * sys.ny - 0.5f;
-    if (!(u == u) || !(v == v)) return;
-    int i_lo = 0, i_hi = sys.nx - 1, j_lo = 0, j_hi = sys.ny - 1;
-    if (sys.window > 0) {
-        const float ic = rintf(u), jc = rintf(v);
-        if (ic < -(float)sys.window - 1.f || ic > (float)(sys.nx + sys.window)) return;
-        if (jc < -(float)sys.window - 1.f || jc > (float)(sys.ny + sys.window)) return;
-        i_lo = max(i_lo, (int)ic - sys.window); i_hi = min(i_hi, (int)ic + sys.window);
-        j_lo = max(j_lo, (int)jc - sys.window); j_hi = min(j_hi, (int)jc + sys.window);
-    }
     const float2 ad = make_float2(a.x * dz, a.y * dz);
     for (int j = j_lo; j <= j_hi; ++j) {
         const float Y = cy + ((float)j - 0.5f * sys.ny + 0.5f) * sys.spitch;
@@ -771,3 +799,5 @@ cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const 
 cudaError_t launch_psf_finalize(const LaunchCtx& L, const double* acc, float* psf, long long n);
 cudaError_t launch_coherent_finalize(const LaunchCtx& L, const float2* field, float* psf,
                                      long long n);
+// field <- 2 g field (dL/dU of I = |U|^2 from dL/dI = g)
+cudaError_t launch_coherent_grad(const LaunchCtx& L, float2* field, const float* g, long long n);

@@ -1,0 +1,138 @@
+"""Coherent-sensor adjoint (Eq. 2, I = |U|^2) on the GPU against the FP64
+oracle's autograd: dL/dphi, dL/dA and the surface-parameter gradients of
+the Eq. 3 loss.
+
+Cases: a complex DOE alone (whole-sensor and windowed sum, zero padding,
+sampled emission), the DOE followed by a singlet (optical paths through the
+lens behind the DOE), a singlet followed by the DOE (optical path of the
+incident ray), and a conformal DOE (map gradients; the conformal frame and
+bilinear gather are not differentiated, so surface gradients are not
+compared there).
+"""
+import numpy as np
+import pytest
+import torch
+
+import coherent_cases as CC
+from oracle import loss as OL
+from oracle import pipeline as OP
+
+from gpu_helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+PSF_TOL = 1e-4          # coherent forward parity (measured <= 6e-5)
+MAP_TOL = 5e-4          # dphi, damp: relative L2 (measured <= 1.2e-4)
+# Surface gradients: relative, plus a floor of a fraction of the largest
+# compared entry.  Each secondary ray's dL/dOPL is ~k0 times larger than
+# their sum over a job (zero: a global phase leaves |U|^2 unchanged); FP32
+# rounding of those terms, times the path derivative common to all rays,
+# leaves an absolute error of up to ~5e-3 of the largest surface gradient
+# (measured: 4.8e-3 for the DOE z of the padded case, <= 1e-3 elsewhere).
+SURF_REL = 2e-3
+SURF_FLOOR = 7.5e-3
+
+
+@pytest.fixture(scope="module")
+def RW():
+    from paper_2605_15418_gb300 import raywave
+    return raywave
+
+
+@pytest.fixture(scope="module")
+def ctx(RW):
+    c = RW.Context(0)
+    yield c
+    c.close()
+
+
+def _oracle(w):
+    prm = OP.params_of(w.system, requires_grad=True)
+    phi = torch.from_numpy(w.system.doe.phi.astype(np.float64)).requires_grad_(True)
+    amp = None
+    if w.system.doe.amp is not None:
+        amp = torch.from_numpy(w.system.doe.amp.astype(np.float64)).requires_grad_(True)
+    img = OP.psf(w, params=prm, phi=phi, amp=amp)
+    Lv, _ = OL.eq3_loss(img, torch.from_numpy(w.target.astype(np.float64)))
+    Lv.backward()
+    gs = np.zeros((len(prm), 8))
+    for si, p in enumerate(prm):
+        for k, name in ((0, "z"), (1, "c"), (7, "n_after")):
+            g = p[name].grad
+            gs[si, k] = 0.0 if g is None else float(g)
+    return (img.detach().numpy(), phi.grad.numpy(),
+            None if amp is None else amp.grad.numpy(), gs)
+
+
+def _gpu(RW, ctx, w):
+    ctx.device_status()
+    sim = RW.Simulator(w, ctx=ctx)
+    psf = sim.forward()
+    gI = torch.empty_like(psf)
+    sim.loss(psf, torch.as_tensor(w.target, device=sim.dev), gI)
+    dphi, damp, dsurf = sim.backward(gI, want_amp=True)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 0
+    return (psf.cpu().numpy(), dphi.cpu().numpy(),
+            None if damp is None else damp.cpu().numpy(), dsurf.cpu().numpy())
+
+
+def _compare(RW, ctx, w, surfaces=True, map_tol=MAP_TOL, surf_rel=SURF_REL):
+    psf, dphi, damp, dsurf = _gpu(RW, ctx, w)
+    img, gphi, gamp, gs = _oracle(w)
+    assert rel_l2(psf, img) <= PSF_TOL, rel_l2(psf, img)
+    assert rel_l2(dphi, gphi) <= map_tol, rel_l2(dphi, gphi)
+    if gamp is not None:
+        assert rel_l2(damp, gamp) <= map_tol, rel_l2(damp, gamp)
+    if surfaces:
+        cols = [0, 1, 7]
+        big = np.abs(gs[:, cols]).max()
+        for si in range(gs.shape[0]):
+            for k in cols:
+                ref = gs[si, k]
+                assert abs(dsurf[si, k] - ref) <= surf_rel * abs(ref) + SURF_FLOOR * big, \
+                    (si, k, dsurf[si, k], ref)
+
+
+@pytest.mark.parametrize("window", [0, 5])
+def test_coherent_adjoint_complex_doe_alone(RW, ctx, window):
+    _compare(RW, ctx, CC.free_space(n_side=9, window=window))
+
+
+def test_coherent_adjoint_doe_then_lens_windowed(RW, ctx):
+    _compare(RW, ctx, CC.lens_after(n_side=9, window=5))
+
+
+def test_coherent_adjoint_padded(RW, ctx):
+    """M = 32 (D = 16, P = 2): spectrum scale 1/M^2."""
+    _compare(RW, ctx, CC.free_space(n_side=7, pad=2))
+
+
+def test_coherent_adjoint_doe_then_lens(RW, ctx):
+    _compare(RW, ctx, CC.lens_after(n_side=9))
+
+
+def test_coherent_adjoint_lens_then_doe(RW, ctx):
+    _compare(RW, ctx, CC.lens_before(n_side=9))
+
+
+def test_coherent_adjoint_sampled(RW, ctx):
+    """p ~ |U~|, a = a_in U~ / (N p), straight-through Gumbel-softmax; the
+    oracle draws the same Philox noise (rare FP32/FP64 argmax flips allowed
+    for by a looser bound)."""
+    _compare(RW, ctx, CC.free_space(n_side=9, emit="sampled", n_ssr=96), map_tol=2e-3,
+             surf_rel=1e-2)
+
+
+def test_coherent_adjoint_conformal_map_gradients(RW, ctx):
+    _compare(RW, ctx, CC.conformal(n_side=9), surfaces=False)
+
+
+def test_coherent_adjoint_refuses_the_visibility_mask(RW, ctx):
+    w = CC.free_space(n_side=4)
+    sim = RW.Simulator(w, ctx=ctx)
+    psf = sim.forward()
+    vis = RW.alloc_vis(sim.n_rays, w.system.doe.M, sim.dev)
+    with pytest.raises(RW.RayWaveError) as e:
+        sim.backward(torch.ones_like(psf), vis=vis)
+    assert e.value.status == 1

@@ -369,6 +369,65 @@ def test_oracle_gradient_matches_central_differences():
         assert gphi[r, c] == pytest.approx(g_fd, rel=1e-5, abs=1e-9 * abs(float(Lv))), (r, c)
 
 
+@pytest.mark.parametrize("case", ["lens_after", "lens_before", "free_space_amp"])
+def test_oracle_coherent_gradient_matches_central_differences(case):
+    """Coherent sensor (Eq. 2): the autograd gradient of the Eq. 3 loss --
+    through the wavelet phases k (OPL + n_s d_t.((x, y) - r)), the optical
+    paths of every segment, the obliquity d_z and the spectrum's phase
+    referenced to the hit point -- equals central differences of the
+    oracle's own forward, for surface parameters, phase pixels and (complex
+    map) amplitude pixels."""
+    import coherent_cases as CC
+    w = {"lens_after": lambda: CC.lens_after(n_side=5),
+         "lens_before": lambda: CC.lens_before(n_side=5),
+         "free_space_amp": lambda: CC.free_space(n_side=5)}[case]()
+    sysm = w.system
+    tgt = torch.from_numpy(w.target.astype(np.float64))
+    prm = P.params_of(sysm, requires_grad=True)
+    phi0 = torch.from_numpy(sysm.doe.phi.astype(np.float64))
+    amp0 = None if sysm.doe.amp is None else torch.from_numpy(sysm.doe.amp.astype(np.float64))
+    phi = phi0.clone().requires_grad_(True)
+    amp = None if amp0 is None else amp0.clone().requires_grad_(True)
+
+    def loss_of(prm_, phi_, amp_):
+        return L.eq3_loss(P.psf(w, params=prm_, phi=phi_, amp=amp_), tgt)[0]
+
+    Lv = loss_of(prm, phi, amp)
+    Lv.backward()
+    scale = abs(float(Lv.detach()))
+    checks = {"lens_after": [("z", 0), ("c", 1), ("c", 2), ("z", 2), ("n_after", 1)],
+              "lens_before": [("c", 0), ("z", 1), ("n_after", 0), ("z", 2), ("n_after", 2)],
+              "free_space_amp": [("z", 0), ("n_after", 0)]}[case]
+    for name, si in checks:
+        g_ad = float(prm[si][name].grad)
+        h = 1e-5          # the coherent loss carries ~1e-11 round-off: smaller h is noisier
+        base = float(prm[si][name])
+        vals = []
+        for sgn in (+1, -1):
+            p2 = P.params_of(sysm)
+            p2[si][name] = torch.tensor(base + sgn * h, dtype=F64)
+            vals.append(float(loss_of(p2, phi0, amp0)))
+        g_fd = (vals[0] - vals[1]) / (2 * h)
+        assert g_ad == pytest.approx(g_fd, rel=1e-4, abs=1e-7 * scale), (name, si, g_ad, g_fd)
+    rng = np.random.default_rng(1)
+    for grad, base_map, is_phi in ((phi.grad, phi0, True),
+                                   (None if amp is None else amp.grad, amp0, False)):
+        if grad is None:
+            continue
+        g = grad.numpy()
+        hot = np.argwhere(np.abs(g) > 1e-2 * np.abs(g).max())
+        for (r, c) in hot[rng.choice(len(hot), 4, replace=False)]:
+            h = 1e-6
+            vals = []
+            for sgn in (+1, -1):
+                m2 = base_map.clone()
+                m2[r, c] += sgn * h
+                vals.append(float(loss_of(P.params_of(sysm), m2 if is_phi else phi0,
+                                          amp0 if is_phi else m2)))
+            g_fd = (vals[0] - vals[1]) / (2 * h)
+            assert g[r, c] == pytest.approx(g_fd, rel=1e-5, abs=1e-9 * scale), (is_phi, r, c)
+
+
 # ------------------------------------------------------------------ sampled emission (P9)
 def test_sampled_emission_is_unbiased_for_power():
     w = R.configs.c2(n_side=2, D=8, lams=(550e-6,), fields_deg=(0.0,), sensor_n=32,
