@@ -38,7 +38,14 @@ Readings (the paper does not fix these):
   (Philox4x32-10 noise); coherent sensor: p ~ |U~|, a = a_in U~ / (N p);
   incoherent sensor: p ~ |U~|^2 and |a|^2 = |a_in|^2 |U~|^2 / (N p) with the
   phase of U~ (the unbiased power weight);
-* phase at wavelength lambda: 'height' model phi * lambda0 / lambda, or 'fixed'.
+* phase at wavelength lambda: 'height' model phi * lambda0 / lambda, or 'fixed';
+* reflective DOE (section "Benchmark and Inverse Design Demonstrations",
+  reflective conformal DOE): the same frame and spectrum, the outgoing
+  normal component reversed, d' = (kappa_u u + kappa_v v - kn n) / (k0 n_in),
+  so secondary rays return into the incident medium (T = 1: the law of
+  reflection);
+* two superposed phase profiles (the same section's complex-amplitude
+  field): U = A (exp(i phi) + exp(i phi2)).
 """
 import math
 
@@ -67,8 +74,9 @@ def frame(hit, doe_surface, d_in):
     return u, v, n
 
 
-def transmission(phi, amp, rows, cols, lam, doe):
-    """T = A exp(i phi_lambda) at integer pixel indices, 0 outside the map."""
+def transmission(phi, amp, rows, cols, lam, doe, phi2=None):
+    """T = A exp(i phi_lambda) (+ A exp(i phi2_lambda)) at integer pixel
+    indices, 0 outside the map."""
     H, W = phi.shape
     inside = (rows >= 0) & (rows < H) & (cols >= 0) & (cols < W)
     r = rows.clamp(0, H - 1)
@@ -76,12 +84,15 @@ def transmission(phi, amp, rows, cols, lam, doe):
     scale = doe.lambda0 / lam if doe.phase_model == "height" else 1.0
     ph = phi[r, c] * scale
     T = torch.polar(torch.ones_like(ph), ph)
+    if phi2 is not None:
+        ph2 = phi2[r, c] * scale
+        T = T + torch.polar(torch.ones_like(ph2), ph2)
     if amp is not None:
         T = T * amp[r, c]
     return torch.where(inside, T, torch.zeros_like(T))
 
 
-def gather_nearest(hit, phi, amp, lam, doe):
+def gather_nearest(hit, phi, amp, lam, doe, phi2=None):
     """Planar nearest-pixel patch.  Returns T [N, D(rows b), D(cols a)],
     offsets s [N, D] (along u = x) and t [N, D] (along v = y)."""
     D, p = doe.D, doe.pitch
@@ -92,13 +103,13 @@ def gather_nearest(hit, phi, amp, lam, doe):
     ar = torch.arange(D)
     cols = cstar[:, None] - D // 2 + ar[None, :]
     rows = rstar[:, None] - D // 2 + ar[None, :]
-    T = transmission(phi, amp, rows[:, :, None], cols[:, None, :], lam, doe)
+    T = transmission(phi, amp, rows[:, :, None], cols[:, None, :], lam, doe, phi2)
     s = (cols.to(torch.float64) - W / 2 + 0.5) * p - x[:, None]
     t = (rows.to(torch.float64) - H / 2 + 0.5) * p - y[:, None]
     return T, s, t
 
 
-def gather_bilinear(hit, u, v, phi, amp, lam, doe):
+def gather_bilinear(hit, u, v, phi, amp, lam, doe, phi2=None):
     """Bilinear complex patch at P + s_a u + t_b v (orthographic map lookup)."""
     D, p = doe.D, doe.pitch
     H, W = phi.shape
@@ -112,10 +123,10 @@ def gather_bilinear(hit, u, v, phi, amp, lam, doe):
     j0 = torch.floor(vc.detach()).long()
     fu = uc - i0
     fv = vc - j0
-    T = ((1 - fu) * (1 - fv) * transmission(phi, amp, j0, i0, lam, doe)
-         + fu * (1 - fv) * transmission(phi, amp, j0, i0 + 1, lam, doe)
-         + (1 - fu) * fv * transmission(phi, amp, j0 + 1, i0, lam, doe)
-         + fu * fv * transmission(phi, amp, j0 + 1, i0 + 1, lam, doe))
+    T = ((1 - fu) * (1 - fv) * transmission(phi, amp, j0, i0, lam, doe, phi2)
+         + fu * (1 - fv) * transmission(phi, amp, j0, i0 + 1, lam, doe, phi2)
+         + (1 - fu) * fv * transmission(phi, amp, j0 + 1, i0, lam, doe, phi2)
+         + fu * fv * transmission(phi, amp, j0 + 1, i0 + 1, lam, doe, phi2))
     N = hit.shape[0]
     s = off[None, :].expand(N, D)
     return T, s, s.clone()
@@ -158,7 +169,7 @@ def outgoing(d_in, u, v, n, k0, n_in, n_out, M, pitch):
 
 
 def doe_step(ray, doe_surface, doe, phi, amp, lam, n_in, n_out, ray_ids=None,
-             coherent=False):
+             coherent=False, phi2=None):
     """Intersect the DOE, build the patch spectrum and emit secondary rays.
 
     Exhaustive mode: returns a dict with d [N, M, M, 3], a [N, M, M],
@@ -171,10 +182,13 @@ def doe_step(ray, doe_surface, doe, phi, amp, lam, n_in, n_out, ray_ids=None,
     hit = o + tt[:, None] * d
     opl = ray["opl"] + n_in * tt
     u, v, nrm = frame(hit, doe_surface, d)
+    if getattr(doe, "reflective", False):
+        nrm = -nrm                       # outgoing side: back into the incident medium
+        n_out = n_in
     if doe.gather == "nearest":
-        T, s, t = gather_nearest(hit, phi, amp, lam, doe)
+        T, s, t = gather_nearest(hit, phi, amp, lam, doe, phi2)
     else:
-        T, s, t = gather_bilinear(hit, u, v, phi, amp, lam, doe)
+        T, s, t = gather_bilinear(hit, u, v, phi, amp, lam, doe, phi2)
     M = doe.pad * doe.D
     U = spectrum(T, s, t, doe.pitch, M=M, coherent=coherent)
     k0 = TWO_PI / lam

@@ -17,14 +17,19 @@ gives no formulas; this module writes out the textbook ones:
 * the surface normal grad(z - z_v - sag) and vector Snell refraction
       d' = eta d + (sqrt(1 - eta^2 (1 - cos_i^2)) - eta cos_i) n,
   eta = n1 / n2, n oriented along d; total internal reflection drops the ray;
-* optical path length OPL += n1 * t; a clear-aperture radius drops rays.
+* optical path length OPL += n1 * t; a clear-aperture radius drops rays;
+* a Gaussian bump z - z_v = c exp(-s / (2 k^2)) (height c, width k), the
+  "Gaussian-like sag" substrate of a conformal DOE (section "Benchmark and
+  Inverse Design Demonstrations", reflective conformal DOE), intersected by
+  Newton's method on g(t) = F(t) - sag(s(t)) from the plane through the
+  sag at the ray's current (x, y).
 
 Rays are dicts of tensors: o [N,3], d [N,3], a complex [N], opl [N],
 alive bool [N].  Dropped rays keep finite placeholder values.
 """
 import torch
 
-PLANE, SPHERE, ASPHERE = 0, 1, 2
+PLANE, SPHERE, ASPHERE, GAUSS = 0, 1, 2, 3
 NEWTON_TOL = 1e-13
 NEWTON_MAXIT = 50
 
@@ -41,6 +46,9 @@ def surface_params(s, requires_grad=False):
 def sag(s, p):
     """Sag z - z_v at radius^2 s, its derivative d(sag)/ds, and the domain mask."""
     c, k = p["c"], p["k"]
+    if p["kind"] == GAUSS:
+        e = torch.exp(-s / (2.0 * k * k))
+        return c * e, -c * e / (2.0 * k * k), torch.ones_like(s, dtype=torch.bool)
     arg = 1.0 - (1.0 + k) * c * c * s
     ok = arg > 0
     q = torch.sqrt(torch.where(ok, arg, torch.ones_like(arg)))
@@ -83,10 +91,16 @@ def intersect(o, d, p):
         ok = d[:, 2] != 0
         t = (p["z"] - o[:, 2]) / torch.where(ok, d[:, 2], torch.ones_like(d[:, 2]))
         return t, ok
-    t, ok = _sphere_root(o, d, p["z"], p["c"])
+    if kind == GAUSS:
+        z0, _, _ = sag(o[:, 0] ** 2 + o[:, 1] ** 2, p)
+        t = (p["z"] + z0 - o[:, 2]) / d[:, 2]
+        ok = torch.ones_like(t, dtype=torch.bool)
+    else:
+        t, ok = _sphere_root(o, d, p["z"], p["c"])
     if kind == SPHERE:
         return t, ok
-    # even asphere: Newton from the base-sphere root (plane root if that fails);
+    # even asphere (Gaussian bump): Newton from the base-sphere root (from the
+    # plane through the sag at the ray's (x, y)); the plane root if that fails;
     # iterate without autograd, then one differentiable step, whose derivative
     # at convergence is the implicit-function derivative -g_theta / g_t.
     with torch.no_grad():

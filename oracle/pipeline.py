@@ -54,18 +54,28 @@ def map_tensors(system, phi=None, amp=None):
     return phi, amp
 
 
-def emit_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0):
-    """Pre-DOE trace + DOE step for (a subset of) one job's rays."""
+def phi2_tensor(system, phi2=None):
+    """The second phase map (float64) or None."""
+    if phi2 is None and getattr(system.doe, "phi2", None) is not None:
+        phi2 = torch.from_numpy(np.asarray(system.doe.phi2, dtype=np.float64))
+    return phi2
+
+
+def emit_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0, phi2=None):
+    """Pre-DOE trace + DOE step for (a subset of) one job's rays.  Returns
+    the DOE step and the index of the medium the secondary rays enter."""
     di = system.doe_index
     ray = job_rays(job, z_start, system.n_object, idx)
     ray, n_in = G.trace(ray, params[:di], torch.tensor(system.n_object, dtype=torch.float64))
-    n_out = params[di]["n_after"]
+    # a reflective DOE sends the secondary rays back into the incident medium
+    n_out = n_in if getattr(system.doe, "reflective", False) else params[di]["n_after"]
     ids = (np.arange(job.n_rays) if idx is None else np.asarray(idx)) + ray_base
     return DO.doe_step(ray, params[di], system.doe, phi, amp, job.lam, n_in, n_out,
-                       ray_ids=ids, coherent=system.sensor.coherent), n_out
+                       ray_ids=ids, coherent=system.sensor.coherent, phi2=phi2), n_out
 
 
-def psf_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0, chunk=256):
+def psf_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0, chunk=256,
+            phi2=None):
     """Sensor image [ny, nx] of one job (intensity)."""
     sen = system.sensor
     di = system.doe_index
@@ -76,7 +86,7 @@ def psf_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0, chunk=
     field = torch.zeros(nx * ny, dtype=torch.complex128)
     for c0 in range(0, n_rays, chunk):
         sub = all_idx[c0:c0 + chunk]
-        em, n_out = emit_job(system, job, z_start, params, phi, amp, sub, ray_base)
+        em, n_out = emit_job(system, job, z_start, params, phi, amp, sub, ray_base, phi2)
         dsec = em["d"]
         shp = dsec.shape[:-1]
         Nin = shp[0]
@@ -100,16 +110,18 @@ def psf_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0, chunk=
     return img.reshape(ny, nx)
 
 
-def psf(workload, params=None, phi=None, amp=None, subsets=None, chunk=256):
+def psf(workload, params=None, phi=None, amp=None, subsets=None, chunk=256, phi2=None):
     """PSF stack [njob, ny, nx].  subsets[j] optionally lists ray indices of job j."""
     system = workload.system
     if params is None:
         params = params_of(system)
     phi, amp = map_tensors(system, phi, amp)
+    phi2 = phi2_tensor(system, phi2)
     out = []
     base = 0
     for j, job in enumerate(workload.jobs):
         idx = None if subsets is None else subsets[j]
-        out.append(psf_job(system, job, workload.z_start, params, phi, amp, idx, base, chunk))
+        out.append(psf_job(system, job, workload.z_start, params, phi, amp, idx, base, chunk,
+                           phi2))
         base += job.n_rays
     return torch.stack(out, 0)

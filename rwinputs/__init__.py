@@ -7,7 +7,7 @@ Both sides read exactly the same float32 arrays produced here.
 """
 from .systems import (  # noqa: F401
     Surface, DOE, Sensor, System, Job, Workload, jobs_offsets,
-    PLANE, SPHERE, ASPHERE, PLANAR, CONFORMAL,
+    PLANE, SPHERE, ASPHERE, GAUSS, PLANAR, CONFORMAL,
 )
 from .maps import (  # noqa: F401
     binary_grating, staircase_grating, zernike_holographic_phase,

@@ -12,7 +12,7 @@ from typing import List, Optional, Tuple
 
 import numpy as np
 
-PLANE, SPHERE, ASPHERE = 0, 1, 2
+PLANE, SPHERE, ASPHERE, GAUSS = 0, 1, 2, 3
 PLANAR, CONFORMAL = 0, 1
 
 
@@ -21,7 +21,9 @@ class Surface:
     """One refracting surface (vertex form, rotationally symmetric).
 
     kind: PLANE, SPHERE (curvature c) or ASPHERE (even asphere: conic k and
-    A4..A10 polynomial terms on r^2).  n_after is the refractive index of the
+    A4..A10 polynomial terms on r^2); GAUSS only as the substrate of a
+    conformal DOE: a Gaussian bump z - z = c exp(-r^2 / (2 k^2)) of height c
+    and width k.  n_after is the refractive index of the
     medium behind the surface.  r_ap > 0 clips rays whose hit radius exceeds
     it; r_ap <= 0 means no clip.
     """
@@ -48,6 +50,11 @@ class DOE:
     (n_ssr Gumbel-max draws from p ~ |U~|).
     pad P >= 1: the D x D patch is zero-padded to M = P D samples before its
     transform, so the spectrum is sampled on the finer k-grid 2 pi j / (M p).
+    reflective: the DOE reflects; secondary rays leave on the incident side
+    (outgoing normal component reversed, index n_in); it must be the last
+    surface and the sensor lies in front of it.
+    phi2: optional second phase map [H, W]: U = A (exp(i phi) + exp(i phi2)),
+    the complex-amplitude field of two superposed phase profiles.
     """
     phi: np.ndarray
     pitch: float
@@ -62,6 +69,8 @@ class DOE:
     seed: int = 0
     rng_offset: int = 0
     pad: int = 1
+    reflective: bool = False
+    phi2: Optional[np.ndarray] = None
 
     @property
     def M(self):

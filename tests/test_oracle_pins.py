@@ -647,3 +647,146 @@ def test_overlapping_patches_reproduce_rayleigh_sommerfeld_with_padding():
     n1, n2, n4 = (_rs_vs_raywave(P) for P in (1, 2, 4))
     assert n4 >= 0.99, n4
     assert n1 < n2 < n4, (n1, n2, n4)
+
+
+# ------------------------------------------------------------------ reflective / conformal Gaussian / two phases
+def _reflective_system(surface, phi, D, p, sensor_z, coherent=False, lam0=550e-6, amp=None,
+                       phi2=None, gather="nearest", kind=R.PLANAR):
+    doe = R.DOE(phi=phi, amp=amp, pitch=p, D=D, lambda0=lam0, kind=kind, gather=gather,
+                reflective=True, phi2=phi2)
+    sen = R.Sensor(z=sensor_z, nx=D, ny=D, pitch=p, coherent=coherent)
+    return R.System([surface], 0, doe, sen)
+
+
+@pytest.mark.parametrize("theta_deg", [0.0, 10.0])
+def test_reflective_binary_grating_orders_obey_the_reflection_grating_equation(theta_deg):
+    """Reflective DOE: the same Fourier-series efficiencies, tangential
+    components sin(theta_i) + m lambda / Lambda, and the normal component
+    reversed (every order returns towards -z)."""
+    w = R.configs.c1(n_side=4, angles_deg=(theta_deg,))
+    sysm, job = w.system, w.jobs[0]
+    sysm.doe.reflective = True
+    sysm.sensor.z = -0.5
+    em, n_out = P.emit_job(sysm, job, w.z_start, P.params_of(sysm), *P.map_tensors(sysm))
+    assert float(n_out) == 1.0
+    eta = em["U"].abs() ** 2
+    c = sysm.doe.D // 2
+    lam, period = job.lam, 16 * sysm.doe.pitch
+    sin_in = float(P.job_rays(job, w.z_start)["d"][0, 0])
+    for m in range(-7, 8, 2):
+        assert float(eta[0, c, c + 2 * m]) == pytest.approx(binary_grating_efficiency(m, 16),
+                                                            abs=1e-12)
+        dvec = em["d"][0, c, c + 2 * m]
+        s_out = sin_in + m * lam / period
+        assert float(dvec[0]) == pytest.approx(s_out, abs=1e-13)
+        assert float(dvec[2]) == pytest.approx(-math.sqrt(1.0 - s_out ** 2), abs=1e-13)
+
+
+def _gauss_bump(h=0.02, width=0.1, z=0.0):
+    return R.Surface(R.GAUSS, z, c=h, k=width)
+
+
+def test_gaussian_substrate_hit_normal_and_law_of_reflection():
+    """A conformal reflective DOE on a Gaussian bump z = h exp(-r^2/(2 w^2)),
+    T = 1: Newton puts every hit on the surface, the frame's normal is the
+    analytic gradient normal, and the single bin (j = 0) leaves along the
+    mirror reflection d - 2 (d.n) n."""
+    h, wd = 0.02, 0.1
+    D, p = 16, 0.5e-3
+    phi = np.zeros((512, 512), np.float32)
+    sysm = _reflective_system(_gauss_bump(h, wd), phi, D, p, -0.3, kind=R.CONFORMAL,
+                              gather="bilinear")
+    job = R.Job(lam=1e-3, theta_x=math.radians(4.0), grid_n=5, spacing=0.02, x0=0.01,
+                y0=-0.015)
+    em, _ = P.emit_job(sysm, job, -0.2, P.params_of(sysm), *P.map_tensors(sysm))
+    hit = em["o"].numpy()
+    r2 = hit[:, 0] ** 2 + hit[:, 1] ** 2
+    assert np.abs(hit[:, 2] - h * np.exp(-r2 / (2 * wd * wd))).max() < 1e-13
+    # analytic normal of z = h exp(-r^2/(2 w^2)): (h x / w^2 e, h y / w^2 e, 1) / norm
+    e = np.exp(-r2 / (2 * wd * wd))
+    nvec = np.stack([h * hit[:, 0] / wd ** 2 * e, h * hit[:, 1] / wd ** 2 * e, np.ones_like(e)], -1)
+    nvec /= np.linalg.norm(nvec, axis=-1, keepdims=True)
+    d_in = P.job_rays(job, -0.2)["d"].numpy()
+    # the ray inputs are float32, unit only to ~1e-7: the emission keeps the
+    # tangential part of d and completes it to a unit vector on the incident
+    # side; for a unit d that is the mirror image d - 2 (d.n) n
+    dt = d_in - (d_in * nvec).sum(-1, keepdims=True) * nvec
+    refl = dt - np.sqrt(1.0 - (dt * dt).sum(-1, keepdims=True)) * nvec
+    U = em["U"].numpy()
+    c = D // 2
+    assert np.abs(np.abs(U[:, c, c]) - 1.0).max() < 1e-12
+    U[:, c, c] = 0
+    assert np.abs(U).max() < 1e-12
+    dout = em["d"].numpy()[:, c, c]
+    assert np.abs(dout - refl).max() < 1e-13
+    du = d_in / np.linalg.norm(d_in, axis=-1, keepdims=True)
+    mirror = du - 2 * (du * nvec).sum(-1, keepdims=True) * nvec
+    assert np.abs(dout - mirror).max() < 1e-7
+
+
+def test_gaussian_substrate_apex_radius_of_curvature():
+    """The bump's apex radius of curvature is w^2 / h; with the paper's
+    numbers (minimum substrate radius ~ 506 lambda at lambda = 1 um) the
+    curvature bound of a 100 lambda patch is arcsin(D / (2R)) = 0.0990 rad,
+    the worked example.  The oracle's sag reproduces the apex curvature by
+    finite differences."""
+    lam = 1e-3
+    R_min = 506 * lam
+    wd = 0.1
+    h = wd * wd / R_min
+    p = G.surface_params(_gauss_bump(h, wd))
+    s = torch.tensor([0.0, 1e-8], dtype=F64)
+    z, dz, _ = G.sag(s, p)
+    # z(r) ~ r^2 / (2 R) near the apex (a dip of the sag: the bump curves away)
+    assert float(-dz[0] * 2.0) == pytest.approx(1.0 / R_min, rel=1e-12)
+    assert math.asin(100 * lam / (2 * R_min)) == pytest.approx(0.0990, abs=5e-5)
+
+
+@pytest.mark.parametrize("zs", [0.02, 0.05])
+def test_reflective_full_patch_equals_angular_spectrum_in_front(zs):
+    """One patch covering a whole reflective planar DOE, sensor a distance
+    zs in FRONT of it: the coherent wavelet sum equals angular-spectrum
+    propagation of T over zs (reflection mirrors the propagation direction,
+    not the transverse coordinates)."""
+    D, p, lam = 32, 1e-3, 0.8e-3
+    rng = np.random.Generator(np.random.PCG64(6))
+    phi = rng.uniform(0, 2 * math.pi, (D, D)).astype(np.float32)
+    amp = rng.uniform(0.3, 1.0, (D, D)).astype(np.float32)
+    sysm = _reflective_system(R.Surface(R.PLANE, 0.0), phi, D, p, -zs, coherent=True,
+                              lam0=lam, amp=amp)
+    job = R.Job(lam=lam, grid_n=1, spacing=0.0, x0=0.31 * p, y0=0.77 * p)
+    w = R.systems.Workload("reflective P5", sysm, [job], z_start=-0.01)
+    img = P.psf(w)[0].numpy()
+    T = amp.astype(np.float64) * np.exp(1j * phi.astype(np.float64))
+    ref = np.abs(asm_propagate(T, p, lam, zs)) ** 2
+    assert np.allclose(img, ref, rtol=1e-9, atol=1e-12 * ref.max())
+
+
+def test_two_phase_field_of_opposite_ramps_is_two_plane_waves():
+    """U = exp(i phi1) + exp(i phi2) with phi1 = -phi2 = k_m x (on the k-grid)
+    is 2 cos(k_m x): the patch spectrum is two bins, +-m, of magnitude 1
+    each (the two-focus beam splitter of the paper's conformal demonstration
+    in its simplest form), and |U|^2 = 2 + 2 cos(phi1 - phi2) everywhere."""
+    D, p, lam = 32, 0.5e-3, 1e-3
+    m = 5
+    km = 2 * math.pi * m / (D * p)
+    H = W = 128
+    x = (np.arange(W) - W / 2 + 0.5) * p
+    ph1 = np.broadcast_to(km * x, (H, W)).astype(np.float64)
+    phi1 = torch.from_numpy(ph1)
+    phi2 = -phi1
+    doe = R.DOE(phi=ph1.astype(np.float32), pitch=p, D=D, lambda0=lam, phi2=(-ph1).astype(np.float32))
+    rows = torch.arange(H)[:, None].expand(H, W)
+    cols = torch.arange(W)[None, :].expand(H, W)
+    T = DO.transmission(phi1, None, rows, cols, lam, doe, phi2)
+    assert torch.allclose(T.abs() ** 2, 2 + 2 * torch.cos(phi1 - phi2), atol=1e-12)
+    sysm = R.System([R.Surface(R.PLANE, 0.0)], 0, doe, R.Sensor(1.0, 8, 8, 1e-3))
+    job = R.Job(lam=lam, grid_n=2, spacing=3.1e-3, x0=0.2e-3)
+    em, _ = P.emit_job(sysm, job, -0.1, P.params_of(sysm), phi1, None, phi2=phi2)
+    U = em["U"].abs().numpy()
+    c = D // 2
+    assert np.abs(U[:, c, c + m] - 1.0).max() < 1e-12
+    assert np.abs(U[:, c, c - m] - 1.0).max() < 1e-12
+    U[:, c, c + m] = 0
+    U[:, c, c - m] = 0
+    assert U.max() < 1e-12
