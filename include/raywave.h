@@ -64,8 +64,8 @@ typedef enum {
     RW_ENOTCONV = 6    /* Newton iteration did not converge for some rays */
 } rw_status;
 
-/* surface kinds */
-enum { RW_PLANE = 0, RW_SPHERE = 1, RW_ASPHERE = 2 };
+/* surface kinds (RW_GAUSS only as the substrate of a conformal DOE) */
+enum { RW_PLANE = 0, RW_SPHERE = 1, RW_ASPHERE = 2, RW_GAUSS = 3 };
 /* DOE patch gather: nearest pixel window (planar) / bilinear (conformal) */
 enum { RW_GATHER_NEAREST = 0, RW_GATHER_BILINEAR = 1 };
 /* secondary-ray emission */
@@ -74,17 +74,28 @@ enum { RW_EMIT_EXHAUSTIVE = 0, RW_EMIT_SAMPLED = 1 };
 enum { RW_PHASE_HEIGHT = 0, RW_PHASE_FIXED = 1 };
 /* patch transform implementation */
 enum { RW_DFT_FFT32 = 0, RW_DFT_TC = 1 };
-/* rw_doe.flags: trace every secondary ray (no block culling; the results are
- * the same, only slower -- for verification) */
-enum { RW_DOE_TRACE_ALL = 1 };
+/* rw_doe.flags:
+ *   RW_DOE_TRACE_ALL: trace every secondary ray (no block culling; the
+ *     results are the same, only slower -- for verification);
+ *   RW_DOE_REFLECTIVE: the DOE reflects (the reflective conformal DOE of the
+ *     paper's inverse-design section): secondary rays leave with the normal
+ *     component of their wavevector reversed, d = (kappa_u u + kappa_v v -
+ *     kn n) / (k0 n_in), back into the incident medium (index n_in; the DOE
+ *     surface's n_after is unused).  The DOE must be the last surface and the
+ *     sensor must lie in front of it (sensor z < DOE vertex z); incident rays
+ *     cross the sensor plane without interacting. */
+enum { RW_DOE_TRACE_ALL = 1, RW_DOE_REFLECTIVE = 2 };
 
 #define RW_MAX_SURFACES 16
 
 /* One rotationally symmetric surface in vertex form:
  *   z - z_vertex = c s / (1 + sqrt(1 - (1 + k) c^2 s)) + A4 s^2 + A6 s^3 + A8 s^4 + A10 s^5,
  *   s = x^2 + y^2.
- * PLANE ignores c, k, A; SPHERE ignores k, A.  n_after is the index of the
- * medium behind the surface.  r_ap > 0 drops rays hitting at radius > r_ap. */
+ * PLANE ignores c, k, A; SPHERE ignores k, A.  RW_GAUSS (DOE substrate only)
+ * is the Gaussian bump z - z_vertex = c exp(-s / (2 k^2)): height c (mm,
+ * either sign), width k > 0 (mm); its apex radius of curvature is k^2 / |c|.
+ * n_after is the index of the medium behind the surface.  r_ap > 0 drops
+ * rays hitting at radius > r_ap. */
 typedef struct {
     int32_t kind;
     int32_t reserved;
@@ -97,8 +108,9 @@ typedef struct {
 } rw_surface;
 
 /* The DOE: its transmission map and the ray-wave parameters.  The geometry
- * is surfaces[doe_index] of the system (PLANE = planar DOE, SPHERE =
- * conformal DOE on a sphere).  Pixel (r, c) is centred at
+ * is surfaces[doe_index] of the system (PLANE = planar DOE, SPHERE or GAUSS =
+ * conformal DOE; a conformal hit is refined in double precision by Newton's
+ * method, RW_ENOTCONV if it fails).  Pixel (r, c) is centred at
  * x = (c - W/2 + 1/2) pitch, y = (r - H/2 + 1/2) pitch. */
 typedef struct {
     int32_t H, W;
@@ -123,6 +135,11 @@ typedef struct {
                             * surfaces skips blocks of bins whose affine-arithmetic
                             * enclosure of the sensor hit lies two pixels or more
                             * outside the sensor window (they cannot deposit) */
+    const float* phi2;     /* device, [H][W] radians, or NULL: with a second phase
+                            * profile the field is U = A (exp(i phi) + exp(i phi2))
+                            * (the complex-amplitude DOE of the paper's conformal
+                            * beam-splitting demonstration); both profiles follow
+                            * phase_model */
 } rw_doe;
 
 /* Sensor plane z = const.  Pixel (i, j) of job J is centred at
@@ -303,7 +320,8 @@ rw_status rw_loss_eq3(rw_ctx* ctx, const float* psf, const float* target, int64_
 /* ---- A9: adjoint -------------------------------------------------------- */
 
 /* Given dL/dpsf (device float [njob][ny][nx]), ACCUMULATE (+=) into
- *   dphi  device float [H][W]   (may be NULL)
+ *   dphi  device float [H][W]   (may be NULL); with doe.phi2 set,
+ *         [2][H][W]: dL/dphi, then dL/dphi2
  *   damp  device float [H][W]   (may be NULL; needs doe.amp)
  *   dsurf device double [nsurf][8] = d/d(z, c, k, A4, A6, A8, A10, n_after)
  *         (may be NULL).

@@ -12,12 +12,12 @@ LIB_PATH = os.path.join(HERE, "librw.so")
 RW_OK, RW_EINVAL, RW_ENOMEM, RW_ECUDA, RW_ECAPACITY, RW_ETIMEOUT, RW_ENOTCONV = range(7)
 STATUS_NAMES = {0: "RW_OK", 1: "RW_EINVAL", 2: "RW_ENOMEM", 3: "RW_ECUDA", 4: "RW_ECAPACITY",
                 5: "RW_ETIMEOUT", 6: "RW_ENOTCONV"}
-RW_PLANE, RW_SPHERE, RW_ASPHERE = 0, 1, 2
+RW_PLANE, RW_SPHERE, RW_ASPHERE, RW_GAUSS = 0, 1, 2, 3
 RW_GATHER_NEAREST, RW_GATHER_BILINEAR = 0, 1
 RW_EMIT_EXHAUSTIVE, RW_EMIT_SAMPLED = 0, 1
 RW_PHASE_HEIGHT, RW_PHASE_FIXED = 0, 1
 RW_DFT_FFT32, RW_DFT_TC = 0, 1
-RW_DOE_TRACE_ALL = 1
+RW_DOE_TRACE_ALL, RW_DOE_REFLECTIVE = 1, 2
 KERNEL_KINDS = ("k_forward", "k_cull", "k_bs_spectra", "k_bs_trace", "k_bs_scatter",
                 "k_backward", "k_spectra")
 RW_MAX_SURFACES = 16
@@ -39,7 +39,7 @@ class rw_doe(C.Structure):
                 ("D", C.c_int32), ("gather", C.c_int32), ("emit", C.c_int32),
                 ("n_ssr", C.c_int32), ("phase_model", C.c_int32), ("dft", C.c_int32),
                 ("seed", C.c_uint64), ("rng_offset", C.c_uint64),
-                ("pad", C.c_int32), ("flags", C.c_int32)]
+                ("pad", C.c_int32), ("flags", C.c_int32), ("phi2", C.c_void_p)]
 
 
 class rw_sensor(C.Structure):

@@ -278,6 +278,9 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
         return fail(ctx, RW_EINVAL, "doe.lambda0 must be > 0 for the height model");
     if (doe.dft != RW_DFT_FFT32 && doe.dft != RW_DFT_TC)
         return fail(ctx, RW_EINVAL, "doe.dft invalid");
+    if (doe.flags & ~(RW_DOE_TRACE_ALL | RW_DOE_REFLECTIVE))
+        return fail(ctx, RW_EINVAL, "doe.flags has unknown bits");
+    const bool reflective = (doe.flags & RW_DOE_REFLECTIVE) != 0;
     const rw_sensor& sen = sys->sensor;
     if (sen.nx < 1 || sen.ny < 1 || !(sen.pitch > 0))
         return fail(ctx, RW_EINVAL, "sensor size and pitch must be positive");
@@ -290,8 +293,13 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
     double prev_z = 0.0, n_prev = sys->n_object;
     for (int i = 0; i < sys->nsurf; ++i) {
         const rw_surface& s = sys->surfaces[i];
-        if (s.kind != RW_PLANE && s.kind != RW_SPHERE && s.kind != RW_ASPHERE)
+        if (s.kind != RW_PLANE && s.kind != RW_SPHERE && s.kind != RW_ASPHERE &&
+            s.kind != RW_GAUSS)
             return fail(ctx, RW_EINVAL, "surface kind invalid");
+        if (s.kind == RW_GAUSS && i != sys->doe_index)
+            return fail(ctx, RW_EINVAL, "RW_GAUSS is only a DOE substrate");
+        if (s.kind == RW_GAUSS && !(s.k > 0) )
+            return fail(ctx, RW_EINVAL, "RW_GAUSS width k must be > 0");
         if (i > 0 && s.z < sys->surfaces[i - 1].z)
             return fail(ctx, RW_EINVAL, "surfaces must be sorted by z");
         if (!(s.n_after > 0)) return fail(ctx, RW_EINVAL, "surface n_after must be > 0");
@@ -300,6 +308,7 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
         o.kind = s.kind;
         o.c = (float)(s.kind == RW_PLANE ? 0.0 : s.c);
         o.cd = (s.kind == RW_PLANE ? 0.0 : s.c);
+        o.kd = s.k;
         o.k = (float)s.k;
         o.A4 = (float)s.A4; o.A6 = (float)s.A6; o.A8 = (float)s.A8; o.A10 = (float)s.A10;
         o.n_before = (float)n_prev;
@@ -308,16 +317,37 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
         o.gap = (float)(s.z - prev_z);
         o.z = s.z;
         if (i == sys->doe_index) {
-            if (s.kind == RW_ASPHERE) return fail(ctx, RW_EINVAL, "DOE surface must be PLANE or SPHERE");
+            if (s.kind == RW_ASPHERE)
+                return fail(ctx, RW_EINVAL, "DOE surface must be PLANE, SPHERE or GAUSS");
             d.n_in = (float)n_prev;
             d.n_in_d = n_prev;
-            d.n_out = (float)s.n_after;
-            d.conformal = (s.kind == RW_SPHERE) ? 1 : 0;
+            // a reflective DOE sends the secondary rays back into the incident medium
+            d.n_out = reflective ? (float)n_prev : (float)s.n_after;
+            d.conformal = (s.kind == RW_SPHERE || s.kind == RW_GAUSS) ? 1 : 0;
         }
         prev_z = s.z;
-        n_prev = s.n_after;
+        // behind a reflective DOE (the last surface) the rays travel in n_in
+        if (!(reflective && i == sys->doe_index)) n_prev = s.n_after;
     }
-    if (sen.z < prev_z) return fail(ctx, RW_EINVAL, "sensor must lie behind the last surface");
+    if (reflective) {
+        if (sys->doe_index != sys->nsurf - 1)
+            return fail(ctx, RW_EINVAL, "a reflective DOE must be the last surface");
+        if (!(sen.z < sys->surfaces[sys->doe_index].z))
+            return fail(ctx, RW_EINVAL, "the sensor must lie in front of a reflective DOE");
+        if (sys->surfaces[sys->doe_index].kind == RW_GAUSS &&
+            sen.z > sys->surfaces[sys->doe_index].z + std::min(0.0, sys->surfaces[sys->doe_index].c))
+            return fail(ctx, RW_EINVAL, "the sensor must lie in front of a reflective DOE");
+    } else if (sen.z < prev_z) {
+        return fail(ctx, RW_EINVAL, "sensor must lie behind the last surface");
+    }
+    d.reflective = reflective ? 1 : 0;
+    // surface whose n_after is the index the secondary rays enter / the
+    // sensor medium (-1: the object space index, no gradient slot)
+    d.nout_slot = reflective ? sys->doe_index - 1 : sys->doe_index;
+    d.nsen_slot = reflective ? sys->doe_index - 1 : sys->nsurf - 1;
+    d.two_phase = doe.phi2 ? 1 : 0;
+    d.phi = doe.phi;
+    d.phi2 = doe.phi2;
     // surfaces behind the DOE for the specialised plane/sphere trace
     d.n_post = sys->nsurf - sys->doe_index - 1;
     d.fast_ok = d.n_post <= 8 ? 1 : 0;
@@ -438,8 +468,8 @@ static rw_status prepare(rw_ctx* ctx, const rw_system* sys, const Packed& P, flo
                     "transmission-map scratch");
     if (st != RW_OK) return st;
     *T = (float2*)ctx->tmaps.p;
-    RW_CUDA(launch_prep_maps(lctx(ctx), sys->doe.phi, sys->doe.amp, npix, (const float*)ptrs[2],
-                             nslot, *T),
+    RW_CUDA(launch_prep_maps(lctx(ctx), sys->doe.phi, sys->doe.phi2, sys->doe.amp, npix,
+                             (const float*)ptrs[2], nslot, *T),
             "prep maps");
     ctx->launches++;
     return RW_OK;

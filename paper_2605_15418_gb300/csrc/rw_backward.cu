@@ -497,7 +497,7 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                 trace_one<false>(sys.s[s], x, y, zl, dx, dy, dz, dummy, status);
             }
             // index gradients of the DOE emission
-            gs[sys.doe_index * RW_NGRAD + 7] += B.gnout;
+            if (sys.nout_slot >= 0) gs[sys.nout_slot * RW_NGRAD + 7] += B.gnout;
             if (sys.doe_index > 0) gs[(sys.doe_index - 1) * RW_NGRAD + 7] += B.gnin;
             float gx = B.gpx, gy = B.gpy, gz = B.gpz;
             float gdx = B.gdx, gdy = B.gdy, gdz = B.gdz;

@@ -210,7 +210,8 @@ __device__ __forceinline__ bool secondary_adjoint_coh(const DSys& sys, const Ray
     gz = -gts / ez;
     gdz = (W0.x * a.x + W0.y * a.y) - gts * ts / ez;
     // the index at the sensor enters the tilt term and the last segment
-    gs[(sys.nsurf - 1) * RW_NGRAD + 7] += k0 * (ex * hx + ey * hy) + ts * gopl;
+    if (sys.nsen_slot >= 0)
+        gs[sys.nsen_slot * RW_NGRAD + 7] += k0 * (ex * hx + ey * hy) + ts * gopl;
     for (int s = sys.nsurf - 1; s > sys.doe_index; --s) {
         float gnb = 0.f;
         trace_one_adjoint<true>(sys.s[s], st[s], gx, gy, gz, gdx, gdy, gdz, gs + s * RW_NGRAD,
@@ -245,7 +246,31 @@ __device__ __forceinline__ void emission_adjoint(const DSys& sys, const RayAtDoe
 // Reverse of the patch gather: dL/dT on the D x D patch (the top-left
 // corner of the M x M buffer G, natural order after the conjugate FFT; the
 // padding carries no map samples) -> dphi = (lambda0/lambda) Im(conj(T) g),
-// dA = Re(conj(T) g) / A, added to the maps with atomics.
+// dA = Re(conj(T) g) / A, added to the maps with atomics.  Two phase
+// profiles (T = A (e1 + e2), ek = exp(i s phik)): dphik = s Im(conj(A ek) g)
+// into dphi[k H W], dA = Re(conj(e1 + e2) g).
+__device__ __forceinline__ void map_grad_at(const DSys& sys, long long p, float2 t, float2 g,
+                                            const float* __restrict__ amp, float scale,
+                                            float* __restrict__ dphi, float* __restrict__ damp) {
+    if (sys.two_phase) {
+        float s1, c1, s2, c2;
+        sincosf(__ldg(sys.phi + p) * scale, &s1, &c1);
+        sincosf(__ldg(sys.phi2 + p) * scale, &s2, &c2);
+        const float A = amp ? __ldg(amp + p) : 1.f;
+        if (dphi) {
+            atomicAdd(dphi + p, scale * A * (c1 * g.y - s1 * g.x));
+            atomicAdd(dphi + (long long)sys.H * sys.W + p, scale * A * (c2 * g.y - s2 * g.x));
+        }
+        if (damp) atomicAdd(damp + p, (c1 + c2) * g.x + (s1 + s2) * g.y);
+        return;
+    }
+    if (dphi) atomicAdd(dphi + p, scale * (t.x * g.y - t.y * g.x));
+    if (damp) {
+        const float A = __ldg(amp + p);
+        if (A != 0.f) atomicAdd(damp + p, (t.x * g.x + t.y * g.y) / A);
+    }
+}
+
 template <int M>
 __device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
                                             const float2* __restrict__ T,
@@ -253,7 +278,8 @@ __device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
                                             float scale, float* __restrict__ dphi,
                                             float* __restrict__ damp) {
     const int H = sys.H, W = sys.W, D = sys.D;
-    if (sys.gather == RW_GATHER_NEAREST && dphi && !damp && D == M && R.r0 >= 0 &&
+    if (sys.gather == RW_GATHER_NEAREST && dphi && !damp && !sys.two_phase && D == M &&
+        R.r0 >= 0 &&
         R.r0 + M <= H && R.c0 >= 0 && R.c0 + M <= W) {
         // interior patch: loads of T in batches of 4 ahead of their atomics
         constexpr int PER = M * M / RW_THREADS, B = PER < 4 ? PER : 4;
@@ -288,12 +314,7 @@ __device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
             const int rr = R.r0 + b, cc = R.c0 + a;
             if ((unsigned)rr < (unsigned)H && (unsigned)cc < (unsigned)W) {
                 const long long p = (long long)rr * W + cc;
-                const float2 t = __ldg(&T[p]);
-                if (dphi) atomicAdd(dphi + p, scale * (t.x * gT.y - t.y * gT.x));
-                if (damp) {
-                    const float A = __ldg(amp + p);
-                    if (A != 0.f) atomicAdd(damp + p, (t.x * gT.x + t.y * gT.y) / A);
-                }
+                map_grad_at(sys, p, __ldg(&T[p]), gT, amp, scale, dphi, damp);
             }
         } else {
             const float oa = (float)(a - D / 2), ob = (float)(b - D / 2);
@@ -309,13 +330,8 @@ __device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
                 const int rr = j0 + dj[q], cc = i0 + di[q];
                 if ((unsigned)rr < (unsigned)H && (unsigned)cc < (unsigned)W) {
                     const long long p = (long long)rr * W + cc;
-                    const float2 t = __ldg(&T[p]);
-                    const float2 g = cscale(gT, wt[q]);
-                    if (dphi) atomicAdd(dphi + p, scale * (t.x * g.y - t.y * g.x));
-                    if (damp) {
-                        const float A = __ldg(amp + p);
-                        if (A != 0.f) atomicAdd(damp + p, (t.x * g.x + t.y * g.y) / A);
-                    }
+                    map_grad_at(sys, p, __ldg(&T[p]), cscale(gT, wt[q]), amp, scale, dphi,
+                                damp);
                 }
             }
         }
@@ -340,7 +356,7 @@ __device__ __forceinline__ void incident_adjoint(const DSys& sys, const DJob* __
     float gdy = kn_in * (s[3] * R.u[1] + s[4] * R.v[1]);
     float gdz = kn_in * (s[3] * R.u[2] + s[4] * R.v[2]);
     // index gradients of the emission: kappa_in = k0 n_in (d.u, d.v), K = k0 n_out
-    gs[sys.doe_index * RW_NGRAD + 7] += J.k0 * s[5];
+    if (sys.nout_slot >= 0) gs[sys.nout_slot * RW_NGRAD + 7] += J.k0 * s[5];
     if (sys.doe_index > 0)
         gs[(sys.doe_index - 1) * RW_NGRAD + 7] += (R.kin_u * s[3] + R.kin_v * s[4]) / sys.n_in;
     const long long ri = J.off + (R.gid - prefix[R.job]);

@@ -160,10 +160,9 @@ __device__ __noinline__ bool af_block_misses_sensor(const DSys& sys, const RayAt
     const float iK = R.invK;
     AF dx, dy, dz;
     if (!sys.conformal) {
-        const float sgn = R.n[2];
         dx = af_scale(ku, iK);
-        dy = af_scale(kv, sgn * iK);
-        dz = af_scale(kn, sgn * iK);
+        dy = af_scale(kv, R.v[1] * iK);
+        dz = af_scale(kn, R.n[2] * iK);
     } else {
         dx = af_scale(af_add(af_add(af_scale(ku, R.u[0]), af_scale(kv, R.v[0])),
                              af_scale(kn, R.n[0])), iK);

@@ -30,7 +30,8 @@ struct DSurf {
     float r_ap2;       // <= 0: no clip
     float gap;         // z_vertex - z of the previous local reference (float)
     double z;          // global vertex z
-    double cd;         // curvature in double (FP64 Newton refinement)
+    double cd;         // curvature (Gaussian bump: height) in double, FP64 hit refinement
+    double kd;         // Gaussian bump: width, in double
 };
 
 // Post-DOE plane/sphere in the form the specialised trace uses.
@@ -48,6 +49,12 @@ struct DSys {
     double n_object;
     // DOE
     int H, W, D, gather, emit, n_ssr, phase_model, conformal;
+    int reflective;    // secondary rays return into the incident medium
+    int two_phase;     // U = A (exp(i phi) + exp(i phi2))
+    const float* phi;  // device phase maps (read by the two-phase adjoint)
+    const float* phi2;
+    int nout_slot;     // surface whose n_after is n_out (-1: object space)
+    int nsen_slot;     // surface whose n_after is the sensor medium (-1: object space)
     int M;             // transform size P D (zero-padded patch)
     int cull;          // 1: exhaustive incoherent forward drops blocks that miss the sensor
     float norm;        // spectrum scale: 1/M^2 (coherent sensor) or 1/(D M)

@@ -15,8 +15,9 @@
 // ------------------------------------------------------------- A3 input
 // T_slot[r][c] = A[r][c] exp(i phi[r][c] scale_slot): one complex map per
 // wavelength, so the per-patch gather is a plain 8-byte load.
-__global__ void k_prep_maps(const float* __restrict__ phi, const float* __restrict__ amp,
-                            int64_t npix, const float* __restrict__ scales, int nslot,
+__global__ void k_prep_maps(const float* __restrict__ phi, const float* __restrict__ phi2,
+                            const float* __restrict__ amp, int64_t npix,
+                            const float* __restrict__ scales, int nslot,
                             float2* __restrict__ T) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < npix * nslot;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -25,6 +26,13 @@ __global__ void k_prep_maps(const float* __restrict__ phi, const float* __restri
         float ph = phi[p] * scales[slot];
         float s, c;
         sincosf(ph, &s, &c);
+        if (phi2) {
+            // two superposed phase profiles: exp(i phi) + exp(i phi2)
+            float s2, c2;
+            sincosf(phi2[p] * scales[slot], &s2, &c2);
+            c += c2;
+            s += s2;
+        }
         float A = amp ? amp[p] : 1.f;
         T[i] = make_float2(A * c, A * s);
     }
@@ -383,14 +391,16 @@ cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const 
 #undef RW_FWD_CASE
 }
 
-cudaError_t launch_prep_maps(const LaunchCtx& L, const float* phi, const float* amp,
-                             int64_t npix, const float* scales_dev, int nslot, float2* T) {
+cudaError_t launch_prep_maps(const LaunchCtx& L, const float* phi, const float* phi2,
+                             const float* amp, int64_t npix, const float* scales_dev, int nslot,
+                             float2* T) {
     long long n = npix * nslot;
     long long grid = (n + 255) / 256;
     long long cap = (long long)L.num_sms * 8;
     if (grid > cap) grid = cap;
     RW_MARK(L, "k_prep_maps");
-    k_prep_maps<<<(unsigned)grid, 256, 0, L.stream>>>(phi, amp, npix, scales_dev, nslot, T);
+    k_prep_maps<<<(unsigned)grid, 256, 0, L.stream>>>(phi, phi2, amp, npix, scales_dev, nslot,
+                                                      T);
     RW_MARK(L, nullptr);
     return cudaGetLastError();
 }

@@ -153,6 +153,27 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     float nx, ny, nz;
     if (!sys.conformal) {
         t = -zld / (double)dz;
+    } else if (S.kind == RW_GAUSS) {
+        // Gaussian bump sag(s) = h exp(-s / (2 w^2)): Newton in double on
+        // g(t) = zld + t dz - sag(|q(t)|^2), started on the plane through the
+        // sag at the ray's (x, y)
+        const double h = S.cd, iw2 = 0.5 / (S.kd * S.kd);
+        const double X0 = x, Y0 = y, DX = dx, DY = dy, DZ = dz;
+        t = (h * exp(-(X0 * X0 + Y0 * Y0) * iw2) - zld) / DZ;
+        bool conv = false;
+        for (int it = 0; it < 40; ++it) {
+            const double qx = X0 + t * DX, qy = Y0 + t * DY;
+            const double e = h * exp(-(qx * qx + qy * qy) * iw2);
+            const double gp = DZ + 2.0 * iw2 * e * (qx * DX + qy * DY);
+            if (gp == 0.0) break;
+            const double step = (zld + t * DZ - e) / gp;
+            t -= step;
+            if (fabs(step) <= 1e-13 * (1.0 + fabs(t))) { conv = true; break; }
+        }
+        if (!conv) {
+            if (status) atomicOr(status, RW_ST_NOTCONV);
+            return;
+        }
     } else {
         float tf;
         if (!intersect_local(S, x, y, (float)zld, dx, dy, dz, tf, status)) return;
@@ -171,6 +192,13 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     const double pzl = sys.conformal ? zld + t * (double)dz : 0.0;   // planar: on the plane
     if (!sys.conformal) {
         nx = 0.f; ny = 0.f; nz = 1.f;
+    } else if (S.kind == RW_GAUSS) {
+        // normal grad(z - sag) with -dsag/dx = x h e^{-s/(2 w^2)} / w^2 (same for y)
+        const double iw2 = 0.5 / (S.kd * S.kd);
+        const double e = S.cd * exp(-(pxd * pxd + pyd * pyd) * iw2);
+        const double mx = 2.0 * iw2 * e * pxd, my = 2.0 * iw2 * e * pyd;
+        const double inv = 1.0 / sqrt(mx * mx + my * my + 1.0);
+        nx = (float)(mx * inv); ny = (float)(my * inv); nz = (float)inv;
     } else {
         const double c = S.cd;
         const double s2 = pxd * pxd + pyd * pyd;
@@ -186,6 +214,8 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     float vx = ny * uz - nz * uy, vy = nz * ux - nx * uz, vz = nx * uy - ny * ux;
     R.u[0] = ux; R.u[1] = uy; R.u[2] = uz;
     R.v[0] = vx; R.v[1] = vy; R.v[2] = vz;
+    // R.n is the normal the secondary rays leave along: reversed by a mirror
+    if (sys.reflective) { nx = -nx; ny = -ny; nz = -nz; }
     R.n[0] = nx; R.n[1] = ny; R.n[2] = nz;
     const float k0 = J.k0;
     R.kin_u = k0 * sys.n_in * (dx * ux + dy * uy + dz * uz);
@@ -439,11 +469,10 @@ __device__ __forceinline__ bool bin_direction(const DSys& sys, const RayAtDoe& R
     else kn = sqrtf(K2 - kt2);
     const float invK = R.invK;
     if (FAST && !sys.conformal) {
-        // planar DOE: u = x, n = (0, 0, s), v = n x u = (0, s, 0) with s = +-1
-        const float sgn = R.n[2];
+        // planar DOE: u = x, v = (0, s, 0), outgoing normal (0, 0, +-s), s = +-1
         dx = ku * invK;
-        dy = (kv * sgn) * invK;
-        dz = (kn * sgn) * invK;
+        dy = (kv * R.v[1]) * invK;
+        dz = (kn * R.n[2]) * invK;
         return true;
     }
     dx = (ku * R.u[0] + kv * R.v[0] + kn * R.n[0]) * invK;
@@ -782,8 +811,9 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
 }
 
 // ------------------------------------------------------------------ launchers
-cudaError_t launch_prep_maps(const LaunchCtx& L, const float* phi, const float* amp, int64_t npix,
-                             const float* scales_dev, int nslot, float2* T);
+cudaError_t launch_prep_maps(const LaunchCtx& L, const float* phi, const float* phi2,
+                             const float* amp, int64_t npix, const float* scales_dev, int nslot,
+                             float2* T);
 cudaError_t launch_generate_rays(const LaunchCtx& L, const GenJob* jobs, const long long* prefix,
                                  int njob, long long total, double z_start, double n_object,
                                  const RaysOut& out);

@@ -139,8 +139,9 @@ def surfaces_struct(surfaces):
 
 
 def system_struct(system, phi, amp=None, dft="fft32", surfaces=None, trace_all=False):
-    """rw_system for `system` with device maps phi (and amp).  Returns
-    (struct, keepalive)."""
+    """rw_system for `system` with device maps phi (and amp).  A DOE with two
+    phase profiles takes phi as one contiguous [2, H, W] tensor (phi, phi2).
+    Returns (struct, keepalive)."""
     doe = system.doe
     surfs = surfaces_struct(surfaces if surfaces is not None else system.surfaces)
     s = A.rw_system()
@@ -148,11 +149,17 @@ def system_struct(system, phi, amp=None, dft="fft32", surfaces=None, trace_all=F
     s.nsurf = len(surfs)
     s.doe_index = int(system.doe_index)
     s.n_object = float(system.n_object)
-    H, W = phi.shape
+    H, W = phi.shape[-2:]
     s.doe.H, s.doe.W = int(H), int(W)
     s.doe.pitch = float(doe.pitch)
     s.doe.lambda0 = float(doe.lambda0)
-    s.doe.phi = _ptr(phi)
+    if phi.dim() == 3:
+        if phi.shape[0] != 2 or not phi.is_contiguous():
+            raise ValueError("two phase profiles: phi must be a contiguous [2, H, W] tensor")
+        s.doe.phi = _ptr(phi[0])
+        s.doe.phi2 = _ptr(phi[1])
+    else:
+        s.doe.phi = _ptr(phi)
     s.doe.amp = _ptr(amp)
     s.doe.D = int(doe.D)
     s.doe.gather = _GATHER[doe.gather]
@@ -163,7 +170,8 @@ def system_struct(system, phi, amp=None, dft="fft32", surfaces=None, trace_all=F
     s.doe.seed = int(doe.seed)
     s.doe.rng_offset = int(doe.rng_offset)
     s.doe.pad = int(getattr(doe, "pad", 1))
-    s.doe.flags = A.RW_DOE_TRACE_ALL if trace_all else 0
+    s.doe.flags = ((A.RW_DOE_TRACE_ALL if trace_all else 0)
+                   | (A.RW_DOE_REFLECTIVE if getattr(doe, "reflective", False) else 0))
     sen = system.sensor
     s.sensor.z = float(sen.z)
     s.sensor.nx, s.sensor.ny = int(sen.nx), int(sen.ny)
@@ -312,6 +320,9 @@ class Simulator:
         self.dev = self.ctx.device
         sysm = workload.system
         self.phi = device_map(sysm.doe.phi, self.dev)
+        if getattr(sysm.doe, "phi2", None) is not None:
+            # two phase profiles: one [2, H, W] map (dL/dphi comes back the same shape)
+            self.phi = torch.stack([self.phi, device_map(sysm.doe.phi2, self.dev)]).contiguous()
         self.amp = None if sysm.doe.amp is None else device_map(sysm.doe.amp, self.dev)
         self.dft = dft
         self.jobs = jobs_struct(workload.jobs)

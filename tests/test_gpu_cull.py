@@ -49,8 +49,14 @@ def _c4():
     return w
 
 
+def _reflective():
+    import reflective_cases as RC
+    return RC.planar(n_side=13)
+
+
 CASES = {
     "c2_d64": lambda: _c2(23, 64),
+    "reflective_planar": _reflective,
     "c2_d32_pad2": lambda: _c2(19, 32, 2),
     "c2_d16": lambda: _c2(41, 16),
     "c5_six_spheres": _c5,
