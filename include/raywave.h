@@ -68,8 +68,12 @@ typedef enum {
 enum { RW_PLANE = 0, RW_SPHERE = 1, RW_ASPHERE = 2, RW_GAUSS = 3 };
 /* DOE patch gather: nearest pixel window (planar) / bilinear (conformal) */
 enum { RW_GATHER_NEAREST = 0, RW_GATHER_BILINEAR = 1 };
-/* secondary-ray emission */
-enum { RW_EMIT_EXHAUSTIVE = 0, RW_EMIT_SAMPLED = 1 };
+/* secondary-ray emission: every propagating bin; n_ssr Gumbel-max draws from
+ * p ~ |U~| (coherent sensor) or |U~|^2 (incoherent); or n_ssr draws from the
+ * uniform density over the propagating bins (the paper's p_uni, for
+ * comparison).  Sampled weights: a = a_in U~ / (N p) (coherent) or
+ * a_in U~ / sqrt(N p) (incoherent). */
+enum { RW_EMIT_EXHAUSTIVE = 0, RW_EMIT_SAMPLED = 1, RW_EMIT_SAMPLED_UNIFORM = 2 };
 /* phase at wavelength lambda: phi * lambda0 / lambda (HEIGHT) or phi (FIXED) */
 enum { RW_PHASE_HEIGHT = 0, RW_PHASE_FIXED = 1 };
 /* patch transform implementation */

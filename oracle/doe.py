@@ -37,7 +37,9 @@ Readings (the paper does not fix these):
 * sampled mode draws N bins from p over the propagating bins by Gumbel-max
   (Philox4x32-10 noise); coherent sensor: p ~ |U~|, a = a_in U~ / (N p);
   incoherent sensor: p ~ |U~|^2 and |a|^2 = |a_in|^2 |U~|^2 / (N p) with the
-  phase of U~ (the unbiased power weight);
+  phase of U~ (the unbiased power weight); 'sampled_uniform' draws from the
+  uniform density over the propagating bins instead (the paper's p_uni,
+  convergence section), with the same weights;
 * phase at wavelength lambda: 'height' model phi * lambda0 / lambda, or 'fixed';
 * reflective DOE (section "Benchmark and Inverse Design Demonstrations",
   reflective conformal DOE): the same frame and spectrum, the outgoing
@@ -204,7 +206,11 @@ def doe_step(ray, doe_surface, doe, phi, amp, lam, n_in, n_out, ray_ids=None,
     nb = M * M
     Uf = U.reshape(N, nb)
     propf = prop.reshape(N, nb)
-    mag = Uf.abs() ** (2 if not coherent else 1)
+    if doe.emit == "sampled_uniform":
+        # the uniform density over the propagating bins (p_uni)
+        mag = torch.ones_like(Uf.real)
+    else:
+        mag = Uf.abs() ** (2 if not coherent else 1)
     mag = torch.where(propf, mag, torch.zeros_like(mag))
     tot = mag.sum(-1, keepdim=True)
     pj = mag / torch.where(tot > 0, tot, torch.ones_like(tot))

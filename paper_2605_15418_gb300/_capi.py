@@ -14,7 +14,7 @@ STATUS_NAMES = {0: "RW_OK", 1: "RW_EINVAL", 2: "RW_ENOMEM", 3: "RW_ECUDA", 4: "R
                 5: "RW_ETIMEOUT", 6: "RW_ENOTCONV"}
 RW_PLANE, RW_SPHERE, RW_ASPHERE, RW_GAUSS = 0, 1, 2, 3
 RW_GATHER_NEAREST, RW_GATHER_BILINEAR = 0, 1
-RW_EMIT_EXHAUSTIVE, RW_EMIT_SAMPLED = 0, 1
+RW_EMIT_EXHAUSTIVE, RW_EMIT_SAMPLED, RW_EMIT_SAMPLED_UNIFORM = 0, 1, 2
 RW_PHASE_HEIGHT, RW_PHASE_FIXED = 0, 1
 RW_DFT_FFT32, RW_DFT_TC = 0, 1
 RW_DOE_TRACE_ALL, RW_DOE_REFLECTIVE = 1, 2

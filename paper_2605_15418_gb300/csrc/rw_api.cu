@@ -268,9 +268,10 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
         return fail(ctx, RW_EINVAL, "doe.pad * doe.D must be 16, 32, 64, 96 or 128");
     if (doe.gather != RW_GATHER_NEAREST && doe.gather != RW_GATHER_BILINEAR)
         return fail(ctx, RW_EINVAL, "doe.gather invalid");
-    if (doe.emit != RW_EMIT_EXHAUSTIVE && doe.emit != RW_EMIT_SAMPLED)
+    if (doe.emit != RW_EMIT_EXHAUSTIVE && doe.emit != RW_EMIT_SAMPLED &&
+        doe.emit != RW_EMIT_SAMPLED_UNIFORM)
         return fail(ctx, RW_EINVAL, "doe.emit invalid");
-    if (doe.emit == RW_EMIT_SAMPLED && (doe.n_ssr < 1 || doe.n_ssr > 16384))
+    if (doe.emit != RW_EMIT_EXHAUSTIVE && (doe.n_ssr < 1 || doe.n_ssr > 16384))
         return fail(ctx, RW_EINVAL, "doe.n_ssr must be in 1..16384 for sampled emission");
     if (doe.phase_model != RW_PHASE_HEIGHT && doe.phase_model != RW_PHASE_FIXED)
         return fail(ctx, RW_EINVAL, "doe.phase_model invalid");
@@ -369,7 +370,11 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
     // coherent: Fourier-series coefficient of the padded patch; incoherent:
     // keeps sum |U~|^2 = mean |T|^2 (both 1/D^2 without padding)
     d.norm = sen.coherent ? (float)(1.0 / ((double)d.M * d.M)) : (float)(1.0 / ((double)d.D * d.M));
-    d.gather = doe.gather; d.emit = doe.emit; d.n_ssr = doe.n_ssr;
+    d.gather = doe.gather;
+    // kernels see two modes; uniform sampling is the sampled mode with p = 1/n_prop
+    d.emit = doe.emit == RW_EMIT_EXHAUSTIVE ? RW_EMIT_EXHAUSTIVE : RW_EMIT_SAMPLED;
+    d.uniform = doe.emit == RW_EMIT_SAMPLED_UNIFORM ? 1 : 0;
+    d.n_ssr = doe.n_ssr;
     d.phase_model = doe.phase_model;
     d.pitch = doe.pitch;
     d.pitchf = (float)doe.pitch;

@@ -97,6 +97,7 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
             const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
             m = U.x * U.x + U.y * U.y;
             if (COH) m = sqrtf(m);
+            if (sys.uniform) m = 1.f;
         }
         logp[f] = m;
         gwb[f] = make_float2(0.f, 0.f);
@@ -261,8 +262,8 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
             const float gp = EXPO * (gwv.x * w.x + gwv.y * w.y) / p;
             // logp = log m - log S ; p = m / S
             const float gm = glogp[f] / m - Sg * iS + gp * iS - Sgp * iS;
-            // dm/dU~: 2 U~ (m = |U~|^2) or U~ / m (m = |U~|)
-            const float dm = COH ? 1.f / m : 2.f;
+            // dm/dU~: 2 U~ (m = |U~|^2), U~ / m (m = |U~|), 0 (uniform: m = 1)
+            const float dm = sys.uniform ? 0.f : (COH ? 1.f / m : 2.f);
             gU = make_float2(U.x * dm * gm + gwv.x * isq, U.y * dm * gm + gwv.y * isq);
             if (COH && !sys.conformal) {
                 const float im = gU.x * U.y - gU.y * U.x;          // Im(conj(gU) U)

@@ -51,6 +51,7 @@ struct DSys {
     int H, W, D, gather, emit, n_ssr, phase_model, conformal;
     int reflective;    // secondary rays return into the incident medium
     int two_phase;     // U = A (exp(i phi) + exp(i phi2))
+    int uniform;       // sampled emission from the uniform density over propagating bins
     const float* phi;  // device phase maps (read by the two-phase adjoint)
     const float* phi2;
     int nout_slot;     // surface whose n_after is n_out (-1: object space)

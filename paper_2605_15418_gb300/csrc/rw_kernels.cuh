@@ -732,7 +732,7 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
         if (bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
             const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
             const float p2 = U.x * U.x + U.y * U.y;
-            m = coh ? sqrtf(p2) : p2;
+            m = sys.uniform ? 1.f : (coh ? sqrtf(p2) : p2);
         }
         logp[f] = m;
         part += m;

@@ -13,7 +13,8 @@ import torch
 from . import _capi as A
 
 _GATHER = {"nearest": A.RW_GATHER_NEAREST, "bilinear": A.RW_GATHER_BILINEAR}
-_EMIT = {"exhaustive": A.RW_EMIT_EXHAUSTIVE, "sampled": A.RW_EMIT_SAMPLED}
+_EMIT = {"exhaustive": A.RW_EMIT_EXHAUSTIVE, "sampled": A.RW_EMIT_SAMPLED,
+         "sampled_uniform": A.RW_EMIT_SAMPLED_UNIFORM}
 _PHASE = {"height": A.RW_PHASE_HEIGHT, "fixed": A.RW_PHASE_FIXED}
 _DFT = {"fft32": A.RW_DFT_FFT32, "tc": A.RW_DFT_TC}
 RAY_FIELDS = ("ox", "oy", "oz", "dx", "dy", "dz", "a_re", "a_im")

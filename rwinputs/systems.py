@@ -46,8 +46,10 @@ class DOE:
     i.e. the map is centred on the optical axis and rows run along y.
     phase_model 'height': phi_lambda = phi * lambda0 / lambda; 'fixed': phi.
     gather 'nearest' (planar default) or 'bilinear' (conformal default).
-    emit 'exhaustive' (one secondary ray per propagating bin) or 'sampled'
-    (n_ssr Gumbel-max draws from p ~ |U~|).
+    emit 'exhaustive' (one secondary ray per propagating bin), 'sampled'
+    (n_ssr Gumbel-max draws from p ~ |U~|, |U~|^2 for an incoherent sensor) or
+    'sampled_uniform' (n_ssr draws from the uniform density over the
+    propagating bins).
     pad P >= 1: the D x D patch is zero-padded to M = P D samples before its
     transform, so the spectrum is sampled on the finer k-grid 2 pi j / (M p).
     reflective: the DOE reflects; secondary rays leave on the incident side

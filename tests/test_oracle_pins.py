@@ -458,6 +458,34 @@ def test_sampled_emission_is_unbiased_for_power():
     assert 8.0 < ratio < 32.0
 
 
+@pytest.mark.parametrize("density", ["sampled", "sampled_uniform"])
+def test_sampled_draw_frequencies_and_weights(density):
+    """One ray, 16 384 Gumbel-max draws over a patch spectrum: the bins come
+    up with the probabilities p_mag ~ |U~| (coherent sensor) or p_uni = 1/n
+    over the propagating bins (within 5 binomial standard deviations), and
+    every draw carries a = U~ / (N p)."""
+    D, p, lam = 8, 1e-3, 0.55e-3
+    rng = np.random.Generator(np.random.PCG64(17))
+    phi = rng.uniform(0, 2 * math.pi, (32, 32)).astype(np.float32)
+    doe = R.DOE(phi=phi, pitch=p, D=D, lambda0=lam, emit=density, n_ssr=16384,
+                seed=(5 << 32) | 3)
+    sysm = R.System([R.Surface(R.PLANE, 0.0)], 0, doe,
+                    R.Sensor(0.1, 8, 8, 1e-3, coherent=True))
+    job = R.Job(lam=lam, grid_n=1, x0=0.3 * p, y0=-0.2 * p)
+    em, _ = P.emit_job(sysm, job, -0.1, P.params_of(sysm), *P.map_tensors(sysm))
+    U = em["U"][0].reshape(-1)
+    idx = em["idx"][0].numpy()
+    N = doe.n_ssr
+    prop = np.ones(D * D, bool)             # every bin propagates at this pitch
+    probs = np.abs(U.numpy()) if density == "sampled" else prop.astype(np.float64)
+    probs = probs / probs.sum()
+    counts = np.bincount(idx, minlength=D * D)
+    sd = np.sqrt(N * probs * (1 - probs))
+    assert np.all(np.abs(counts - N * probs) <= 5 * sd + 1e-9)
+    a = em["a"][0].numpy()
+    assert np.allclose(a, U.numpy()[idx] / (N * probs[idx]), rtol=1e-12, atol=0)
+
+
 # ------------------------------------------------------------------ sensor splat
 def test_bilinear_splat_hand_computed_taps():
     nx, ny, pitch, cx, cy = 8, 6, 2e-3, 0.1, -0.05
