@@ -134,7 +134,11 @@ def test_gaussian_bump_emission_directions_match_oracle(RW, ctx):
     steep = np.abs(dref[alive][:, 2]) >= 0.3
     assert ang[steep].max() <= 1e-6, ang[steep].max()
     assert ang.max() <= 1e-5, ang.max()
-    assert (d[alive][:, 2] < 0).all()
+    # every secondary ray leaves on the incident side of the local surface
+    # (grazing ones may still have d_z > 0 where the bump is tilted)
+    n_out = em["frame"][2].numpy()                      # outgoing normal per ray
+    cosn = (d * n_out[:, None, None, :]).sum(-1)
+    assert (cosn[alive] > 0).all()
     ar = em["a"].numpy()
     assert np.abs(a - np.where(alive, ar, 0)).max() <= 1e-5 * np.abs(ar).max()
 
