@@ -49,8 +49,8 @@ def _doe(D, pad, amp, emit, n_ssr, seed=81, kind=R.PLANAR, gather="nearest"):
     phi, a = _maps(64, 64, seed, amp)
     doe = R.DOE(phi=phi, amp=a, pitch=1 * UM, D=D, lambda0=550e-6, pad=pad, kind=kind,
                 gather=gather)
-    if emit == "sampled":
-        doe.emit = "sampled"
+    if emit != "exhaustive":
+        doe.emit = emit
         doe.n_ssr = n_ssr
         doe.seed = (97 << 32) | 5
     return doe

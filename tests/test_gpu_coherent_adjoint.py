@@ -124,6 +124,13 @@ def test_coherent_adjoint_sampled(RW, ctx):
              surf_rel=1e-2)
 
 
+def test_coherent_adjoint_sampled_uniform_density(RW, ctx):
+    """p = 1 / (number of propagating bins): the draw does not depend on U~,
+    so only the hard path's weight U~ / (N p) carries gradient."""
+    _compare(RW, ctx, CC.free_space(n_side=9, emit="sampled_uniform", n_ssr=96),
+             map_tol=2e-3, surf_rel=1e-2)
+
+
 def test_coherent_adjoint_conformal_map_gradients(RW, ctx):
     _compare(RW, ctx, CC.conformal(n_side=9), surfaces=False)
 

@@ -280,13 +280,17 @@ def test_backward_matches_oracle_gradient(RW, ctx):
 
 
 # ------------------------------------------------------------------ A5 sampled (Gumbel-max)
-@pytest.mark.parametrize("coherent", [False, True])
-def test_sampled_emission_matches_oracle(RW, ctx, coherent):
+@pytest.mark.parametrize("coherent,density", [(False, "sampled"), (True, "sampled"),
+                                              (False, "sampled_uniform"),
+                                              (True, "sampled_uniform")])
+def test_sampled_emission_matches_oracle(RW, ctx, coherent, density):
     """Same Philox stream on both sides: the chosen bins agree except for
     near-ties decided in different precision (FP32 scores here, FP64 in the
-    oracle); on every agreeing draw the direction and weight match."""
+    oracle); on every agreeing draw the direction and weight match.  Both
+    densities: p ~ |U~| (|U~|^2 incoherent) and uniform over the propagating
+    bins."""
     w = _c2_small(n_side=10, D=16, map_side=128, lams=(550e-6, 656e-6), fields=(0.0, 1.0))
-    w.system.doe.emit = "sampled"
+    w.system.doe.emit = density
     w.system.doe.n_ssr = 64
     w.system.doe.seed = (12345 << 32) | 777
     w.system.doe.rng_offset = 5
