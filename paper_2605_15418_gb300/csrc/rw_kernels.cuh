@@ -455,6 +455,86 @@ __device__ __forceinline__ void splat_coherent(const DSys& sys, float k0, float 
     }
 }
 
+// Eq. 2 over the whole sensor (window 0) for the 32 secondary rays of a warp
+// at once.  Every lane evaluates its wavelet (amplitude zero if `ok` is
+// false) on the same group of 8 pixels; a transpose-reduction across the warp
+// (9 shuffles per component) leaves the group's 8 sums in 8 lanes, which add
+// them to the field: 8 atomics per group instead of 32 per pixel on one
+// address.  Must be called by all 32 lanes of the warp together.
+__device__ __forceinline__ void splat_coherent_warp(const DSys& sys, float k0, float cx, float cy,
+                                                    bool ok, float x, float y, double opl,
+                                                    float dx, float dy, float dz, float2 a,
+                                                    float2* __restrict__ fld) {
+    const int lane = threadIdx.x & 31;
+    int i_lo, i_hi, j_lo, j_hi;
+    float phb = 0.f;
+    if (ok) ok = coherent_range(sys, k0, cx, cy, x, y, opl, i_lo, i_hi, j_lo, j_hi, phb);
+    const float kx = ok ? k0 * sys.n_sensor * dx : 0.f;
+    const float ky = ok ? k0 * sys.n_sensor * dy : 0.f;
+    const float2 ad = ok ? make_float2(a.x * dz, a.y * dz) : make_float2(0.f, 0.f);
+    if (!ok) { x = 0.f; y = 0.f; }
+    const int nx = sys.nx, npx = sys.nx * sys.ny;
+    // the pixel this lane adds after the reduction
+    const int q_out = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    for (int p0 = 0; p0 < npx; p0 += 8) {
+        float re[8], im[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int p = p0 + q;
+            re[q] = 0.f;
+            im[q] = 0.f;
+            if (p < npx) {
+                const int j = p / nx, i = p - j * nx;
+                const float X = cx + ((float)i - 0.5f * sys.nx + 0.5f) * sys.spitch;
+                const float Y = cy + ((float)j - 0.5f * sys.ny + 0.5f) * sys.spitch;
+                const float ph = phb + kx * (X - x) + ky * (Y - y);
+                float sn, cs;
+                sincosf(ph, &sn, &cs);
+                re[q] = ad.x * cs - ad.y * sn;
+                im[q] = ad.x * sn + ad.y * cs;
+            }
+        }
+        // 8 -> 4 (lanes xor 16), 4 -> 2 (xor 8), 2 -> 1 (xor 4): each lane keeps
+        // the half of its pixels selected by its lane bit and receives the
+        // partner's share of them
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool hi = lane & 16;
+            const float sr = hi ? re[k] : re[k + 4], si = hi ? im[k] : im[k + 4];
+            const float rr = __shfl_xor_sync(0xffffffffu, sr, 16);
+            const float ri = __shfl_xor_sync(0xffffffffu, si, 16);
+            re[k] = (hi ? re[k + 4] : re[k]) + rr;
+            im[k] = (hi ? im[k + 4] : im[k]) + ri;
+        }
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const bool hi = lane & 8;
+            const float sr = hi ? re[k] : re[k + 2], si = hi ? im[k] : im[k + 2];
+            const float rr = __shfl_xor_sync(0xffffffffu, sr, 8);
+            const float ri = __shfl_xor_sync(0xffffffffu, si, 8);
+            re[k] = (hi ? re[k + 2] : re[k]) + rr;
+            im[k] = (hi ? im[k + 2] : im[k]) + ri;
+        }
+        {
+            const bool hi = lane & 4;
+            const float sr = hi ? re[0] : re[1], si = hi ? im[0] : im[1];
+            const float rr = __shfl_xor_sync(0xffffffffu, sr, 4);
+            const float ri = __shfl_xor_sync(0xffffffffu, si, 4);
+            re[0] = (hi ? re[1] : re[0]) + rr;
+            im[0] = (hi ? im[1] : im[0]) + ri;
+        }
+        re[0] += __shfl_xor_sync(0xffffffffu, re[0], 2);
+        im[0] += __shfl_xor_sync(0xffffffffu, im[0], 2);
+        re[0] += __shfl_xor_sync(0xffffffffu, re[0], 1);
+        im[0] += __shfl_xor_sync(0xffffffffu, im[0], 1);
+        const int p = p0 + q_out;
+        if ((lane & 3) == 0 && p < npx && (re[0] != 0.f || im[0] != 0.f)) {
+            atomicAdd(&fld[p].x, re[0]);
+            atomicAdd(&fld[p].y, im[0]);
+        }
+    }
+}
+
 // Direction of spectral bin (ju, jv) for the incident state R; false if evanescent.
 template <bool FAST = false>
 __device__ __forceinline__ bool bin_direction(const DSys& sys, const RayAtDoe& R, int ju, int jv,
@@ -683,6 +763,21 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
             if (eo.bin) eo.bin[s] = f;
             continue;
         }
+        if (MODE == MODE_COHERENT && sys.window == 0) {
+            // whole-sensor sum: each lane traces its ray, the warp sums its 32 wavelets
+            float x = R.px, y = R.py, zl = R.pz;
+            double opl = R.opl;
+            float2 a = make_float2(0.f, 0.f);
+            bool ok = false;
+            if (prop) {
+                a = cmul(ain, spectrum_at<M>(X, phu, phv, jui, jvi, norm));
+                ok = trace_to_sensor<true>(sys, x, y, zl, dx, dy, dz, opl, status);
+            }
+            __syncwarp();
+            splat_coherent_warp(sys, J.k0, R.cx, R.cy, ok, x, y, opl, dx, dy, dz, a,
+                                field + (long long)R.job * sys.nx * sys.ny);
+            continue;
+        }
         bool landed = false;
         if (prop) {
             float2 a = make_float2(0.f, 0.f);
@@ -785,6 +880,30 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
         eo.opl[g] = R.opl;
     }
     const float N = (float)sys.n_ssr;
+    if (MODE == MODE_COHERENT && sys.window == 0) {
+        // whole-sensor sum, a warp's 32 draws at a time (warps past n_ssr skip)
+        for (int i0 = 0; i0 < sys.n_ssr; i0 += RW_THREADS) {
+            if (i0 + (int)(threadIdx.x & ~31u) >= sys.n_ssr) continue;
+            const int i = i0 + threadIdx.x;
+            const int jb = i < sys.n_ssr ? sel[i] : -1;
+            float dx = 0.f, dy = 0.f, dz = 0.f;
+            float x = R.px, y = R.py, zl = R.pz;
+            double opl = R.opl;
+            float2 a = make_float2(0.f, 0.f);
+            bool ok = false;
+            if (jb >= 0) {
+                const int jvi = jb / M, jui = jb - (jb / M) * M;
+                ok = bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz);
+                const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
+                a = cscale(cmul(ain, U), 1.f / (N * expf(logp[jb])));
+                if (ok) ok = trace_to_sensor<true>(sys, x, y, zl, dx, dy, dz, opl, status);
+            }
+            __syncwarp();
+            splat_coherent_warp(sys, J.k0, R.cx, R.cy, ok, x, y, opl, dx, dy, dz, a,
+                                field + (long long)R.job * sys.nx * sys.ny);
+        }
+        return;
+    }
     for (int i = threadIdx.x; i < sys.n_ssr; i += RW_THREADS) {
         const int jb = sel[i];
         float dx = 0.f, dy = 0.f, dz = 0.f;
