@@ -38,9 +38,35 @@ def surface_params(s, requires_grad=False):
     """float64 scalar tensors for one rwinputs.Surface (leaves if requires_grad)."""
     def t(v):
         return torch.tensor(float(v), dtype=torch.float64, requires_grad=requires_grad)
+    sm = getattr(s, "sellmeier", None)
     return {"kind": int(s.kind), "z": t(s.z), "c": t(s.c), "k": t(s.k),
             "A4": t(s.A[0]), "A6": t(s.A[1]), "A8": t(s.A[2]), "A10": t(s.A[3]),
-            "n_after": t(s.n_after), "r_ap": float(s.r_ap)}
+            "n_after": t(s.n_after), "r_ap": float(s.r_ap),
+            "sellmeier": None if sm is None else tuple(float(v) for v in sm)}
+
+
+def sellmeier_index(coeffs, lam_mm):
+    """Sellmeier dispersion formula: n^2 = 1 + sum_i B_i L^2 / (L^2 - C_i), with
+    L the vacuum wavelength in micrometres and (B1, B2, B3, C1, C2, C3)."""
+    L2 = (lam_mm * 1e3) ** 2
+    B, C = coeffs[:3], coeffs[3:]
+    return (1.0 + sum(b * L2 / (L2 - c) for b, c in zip(B, C))) ** 0.5
+
+
+def at_wavelength(params, lam_mm):
+    """Surface parameters at one wavelength: a dispersive medium gets its
+    Sellmeier index.  Its n_after leaf still carries the gradient, as the
+    derivative with respect to an index shift common to every wavelength."""
+    out = []
+    for p in params:
+        if p.get("sellmeier") is None:
+            out.append(p)
+            continue
+        q = dict(p)
+        leaf = p["n_after"]
+        q["n_after"] = leaf - leaf.detach() + sellmeier_index(p["sellmeier"], lam_mm)
+        out.append(q)
+    return out
 
 
 def sag(s, p):

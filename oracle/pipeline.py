@@ -121,7 +121,8 @@ def psf(workload, params=None, phi=None, amp=None, subsets=None, chunk=256, phi2
     base = 0
     for j, job in enumerate(workload.jobs):
         idx = None if subsets is None else subsets[j]
-        out.append(psf_job(system, job, workload.z_start, params, phi, amp, idx, base, chunk,
+        pj = G.at_wavelength(params, job.lam)          # Sellmeier media at this job's lambda
+        out.append(psf_job(system, job, workload.z_start, pj, phi, amp, idx, base, chunk,
                            phi2))
         base += job.n_rays
     return torch.stack(out, 0)

@@ -19,6 +19,18 @@ from .systems import (Surface, DOE, Sensor, System, Job, Workload,
 from . import maps
 
 N_BK7 = 1.5168
+# Sellmeier coefficients of N-BK7 (B1, B2, B3, C1, C2, C3; C in um^2), from
+# the glass maker's published data sheet
+N_BK7_SELLMEIER = (1.03961212, 0.231792344, 1.01046945, 0.00600069867, 0.0200179144,
+                   103.560653)
+
+
+def dispersive(surfaces):
+    """Copies of `surfaces` whose N-BK7 media (n_after = 1.5168) follow the
+    N-BK7 Sellmeier formula."""
+    import dataclasses
+    return [dataclasses.replace(s, sellmeier=N_BK7_SELLMEIER) if s.n_after == N_BK7 else
+            dataclasses.replace(s) for s in surfaces]
 UM = 1e-3  # one micrometre in mm
 
 

@@ -25,7 +25,10 @@ class Surface:
     conformal DOE: a Gaussian bump z - z = c exp(-r^2 / (2 k^2)) of height c
     and width k.  n_after is the refractive index of the
     medium behind the surface.  r_ap > 0 clips rays whose hit radius exceeds
-    it; r_ap <= 0 means no clip.
+    it; r_ap <= 0 means no clip.  sellmeier = (B1, B2, B3, C1, C2, C3), C in
+    um^2, makes that medium dispersive: at vacuum wavelength lambda its index
+    is sqrt(1 + sum_i B_i lambda^2 / (lambda^2 - C_i)) (lambda in um) and
+    n_after is not used.
     """
     kind: int
     z: float
@@ -34,6 +37,7 @@ class Surface:
     A: Tuple[float, float, float, float] = (0.0, 0.0, 0.0, 0.0)
     n_after: float = 1.0
     r_ap: float = 0.0
+    sellmeier: Optional[Tuple[float, float, float, float, float, float]] = None
 
 
 @dataclass

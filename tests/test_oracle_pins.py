@@ -152,6 +152,37 @@ def test_thick_singlet_paraxial_focus():
     assert zf == pytest.approx(3.0 + bfl, abs=1e-7)
 
 
+def test_sellmeier_n_bk7_catalogue_indices():
+    """The Sellmeier formula with N-BK7's published coefficients gives the
+    catalogue indices n_F = 1.52238, n_d = 1.51680, n_C = 1.51432 (to 1e-5) and
+    the Abbe number 64.17."""
+    c = R.configs.N_BK7_SELLMEIER
+    nF = G.sellmeier_index(c, 486.1327e-6)
+    nd = G.sellmeier_index(c, 587.5618e-6)
+    nC = G.sellmeier_index(c, 656.2725e-6)
+    assert (nF, nd, nC) == pytest.approx((1.52238, 1.51680, 1.51432), abs=1e-5)
+    assert (nd - 1) / (nF - nC) == pytest.approx(64.17, abs=0.02)
+
+
+def test_dispersive_singlet_chromatic_focal_shift():
+    """A dispersive BK7 singlet focuses each wavelength at the lensmaker's
+    back focal length for that wavelength's index (longitudinal chromatic
+    aberration: blue focuses closer), through the per-job parameters."""
+    s = R.configs.dispersive(R.configs._singlet(0.0))
+    prm = [G.surface_params(x) for x in s]
+    zf = {}
+    for lam in (486.1327e-6, 587.5618e-6, 656.2725e-6):
+        n = G.sellmeier_index(R.configs.N_BK7_SELLMEIER, lam)
+        bfl, _ = thick_lens_bfl(n, 20.0, -20.0, 3.0)
+        h = 1e-5
+        ray, _ = G.trace(_ray([h, 0, -1.0], [0, 0, 1]), G.at_wavelength(prm, lam),
+                         torch.tensor(1.0, dtype=F64))
+        t = -ray["o"][0, 0] / ray["d"][0, 0]
+        zf[lam] = float(ray["o"][0, 2] + t * ray["d"][0, 2])
+        assert zf[lam] == pytest.approx(3.0 + bfl, abs=1e-7)
+    assert zf[486.1327e-6] < zf[587.5618e-6] < zf[656.2725e-6]
+
+
 def test_cartesian_ellipsoid_focuses_all_axial_rays():
     """k = -1/n^2 ellipsoid: every axial ray refracts to z = n R / (n - 1)."""
     n, Rv = 1.5, 10.0
