@@ -109,6 +109,14 @@ typedef struct {
     double A4, A6, A8, A10;
     double n_after;
     double r_ap;
+    double sellmeier[6];   /* B1, B2, B3, C1, C2, C3 (C in um^2); all zero: the medium
+                            * behind has the constant index n_after.  Otherwise its
+                            * index at a job's vacuum wavelength L (um) is
+                            * sqrt(1 + sum_i B_i L^2 / (L^2 - C_i)) and n_after is
+                            * unused: rw_forward and rw_backward run one launch per
+                            * distinct wavelength (not rw_doe_emit, rw_patch_spectra
+                            * or the visibility mask: RW_EINVAL), and dsurf's n_after
+                            * slot is dL/dn for a shift common to all wavelengths. */
 } rw_surface;
 
 /* The DOE: its transmission map and the ray-wave parameters.  The geometry

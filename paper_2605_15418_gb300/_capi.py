@@ -30,7 +30,7 @@ class rw_surface(C.Structure):
     _fields_ = [("kind", C.c_int32), ("reserved", C.c_int32), ("z", C.c_double),
                 ("c", C.c_double), ("k", C.c_double), ("A4", C.c_double), ("A6", C.c_double),
                 ("A8", C.c_double), ("A10", C.c_double), ("n_after", C.c_double),
-                ("r_ap", C.c_double)]
+                ("r_ap", C.c_double), ("sellmeier", C.c_double * 6)]
 
 
 class rw_doe(C.Structure):

@@ -24,13 +24,14 @@ def surfaces_from_params(template, params):
     out = []
     for s, v in zip(template, p):
         out.append(Surface(s.kind, v[0], c=v[1], k=v[2], A=tuple(v[3:7]), n_after=v[7],
-                           r_ap=s.r_ap))
+                           r_ap=s.r_ap, sellmeier=getattr(s, "sellmeier", None)))
     return out
 
 
 def _vis_ok(sim):
     sysm = sim.w.system
-    return sysm.doe.emit == "exhaustive" and not sysm.sensor.coherent
+    return (sysm.doe.emit == "exhaustive" and not sysm.sensor.coherent
+            and all(getattr(s, "sellmeier", None) is None for s in sysm.surfaces))
 
 
 class RayWavePSF(torch.autograd.Function):

@@ -250,6 +250,80 @@ static unsigned long long* tape_counter(rw_ctx* ctx) {
     return reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(ctx->misc.p) + 192);
 }
 
+// ---------------------------------------------------------------- dispersion
+// A surface with Sellmeier coefficients makes the medium behind it
+// dispersive.  Such systems run one launch per distinct wavelength, each with
+// that wavelength's indices; the job table of a launch carries every job's
+// image index and ray-id offset, so the results equal one launch over all jobs.
+static bool is_dispersive(const rw_system* sys) {
+    if (!sys || !sys->surfaces || sys->nsurf < 1 || sys->nsurf > RW_MAX_SURFACES) return false;
+    for (int i = 0; i < sys->nsurf; ++i)
+        for (int k = 0; k < 6; ++k)
+            if (sys->surfaces[i].sellmeier[k] != 0.0) return true;
+    return false;
+}
+
+// n^2 = 1 + sum_i B_i L^2 / (L^2 - C_i), L the vacuum wavelength in micrometres
+static double sellmeier_index(const double* c, double lambda_mm) {
+    const double L2 = (lambda_mm * 1e3) * (lambda_mm * 1e3);
+    double n2 = 1.0;
+    for (int i = 0; i < 3; ++i) n2 += c[i] * L2 / (L2 - c[3 + i]);
+    return n2 > 0.0 ? std::sqrt(n2) : std::nan("");
+}
+
+struct WaveGroups {
+    std::vector<double> lambda;
+    std::vector<std::vector<rw_job>> jobs;
+    std::vector<std::vector<int>> out;        // job index in the caller's table
+    std::vector<std::vector<long long>> sid;  // ray id in the full table - ray id in the group
+};
+
+static rw_status group_by_wavelength(rw_ctx* ctx, const rw_job* jobs, int njob, WaveGroups& G) {
+    if (njob < 1) return fail(ctx, RW_EINVAL, "njob must be >= 1");
+    if (!jobs) return fail(ctx, RW_EINVAL, "jobs is NULL");
+    std::map<double, int> index;
+    std::vector<long long> gprefix;
+    long long prefix = 0;
+    for (int i = 0; i < njob; ++i) {
+        auto it = index.find(jobs[i].lambda);
+        int g;
+        if (it == index.end()) {
+            g = (int)G.lambda.size();
+            index[jobs[i].lambda] = g;
+            G.lambda.push_back(jobs[i].lambda);
+            G.jobs.emplace_back();
+            G.out.emplace_back();
+            G.sid.emplace_back();
+            gprefix.push_back(0);
+        } else {
+            g = it->second;
+        }
+        G.jobs[g].push_back(jobs[i]);
+        G.out[g].push_back(i);
+        G.sid[g].push_back(prefix - gprefix[g]);
+        gprefix[g] += jobs[i].ray_count;
+        prefix += jobs[i].ray_count;
+    }
+    return RW_OK;
+}
+
+// The system at one wavelength: every Sellmeier medium gets its index there.
+static rw_status system_at(rw_ctx* ctx, const rw_system* sys, double lambda, rw_system& out,
+                           std::vector<rw_surface>& surf) {
+    surf.assign(sys->surfaces, sys->surfaces + sys->nsurf);
+    for (auto& s : surf) {
+        bool disp = false;
+        for (int k = 0; k < 6; ++k) disp = disp || s.sellmeier[k] != 0.0;
+        if (!disp) continue;
+        s.n_after = sellmeier_index(s.sellmeier, lambda);
+        if (!(s.n_after > 0.0) || !std::isfinite(s.n_after))
+            return fail(ctx, RW_EINVAL, "Sellmeier index not real and positive at a job wavelength");
+    }
+    out = *sys;
+    out.surfaces = surf.data();
+    return RW_OK;
+}
+
 static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
     if (!sys) return fail(ctx, RW_EINVAL, "sys is NULL");
     if (sys->nsurf < 1 || sys->nsurf > RW_MAX_SURFACES)
@@ -394,8 +468,11 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
     return RW_OK;
 }
 
+// outs[i]: image of job i in the psf / dL/dpsf arrays (default i); sids[i]: added
+// to the launch's ray ids in the sampling stream (default 0)
 static rw_status pack_jobs(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int njob,
-                           int64_t n_rays, Packed& P) {
+                           int64_t n_rays, Packed& P, const int* outs = nullptr,
+                           const long long* sids = nullptr) {
     if (njob < 1) return fail(ctx, RW_EINVAL, "njob must be >= 1");
     if (!jobs) return fail(ctx, RW_EINVAL, "jobs is NULL");
     std::map<double, int> slot_of;
@@ -426,7 +503,8 @@ static rw_status pack_jobs(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs
         d.cx = (float)j.sensor_cx;
         d.cy = (float)j.sensor_cy;
         d.slot = slot;
-        d.pad = 0;
+        d.out = outs ? outs[i] : i;
+        d.sid = sids ? sids[i] : 0;
         P.prefix[i + 1] = P.prefix[i] + j.ray_count;
     }
     P.total = P.prefix[njob];
@@ -671,6 +749,8 @@ rw_status rw_doe_emit(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int
                       const rw_rays* rays, rw_emitted* out) {
     if (!ctx) return RW_EINVAL;
     ctx->err.clear();
+    if (is_dispersive(sys))
+        return fail(ctx, RW_EINVAL, "dispersive surfaces: rw_forward and rw_backward only");
     Packed P;
     rw_status st = pack_system(ctx, sys, P);
     if (st != RW_OK) return st;
@@ -698,11 +778,21 @@ rw_status rw_doe_emit(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int
     return RW_OK;
 }
 
+static rw_status forward_dispersive(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
+                                    int32_t njob, const rw_rays* rays, float* psf);
+static rw_status backward_dispersive(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
+                                     int32_t njob, const rw_rays* rays, const float* dl_dpsf,
+                                     float* dphi, float* damp, double* dsurf);
+
 static rw_status forward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
                               int32_t njob, const rw_rays* rays, float* psf, uint32_t* vis,
                               int64_t vis_words) {
     if (!ctx) return RW_EINVAL;
     ctx->err.clear();
+    if (is_dispersive(sys)) {
+        if (vis) return fail(ctx, RW_EINVAL, "the visibility mask needs non-dispersive media");
+        return forward_dispersive(ctx, sys, jobs, njob, rays, psf);
+    }
     Packed P;
     rw_status st = pack_system(ctx, sys, P);
     if (st != RW_OK) return st;
@@ -812,6 +902,10 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
                                double* dsurf) {
     if (!ctx) return RW_EINVAL;
     ctx->err.clear();
+    if (is_dispersive(sys)) {
+        if (vis) return fail(ctx, RW_EINVAL, "the visibility mask needs non-dispersive media");
+        return backward_dispersive(ctx, sys, jobs, njob, rays, dl_dpsf, dphi, damp, dsurf);
+    }
     Packed P;
     rw_status st = pack_system(ctx, sys, P);
     if (st != RW_OK) return st;
@@ -935,6 +1029,156 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
     return RW_OK;
 }
 
+// One launch per wavelength group into shared outputs (see is_dispersive).
+static rw_status forward_dispersive(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
+                                    int32_t njob, const rw_rays* rays, float* psf) {
+    WaveGroups G;
+    rw_status st = group_by_wavelength(ctx, jobs, njob, G);
+    if (st != RW_OK) return st;
+    if (sys->doe.dft == RW_DFT_TC)
+        return fail(ctx, RW_EINVAL, "the fused kernels use the FP32 FFT; the tensor-core "
+                                    "transform is available through rw_patch_spectra");
+    if ((st = check_rays(ctx, rays)) != RW_OK) return st;
+    if (!psf) return fail(ctx, RW_EINVAL, "psf is NULL");
+    std::vector<rw_system> sg(G.lambda.size());
+    std::vector<std::vector<rw_surface>> surf(G.lambda.size());
+    std::vector<Packed> P(G.lambda.size());
+    long long total = 0;
+    for (size_t g = 0; g < G.lambda.size(); ++g) {
+        if ((st = system_at(ctx, sys, G.lambda[g], sg[g], surf[g])) != RW_OK) return st;
+        if ((st = pack_system(ctx, &sg[g], P[g])) != RW_OK) return st;
+        if ((st = pack_jobs(ctx, &sg[g], G.jobs[g].data(), (int)G.jobs[g].size(), rays->n, P[g],
+                            G.out[g].data(), G.sid[g].data())) != RW_OK)
+            return st;
+        total += P[g].total;
+    }
+    const bool coherent = P[0].sys.coherent != 0;
+    const long long npx = (long long)P[0].sys.nx * P[0].sys.ny * njob;
+    RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    RW_CUDA(cudaMemsetAsync(psf, 0, npx * sizeof(float), ctx->stream), "psf clear");
+    if (total == 0) return RW_OK;
+    DevBuf& acc = coherent ? ctx->field : ctx->acc;
+    const size_t bytes = npx * (coherent ? sizeof(float2) : sizeof(double));
+    if ((st = ensure_buf(ctx, acc, bytes, "image accumulator scratch")) != RW_OK) return st;
+    RW_CUDA(cudaMemsetAsync(acc.p, 0, bytes, ctx->stream), "accumulator clear");
+    EmitOut eo;
+    std::memset(&eo, 0, sizeof(eo));
+    for (size_t g = 0; g < G.lambda.size(); ++g) {
+        if (P[g].total == 0) continue;
+        float2* T; DJob* dj; long long* dp;
+        if ((st = prepare(ctx, &sg[g], P[g], &T, &dj, &dp)) != RW_OK) return st;
+        const int nj = (int)G.jobs[g].size();
+        if (coherent) {
+            RW_CUDA(launch_forward(lctx(ctx), MODE_COHERENT, P[g].sys, dj, dp, nj, P[g].total,
+                                   rays_in(rays), T, nullptr, (float2*)acc.p, eo,
+                                   status_word(ctx)), "coherent forward");
+        } else {
+            unsigned* keep = nullptr;
+            if (forward_culls(P[g].sys)) {
+                const size_t kb = (size_t)P[g].total * cull_keep_words(P[g].sys.M) * sizeof(unsigned);
+                if ((st = ensure_buf(ctx, ctx->keep, kb, "block-culling scratch")) != RW_OK)
+                    return st;
+                keep = (unsigned*)ctx->keep.p;
+                ctx->launches++;      // k_cull
+            }
+            RW_CUDA(launch_forward(lctx(ctx), MODE_SPLAT, P[g].sys, dj, dp, nj, P[g].total,
+                                   rays_in(rays), T, (double*)acc.p, nullptr, eo,
+                                   status_word(ctx), nullptr, keep, nullptr), "forward kernel");
+        }
+        ctx->launches++;
+    }
+    if (coherent)
+        RW_CUDA(launch_coherent_finalize(lctx(ctx), (float2*)acc.p, psf, npx), "finalize");
+    else
+        RW_CUDA(launch_psf_finalize(lctx(ctx), (const double*)acc.p, psf, npx), "psf finalize");
+    ctx->launches++;
+    return RW_OK;
+}
+
+static rw_status backward_dispersive(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
+                                     int32_t njob, const rw_rays* rays, const float* dl_dpsf,
+                                     float* dphi, float* damp, double* dsurf) {
+    WaveGroups G;
+    rw_status st = group_by_wavelength(ctx, jobs, njob, G);
+    if (st != RW_OK) return st;
+    if (sys->doe.dft == RW_DFT_TC)
+        return fail(ctx, RW_EINVAL, "the fused kernels use the FP32 FFT; the tensor-core "
+                                    "transform is available through rw_patch_spectra");
+    if ((st = check_rays(ctx, rays)) != RW_OK) return st;
+    if (!dl_dpsf) return fail(ctx, RW_EINVAL, "dl_dpsf is NULL");
+    if (damp && !sys->doe.amp) return fail(ctx, RW_EINVAL, "damp requires doe.amp");
+    std::vector<rw_system> sg(G.lambda.size());
+    std::vector<std::vector<rw_surface>> surf(G.lambda.size());
+    std::vector<Packed> P(G.lambda.size());
+    long long total = 0;
+    int lim = 0;
+    cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    for (size_t g = 0; g < G.lambda.size(); ++g) {
+        if ((st = system_at(ctx, sys, G.lambda[g], sg[g], surf[g])) != RW_OK) return st;
+        if ((st = pack_system(ctx, &sg[g], P[g])) != RW_OK) return st;
+        if ((st = pack_jobs(ctx, &sg[g], G.jobs[g].data(), (int)G.jobs[g].size(), rays->n, P[g],
+                            G.out[g].data(), G.sid[g].data())) != RW_OK)
+            return st;
+        if (P[g].sys.M > 96 || backward_smem_needed(P[g].sys) > (size_t)lim)
+            return fail(ctx, RW_EINVAL, "patch size / n_ssr too large for the fused adjoint's "
+                                        "shared memory");
+        total += P[g].total;
+    }
+    if (total == 0 || (!dphi && !damp && !dsurf)) return RW_OK;
+    RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const bool coherent = P[0].sys.coherent != 0;
+    const long long npx = (long long)P[0].sys.nx * P[0].sys.ny * njob;
+    float2* gfield = nullptr;
+    EmitOut eo;
+    std::memset(&eo, 0, sizeof(eo));
+    if (coherent) {
+        // the whole field of every job first, then dL/dU = 2 (dL/dI) U
+        if ((st = ensure_buf(ctx, ctx->field, npx * sizeof(float2), "coherent field scratch")) !=
+            RW_OK)
+            return st;
+        gfield = (float2*)ctx->field.p;
+        RW_CUDA(cudaMemsetAsync(gfield, 0, npx * sizeof(float2), ctx->stream), "field clear");
+        for (size_t g = 0; g < G.lambda.size(); ++g) {
+            if (P[g].total == 0) continue;
+            float2* T; DJob* dj; long long* dp;
+            if ((st = prepare(ctx, &sg[g], P[g], &T, &dj, &dp)) != RW_OK) return st;
+            RW_CUDA(launch_forward(lctx(ctx), MODE_COHERENT, P[g].sys, dj, dp,
+                                   (int)G.jobs[g].size(), P[g].total, rays_in(rays), T, nullptr,
+                                   gfield, eo, status_word(ctx)), "coherent field");
+            ctx->launches++;
+        }
+        RW_CUDA(launch_coherent_grad(lctx(ctx), gfield, dl_dpsf, npx), "field gradient");
+        ctx->launches++;
+    }
+    for (size_t g = 0; g < G.lambda.size(); ++g) {
+        if (P[g].total == 0) continue;
+        float2* T; DJob* dj; long long* dp;
+        if ((st = prepare(ctx, &sg[g], P[g], &T, &dj, &dp)) != RW_OK) return st;
+        const int nj = (int)G.jobs[g].size();
+        float* coh_rsum = nullptr;
+        double* coh_jsum = nullptr;
+        if (coherent) {
+            if ((st = ensure_buf(ctx, ctx->coh_rsum, (size_t)P[g].total * 7 * sizeof(float),
+                                 "coherent adjoint scratch")) != RW_OK)
+                return st;
+            if ((st = ensure_buf(ctx, ctx->coh_jsum, (size_t)nj * 2 * sizeof(double),
+                                 "coherent adjoint scratch")) != RW_OK)
+                return st;
+            coh_rsum = (float*)ctx->coh_rsum.p;
+            coh_jsum = (double*)ctx->coh_jsum.p;
+            RW_CUDA(cudaMemsetAsync(coh_jsum, 0, (size_t)nj * 2 * sizeof(double), ctx->stream),
+                    "job sums clear");
+        }
+        int nl = 0;
+        RW_CUDA(launch_backward(lctx(ctx), P[g].sys, dj, dp, nj, P[g].total, rays_in(rays), T,
+                                sys->doe.amp, dl_dpsf, gfield, coh_rsum, coh_jsum, dphi, damp,
+                                dsurf, nullptr, status_word(ctx), &nl),
+                "backward kernel");
+        ctx->launches += nl;
+    }
+    return RW_OK;
+}
+
 rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int32_t njob,
                       const rw_rays* rays, const float* dl_dpsf, float* dphi, float* damp,
                       double* dsurf) {
@@ -1013,6 +1257,8 @@ rw_status rw_patch_spectra(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs
                            const rw_rays* rays, float* spectra, int64_t capacity) {
     if (!ctx) return RW_EINVAL;
     ctx->err.clear();
+    if (is_dispersive(sys))
+        return fail(ctx, RW_EINVAL, "dispersive surfaces: rw_forward and rw_backward only");
     Packed P;
     rw_status st = pack_system(ctx, sys, P);
     if (st != RW_OK) return st;

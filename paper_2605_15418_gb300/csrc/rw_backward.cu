@@ -64,7 +64,8 @@ __device__ __forceinline__ void gumbel_group(const DSys& sys, long long gid, int
 
 template <int M, int NS, bool COH>
 __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAtDoe& R,
-                                                    float k0, const float2* X, const float2* phu,
+                                                    float k0, long long stream,
+                                                    const float2* X, const float2* phu,
                                                     const float2* phv,
                                                     const float* __restrict__ gimg,
                                                     const float2* __restrict__ gf, float2* G,
@@ -117,7 +118,7 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
         int bj = 0x7fffffff;
         for (int Gq = lane; Gq * 4 < NB; Gq += 32) {
             float g4[4];
-            gumbel_group(sys, R.gid, i, Gq, g4);
+            gumbel_group(sys, stream, i, Gq, g4);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int jb = 4 * Gq + q;
@@ -210,7 +211,7 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
             float accd = 0.f;
             for (int Gq = lane; Gq * 4 < NB; Gq += 32) {
                 float g4[4];
-                gumbel_group(sys, R.gid, i, Gq, g4);
+                gumbel_group(sys, stream, i, Gq, g4);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int jb = 4 * Gq + q;
@@ -392,8 +393,8 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
             __syncthreads();
             fft2d<M, false>(X, tw);
             const float2 ain = make_float2(R.a_re, R.a_im);
-            const float* gimg = gpsf + (long long)R.job * npx;
-            const float2* gf = COH ? gfield + (long long)R.job * npx : nullptr;
+            const float* gimg = gpsf + (long long)J.out * npx;
+            const float2* gf = COH ? gfield + (long long)J.out * npx : nullptr;
             float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
                 constexpr int KW = M * M / RW_THREADS;   // visibility words per warp and ray
@@ -441,8 +442,8 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                                                status);
                 }
             } else {
-                sampled_ray_adjoint<M, NS, COH>(sys, R, J.k0, X, phu, phv, gimg, gf, G, sscr, acc,
-                                                SG, gs, status);
+                sampled_ray_adjoint<M, NS, COH>(sys, R, J.k0, R.gid + J.sid, X, phu, phv, gimg,
+                                                gf, G, sscr, acc, SG, gs, status);
             }
             // ---- per-ray reduction of the geometric gradients
 #pragma unroll

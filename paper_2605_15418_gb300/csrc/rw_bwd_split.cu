@@ -141,6 +141,8 @@ k_bs_trace(const DSys sys, const float* __restrict__ gpsf, SplitBufs B, long lon
             g = __ldg(B.iray + t);
             const int f = __ldg(B.ibin + t);
             const float2 U = B.iU[t];
+            // the split adjoint runs only in single-launch calls (no wavelength
+            // groups), where a job's image index is its index in the job table
             const RayAtDoe& R = B.rinfo[g];
             const int jvi = f / M, jui = f - (f / M) * M;
             float2 gU = make_float2(0.f, 0.f);

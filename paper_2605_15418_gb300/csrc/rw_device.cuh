@@ -81,7 +81,8 @@ struct DJob {
     long long off, cnt;
     float cx, cy;
     int slot;          // wavelength slot of the transmission map
-    int pad;
+    int out;           // index of the job's image in the psf / dL/dpsf arrays
+    long long sid;     // added to the launch's ray id in the sampling stream
 };
 
 // Incident ray state at the DOE (one per incident ray of a tile).

@@ -583,14 +583,14 @@ __device__ __forceinline__ bool deposit(const DSys& sys, const DJob& J, const Ra
     const long long npx = (long long)sys.nx * sys.ny;
     if (MODE == MODE_SPLAT && NS >= 0) {
         if (!fast_to_sensor<NS>(sys, x, y, zl, dx, dy, dz)) return false;
-        return splat_bilinear(sys, R.cx, R.cy, x, y, w, psf + (long long)R.job * npx);
+        return splat_bilinear(sys, R.cx, R.cy, x, y, w, psf + (long long)J.out * npx);
     } else if (MODE == MODE_SPLAT) {
         if (!trace_to_sensor<false>(sys, x, y, zl, dx, dy, dz, opl, status)) return false;
-        return splat_bilinear(sys, R.cx, R.cy, x, y, w, psf + (long long)R.job * npx);
+        return splat_bilinear(sys, R.cx, R.cy, x, y, w, psf + (long long)J.out * npx);
     } else {
         if (!trace_to_sensor<true>(sys, x, y, zl, dx, dy, dz, opl, status)) return false;
         splat_coherent(sys, J.k0, R.cx, R.cy, x, y, opl, dx, dy, dz, a,
-                       field + (long long)R.job * npx);
+                       field + (long long)J.out * npx);
         return true;
     }
 }
@@ -775,7 +775,7 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
             }
             __syncwarp();
             splat_coherent_warp(sys, J.k0, R.cx, R.cy, ok, x, y, opl, dx, dy, dz, a,
-                                field + (long long)R.job * sys.nx * sys.ny);
+                                field + (long long)J.out * sys.nx * sys.ny);
             continue;
         }
         bool landed = false;
@@ -850,7 +850,8 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
         float best = -INFINITY;
         int bj = 0x7fffffff;
         for (int G = lane; G * 4 < M * M; G += 32) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)i, (uint32_t)R.gid,
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)i,
+                                                     (uint32_t)(R.gid + J.sid),
                                                      (uint32_t)sys.rng_offset), k0, k1);
             const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
@@ -900,7 +901,7 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
             }
             __syncwarp();
             splat_coherent_warp(sys, J.k0, R.cx, R.cy, ok, x, y, opl, dx, dy, dz, a,
-                                field + (long long)R.job * sys.nx * sys.ny);
+                                field + (long long)J.out * sys.nx * sys.ny);
         }
         return;
     }

@@ -136,6 +136,10 @@ def surfaces_struct(surfaces):
         arr[i].A4, arr[i].A6, arr[i].A8, arr[i].A10 = (float(a) for a in s.A)
         arr[i].n_after = float(s.n_after)
         arr[i].r_ap = float(s.r_ap)
+        sm = getattr(s, "sellmeier", None)
+        if sm is not None:
+            for k in range(6):
+                arr[i].sellmeier[k] = float(sm[k])
     return arr
 
 
