@@ -61,11 +61,18 @@ def phi2_tensor(system, phi2=None):
     return phi2
 
 
-def emit_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0, phi2=None):
+def emit_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0, phi2=None,
+             rays=None):
     """Pre-DOE trace + DOE step for (a subset of) one job's rays.  Returns
-    the DOE step and the index of the medium the secondary rays enter."""
+    the DOE step and the index of the medium the secondary rays enter.
+    `rays` (dict of o, d, a, opl, alive) replaces the job's collimated grid,
+    e.g. the secondary rays of another DOE."""
     di = system.doe_index
-    ray = job_rays(job, z_start, system.n_object, idx)
+    if rays is None:
+        ray = job_rays(job, z_start, system.n_object, idx)
+    else:
+        sel = np.arange(rays["o"].shape[0]) if idx is None else np.asarray(idx)
+        ray = {k: v[sel] for k, v in rays.items()}
     ray, n_in = G.trace(ray, params[:di], torch.tensor(system.n_object, dtype=torch.float64))
     # a reflective DOE sends the secondary rays back into the incident medium
     n_out = n_in if getattr(system.doe, "reflective", False) else params[di]["n_after"]
@@ -75,18 +82,19 @@ def emit_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0, phi2=
 
 
 def psf_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0, chunk=256,
-            phi2=None):
-    """Sensor image [ny, nx] of one job (intensity)."""
+            phi2=None, rays=None):
+    """Sensor image [ny, nx] of one job (intensity); `rays` as in emit_job."""
     sen = system.sensor
     di = system.doe_index
     nx, ny = sen.nx, sen.ny
-    n_rays = job.n_rays if idx is None else len(idx)
-    all_idx = np.arange(job.n_rays) if idx is None else np.asarray(idx)
+    n_all = job.n_rays if rays is None else int(rays["o"].shape[0])
+    n_rays = n_all if idx is None else len(idx)
+    all_idx = np.arange(n_all) if idx is None else np.asarray(idx)
     img = torch.zeros(nx * ny, dtype=torch.float64)
     field = torch.zeros(nx * ny, dtype=torch.complex128)
     for c0 in range(0, n_rays, chunk):
         sub = all_idx[c0:c0 + chunk]
-        em, n_out = emit_job(system, job, z_start, params, phi, amp, sub, ray_base, phi2)
+        em, n_out = emit_job(system, job, z_start, params, phi, amp, sub, ray_base, phi2, rays)
         dsec = em["d"]
         shp = dsec.shape[:-1]
         Nin = shp[0]

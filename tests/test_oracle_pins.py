@@ -849,3 +849,39 @@ def test_two_phase_field_of_opposite_ramps_is_two_plane_waves():
     U[:, c, c + m] = 0
     U[:, c, c - m] = 0
     assert U.max() < 1e-12
+
+
+# ------------------------------------------------------------------ two DOEs in cascade
+def test_two_grating_cascade_orders_convolve():
+    """Two binary gratings in cascade (the secondary rays of the first are
+    the incident rays of the second): every ray leaves along sin(theta_i) +
+    (m1 + m2) lambda / Lambda, the power in combined order m is
+    sum_{m1 + m2 = m} eta_m1 eta_m2 over the orders each patch spectrum holds,
+    and the total power stays 1 per ray."""
+    w = R.configs.c1(n_side=2, angles_deg=(0.0,))
+    sys1, job = w.system, w.jobs[0]
+    em1, _ = P.emit_job(sys1, job, w.z_start, P.params_of(sys1), *P.map_tensors(sys1))
+    N, M = em1["U"].shape[0], sys1.doe.M
+    alive = em1["alive"].reshape(-1)
+    rays2 = {"o": em1["o"][:, None, :].expand(N, M * M, 3).reshape(-1, 3)[alive],
+             "d": em1["d"].reshape(-1, 3)[alive], "a": em1["a"].reshape(-1)[alive],
+             "opl": em1["opl"][:, None].expand(N, M * M).reshape(-1)[alive],
+             "alive": alive[alive]}
+    sys2 = R.configs.c1(n_side=2).system
+    sys2.surfaces = [R.Surface(R.PLANE, 0.01)]
+    em2, _ = P.emit_job(sys2, job, w.z_start, P.params_of(sys2), *P.map_tensors(sys2),
+                        rays=rays2)
+    a2 = em2["a"].reshape(len(rays2["a"]), -1)
+    d2 = em2["d"].reshape(len(rays2["a"]), -1, 3)
+    pw = (a2.abs() ** 2).numpy()
+    assert pw.sum() == pytest.approx(N, rel=1e-12)
+    lam, period = job.lam, 16 * sys1.doe.pitch
+    m_of = np.rint(d2[..., 0].numpy() * period / lam)
+    assert np.allclose(d2[..., 0].numpy()[pw > 1e-20], (m_of * lam / period)[pw > 1e-20],
+                       atol=1e-12)
+    # each stage's orders are its spectrum's bins j = 2 m1, j in [-M/2, M/2)
+    orders = range(-M // 4, M // 4)
+    for m in range(-12, 13):
+        want = sum(binary_grating_efficiency(m1, 16) * binary_grating_efficiency(m - m1, 16)
+                   for m1 in orders if (m - m1) in orders)
+        assert pw[m_of == m].sum() / N == pytest.approx(want, abs=1e-12), m
