@@ -149,15 +149,24 @@ __device__ __forceinline__ bool coherent_sums(const DSys& sys, float k0, float c
     float phb;
     if (!coherent_range(sys, k0, cx, cy, x, y, opl, i_lo, i_hi, j_lo, j_hi, phb)) return false;
     const float kx = k0 * sys.n_sensor * dx, ky = k0 * sys.n_sensor * dy;
+    // e^{-i theta} along a row: one sincos every 8 pixels, rotations by the
+    // per-pixel step kx * pitch in between
+    float st_s, st_c;
+    sincosf(kx * sys.spitch, &st_s, &st_c);
     for (int j = j_lo; j <= j_hi; ++j) {
         const float Y = cy + ((float)j - 0.5f * sys.ny + 0.5f) * sys.spitch;
         const float ry = Y - y;
+        float sn = 0.f, cs = 1.f;
         for (int i = i_lo; i <= i_hi; ++i) {
             const float X = cx + ((float)i - 0.5f * sys.nx + 0.5f) * sys.spitch;
             const float rx = X - x;
-            const float ph = phb + kx * rx + ky * ry;
-            float sn, cs;
-            sincosf(ph, &sn, &cs);
+            if (((i - i_lo) & 7) == 0) {
+                sincosf(phb + kx * rx + ky * ry, &sn, &cs);
+            } else {
+                const float t = cs * st_c - sn * st_s;
+                sn = sn * st_c + cs * st_s;
+                cs = t;
+            }
             const float2 g = __ldg(gf + j * sys.nx + i);
             const float wr = g.x * cs + g.y * sn, wi = g.y * cs - g.x * sn;
             W0.x += wr; W0.y += wi;

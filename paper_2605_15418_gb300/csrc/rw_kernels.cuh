@@ -476,22 +476,44 @@ __device__ __forceinline__ void splat_coherent_warp(const DSys& sys, float k0, f
     const int nx = sys.nx, npx = sys.nx * sys.ny;
     // the pixel this lane adds after the reduction
     const int q_out = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    // along a row the phase grows by kx * pitch per pixel: a group of 8 pixels
+    // in one row takes one sincos and 7 rotations by that step
+    float st_s, st_c;
+    sincosf(kx * sys.spitch, &st_s, &st_c);
+    const bool rows8 = (nx & 7) == 0;
     for (int p0 = 0; p0 < npx; p0 += 8) {
         float re[8], im[8];
+        if (rows8) {
+            const int j = p0 / nx, i = p0 - j * nx;
+            const float X = cx + ((float)i - 0.5f * sys.nx + 0.5f) * sys.spitch;
+            const float Y = cy + ((float)j - 0.5f * sys.ny + 0.5f) * sys.spitch;
+            float sn, cs;
+            sincosf(phb + kx * (X - x) + ky * (Y - y), &sn, &cs);
+            float er = ad.x * cs - ad.y * sn, ei = ad.x * sn + ad.y * cs;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int p = p0 + q;
-            re[q] = 0.f;
-            im[q] = 0.f;
-            if (p < npx) {
-                const int j = p / nx, i = p - j * nx;
-                const float X = cx + ((float)i - 0.5f * sys.nx + 0.5f) * sys.spitch;
-                const float Y = cy + ((float)j - 0.5f * sys.ny + 0.5f) * sys.spitch;
-                const float ph = phb + kx * (X - x) + ky * (Y - y);
-                float sn, cs;
-                sincosf(ph, &sn, &cs);
-                re[q] = ad.x * cs - ad.y * sn;
-                im[q] = ad.x * sn + ad.y * cs;
+            for (int q = 0; q < 8; ++q) {
+                re[q] = er;
+                im[q] = ei;
+                const float t = er * st_c - ei * st_s;
+                ei = er * st_s + ei * st_c;
+                er = t;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int p = p0 + q;
+                re[q] = 0.f;
+                im[q] = 0.f;
+                if (p < npx) {
+                    const int j = p / nx, i = p - j * nx;
+                    const float X = cx + ((float)i - 0.5f * sys.nx + 0.5f) * sys.spitch;
+                    const float Y = cy + ((float)j - 0.5f * sys.ny + 0.5f) * sys.spitch;
+                    const float ph = phb + kx * (X - x) + ky * (Y - y);
+                    float sn, cs;
+                    sincosf(ph, &sn, &cs);
+                    re[q] = ad.x * cs - ad.y * sn;
+                    im[q] = ad.x * sn + ad.y * cs;
+                }
             }
         }
         // 8 -> 4 (lanes xor 16), 4 -> 2 (xor 8), 2 -> 1 (xor 4): each lane keeps
