@@ -441,13 +441,21 @@ __device__ __forceinline__ void splat_coherent(const DSys& sys, float k0, float 
     if (!coherent_range(sys, k0, cx, cy, x, y, opl, i_lo, i_hi, j_lo, j_hi, phb)) return;
     const float kx = k0 * sys.n_sensor * dx, ky = k0 * sys.n_sensor * dy;
     const float2 ad = make_float2(a.x * dz, a.y * dz);
+    // one sincos every 8 pixels of a row, rotations by the step kx * pitch between
+    float st_s, st_c;
+    sincosf(kx * sys.spitch, &st_s, &st_c);
     for (int j = j_lo; j <= j_hi; ++j) {
         const float Y = cy + ((float)j - 0.5f * sys.ny + 0.5f) * sys.spitch;
+        float s = 0.f, c = 1.f;
         for (int i = i_lo; i <= i_hi; ++i) {
-            const float X = cx + ((float)i - 0.5f * sys.nx + 0.5f) * sys.spitch;
-            const float ph = phb + kx * (X - x) + ky * (Y - y);
-            float s, c;
-            sincosf(ph, &s, &c);
+            if (((i - i_lo) & 7) == 0) {
+                const float X = cx + ((float)i - 0.5f * sys.nx + 0.5f) * sys.spitch;
+                sincosf(phb + kx * (X - x) + ky * (Y - y), &s, &c);
+            } else {
+                const float t = c * st_c - s * st_s;
+                s = s * st_c + c * st_s;
+                c = t;
+            }
             float2* p = fld + j * sys.nx + i;
             atomicAdd(&p->x, ad.x * c - ad.y * s);
             atomicAdd(&p->y, ad.x * s + ad.y * c);
