@@ -37,7 +37,7 @@ FP32_LANES_PER_SM = 128
 # count (16x): see the profiles/ summaries.  A kernel missing here has no
 # capture of its current code.
 TRAFFIC = {"k_bs_scatter": 16 * (1.535592e9 + 0.192266e9),
-           "k_bs_trace": 16 * (1.376237e9 + 0.734716e9),
+           "k_bs_trace": 16 * (1.408312e9 + 0.820282e9),
            "k_cull": 16 * 0.023748e9,
            "k_forward": 16 * (0.308211e9 + 1.473743e9)}
 NUM_SMS = 152

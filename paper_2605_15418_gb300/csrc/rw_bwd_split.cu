@@ -119,7 +119,7 @@ k_bs_spectra(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
 
 // ------------------------------------------------------------------ 2: trace + reverse
 template <int M, int NS>
-__global__ void __launch_bounds__(RW_THREADS, 2)
+__global__ void __launch_bounds__(RW_THREADS, NS >= 6 ? 2 : 3)
 k_bs_trace(const DSys sys, const float* __restrict__ gpsf, SplitBufs B, long long nitems,
            double* __restrict__ dsurf, unsigned* status) {
     __shared__ double dred[RW_MAXS * RW_NGRAD * (RW_THREADS / 32)];
