@@ -12,11 +12,22 @@ import rwinputs as R
 pytestmark = pytest.mark.gpu
 
 
-def test_step_captured_in_cuda_graph_matches_eager():
+def _coherent():
+    import coherent_cases as CC
+    return CC.lens_after(n_side=9)
+
+
+@pytest.mark.parametrize("case", ["incoherent", "coherent"])
+def test_step_captured_in_cuda_graph_matches_eager(case):
+    """Coherent: the step's backward also recomputes the field, forms dL/dU
+    and runs the incident-side kernel with its per-job sums."""
     from paper_2605_15418_gb300 import raywave as RW
-    w = R.configs.c2(n_side=48, D=32, lams=(486e-6, 656e-6), fields_deg=(0.0, 1.5),
-                     sensor_n=96, map_side=256)
-    w.system.sensor.pitch = 8e-3
+    if case == "coherent":
+        w = _coherent()
+    else:
+        w = R.configs.c2(n_side=48, D=32, lams=(486e-6, 656e-6), fields_deg=(0.0, 1.5),
+                         sensor_n=96, map_side=256)
+        w.system.sensor.pitch = 8e-3
     sim = RW.Simulator(w)
     tgt = torch.as_tensor(w.target, device=sim.dev)
     psf = torch.empty(sim.psf_shape, device=sim.dev)
