@@ -1004,6 +1004,9 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
         coh_jsum = (double*)ctx->coh_jsum.p;
         RW_CUDA(cudaMemsetAsync(coh_jsum, 0, (size_t)njob * 2 * sizeof(double), ctx->stream),
                 "job sums clear");
+        // per-ray sums: bin slices of one ray add into them
+        RW_CUDA(cudaMemsetAsync(coh_rsum, 0, (size_t)P.total * 7 * sizeof(float), ctx->stream),
+                "ray sums clear");
         // I = |U|^2 loses the phase of U: recompute the field, then
         // dL/dU = 2 (dL/dI) U in place
         const long long npx = (long long)P.sys.nx * P.sys.ny * njob;
@@ -1168,6 +1171,8 @@ static rw_status backward_dispersive(rw_ctx* ctx, const rw_system* sys, const rw
             coh_jsum = (double*)ctx->coh_jsum.p;
             RW_CUDA(cudaMemsetAsync(coh_jsum, 0, (size_t)nj * 2 * sizeof(double), ctx->stream),
                     "job sums clear");
+            RW_CUDA(cudaMemsetAsync(coh_rsum, 0, (size_t)P[g].total * 7 * sizeof(float),
+                                    ctx->stream), "ray sums clear");
         }
         int nl = 0;
         RW_CUDA(launch_backward(lctx(ctx), P[g].sys, dj, dp, nj, P[g].total, rays_in(rays), T,

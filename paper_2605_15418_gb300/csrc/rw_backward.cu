@@ -378,7 +378,15 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
     const long long npx = (long long)sys.nx * sys.ny;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // work unit = (tile, slice of each ray's bins): coherent exhaustive launches split
+    // the bins when the tiles cannot fill the GPU (see launch_backward_d)
+    const int nslice = (COH && sys.nslice > 1) ? sys.nslice : 1;
+    constexpr int CH = M * M / RW_THREADS;
+    const int per = COH ? ((CH + nslice - 1) / nslice) * RW_THREADS : M * M;
+    for (long long unit = blockIdx.x; unit < ntiles * nslice; unit += gridDim.x) {
+        const long long tile = COH ? unit / nslice : unit;
+        const int slice = COH ? (int)(unit - tile * nslice) : 0;
+        const int f0 = slice * per, f1 = COH ? min(M * M, f0 + per) : M * M;
         __syncthreads();
         if (threadIdx.x < RW_TILE)
             incident_to_doe(sys, jobs, prefix, njob, total, rays, tile * RW_TILE + threadIdx.x,
@@ -399,7 +407,13 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
                 constexpr int KW = M * M / RW_THREADS;   // visibility words per warp and ray
                 if (COH) {
-                    for (int f = threadIdx.x; f < M * M; f += RW_THREADS)
+                    if (nslice > 1) {
+                        // bins outside the slice contribute nothing to this dL/dX
+                        for (int f = threadIdx.x; f < Patch<M>::ELEMS; f += RW_THREADS)
+                            G[f] = make_float2(0.f, 0.f);
+                        __syncthreads();
+                    }
+                    for (int f = f0 + threadIdx.x; f < f1; f += RW_THREADS)
                         exh_bin_adjoint_coh<M>(sys, R, J.k0, X, phu, phv, gf, G, ain, f, acc, gs,
                                                status);
                 } else if (vis && KW <= 32) {
@@ -472,10 +486,15 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                     // the incident side runs in k_coh_incident once every ray's
                     // dL/dOPL is known (see there)
                     float* o = coh_rsum + R.gid * 7;
+                    if (nslice > 1) {
 #pragma unroll
-                    for (int k = 0; k < 7; ++k) o[k] = s[k];
+                        for (int k = 0; k < 7; ++k) atomicAdd(o + k, s[k]);   // zeroed by the host
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 7; ++k) o[k] = s[k];
+                    }
                     atomicAdd(coh_jsum + 2 * R.job, (double)s[6]);
-                    atomicAdd(coh_jsum + 2 * R.job + 1, 1.0);
+                    if (slice == 0) atomicAdd(coh_jsum + 2 * R.job + 1, 1.0);
                 }
             }
             // ---- adjoint patch transform and map scatter
@@ -611,10 +630,18 @@ static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const 
     long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     long long grid = (long long)L.num_sms * per_sm;
     grid = pick_grid(L, RW_K_BACKWARD, grid);
-    if (grid > ntiles) grid = ntiles;
+    // coherent exhaustive: split each ray's bins when the tiles cannot fill the GPU
+    DSys s = sys;
+    s.nslice = 1;
+    if (COH && sys.emit == RW_EMIT_EXHAUSTIVE && ntiles < grid) {
+        const long long want = (grid + ntiles - 1) / ntiles;
+        const long long most = (long long)M * M / RW_THREADS;
+        s.nslice = (int)(want < most ? want : most);
+    }
+    if (grid > ntiles * s.nslice) grid = ntiles * s.nslice;
     if (grid < 1) grid = 1;
     RW_MARK(L, "k_backward");
-    kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(sys, jobs, prefix, njob, total, rays, T,
+    kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(s, jobs, prefix, njob, total, rays, T,
                                                           amp, gpsf, gfield, dphi, damp, dsurf,
                                                           status, vis, coh_rsum, coh_jsum);
     RW_MARK(L, nullptr);

@@ -52,6 +52,8 @@ struct DSys {
     int reflective;    // secondary rays return into the incident medium
     int two_phase;     // U = A (exp(i phi) + exp(i phi2))
     int uniform;       // sampled emission from the uniform density over propagating bins
+    int nslice;        // coherent exhaustive launches: each ray's bins in this many slices,
+                       // one CTA work unit per (tile, slice); 1 elsewhere
     const float* phi;  // device phase maps (read by the two-phase adjoint)
     const float* phi2;
     int nout_slot;     // surface whose n_after is n_out (-1: object space)

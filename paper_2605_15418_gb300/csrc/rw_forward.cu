@@ -98,7 +98,14 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
     fft_twiddles<M>(tw);
     const long long npix_map = (long long)sys.H * sys.W;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // work unit = (tile, slice of each ray's bins); one slice outside coherent launches
+    const int nslice = (MODE == MODE_COHERENT && sys.nslice > 1) ? sys.nslice : 1;
+    constexpr int CH = M * M / RW_THREADS;                    // bin chunks of RW_THREADS
+    const int per = (MODE == MODE_COHERENT) ? ((CH + nslice - 1) / nslice) * RW_THREADS : M * M;
+    for (long long unit = blockIdx.x; unit < ntiles * nslice; unit += gridDim.x) {
+        const long long tile = (MODE == MODE_COHERENT) ? unit / nslice : unit;
+        const int f0 = (MODE == MODE_COHERENT) ? (int)(unit - tile * nslice) * per : 0;
+        const int f1 = (MODE == MODE_COHERENT) ? min(M * M, f0 + per) : M * M;
         __syncthreads();
         if (threadIdx.x < RW_TILE) {
             const long long g = tile * RW_TILE + threadIdx.x;
@@ -144,7 +151,7 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
                 emit_exhaustive<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                              tile * RW_TILE + r, status, vis,
                                              keep ? skeep + r * cull_keep_words(M) : nullptr,
-                                             vw, tape);
+                                             vw, tape, f0, f1);
             } else {
                 emit_sampled<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                           tile * RW_TILE + r, status,
@@ -325,10 +332,21 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
     if (per_sm < 1) per_sm = 1;
     long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     long long grid = pick_grid(L, RW_K_FORWARD, (long long)L.num_sms * per_sm);
-    if (grid > ntiles) grid = ntiles;
+    // Coherent exhaustive emission: each ray's wavelet sums outweigh its patch
+    // FFT by orders of magnitude, so when the tiles alone cannot fill the GPU
+    // every ray's bins are split into slices (the FFT is redone per slice).
+    DSys s = sys;
+    s.nslice = 1;
+    if (MODE == MODE_COHERENT && sys.emit == RW_EMIT_EXHAUSTIVE && ntiles < grid) {
+        const long long want = (grid + ntiles - 1) / ntiles;
+        const long long most = (long long)M * M / RW_THREADS;
+        s.nslice = (int)(want < most ? want : most);
+    }
+    const long long units = ntiles * s.nslice;
+    if (grid > units) grid = units;
     if (grid < 1) grid = 1;
     RW_MARK(L, "k_forward");
-    kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(sys, jobs, prefix, njob, total, rays,
+    kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(s, jobs, prefix, njob, total, rays,
                                                           T, psf, field, eo, status, vis, keep,
                                                           tape);
     RW_MARK(L, nullptr);

@@ -763,7 +763,10 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
                                                 const EmitOut& eo, long long g, unsigned* status,
                                                 unsigned* __restrict__ vis,
                                                 const unsigned* keepw, unsigned* vw,
-                                                const SplitBufs& tape) {
+                                                const SplitBufs& tape, int f0 = 0,
+                                                int f1 = M * M) {
+    // bins f0 .. f1-1 of the ray (a slice in coherent launches; both multiples
+    // of RW_THREADS or M * M, so every warp runs the loop the same number of times)
     if constexpr (MODE == MODE_SPLAT && NS >= 0 && M <= 64) {
         if (keepw) {
             emit_culled<M, NS>(sys, J, R, X, phu, phv, psf, g, status, vis, keepw, vw, tape);
@@ -778,7 +781,7 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
         eo.hx[g] = R.px; eo.hy[g] = R.py; eo.hz[g] = (float)((double)R.pz + sys.s[sys.doe_index].z);
         eo.opl[g] = R.opl;
     }
-    for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
+    for (int f = f0 + threadIdx.x; f < f1; f += RW_THREADS) {
         const int jvi = f / M, jui = f - (f / M) * M;
         float dx, dy, dz;
         const bool prop = bin_direction<(NS >= 0)>(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz);
