@@ -488,6 +488,9 @@ __device__ __forceinline__ void splat_coherent_warp(const DSys& sys, float k0, f
     // in one row takes one sincos and 7 rotations by that step
     float st_s, st_c;
     sincosf(kx * sys.spitch, &st_s, &st_c);
+    // the step to the power 4: pixels 4..7 of a group run as a second chain
+    const float s2c = st_c * st_c - st_s * st_s, s2s = 2.f * st_c * st_s;
+    const float s4c = s2c * s2c - s2s * s2s, s4s = 2.f * s2c * s2s;
     const bool rows8 = (nx & 7) == 0;
     for (int p0 = 0; p0 < npx; p0 += 8) {
         float re[8], im[8];
@@ -498,13 +501,19 @@ __device__ __forceinline__ void splat_coherent_warp(const DSys& sys, float k0, f
             float sn, cs;
             sincosf(phb + kx * (X - x) + ky * (Y - y), &sn, &cs);
             float er = ad.x * cs - ad.y * sn, ei = ad.x * sn + ad.y * cs;
+            float fr = er * s4c - ei * s4s, fi = er * s4s + ei * s4c;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
+            for (int q = 0; q < 4; ++q) {
                 re[q] = er;
                 im[q] = ei;
+                re[q + 4] = fr;
+                im[q + 4] = fi;
                 const float t = er * st_c - ei * st_s;
                 ei = er * st_s + ei * st_c;
                 er = t;
+                const float u = fr * st_c - fi * st_s;
+                fi = fr * st_s + fi * st_c;
+                fr = u;
             }
         } else {
 #pragma unroll
