@@ -149,30 +149,58 @@ __device__ __forceinline__ bool coherent_sums(const DSys& sys, float k0, float c
     float phb;
     if (!coherent_range(sys, k0, cx, cy, x, y, opl, i_lo, i_hi, j_lo, j_hi, phb)) return false;
     const float kx = k0 * sys.n_sensor * dx, ky = k0 * sys.n_sensor * dy;
-    // e^{-i theta} along a row: one sincos every 8 pixels, rotations by the
-    // per-pixel step kx * pitch in between
+    // Along a row: one sincos every 8 pixels and rotations by the per-pixel
+    // step kx * pitch, run as two interleaved chains (pixels q and q + 4 of a
+    // group).  With ry constant in a row and rx = rx_lo + k pitch, the row
+    // needs only R = sum_k w_k and K = sum_k k w_k:
+    // W0 += R, WY += ry R, WX += rx_lo R + pitch K.
     float st_s, st_c;
     sincosf(kx * sys.spitch, &st_s, &st_c);
+    const float s2c = st_c * st_c - st_s * st_s, s2s = 2.f * st_c * st_s;
+    const float s4c = s2c * s2c - s2s * s2s, s4s = 2.f * s2c * s2s;
+    const float rx_lo = cx + ((float)i_lo - 0.5f * sys.nx + 0.5f) * sys.spitch - x;
     for (int j = j_lo; j <= j_hi; ++j) {
         const float Y = cy + ((float)j - 0.5f * sys.ny + 0.5f) * sys.spitch;
         const float ry = Y - y;
-        float sn = 0.f, cs = 1.f;
-        for (int i = i_lo; i <= i_hi; ++i) {
-            const float X = cx + ((float)i - 0.5f * sys.nx + 0.5f) * sys.spitch;
-            const float rx = X - x;
-            if (((i - i_lo) & 7) == 0) {
-                sincosf(phb + kx * rx + ky * ry, &sn, &cs);
-            } else {
-                const float t = cs * st_c - sn * st_s;
-                sn = sn * st_c + cs * st_s;
-                cs = t;
+        const float2* grow = gf + j * sys.nx;
+        float ra_x = 0.f, ra_y = 0.f, rb_x = 0.f, rb_y = 0.f;     // row sums, chains A and B
+        float ka_x = 0.f, ka_y = 0.f, kb_x = 0.f, kb_y = 0.f;     // k-weighted row sums
+        for (int i0 = i_lo; i0 <= i_hi; i0 += 8) {
+            const float rx0 = cx + ((float)i0 - 0.5f * sys.nx + 0.5f) * sys.spitch - x;
+            float sa, ca;
+            sincosf(phb + kx * rx0 + ky * ry, &sa, &ca);
+            float cb = ca * s4c - sa * s4s, sb = sa * s4c + ca * s4s;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int ia = i0 + q, ib = i0 + 4 + q;
+                if (ia <= i_hi) {
+                    const float2 g = __ldg(grow + ia);
+                    const float wr = g.x * ca + g.y * sa, wi = g.y * ca - g.x * sa;
+                    const float k = (float)(ia - i_lo);
+                    ra_x += wr; ra_y += wi;
+                    ka_x = fmaf(k, wr, ka_x); ka_y = fmaf(k, wi, ka_y);
+                }
+                if (ib <= i_hi) {
+                    const float2 g = __ldg(grow + ib);
+                    const float wr = g.x * cb + g.y * sb, wi = g.y * cb - g.x * sb;
+                    const float k = (float)(ib - i_lo);
+                    rb_x += wr; rb_y += wi;
+                    kb_x = fmaf(k, wr, kb_x); kb_y = fmaf(k, wi, kb_y);
+                }
+                const float ta = ca * st_c - sa * st_s;
+                sa = sa * st_c + ca * st_s;
+                ca = ta;
+                const float tb = cb * st_c - sb * st_s;
+                sb = sb * st_c + cb * st_s;
+                cb = tb;
             }
-            const float2 g = __ldg(gf + j * sys.nx + i);
-            const float wr = g.x * cs + g.y * sn, wi = g.y * cs - g.x * sn;
-            W0.x += wr; W0.y += wi;
-            WX.x = fmaf(wr, rx, WX.x); WX.y = fmaf(wi, rx, WX.y);
-            WY.x = fmaf(wr, ry, WY.x); WY.y = fmaf(wi, ry, WY.y);
         }
+        const float Rx = ra_x + rb_x, Ry = ra_y + rb_y;
+        const float Kx = ka_x + kb_x, Ky = ka_y + kb_y;
+        W0.x += Rx; W0.y += Ry;
+        WY.x = fmaf(ry, Rx, WY.x); WY.y = fmaf(ry, Ry, WY.y);
+        WX.x += rx_lo * Rx + sys.spitch * Kx;
+        WX.y += rx_lo * Ry + sys.spitch * Ky;
     }
     return true;
 }
