@@ -100,12 +100,14 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
     // work unit = (tile, slice of each ray's bins); one slice outside coherent launches
     const int nslice = (MODE == MODE_COHERENT && sys.nslice > 1) ? sys.nslice : 1;
-    constexpr int CH = M * M / RW_THREADS;                    // bin chunks of RW_THREADS
+    // a slice is a range of bins (exhaustive) or of draws (sampled), in chunks of RW_THREADS
+    const int nwork = (MODE == MODE_COHERENT && sys.emit != RW_EMIT_EXHAUSTIVE) ? sys.n_ssr : M * M;
+    const int CH = (nwork + RW_THREADS - 1) / RW_THREADS;
     const int per = (MODE == MODE_COHERENT) ? ((CH + nslice - 1) / nslice) * RW_THREADS : M * M;
     for (long long unit = blockIdx.x; unit < ntiles * nslice; unit += gridDim.x) {
         const long long tile = (MODE == MODE_COHERENT) ? unit / nslice : unit;
         const int f0 = (MODE == MODE_COHERENT) ? (int)(unit - tile * nslice) * per : 0;
-        const int f1 = (MODE == MODE_COHERENT) ? min(M * M, f0 + per) : M * M;
+        const int f1 = (MODE == MODE_COHERENT) ? min(nwork, f0 + per) : M * M;
         __syncthreads();
         if (threadIdx.x < RW_TILE) {
             const long long g = tile * RW_TILE + threadIdx.x;
@@ -155,7 +157,9 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             } else {
                 emit_sampled<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
                                           tile * RW_TILE + r, status,
-                                          smem + sampled_scratch_offset(M));
+                                          smem + sampled_scratch_offset(M),
+                                          MODE == MODE_COHERENT ? f0 : 0,
+                                          MODE == MODE_COHERENT ? f1 : -1);
             }
             // the next patch's bulk copies write X through the async proxy
             if (M == 64) fence_async_smem();
@@ -337,9 +341,11 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
     // every ray's bins are split into slices (the FFT is redone per slice).
     DSys s = sys;
     s.nslice = 1;
-    if (MODE == MODE_COHERENT && sys.emit == RW_EMIT_EXHAUSTIVE && ntiles < grid) {
+    if (MODE == MODE_COHERENT && ntiles < grid) {
         const long long want = (grid + ntiles - 1) / ntiles;
-        const long long most = (long long)M * M / RW_THREADS;
+        const long long most = sys.emit == RW_EMIT_EXHAUSTIVE
+                                   ? (long long)M * M / RW_THREADS
+                                   : ((long long)sys.n_ssr + RW_THREADS - 1) / RW_THREADS;
         s.nslice = (int)(want < most ? want : most);
     }
     const long long units = ntiles * s.nslice;

@@ -854,7 +854,9 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
                                              const float2* X, const float2* phu, const float2* phv,
                                              double* psf, float2* field, const EmitOut& eo,
                                              long long g, unsigned* status,
-                                             unsigned char* scratch) {
+                                             unsigned char* scratch, int d0 = 0, int d1 = -1) {
+    // draws d0 .. d1-1 (a slice in coherent launches; d0 a multiple of RW_THREADS)
+    if (d1 < 0) d1 = sys.n_ssr;
     float* logp = reinterpret_cast<float*>(scratch);
     int* sel = reinterpret_cast<int*>(logp + M * M);
     float* red = reinterpret_cast<float*>(sel + sys.n_ssr);
@@ -888,7 +890,7 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
     // one warp per draw; each lane scores groups of 4 bins sharing a Philox counter
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t k0 = (uint32_t)(sys.seed & 0xffffffffull), k1 = (uint32_t)(sys.seed >> 32);
-    for (int i = warp; i < sys.n_ssr; i += RW_THREADS / 32) {
+    for (int i = d0 + warp; i < d1; i += RW_THREADS / 32) {
         float best = -INFINITY;
         int bj = 0x7fffffff;
         for (int G = lane; G * 4 < M * M; G += 32) {
@@ -925,10 +927,10 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
     const float N = (float)sys.n_ssr;
     if (MODE == MODE_COHERENT && sys.window == 0) {
         // whole-sensor sum, a warp's 32 draws at a time (warps past n_ssr skip)
-        for (int i0 = 0; i0 < sys.n_ssr; i0 += RW_THREADS) {
-            if (i0 + (int)(threadIdx.x & ~31u) >= sys.n_ssr) continue;
+        for (int i0 = d0; i0 < d1; i0 += RW_THREADS) {
+            if (i0 + (int)(threadIdx.x & ~31u) >= d1) continue;
             const int i = i0 + threadIdx.x;
-            const int jb = i < sys.n_ssr ? sel[i] : -1;
+            const int jb = i < d1 ? sel[i] : -1;
             float dx = 0.f, dy = 0.f, dz = 0.f;
             float x = R.px, y = R.py, zl = R.pz;
             double opl = R.opl;
@@ -947,7 +949,7 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
         }
         return;
     }
-    for (int i = threadIdx.x; i < sys.n_ssr; i += RW_THREADS) {
+    for (int i = d0 + threadIdx.x; i < d1; i += RW_THREADS) {
         const int jb = sel[i];
         float dx = 0.f, dy = 0.f, dz = 0.f;
         float2 a = make_float2(0.f, 0.f);
