@@ -39,7 +39,7 @@ FP32_LANES_PER_SM = 128
 TRAFFIC = {"k_bs_scatter": 16 * (1.535592e9 + 0.192266e9),
            "k_bs_trace": 16 * (1.408312e9 + 0.820282e9),
            "k_cull": 16 * 0.023748e9,
-           "k_forward": 16 * (0.308211e9 + 1.473743e9)}
+           "k_forward": 16 * (0.310524e9 + 1.472937e9)}
 NUM_SMS = 152
 
 
