@@ -885,3 +885,50 @@ def test_two_grating_cascade_orders_convolve():
         want = sum(binary_grating_efficiency(m1, 16) * binary_grating_efficiency(m - m1, 16)
                    for m1 in orders if (m - m1) in orders)
         assert pw[m_of == m].sum() / N == pytest.approx(want, abs=1e-12), m
+
+
+def test_oracle_reflective_two_phase_gradient_matches_central_differences():
+    """Reflective planar DOE with two phase profiles and an amplitude map,
+    coherent sensor in front of it: autograd through the reversed emission,
+    the second profile and the amplitude equals central differences of the
+    oracle's forward (phase pixels of both profiles, amplitude pixels, the
+    DOE's z)."""
+    import reflective_cases as RC
+    w = RC.planar(n_side=4, coherent=True, two_phase=True, amp=True)
+    sysm = w.system
+    tgt = torch.from_numpy(w.target.astype(np.float64))
+    maps0 = [torch.from_numpy(m.astype(np.float64)) for m in (sysm.doe.phi, sysm.doe.phi2,
+                                                             sysm.doe.amp)]
+
+    def loss_of(prm_, ph1, ph2, am):
+        return L.eq3_loss(P.psf(w, params=prm_, phi=ph1, amp=am, phi2=ph2), tgt)[0]
+
+    prm = P.params_of(sysm, requires_grad=True)
+    leaves = [m.clone().requires_grad_(True) for m in maps0]
+    Lv = loss_of(prm, *leaves)
+    Lv.backward()
+    scale = abs(float(Lv.detach()))
+    # a mirror shift dz changes the round-trip phase by ~2 k dz: at 1 um that is
+    # 0.13 rad for dz = 1e-5 mm, so the step is kept small (FD converges
+    # quadratically onto the autograd value as h falls: 1e-5 -> 0.75 %,
+    # 1e-7 -> 1e-6 relative)
+    h = 1e-7
+    vals = []
+    for sgn in (+1, -1):
+        p2 = P.params_of(sysm)
+        p2[0]["z"] = torch.tensor(float(prm[0]["z"]) + sgn * h, dtype=F64)
+        vals.append(float(loss_of(p2, *maps0)))
+    g_fd = (vals[0] - vals[1]) / (2 * h)
+    assert float(prm[0]["z"].grad) == pytest.approx(g_fd, rel=1e-4, abs=1e-7 * scale)
+    rng = np.random.default_rng(4)
+    for which in range(3):
+        g = leaves[which].grad.numpy()
+        hot = np.argwhere(np.abs(g) > 1e-2 * np.abs(g).max())
+        for (r, c) in hot[rng.choice(len(hot), 3, replace=False)]:
+            vals = []
+            for sgn in (+1, -1):
+                ms = [m.clone() for m in maps0]
+                ms[which][r, c] += sgn * 1e-6
+                vals.append(float(loss_of(P.params_of(sysm), *ms)))
+            g_fd = (vals[0] - vals[1]) / 2e-6
+            assert g[r, c] == pytest.approx(g_fd, rel=1e-5, abs=1e-9 * scale), (which, r, c)
