@@ -42,7 +42,8 @@ def surface_params(s, requires_grad=False):
     return {"kind": int(s.kind), "z": t(s.z), "c": t(s.c), "k": t(s.k),
             "A4": t(s.A[0]), "A6": t(s.A[1]), "A8": t(s.A[2]), "A10": t(s.A[3]),
             "n_after": t(s.n_after), "r_ap": float(s.r_ap),
-            "sellmeier": None if sm is None else tuple(float(v) for v in sm)}
+            "sellmeier": None if sm is None else tuple(float(v) for v in sm),
+            "n_after0": float(s.n_after)}
 
 
 def sellmeier_index(coeffs, lam_mm):
@@ -55,16 +56,18 @@ def sellmeier_index(coeffs, lam_mm):
 
 def at_wavelength(params, lam_mm):
     """Surface parameters at one wavelength: a dispersive medium gets its
-    Sellmeier index.  Its n_after leaf still carries the gradient, as the
-    derivative with respect to an index shift common to every wavelength."""
+    Sellmeier index, shifted by the n_after leaf's departure from the
+    surface's nominal n_after -- an index shift common to every wavelength,
+    zero at the nominal value, whose derivative is the sum over wavelengths
+    of dL/dn."""
     out = []
     for p in params:
         if p.get("sellmeier") is None:
             out.append(p)
             continue
         q = dict(p)
-        leaf = p["n_after"]
-        q["n_after"] = leaf - leaf.detach() + sellmeier_index(p["sellmeier"], lam_mm)
+        shift = p["n_after"] - p["n_after0"]
+        q["n_after"] = sellmeier_index(p["sellmeier"], lam_mm) + shift
         out.append(q)
     return out
 

@@ -932,3 +932,39 @@ def test_oracle_reflective_two_phase_gradient_matches_central_differences():
                 vals.append(float(loss_of(P.params_of(sysm), *ms)))
             g_fd = (vals[0] - vals[1]) / 2e-6
             assert g[r, c] == pytest.approx(g_fd, rel=1e-5, abs=1e-9 * scale), (which, r, c)
+
+
+
+def test_oracle_dispersive_index_gradient_matches_central_differences():
+    """Sellmeier media: the n_after leaf shifts every wavelength's index by
+    its departure from the nominal value, so the autograd gradient (the sum
+    over wavelengths of dL/dn) equals central differences of that shift, and
+    the curvature gradients of the dispersive lens agree too."""
+    w = R.configs.c3(n_side=5, D=16)
+    sysm = w.system
+    sysm.surfaces = R.configs.dispersive(sysm.surfaces)
+    w.jobs = [R.Job(lam=lam, grid_n=5, spacing=w.jobs[0].spacing)
+              for lam in (486.1327e-6, 656.2725e-6)]
+    sysm.sensor.nx = sysm.sensor.ny = 48
+    sysm.sensor.pitch = 40e-3
+    w.target = R.gaussian_spots_target(2, 48, 48, seed=5, n_spots=3)
+    tgt = torch.from_numpy(w.target.astype(np.float64))
+
+    def loss_of(prm_):
+        return L.eq3_loss(P.psf(w, params=prm_), tgt)[0]
+
+    prm = P.params_of(sysm, requires_grad=True)
+    Lv = loss_of(prm)
+    Lv.backward()
+    scale = abs(float(Lv.detach()))
+    for name, si in (("n_after", 1), ("n_after", 3), ("c", 2)):
+        assert prm[si]["sellmeier"] is not None or name == "c"
+        g_ad = float(prm[si][name].grad)
+        h = 1e-6
+        vals = []
+        for sgn in (+1, -1):
+            p2 = P.params_of(sysm)
+            p2[si][name] = torch.tensor(float(prm[si][name]) + sgn * h, dtype=F64)
+            vals.append(float(loss_of(p2)))
+        g_fd = (vals[0] - vals[1]) / (2 * h)
+        assert g_ad == pytest.approx(g_fd, rel=2e-4, abs=1e-7 * scale), (name, si, g_ad, g_fd)
