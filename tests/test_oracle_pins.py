@@ -968,3 +968,112 @@ def test_oracle_dispersive_index_gradient_matches_central_differences():
             vals.append(float(loss_of(p2)))
         g_fd = (vals[0] - vals[1]) / (2 * h)
         assert g_ad == pytest.approx(g_fd, rel=2e-4, abs=1e-7 * scale), (name, si, g_ad, g_fd)
+
+
+# ------------------------------------------------------------------ conformal patch gather
+def _affine_map(H, W, p, alpha, beta, gamma):
+    """Amplitude alpha + beta x + gamma y at every pixel centre
+    ((c - W/2 + 1/2) p, (r - H/2 + 1/2) p)."""
+    xc = (np.arange(W) - W / 2 + 0.5) * p
+    yc = (np.arange(H) - H / 2 + 0.5) * p
+    return alpha + beta * xc[None, :] + gamma * yc[:, None]
+
+
+def test_bilinear_gather_reproduces_an_affine_map_on_a_sphere():
+    # Bilinear interpolation is exact on affine functions, so every tangent-plane
+    # sample P + s_a u + t_b v of an off-apex hit must read alpha + beta x + gamma y
+    # at its orthographic (x, y).  A half-pixel shift of the lookup, swapped tap
+    # weights or transposed sample axes all break the equality.
+    H = W = 96
+    p, D = 0.5e-3, 16
+    alpha, beta, gamma = 2.0, 31.0, -17.0
+    amp = torch.from_numpy(_affine_map(H, W, p, alpha, beta, gamma))
+    phi = torch.zeros(H, W, dtype=F64)
+    doe = R.DOE(phi=np.zeros((H, W), np.float32), pitch=p, D=D, kind=R.systems.CONFORMAL,
+                gather="bilinear")
+    s = G.surface_params(R.Surface(R.SPHERE, 0.0, c=1 / 0.4))
+    o = np.array([[3.1e-3, -4.7e-3, -0.1], [-5.3e-3, 2.2e-3, -0.1], [0.9e-3, 6.4e-3, -0.1]])
+    d = np.array([[0.05, -0.02, 1.0], [-0.1, 0.07, 1.0], [0.0, 0.0, 1.0]])
+    r = _ray(o, d)
+    t, ok = G.intersect(r["o"], r["d"], s)
+    assert bool(ok.all())
+    hit = r["o"] + t[:, None] * r["d"]
+    u, v, n = DO.frame(hit, s, r["d"])
+    T, s_off, t_off = DO.gather_bilinear(hit, u, v, phi, amp, 550e-6, doe)
+    off = (np.arange(D) - D // 2) * p
+    assert np.allclose(s_off.numpy(), off[None, :], atol=0)
+    h, uu, vv = hit.numpy(), u.numpy(), v.numpy()
+    for i in range(3):
+        # sample (b, a) sits at P + off[a] u + off[b] v
+        q = h[i][None, None, :] + off[None, :, None] * uu[i] + off[:, None, None] * vv[i]
+        ref = alpha + beta * q[..., 0] + gamma * q[..., 1]
+        assert np.abs(T[i].numpy() - ref).max() < 1e-12
+        # every tap lies on the map (not the zero fill outside it)
+        assert np.abs(q[..., :2]).max() < (H / 2 - 1) * p
+    # a half-pixel shift of the lookup would move every value by beta p / 2
+    assert abs(beta) * p / 2 > 1e-3
+
+
+def test_bilinear_gather_reads_pixel_centres_exactly_on_a_plane():
+    # Planar frame (u = x, v = y) with the hit on a pixel centre: every sample
+    # is a pixel centre, so the bilinear patch equals the map there, here a
+    # linear phase ramp exp(i kappa x_c) (not affine in the complex plane).
+    H = W = 64
+    p, D = 1e-3, 16
+    kappa = 2 * math.pi / (7.3 * p)
+    xc = (np.arange(W) - W / 2 + 0.5) * p
+    phi_np = np.broadcast_to(kappa * xc[None, :], (H, W)).copy()
+    phi = torch.from_numpy(phi_np)
+    doe = R.DOE(phi=phi_np.astype(np.float32), pitch=p, D=D, kind=R.systems.CONFORMAL,
+                gather="bilinear", phase_model="fixed")
+    s = G.surface_params(R.Surface(R.PLANE, 0.0))
+    c_hit, r_hit = 37, 21
+    o = np.array([[(c_hit - W / 2 + 0.5) * p, (r_hit - H / 2 + 0.5) * p, -0.2]])
+    r = _ray(o, np.array([[0.0, 0.0, 1.0]]))
+    t, ok = G.intersect(r["o"], r["d"], s)
+    hit = r["o"] + t[:, None] * r["d"]
+    u, v, n = DO.frame(hit, s, r["d"])
+    T, _, _ = DO.gather_bilinear(hit, u, v, phi, None, 550e-6, doe)
+    cols = c_hit + np.arange(D) - D // 2
+    ref = np.broadcast_to(np.exp(1j * kappa * xc[cols])[None, :], (D, D))
+    assert np.abs(T[0].numpy() - ref).max() < 1e-9
+    # the average of two neighbouring pixels (a half-pixel shift) is far off
+    half = 0.5 * (np.exp(1j * kappa * xc[cols]) + np.exp(1j * kappa * xc[cols + 1]))
+    assert np.abs(half - ref[0]).max() > 0.1
+
+
+# ------------------------------------------------------------------ coherent window
+def test_coherent_window_covers_the_hand_listed_pixels():
+    # 8 x 8 sensor, pitch 1 um, centre (0, 0): pixel (i, j) centre at
+    # ((i - 3.5) um, (j - 3.5) um).  The window of a ray is +-W pixels around
+    # its nearest pixel (continuous index u = x/pitch + 3.5 rounded half to
+    # even), inclusive, clipped to the sensor.  The sets below are written out
+    # by hand from the hit points.
+    nx = ny = 8
+    pitch = 1e-3
+    lam = 0.6e-3
+    um = 1e-3
+    hits = [(0.3 * um, -1.2 * um),    # u = 3.8 -> 4, v = 2.3 -> 2
+            (3.4 * um, 2.9 * um),     # u = 6.9 -> 7, v = 6.4 -> 6
+            (-1.0 * um, -3.4 * um)]   # u = 2.5 -> 2 (half to even), v = 0.1 -> 0
+    W = 1
+    listed = [({3, 4, 5}, {1, 2, 3}), ({6, 7}, {5, 6, 7}), ({1, 2, 3}, {0, 1})]
+    d = torch.tensor([[0.02, -0.01, 1.0], [-0.03, 0.015, 1.0], [0.0, 0.04, 1.0]], dtype=F64)
+    d = d / torch.linalg.norm(d, dim=-1, keepdim=True)
+    a = torch.tensor([1.0 + 0.5j, -0.3 + 0.8j, 0.6 - 0.2j], dtype=torch.complex128)
+    opl = torch.tensor([1.25, 1.2501, 1.2499], dtype=F64)
+    for k in range(3):
+        x = torch.tensor([hits[k][0]], dtype=F64)
+        y = torch.tensor([hits[k][1]], dtype=F64)
+        args = (x, y, opl[k:k + 1], d[k:k + 1], a[k:k + 1], torch.ones(1, dtype=torch.bool),
+                nx, ny, pitch, 0.0, 0.0, lam, 1.0)
+        fw = S.coherent_field(*args, window=W).reshape(ny, nx).numpy()
+        ff = S.coherent_field(*args, window=0).reshape(ny, nx).numpy()
+        cols, rows = listed[k]
+        mask = np.zeros((ny, nx), bool)
+        for j in rows:
+            for i in cols:
+                mask[j, i] = True
+        assert np.array_equal(fw != 0, mask)
+        assert np.abs(fw[mask] - ff[mask]).max() < 1e-15
+        assert np.all(np.abs(ff[mask]) > 0)
