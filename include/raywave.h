@@ -137,7 +137,11 @@ typedef struct {
     int32_t phase_model;   /* RW_PHASE_* */
     int32_t dft;           /* RW_DFT_*: TC only in rw_patch_spectra (fused calls: FFT32) */
     uint64_t seed;         /* Philox key for sampled mode */
-    uint64_t rng_offset;   /* Philox counter word 3 for sampled mode */
+    uint64_t rng_offset;   /* Philox counter word 3 for sampled mode: draw i of the
+                            * incident ray stored at index r of the ray arrays
+                            * perturbs bin j with word j & 3 of Philox4x32-10 at
+                            * counter (j >> 2, i, r, rng_offset), so a ray's draws do
+                            * not depend on how the job table groups the rays */
     int32_t pad;           /* zero-padding factor P (0 or 1: none): the D x D patch is
                             * transformed on M = P D points, M in {16, 32, 64, 96, 128};
                             * bins are k_j = 2 pi j / (M pitch), and U~ is scaled by
@@ -360,16 +364,18 @@ rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
  * device synchronisation of cudaMalloc.  (The paper has no counterpart;
  * this is a deployment interface.)
  *
- * Needs no context and allocates nothing: the job table is copied from a
- * stack buffer into a file-scope device array of the library sized for at
- * most 1024 jobs (about 64 KiB, held by every GPU that loads the library
- * until the process exits).  njob > 1024 returns RW_ECAPACITY; bad
+ * Needs no context and allocates nothing: the job table is built in a
+ * static host buffer (under a mutex; no large stack frame) and copied into a
+ * file-scope device array of the library sized for at most 1024 jobs (about
+ * 64 KiB, held by every GPU that loads the library until the process
+ * exits).  njob > 1024 returns RW_ECAPACITY before anything is written; bad
  * arguments return RW_EINVAL; a failing CUDA call returns RW_ECUDA.  Work is
  * enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy default stream)
- * of the CURRENT device.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make
- * that first call before any stream capture.  Every call shares the array
- * and rewrites the part it uses, so nothing needs clearing, but calls that
+ * of the CURRENT device; the array's device address is looked up on every
+ * call with that device current.  A call while `cuda_stream` is being
+ * captured into a graph returns RW_EINVAL: the upload reads a host buffer
+ * that later calls overwrite.  Every call shares the device array and
+ * rewrites the part it uses, so nothing needs clearing, but calls that
  * overlap on the GPU (different streams, no ordering) race on it. */
 rw_status rw_generate_rays_static(double z_start, double n_object, const rw_job* jobs,
                                   int32_t njob, rw_rays* rays, void* cuda_stream);

@@ -118,8 +118,11 @@ def psf_job(system, job, z_start, params, phi, amp, idx=None, ray_base=0, chunk=
     return img.reshape(ny, nx)
 
 
-def psf(workload, params=None, phi=None, amp=None, subsets=None, chunk=256, phi2=None):
-    """PSF stack [njob, ny, nx].  subsets[j] optionally lists ray indices of job j."""
+def psf(workload, params=None, phi=None, amp=None, subsets=None, chunk=256, phi2=None,
+        ray_bases=None):
+    """PSF stack [njob, ny, nx].  subsets[j] optionally lists ray indices of job j.
+    Ray i of job j has id ray_bases[j] + i in the sampling stream (default: the
+    rays of all jobs numbered consecutively in job order)."""
     system = workload.system
     if params is None:
         params = params_of(system)
@@ -130,7 +133,8 @@ def psf(workload, params=None, phi=None, amp=None, subsets=None, chunk=256, phi2
     for j, job in enumerate(workload.jobs):
         idx = None if subsets is None else subsets[j]
         pj = G.at_wavelength(params, job.lam)          # Sellmeier media at this job's lambda
-        out.append(psf_job(system, job, workload.z_start, pj, phi, amp, idx, base, chunk,
+        b0 = base if ray_bases is None else int(ray_bases[j])
+        out.append(psf_job(system, job, workload.z_start, pj, phi, amp, idx, b0, chunk,
                            phi2))
         base += job.n_rays
     return torch.stack(out, 0)

@@ -275,15 +275,12 @@ struct WaveGroups {
     std::vector<double> lambda;
     std::vector<std::vector<rw_job>> jobs;
     std::vector<std::vector<int>> out;        // job index in the caller's table
-    std::vector<std::vector<long long>> sid;  // ray id in the full table - ray id in the group
 };
 
 static rw_status group_by_wavelength(rw_ctx* ctx, const rw_job* jobs, int njob, WaveGroups& G) {
     if (njob < 1) return fail(ctx, RW_EINVAL, "njob must be >= 1");
     if (!jobs) return fail(ctx, RW_EINVAL, "jobs is NULL");
     std::map<double, int> index;
-    std::vector<long long> gprefix;
-    long long prefix = 0;
     for (int i = 0; i < njob; ++i) {
         auto it = index.find(jobs[i].lambda);
         int g;
@@ -293,16 +290,11 @@ static rw_status group_by_wavelength(rw_ctx* ctx, const rw_job* jobs, int njob, 
             G.lambda.push_back(jobs[i].lambda);
             G.jobs.emplace_back();
             G.out.emplace_back();
-            G.sid.emplace_back();
-            gprefix.push_back(0);
         } else {
             g = it->second;
         }
         G.jobs[g].push_back(jobs[i]);
         G.out[g].push_back(i);
-        G.sid[g].push_back(prefix - gprefix[g]);
-        gprefix[g] += jobs[i].ray_count;
-        prefix += jobs[i].ray_count;
     }
     return RW_OK;
 }
@@ -468,11 +460,9 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
     return RW_OK;
 }
 
-// outs[i]: image of job i in the psf / dL/dpsf arrays (default i); sids[i]: added
-// to the launch's ray ids in the sampling stream (default 0)
+// outs[i]: image of job i in the psf / dL/dpsf arrays (default i)
 static rw_status pack_jobs(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int njob,
-                           int64_t n_rays, Packed& P, const int* outs = nullptr,
-                           const long long* sids = nullptr) {
+                           int64_t n_rays, Packed& P, const int* outs = nullptr) {
     if (njob < 1) return fail(ctx, RW_EINVAL, "njob must be >= 1");
     if (!jobs) return fail(ctx, RW_EINVAL, "jobs is NULL");
     std::map<double, int> slot_of;
@@ -504,7 +494,6 @@ static rw_status pack_jobs(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs
         d.cy = (float)j.sensor_cy;
         d.slot = slot;
         d.out = outs ? outs[i] : i;
-        d.sid = sids ? sids[i] : 0;
         P.prefix[i + 1] = P.prefix[i] + j.ray_count;
     }
     P.total = P.prefix[njob];
@@ -712,25 +701,8 @@ rw_status rw_generate_rays(rw_ctx* ctx, double z_start, double n_object, const r
     if (!(n_object > 0)) return fail(ctx, RW_EINVAL, "n_object must be > 0");
     std::vector<GenJob> g(njob);
     std::vector<long long> prefix(njob + 1, 0);
-    for (int i = 0; i < njob; ++i) {
-        const rw_job& j = jobs[i];
-        if (j.grid_n < 0 || j.ray_count != j.grid_n * j.grid_n)
-            return fail(ctx, RW_EINVAL, "job ray_count must equal grid_n^2");
-        if (j.ray_offset < 0 || j.ray_offset + j.ray_count > rays->n)
-            return fail(ctx, RW_EINVAL, "job ray range outside the ray arrays");
-        const double tx = std::tan(j.theta_x), ty = std::tan(j.theta_y);
-        const double nrm = std::sqrt(tx * tx + ty * ty + 1.0);
-        g[i].off = j.ray_offset;
-        g[i].n = j.grid_n;
-        g[i].spacing = j.spacing;
-        g[i].x0 = j.x0;
-        g[i].y0 = j.y0;
-        g[i].dx = (float)(tx / nrm);
-        g[i].dy = (float)(ty / nrm);
-        g[i].dz = (float)(1.0 / nrm);
-        g[i].pad = 0.f;
-        prefix[i + 1] = prefix[i] + j.ray_count;
-    }
+    if (const char* why = gen_table_fill(jobs, njob, rays->n, g.data(), prefix.data()))
+        return fail(ctx, RW_EINVAL, why);
     if (prefix[njob] == 0) return RW_OK;
     std::vector<void*> ptrs;
     st = upload(ctx, {{g.data(), g.size() * sizeof(GenJob)},
@@ -1051,7 +1023,7 @@ static rw_status forward_dispersive(rw_ctx* ctx, const rw_system* sys, const rw_
         if ((st = system_at(ctx, sys, G.lambda[g], sg[g], surf[g])) != RW_OK) return st;
         if ((st = pack_system(ctx, &sg[g], P[g])) != RW_OK) return st;
         if ((st = pack_jobs(ctx, &sg[g], G.jobs[g].data(), (int)G.jobs[g].size(), rays->n, P[g],
-                            G.out[g].data(), G.sid[g].data())) != RW_OK)
+                            G.out[g].data())) != RW_OK)
             return st;
         total += P[g].total;
     }
@@ -1120,7 +1092,7 @@ static rw_status backward_dispersive(rw_ctx* ctx, const rw_system* sys, const rw
         if ((st = system_at(ctx, sys, G.lambda[g], sg[g], surf[g])) != RW_OK) return st;
         if ((st = pack_system(ctx, &sg[g], P[g])) != RW_OK) return st;
         if ((st = pack_jobs(ctx, &sg[g], G.jobs[g].data(), (int)G.jobs[g].size(), rays->n, P[g],
-                            G.out[g].data(), G.sid[g].data())) != RW_OK)
+                            G.out[g].data())) != RW_OK)
             return st;
         if (P[g].sys.M > 96 || backward_smem_needed(P[g].sys) > (size_t)lim)
             return fail(ctx, RW_EINVAL, "patch size / n_ssr too large for the fused adjoint's "

@@ -34,9 +34,16 @@
 #include "rw_bwd_common.cuh"
 
 // ------------------------------------------------------------------ sampled
-// Shared scratch of the sampled adjoint (after the exhaustive layout).
+// Shared scratch of the sampled adjoint (after the patch, the tile's incident
+// states and the per-ray reduction buffers; dL/dX overwrites X in place):
+//   rec[M*M]  float2: (p_j, kn_j), later (p_j, dL/dlog p_j)
+//   sel[N]    chosen bin per draw
+//   sa[N], sb[N] float4, sc2[N] float2: per-draw sums, then h~ and c~
+//   hU[N]     float2: hard-path dL/dU~ of the draw's bin
+//   red[64]
 __host__ __device__ inline size_t sampled_bwd_bytes(int M, int N) {
-    return (size_t)M * M * (4 + 8 + 4) + (size_t)N * (4 + 4 + 4 + 8 + 12 + 4) + 64 * 4;
+    const size_t n4 = ((size_t)N + 3) & ~size_t(3);
+    return (size_t)M * M * 8 + n4 * 4 + (size_t)N * (16 + 16 + 8 + 8) + 64 * 4;
 }
 
 // Block-wide sum (all threads get the result); `red` holds >= 8 floats.
@@ -50,121 +57,252 @@ __device__ __forceinline__ float block_sum(float v, float* red) {
     return t;
 }
 
-// Gumbel noise g = -log(-log u) of the four bins 4G..4G+3 of draw i.
-__device__ __forceinline__ void gumbel_group(const DSys& sys, long long gid, int i, int G,
-                                             float* g4) {
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)i, (uint32_t)gid,
-                                             (uint32_t)sys.rng_offset),
-                                  (uint32_t)(sys.seed & 0xffffffffull), (uint32_t)(sys.seed >> 32));
-    g4[0] = -logf(-logf(u01(w.x)));
-    g4[1] = -logf(-logf(u01(w.y)));
-    g4[2] = -logf(-logf(u01(w.z)));
-    g4[3] = -logf(-logf(u01(w.w)));
+// X[.] position of bin f (natural order) in the FFT output (row stride M + 1).
+template <int M>
+__device__ __forceinline__ int xpos(int f) {
+    const int jvi = f / M, jui = f - (f / M) * M;
+    int mu = jui + M / 2; if (mu >= M) mu -= M;
+    int mv = jvi + M / 2; if (mv >= M) mv -= M;
+    return mv * Patch<M>::S + mu;
 }
 
+// Pass A of the sampled adjoint (see sampled_ray_adjoint): lane = draw, the
+// warp's 32 draws walk the bins in step (per-bin records and weights are
+// broadcast reads), two Philox blocks per step; the t-weighted sums are
+// straight-line code and the rare screening candidates are scored after
+// them.  Not inlined, so that the loop has registers of its own.
+template <int M>
+__device__ __noinline__ void gumbel_pass_a(const float2* __restrict__ rec,
+                                           const float2* __restrict__ X, int* __restrict__ sel,
+                                           float4* __restrict__ sa, float4* __restrict__ sb,
+                                           int N, uint32_t ray, uint32_t off, uint32_t k0,
+                                           uint32_t k1) {
+    constexpr int NG = M * M / 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i0 = warp * 32; i0 < N; i0 += RW_THREADS) {
+        const uint32_t i = (uint32_t)(i0 + lane);
+        float Z = 0.f, Su = 0.f, Sv = 0.f, Sn = 0.f, Sr = 0.f, Si = 0.f;
+        float best = -INFINITY;
+        int bj = 0x7fffffff;
+        for (int G = 0; G < NG; G += 2) {
+            const uint4 wa = philox4x32_10(make_uint4((uint32_t)G, i, ray, off), k0, k1);
+            const uint4 wb = philox4x32_10(make_uint4((uint32_t)G + 1u, i, ray, off), k0, k1);
+            const uint32_t ws[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+            const int f0 = 4 * G;                       // 8 bins of one row (8 | M)
+            const int jv = f0 / M, ju0 = f0 - jv * M;
+            const int xb = xpos<M>(f0);
+            float z8 = 0.f, zq = 0.f;
+            unsigned mask = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 pk = rec[f0 + q];
+                const float2 wt = X[xb + q];
+                const float E = gumbel_E_fast(ws[q]);
+                const float t = pk.x * rcp_approx(E);
+                z8 += t;
+                zq = fmaf((float)q, t, zq);
+                Sn = fmaf(t, pk.y, Sn);
+                Sr = fmaf(t, wt.x, Sr);
+                Si = fmaf(t, wt.y, Si);
+                mask |= (unsigned)(pk.x > 0.f && E < fmaf(RW_GUMBEL_TAU * 1.001f, pk.x, 1e-6f)) << q;
+            }
+            Z += z8;
+            Su += fmaf((float)(ju0 - M / 2), z8, zq);
+            Sv = fmaf((float)(jv - M / 2), z8, Sv);
+            if (mask) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    if ((mask >> q) & 1u)
+                        gumbel_keep(gumbel_score(rec[f0 + q].x, ws[q]), f0 + q, best, bj);
+            }
+        }
+        if ((int)i < N) {
+            if (!(best > RW_GUMBEL_FLOOR)) {
+                best = -INFINITY;
+                bj = 0x7fffffff;
+                gumbel_full_scan<M, 2>(reinterpret_cast<const float*>(rec), i, ray, off, k0, k1,
+                                       best, bj);
+            }
+            sel[i] = best > -INFINITY ? bj : -1;
+            sa[i] = make_float4(Z, Su, Sv, Sn);
+            sb[i] = make_float4(Sr, Si, 0.f, 0.f);
+        }
+    }
+}
+
+// Pass B of the sampled adjoint: a lane owns a group of 4 bins (KS lanes
+// share one when there are fewer groups than threads) and walks the draws,
+// two Philox blocks per step, accumulating e_ij h~_i and e_ij c~_i; then
+// recf[2 j + 1] = dL/dlog p_j.  Not inlined, like pass A.
+template <int M>
+__device__ __noinline__ void gumbel_pass_b(float* __restrict__ recf, const float2* __restrict__ X,
+                                           const int* __restrict__ sel,
+                                           const float4* __restrict__ sa,
+                                           const float2* __restrict__ sc2, int N, uint32_t ray,
+                                           uint32_t off, uint32_t k0, uint32_t k1, float kin_u,
+                                           float kin_v, float ks) {
+    constexpr int NG = M * M / 4;
+    constexpr int KS = NG >= RW_THREADS ? 1 : RW_THREADS / NG;     // lanes per bin group
+    static_assert(KS <= 32 && (KS & (KS - 1)) == 0, "lanes per group: a power of two <= 32");
+    for (int tt = threadIdx.x; tt < NG * KS; tt += RW_THREADS) {
+        const int G = tt / KS, s0 = tt - (tt / KS) * KS;
+        float a4[4][6];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) a4[q][k] = 0.f;
+        // draws whose bin is -1 carry h~ = c~ = 0: no test needed
+        int i = s0;
+        for (; i + KS < N; i += 2 * KS) {
+            const uint4 wa = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)i, ray, off), k0, k1);
+            const uint4 wb = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)(i + KS), ray, off),
+                                           k0, k1);
+            const float4 ha = sa[i], hb = sa[i + KS];
+            const float2 h2a = sc2[i], h2b = sc2[i + KS];
+            const uint32_t wsa[4] = {wa.x, wa.y, wa.z, wa.w};
+            const uint32_t wsb[4] = {wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float ea = rcp_approx(gumbel_E_fast(wsa[q]));
+                const float eb = rcp_approx(gumbel_E_fast(wsb[q]));
+                a4[q][0] = fmaf(eb, hb.x, fmaf(ea, ha.x, a4[q][0]));
+                a4[q][1] = fmaf(eb, hb.y, fmaf(ea, ha.y, a4[q][1]));
+                a4[q][2] = fmaf(eb, hb.z, fmaf(ea, ha.z, a4[q][2]));
+                a4[q][3] = fmaf(eb, hb.w, fmaf(ea, ha.w, a4[q][3]));
+                a4[q][4] = fmaf(eb, h2b.x, fmaf(ea, h2a.x, a4[q][4]));
+                a4[q][5] = fmaf(eb, h2b.y, fmaf(ea, h2a.y, a4[q][5]));
+            }
+        }
+        for (; i < N; i += KS) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)i, ray, off), k0, k1);
+            const float4 h = sa[i];
+            const float2 h2 = sc2[i];
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float e = rcp_approx(gumbel_E_fast(ws[q]));
+                a4[q][0] = fmaf(e, h.x, a4[q][0]);
+                a4[q][1] = fmaf(e, h.y, a4[q][1]);
+                a4[q][2] = fmaf(e, h.z, a4[q][2]);
+                a4[q][3] = fmaf(e, h.w, a4[q][3]);
+                a4[q][4] = fmaf(e, h2.x, a4[q][4]);
+                a4[q][5] = fmaf(e, h2.y, a4[q][5]);
+            }
+        }
+        if (KS > 1) {
+#pragma unroll
+            for (int o = 1; o < KS; o <<= 1)
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int k = 0; k < 6; ++k)
+                        a4[q][k] += __shfl_xor_sync(0xffffffffu, a4[q][k], o);
+        }
+        if (s0 == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int f = 4 * G + q;
+                const int jvi = f / M, jui = f - (f / M) * M;
+                const float pj = recf[2 * f];
+                float gl = 0.f;
+                if (pj > 0.f) {
+                    const float2 w = X[xpos<M>(f)];
+                    const float ku = kin_u + ks * (float)(jui - M / 2);
+                    const float kv = kin_v + ks * (float)(jvi - M / 2);
+                    gl = pj * (a4[q][0] * w.x + a4[q][1] * w.y + a4[q][2] * ku + a4[q][3] * kv +
+                               a4[q][4] * recf[2 * f + 1] - a4[q][5]);
+                }
+                recf[2 * f + 1] = gl;
+            }
+        }
+    }
+}
+
+// Straight-through Gumbel-softmax adjoint of one incident ray (temperature 1).
+// Draw i's relaxed one-hot is soft_ij = t_ij / Z_i with t_ij = p_j / E_ij,
+// E_ij = -log u_ij (exp of the perturbed score log p_j + g_ij) and
+// Z_i = sum_j t_ij.  With G_ij = dL/dy_ij = Re(conj(q_i) w_j) + gd_i . dir_j
+// (q_i = conj(a_in) dL/da_i, w_j = U~_j sc(p_j) the bin's weight, gd_i = dL/dd_i)
+// the softmax Jacobian gives
+//   dL/dlog p_j = sum_i soft_ij (G_ij - c_i),   c_i = sum_k soft_ik G_ik,
+// and because G is bilinear in (q_i, gd_i) and (w_j, dir_j), with
+// dir_j = (kappa_u u + kappa_v v + kn_j n) / K and kappa affine in the bin
+// index, both sums are two passes of six accumulators over the (draw, bin)
+// pairs:
+//   pass A, per draw (the 32 lanes of a warp are 32 draws walking the bins
+//     in step): Z_i and the t-weighted sums of j_u, j_v, kn_j, w_j -> c_i,
+//     together with the screened argmax (the forward's draw);
+//   pass B, per bin (a lane owns 4 bins and walks the draws):
+//     H_j = sum_i e_ij h~_i and C_j = sum_i e_ij c~_i, e = 1/E,
+//     h~_i = (q_i, gd_i.u/K, gd_i.v/K, gd_i.n/K) / Z_i, c~_i = c_i / Z_i,
+//     dL/dlog p_j = p_j (<H_j, (w_j, kappa_u, kappa_v, kn_j)> - C_j).
+// No soft value is stored and no atomic is issued per pair.
 template <int M, int NS, bool COH>
 __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAtDoe& R,
                                                     float k0, long long stream,
-                                                    const float2* X, const float2* phu,
+                                                    float2* X, const float2* phu,
                                                     const float2* phv,
                                                     const float* __restrict__ gimg,
-                                                    const float2* __restrict__ gf, float2* G,
+                                                    const float2* __restrict__ gf,
                                                     unsigned char* scr, float* acc,
                                                     SurfGrads<NS>& SG, float* gs,
                                                     unsigned* status) {
     constexpr int NB = M * M;
+    constexpr int NG = NB / 4;
     constexpr int S_ = Patch<M>::S;
     const int N = sys.n_ssr;
     const float norm = sys.norm;
-    float* logp = reinterpret_cast<float*>(scr);
-    float2* gwb = reinterpret_cast<float2*>(logp + NB);
-    float* glogp = reinterpret_cast<float*>(gwb + NB);
-    int* sel = reinterpret_cast<int*>(glogp + NB);
-    float* mx = reinterpret_cast<float*>(sel + N);
-    float* zs = mx + N;
-    float2* ga = reinterpret_cast<float2*>(zs + N);
-    float* gd = reinterpret_cast<float*>(ga + N);
-    float* cdot = gd + 3 * N;
-    float* red = cdot + N;
+    float2* rec = reinterpret_cast<float2*>(scr);
+    float* recf = reinterpret_cast<float*>(rec);
+    int* sel = reinterpret_cast<int*>(rec + NB);
+    float4* sa = reinterpret_cast<float4*>(sel + ((N + 3) & ~3));
+    float4* sb = sa + N;
+    float2* sc2 = reinterpret_cast<float2*>(sb + N);
+    float2* hU = sc2 + N;
+    float* red = reinterpret_cast<float*>(hU + N);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float2 ain = make_float2(R.a_re, R.a_im);
-    // ---- weights m = |U~|^2 (|U~| coherent) over propagating bins, p = m / S
-    float part = 0.f;
-    for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
-        const int jvi = f / M, jui = f - (f / M) * M;
-        float dx, dy, dz;
-        float m = 0.f;
-        if (bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
-            const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
-            m = U.x * U.x + U.y * U.y;
-            if (COH) m = sqrtf(m);
-            if (sys.uniform) m = 1.f;
-        }
-        logp[f] = m;
-        gwb[f] = make_float2(0.f, 0.f);
-        glogp[f] = 0.f;
-        part += m;
-    }
-    const float S = block_sum(part, red);
+    const float sN = COH ? (float)N : sqrtf((float)N);
+    constexpr float EXPO = COH ? -1.f : -0.5f;       // d log sc / d log p
+    // ---- p_j (shared with the forward), kn_j, and X <- w~_j = U~_j sc(p_j) in place
+    const float S = sampled_probs<M, 2>(sys, R, X, phu, phv, recf, red);
     const float iS = S > 0.f ? 1.f / S : 0.f;
     for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
-        const float p = logp[f] * iS;
-        logp[f] = p > 0.f ? logf(p) : -INFINITY;
+        const int jvi = f / M, jui = f - (f / M) * M;
+        const float pj = recf[2 * f];
+        const float ku = R.kin_u + sys.kstep * (float)(jui - M / 2);
+        const float kv = R.kin_v + sys.kstep * (float)(jvi - M / 2);
+        const float kt2 = ku * ku + kv * kv, K2 = R.K * R.K;
+        recf[2 * f + 1] = kt2 < K2 ? sqrtf(K2 - kt2) : 0.f;
+        float2 w = make_float2(0.f, 0.f);
+        if (pj > 0.f) {
+            const float sc = COH ? 1.f / (N * pj) : rsqrtf(N * pj);
+            w = cscale(spectrum_at<M>(X, phu, phv, jui, jvi, norm), sc);
+        }
+        X[xpos<M>(f)] = w;
     }
     __syncthreads();
-    // ---- draws: argmax, running max and partition function (warp per draw)
-    for (int i = warp; i < N; i += RW_THREADS / 32) {
-        float best = -INFINITY, z = 0.f;
-        int bj = 0x7fffffff;
-        for (int Gq = lane; Gq * 4 < NB; Gq += 32) {
-            float g4[4];
-            gumbel_group(sys, stream, i, Gq, g4);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int jb = 4 * Gq + q;
-                if (jb < NB && logp[jb] > -INFINITY) {
-                    const float sc = logp[jb] + g4[q];
-                    if (sc > best) {
-                        z = (best > -INFINITY ? z * __expf(best - sc) : 0.f) + 1.f;
-                        best = sc;
-                        bj = jb;
-                    } else {
-                        z += __expf(sc - best);
-                        if (sc == best && jb < bj) bj = jb;
-                    }
-                }
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const float oz = __shfl_xor_sync(0xffffffffu, z, o);
-            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-            const float nb = fmaxf(best, ob);
-            const float nz = (best > -INFINITY ? z * __expf(best - nb) : 0.f) +
-                             (ob > -INFINITY ? oz * __expf(ob - nb) : 0.f);
-            if (ob > best || (ob == best && oj < bj)) bj = oj;
-            best = nb;
-            z = nz;
-        }
-        if (lane == 0) { sel[i] = best > -INFINITY ? bj : -1; mx[i] = best; zs[i] = z; }
-    }
+    const uint32_t k0w = (uint32_t)(sys.seed & 0xffffffffull), k1w = (uint32_t)(sys.seed >> 32);
+    const uint32_t ray = (uint32_t)stream, off = (uint32_t)sys.rng_offset;
+    // ---- pass A: per draw, the forward's screened argmax and the t-weighted sums
+    gumbel_pass_a<M>(rec, X, sel, sa, sb, N, ray, off, k0w, k1w);
     __syncthreads();
-    // ---- every draw: trace + reverse of its (hard) secondary ray
-    // weight scale sc(p) = 1 / sqrt(N p) (incoherent) or 1 / (N p) (coherent)
-    const float sqN = sqrtf((float)N);
-    constexpr float EXPO = COH ? -1.f : -0.5f;       // d log sc / d log p
-    const float sN = COH ? (float)N : sqN;
+    // ---- every draw: trace + reverse of its (hard) secondary ray; h~, c~ and
+    // the hard path's dL/dU~ of its bin
+    const float ks = sys.kstep;
+    float sgp = 0.f;
     for (int i = threadIdx.x; i < N; i += RW_THREADS) {
         const int jb = sel[i];
-        float2 g_a = make_float2(0.f, 0.f);
+        float2 q = make_float2(0.f, 0.f);
         float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+        float2 hu = make_float2(0.f, 0.f);
         if (jb >= 0) {
             const int jvi = jb / M, jui = jb - (jb / M) * M;
             float dx, dy, dz;
             if (bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
-                const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
-                const float sc = __expf(EXPO * logp[jb]) / sN;
-                const float2 a = cscale(cmul(ain, U), sc);
+                const float2 w = X[xpos<M>(jb)];
+                const float2 a = cmul(ain, w);
+                float2 g_a = make_float2(0.f, 0.f);
                 float gx, gy, gz;
                 bool hit;
                 if constexpr (COH) {
@@ -173,108 +311,102 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
                                                 gdx, gdy, gdz, gopl, gs, status);
                     if (hit) acc[6] += gopl;
                 } else {
-                    const float w = a.x * a.x + a.y * a.y;
+                    const float wi = a.x * a.x + a.y * a.y;
                     float gw;
-                    hit = secondary_adjoint<NS>(sys, R, gimg, dx, dy, dz, w, gw, gx, gy, gz, gdx,
+                    hit = secondary_adjoint<NS>(sys, R, gimg, dx, dy, dz, wi, gw, gx, gy, gz, gdx,
                                                 gdy, gdz, SG, gs, status);
                     if (hit) g_a = make_float2(2.f * a.x * gw, 2.f * a.y * gw);
                 }
                 if (hit) {
                     emission_adjoint(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz, gx, gy, gz,
                                      gdx, gdy, gdz, acc);
-                    // hard path: a = a_in w_jb  ->  dL/dw_jb += conj(a_in) dL/da
-                    const float2 gwv = cmulc(g_a, ain);
-                    atomicAdd(&gwb[jb].x, gwv.x);
-                    atomicAdd(&gwb[jb].y, gwv.y);
+                    // hard path: a = a_in w_jb  ->  dL/dw_jb = conj(a_in) dL/da
+                    q = cmulc(g_a, ain);
+                    const float pj = recf[2 * jb];
+                    const float sc = COH ? 1.f / (N * pj) : rsqrtf(N * pj);
+                    const float2 U = cscale(w, 1.f / sc);
+                    const float gpw = EXPO * (q.x * w.x + q.y * w.y);   // dL/dlog p via sc(p)
+                    sgp += gpw;
+                    const float dm = sys.uniform ? 0.f : (COH ? 1.f / (pj * S) : 2.f);
+                    const float gm = gpw / pj * iS;
+                    hu = make_float2(U.x * dm * gm + q.x * sc, U.y * dm * gm + q.y * sc);
+                    if (COH && !sys.conformal) {
+                        const float im = hu.x * U.y - hu.y * U.x;          // Im(conj(gU) U)
+                        acc[0] -= ks * (float)(jui - M / 2) * im;
+                        acc[1] -= ks * (float)(jvi - M / 2) * im;
+                    }
                 } else {
-                    g_a = make_float2(0.f, 0.f);
                     gdx = gdy = gdz = 0.f;
                 }
             }
         }
-        ga[i] = g_a;
-        gd[3 * i] = gdx; gd[3 * i + 1] = gdy; gd[3 * i + 2] = gdz;
-    }
-    __syncthreads();
-    // ---- soft path: dL/dlogp_j += sum_i soft_ij (g_y_ij - sum_k soft_ik g_y_ik)
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int i = warp; i < N; i += RW_THREADS / 32) {
-            if (sel[i] < 0) continue;
-            const float2 gai = ga[i];
-            const float gdi0 = gd[3 * i], gdi1 = gd[3 * i + 1], gdi2 = gd[3 * i + 2];
-            if (gai.x == 0.f && gai.y == 0.f && gdi0 == 0.f && gdi1 == 0.f && gdi2 == 0.f) {
-                if (pass == 0 && lane == 0) cdot[i] = 0.f;
-                continue;
-            }
-            const float iz = 1.f / zs[i], mxi = mx[i];
-            const float ci = pass ? cdot[i] : 0.f;
-            float accd = 0.f;
-            for (int Gq = lane; Gq * 4 < NB; Gq += 32) {
-                float g4[4];
-                gumbel_group(sys, stream, i, Gq, g4);
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int jb = 4 * Gq + q;
-                    if (jb >= NB || !(logp[jb] > -INFINITY)) continue;
-                    const float soft = __expf(logp[jb] + g4[q] - mxi) * iz;
-                    const int jvi = jb / M, jui = jb - (jb / M) * M;
-                    float dx, dy, dz;
-                    bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz);
-                    const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
-                    const float2 aw = cscale(cmul(ain, U), __expf(EXPO * logp[jb]) / sN);
-                    const float gy = gai.x * aw.x + gai.y * aw.y + gdi0 * dx + gdi1 * dy + gdi2 * dz;
-                    if (pass == 0) accd += soft * gy;
-                    else atomicAdd(&glogp[jb], soft * (gy - ci));
-                }
-            }
-            if (pass == 0) {
-                for (int o = 16; o > 0; o >>= 1) accd += __shfl_xor_sync(0xffffffffu, accd, o);
-                if (lane == 0) cdot[i] = accd;
-            }
+        const float4 A = sa[i];
+        const float Z = jb >= 0 ? A.x : 0.f;
+        float4 h = make_float4(0.f, 0.f, 0.f, 0.f);
+        float2 h2 = make_float2(0.f, 0.f);
+        if (jb >= 0 && Z > 0.f) {
+            const float2 B = make_float2(sb[i].x, sb[i].y);
+            const float gdu = gdx * R.u[0] + gdy * R.u[1] + gdz * R.u[2];
+            const float gdv = gdx * R.v[0] + gdy * R.v[1] + gdz * R.v[2];
+            const float gdn = gdx * R.n[0] + gdy * R.n[1] + gdz * R.n[2];
+            const float iZ = 1.f / Z, iK = R.invK;
+            const float zc = q.x * B.x + q.y * B.y +
+                             (gdu * fmaf(ks, A.y, R.kin_u * Z) + gdv * fmaf(ks, A.z, R.kin_v * Z) +
+                              gdn * A.w) * iK;
+            h = make_float4(q.x * iZ, q.y * iZ, gdu * iK * iZ, gdv * iK * iZ);
+            h2 = make_float2(gdn * iK * iZ, zc * iZ * iZ);
         }
-        __syncthreads();
+        sa[i] = h;
+        sc2[i] = h2;
+        hU[i] = hu;
     }
-    // ---- p = m / S, w = U~ sc(p), m = |U~|^2 or |U~|  ->  dL/dU~  ->  dL/dX
-    float sg = 0.f, sgp = 0.f;
-    for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
-        if (!(logp[f] > -INFINITY)) continue;
-        const int jvi = f / M, jui = f - (f / M) * M;
-        const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
-        const float2 w = cscale(U, __expf(EXPO * logp[f]) / sN);
-        const float2 gwv = gwb[f];
-        // dL/dp from w (times p)
-        sgp += EXPO * (gwv.x * w.x + gwv.y * w.y);
-        sg += glogp[f];
-    }
-    const float Sg = block_sum(sg, red);
     const float Sgp = block_sum(sgp, red);
+    // ---- pass B: per bin, the draws' softmax weights against h~ and c~ (the
+    // uniform density does not depend on U~: no soft path)
+    if (!sys.uniform)
+        gumbel_pass_b<M>(recf, X, sel, sa, sc2, N, ray, off, k0w, k1w, R.kin_u, R.kin_v, ks);
+    __syncthreads();
+    float sg = 0.f;
+    if (!sys.uniform)
+        for (int f = threadIdx.x; f < NB; f += RW_THREADS) sg += recf[2 * f + 1];
+    const float Sg = block_sum(sg, red);
+    // ---- soft chain p = m / S, m = |U~|^2 (|U~| coherent, 1 uniform) -> dL/dU~,
+    // written as dL/dX = conj(phase) norm dL/dU~ over X in place
     for (int f = threadIdx.x; f < NB; f += RW_THREADS) {
         const int jvi = f / M, jui = f - (f / M) * M;
-        int mu = jui + M / 2; if (mu >= M) mu -= M;
-        int mv = jvi + M / 2; if (mv >= M) mv -= M;
+        const int xp = xpos<M>(f);
+        const float pj = recf[2 * f];
         float2 gU = make_float2(0.f, 0.f);
-        if (logp[f] > -INFINITY) {
-            const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
-            const float p = __expf(logp[f]);
-            const float m = p * S;
-            const float isq = __expf(EXPO * logp[f]) / sN;
-            const float2 w = cscale(U, isq);
-            const float2 gwv = gwb[f];
-            const float gp = EXPO * (gwv.x * w.x + gwv.y * w.y) / p;
-            // logp = log m - log S ; p = m / S
-            const float gm = glogp[f] / m - Sg * iS + gp * iS - Sgp * iS;
-            // dm/dU~: 2 U~ (m = |U~|^2), U~ / m (m = |U~|), 0 (uniform: m = 1)
-            const float dm = sys.uniform ? 0.f : (COH ? 1.f / m : 2.f);
-            gU = make_float2(U.x * dm * gm + gwv.x * isq, U.y * dm * gm + gwv.y * isq);
+        if (pj > 0.f && !sys.uniform) {
+            const float sc = COH ? 1.f / (N * pj) : rsqrtf(N * pj);
+            const float2 U = cscale(X[xp], 1.f / sc);
+            const float m = pj * S;
+            const float gm = recf[2 * f + 1] / m - (Sg + Sgp) * iS;
+            const float dm = COH ? 1.f / m : 2.f;
+            gU = make_float2(U.x * dm * gm, U.y * dm * gm);
             if (COH && !sys.conformal) {
-                const float im = gU.x * U.y - gU.y * U.x;          // Im(conj(gU) U)
-                acc[0] -= sys.kstep * (float)(jui - M / 2) * im;
-                acc[1] -= sys.kstep * (float)(jvi - M / 2) * im;
+                const float im = gU.x * U.y - gU.y * U.x;
+                acc[0] -= ks * (float)(jui - M / 2) * im;
+                acc[1] -= ks * (float)(jvi - M / 2) * im;
             }
         }
         const float2 ph = cmul(phu[jui], phv[jvi]);
-        G[mv * S_ + mu] = cscale(cmulc(gU, ph), norm);
+        X[xp] = cscale(cmulc(gU, ph), norm);
     }
+    __syncthreads();
+    // ---- hard path of every draw into its bin
+    for (int i = threadIdx.x; i < N; i += RW_THREADS) {
+        const int jb = sel[i];
+        const float2 hu = hU[i];
+        if (jb < 0 || (hu.x == 0.f && hu.y == 0.f)) continue;
+        const int jvi = jb / M, jui = jb - (jb / M) * M;
+        const float2 ph = cmul(phu[jui], phv[jvi]);
+        const float2 gx = cscale(cmulc(hu, ph), norm);
+        float2* dst = X + xpos<M>(jb);
+        atomicAdd(&dst->x, gx.x);
+        atomicAdd(&dst->y, gx.y);
+    }
+    __syncthreads();
 }
 
 // Coherent sensor: reverse of exhaustive bin f; writes its dL/dX.
@@ -364,8 +496,11 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
     float2* phu = tw + M;
     float2* phv = phu + M;
     RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + M);
-    float2* G = reinterpret_cast<float2*>(smem + sampled_scratch_offset(M));
-    BwdRay* bray = reinterpret_cast<BwdRay*>(G + Patch<M>::ELEMS);
+    // sampled emission writes dL/dX over X in place; exhaustive keeps X and dL/dX apart
+    const bool smp = sys.emit != RW_EMIT_EXHAUSTIVE;
+    float2* G = smp ? X : reinterpret_cast<float2*>(smem + sampled_scratch_offset(M));
+    BwdRay* bray = reinterpret_cast<BwdRay*>(smem + sampled_scratch_offset(M) +
+                                             (smp ? 0 : sizeof(float2) * Patch<M>::ELEMS));
     float* red = reinterpret_cast<float*>(bray + RW_TILE);   // [8 warps][9]
     unsigned char* sscr = reinterpret_cast<unsigned char*>(red + 9 * (RW_THREADS / 32));
     fft_twiddles<M>(tw);
@@ -456,8 +591,8 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                                                status);
                 }
             } else {
-                sampled_ray_adjoint<M, NS, COH>(sys, R, J.k0, R.gid + J.sid, X, phu, phv, gimg,
-                                                gf, G, sscr, acc, SG, gs, status);
+                sampled_ray_adjoint<M, NS, COH>(sys, R, J.k0, R.rid, X, phu, phv, gimg,
+                                                gf, sscr, acc, SG, gs, status);
             }
             // ---- per-ray reduction of the geometric gradients
 #pragma unroll
@@ -601,9 +736,10 @@ k_coh_incident(const DSys sys, const DJob* __restrict__ jobs, const long long* _
 }
 
 inline size_t backward_smem_bytes(int M, int emit, int n_ssr) {
-    size_t b = sampled_scratch_offset(M) + sizeof(float2) * (size_t)M * (M + 2) +
-               sizeof(BwdRay) * RW_TILE + sizeof(float) * 9 * (RW_THREADS / 32);
-    if (emit == RW_EMIT_SAMPLED) b += sampled_bwd_bytes(M, n_ssr);
+    size_t b = sampled_scratch_offset(M) + sizeof(BwdRay) * RW_TILE +
+               sizeof(float) * 9 * (RW_THREADS / 32);
+    if (emit == RW_EMIT_SAMPLED) b += sampled_bwd_bytes(M, n_ssr);   // dL/dX over X
+    else b += sizeof(float2) * (size_t)M * (M + 2);
     size_t red = sizeof(double) * RW_MAXS * RW_NGRAD * (RW_THREADS / 32);
     return b > red ? b : red;
 }

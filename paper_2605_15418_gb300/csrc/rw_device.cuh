@@ -84,7 +84,6 @@ struct DJob {
     float cx, cy;
     int slot;          // wavelength slot of the transmission map
     int out;           // index of the job's image in the psf / dL/dpsf arrays
-    long long sid;     // added to the launch's ray id in the sampling stream
 };
 
 // Incident ray state at the DOE (one per incident ray of a tile).
@@ -101,7 +100,8 @@ struct RayAtDoe {
     float s0, t0;           // nearest: offset of sample 0 from the hit / (M p);
                             // bilinear: fractional pixel coordinate of the hit
     float cx, cy;           // sensor window centre of the job
-    long long gid;          // global incident ray id (sampling stream)
+    long long gid;          // position of the ray in the launch's job order
+    long long rid;          // index of the ray in the caller's ray arrays: its sampling stream
 };
 
 struct RaysIn {

@@ -1,6 +1,8 @@
 // Per-incident-ray building blocks shared by the forward, emit and adjoint
 // kernels, plus the host-side launcher declarations.
 #pragma once
+#include <cmath>
+
 #include "rw_device.cuh"
 #include "rw_fast.cuh"
 #include "rw_fft.cuh"
@@ -42,6 +44,35 @@ struct GenJob {
     double spacing, x0, y0;
     float dx, dy, dz, pad;
 };
+
+// Host side of A0: check every job against n_rays and fill g[0..njob) and
+// prefix[0..njob] (exclusive prefix sum of the ray counts).  Returns nullptr,
+// or the reason the jobs are invalid.  Shared by rw_generate_rays and its
+// allocation-free variant so that both build the same table.
+inline const char* gen_table_fill(const rw_job* jobs, int njob, long long n_rays, GenJob* g,
+                                  long long* prefix) {
+    prefix[0] = 0;
+    for (int i = 0; i < njob; ++i) {
+        const rw_job& j = jobs[i];
+        if (j.grid_n < 0 || j.ray_count != j.grid_n * j.grid_n)
+            return "job ray_count must equal grid_n^2";
+        if (j.ray_offset < 0 || j.ray_offset + j.ray_count > n_rays)
+            return "job ray range outside the ray arrays";
+        const double tx = std::tan(j.theta_x), ty = std::tan(j.theta_y);
+        const double nrm = std::sqrt(tx * tx + ty * ty + 1.0);
+        g[i].off = j.ray_offset;
+        g[i].n = j.grid_n;
+        g[i].spacing = j.spacing;
+        g[i].x0 = j.x0;
+        g[i].y0 = j.y0;
+        g[i].dx = (float)(tx / nrm);
+        g[i].dy = (float)(ty / nrm);
+        g[i].dz = (float)(1.0 / nrm);
+        g[i].pad = 0.f;
+        prefix[i + 1] = prefix[i] + j.ray_count;
+    }
+    return nullptr;
+}
 
 // Work list of visible secondary rays of the split adjoint (and the forward's
 // tape of it): per incident ray its state at the DOE and its items, each item
@@ -90,7 +121,8 @@ __host__ __device__ inline size_t cull_scratch_bytes(int M) {
 }
 inline size_t forward_smem_bytes(int M, int emit = RW_EMIT_EXHAUSTIVE, int n_ssr = 0) {
     size_t b = sampled_scratch_offset(M);
-    if (emit == RW_EMIT_SAMPLED) b += sizeof(float) * (size_t)M * M + sizeof(int) * n_ssr + 128;
+    // sampled: p and screening words per bin, chosen bin per draw, reduction
+    if (emit == RW_EMIT_SAMPLED) b += 8 * (size_t)M * M + sizeof(int) * n_ssr + 128;
     else b += cull_scratch_bytes(M);
     return b;
 }
@@ -138,6 +170,7 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     const int j = find_job(prefix, njob, g);
     const DJob& J = jobs[j];
     const long long ri = J.off + (g - prefix[j]);
+    R.rid = ri;
     float x = rays.ox[ri], y = rays.oy[ri], zl = rays.oz[ri];
     float dx = rays.dx[ri], dy = rays.dy[ri], dz = rays.dz[ri];
     double opl = rays.opl[ri];
@@ -845,10 +878,166 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
 
 // ------------------------------------------------------------------ A5 sampled
 // Gumbel-max: draw i picks argmax_j (log p_j + g_ij) over propagating bins,
-// g = -log(-log u), u from Philox (counter (j>>2, i, ray, offset), word j&3).
+// g = -log(-log u), u from Philox (counter (j>>2, i, ray, offset), word j&3),
+// ray = the incident ray's index in the caller's ray arrays.
 // Coherent sensor: p ~ |U~|, a = a_in U~ / (N p).  Incoherent: p ~ |U~|^2,
 // a = a_in U~ / sqrt(N p) so that |a|^2 is the unbiased power weight.
-// Shared scratch after the patch: logp[M*M] floats, sel[n_ssr] ints, red[32].
+//
+// Screening (exact).  Bin j scores above -log(tau) only if E_j = -log u_j <
+// tau p_j, i.e. u_j > exp(-tau p_j): its 23-bit uniform exceeds a per-bin
+// threshold that is fixed for the whole patch.  A draw compares every
+// Philox word with that threshold (integer compares, no logarithm) and
+// evaluates the score, with the same float expression as a full scan, only
+// for the few candidates (tau of them on average).  The thresholds are
+// rounded towards more candidates, and a candidate is accepted only when its
+// score clears -log(tau) by a margin far above float rounding; otherwise the
+// draw rescans every bin.  The chosen bin is therefore always the full
+// scan's (ties: the lowest bin).
+#define RW_GUMBEL_TAU 12.0f
+#define RW_GUMBEL_FLOOR (-2.4849066497880004f + 1e-3f)   // -log(tau) + margin
+
+// score of bin j with probability p > 0 and Philox word w: the decision rule
+__device__ __forceinline__ float gumbel_score(float p, uint32_t w) {
+    return logf(p) - logf(-logf(u01(w)));
+}
+
+// Smallest Philox word with which a bin of probability p can score above
+// -log(tau): u > exp(-tau p) implies (w >> 9) >= tm (tm rounded down).
+__device__ __forceinline__ uint32_t gumbel_screen_word(float p) {
+    if (!(p > 0.f)) return 0xffffffffu;
+    const float e = expf(-RW_GUMBEL_TAU * p);
+    const float tm = floorf(e * 8388608.f * (1.f - 1e-6f)) - 1.f;
+    return tm <= 0.f ? 0u : ((uint32_t)tm << 9);
+}
+
+// E = -log u of the uniform of word w, to a few 1e-7 relative: near u = 1
+// (v = 1 - u < 1/16, where a logarithm of u loses relative accuracy) the
+// series -log(1 - v) = v + v^2/2 + v^3/3 + v^4/4 + v^5/5 (truncation
+// < v^5/6 relative), elsewhere the hardware base-2 logarithm.
+__device__ __forceinline__ float gumbel_E_fast(uint32_t w) {
+    const float m = (float)(w >> 9);
+    const float v = (8388607.5f - m) * 1.1920928955078125e-7f;            // 1 - u, exact
+    const float series = v * (1.f + v * (0.5f + v * (0.33333334f + v * (0.25f + v * 0.2f))));
+    float lg;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"((m + 0.5f) * 1.1920928955078125e-7f));
+    return v < 0.0625f ? series : -0.69314718f * lg;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void gumbel_keep(float sc, int jb, float& best, int& bj) {
+    if (sc > best || (sc == best && jb < bj)) { best = sc; bj = jb; }
+}
+
+// Full scan of draw i (every propagating bin scored): the fallback when no
+// screened candidate clears the floor.  p[j] = 0 marks bins that cannot be drawn.
+template <int M, int STRIDE = 1>
+__device__ __forceinline__ void gumbel_full_scan(const float* p, uint32_t i, uint32_t ray,
+                                                 uint32_t off, uint32_t k0, uint32_t k1,
+                                                 float& best, int& bj) {
+    for (int G = 0; G < M * M / 4; ++G) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)G, i, ray, off), k0, k1);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float pj = p[(4 * G + q) * STRIDE];
+            if (pj > 0.f) gumbel_keep(gumbel_score(pj, ws[q]), 4 * G + q, best, bj);
+        }
+    }
+}
+
+// Draws d0 .. d1-1 of one incident ray into sel[] (-1: no bin can be
+// drawn).  The 32 lanes of a warp make 32 draws together, walking the bins in
+// step so that the thresholds are broadcast reads; four independent Philox
+// blocks per step keep the integer pipes busy, and the rare candidates are
+// scored after the block's compares.  Not inlined: the hot loop gets the
+// registers of its own, apart from the rest of the fused kernel.
+template <int M>
+__device__ __noinline__ void gumbel_draws(const float* __restrict__ p,
+                                          const uint4* __restrict__ thr4, int* __restrict__ sel,
+                                          int d0, int d1, uint32_t ray, uint32_t off,
+                                          uint32_t k0, uint32_t k1) {
+    constexpr int NG = M * M / 4;
+    static_assert(NG % 4 == 0, "bin groups in blocks of four");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i0 = d0 + warp * 32; i0 < d1; i0 += RW_THREADS) {
+        const uint32_t i = (uint32_t)(i0 + lane);
+        float best = -INFINITY;
+        int bj = 0x7fffffff;
+        for (int G = 0; G < NG; G += 4) {
+            uint32_t ws[16];
+            unsigned mask = 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint4 w = philox4x32_10(make_uint4((uint32_t)(G + k), i, ray, off), k0, k1);
+                const uint4 t = thr4[G + k];
+                ws[4 * k] = w.x; ws[4 * k + 1] = w.y; ws[4 * k + 2] = w.z; ws[4 * k + 3] = w.w;
+                mask |= ((unsigned)(w.x >= t.x) | ((unsigned)(w.y >= t.y) << 1) |
+                         ((unsigned)(w.z >= t.z) << 2) | ((unsigned)(w.w >= t.w) << 3)) << (4 * k);
+            }
+            if (mask) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    if ((mask >> q) & 1u) {
+                        const int jb = 4 * G + q;
+                        const float pj = p[jb];
+                        if (pj > 0.f) gumbel_keep(gumbel_score(pj, ws[q]), jb, best, bj);
+                    }
+                }
+            }
+        }
+        if ((int)i < d1) {
+            if (!(best > RW_GUMBEL_FLOOR)) {
+                best = -INFINITY;
+                bj = 0x7fffffff;
+                gumbel_full_scan<M>(p, i, ray, off, k0, k1, best, bj);
+            }
+            sel[i] = (best > -INFINITY) ? bj : -1;
+        }
+    }
+}
+
+// Probabilities of the patch's bins, shared by the forward and the adjoint so
+// that both make the same draws: m_j = |U~_j|^2 (incoherent), |U~_j|
+// (coherent) or 1 (uniform density) over propagating bins, p_j = m_j / S.
+// Writes p[f * STRIDE] (0 for bins that cannot be drawn) and returns S;
+// `red` holds >= 8 floats.  Ends with a barrier.
+template <int M, int STRIDE = 1>
+__device__ __forceinline__ float sampled_probs(const DSys& sys, const RayAtDoe& R,
+                                               const float2* X, const float2* phu,
+                                               const float2* phv, float* p, float* red) {
+    const bool coh = sys.coherent != 0;
+    float part = 0.f;
+    for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
+        const int jvi = f / M, jui = f - (f / M) * M;
+        float dx, dy, dz;
+        float m = 0.f;
+        if (bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
+            const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, sys.norm);
+            const float p2 = U.x * U.x + U.y * U.y;
+            m = sys.uniform ? 1.f : (coh ? sqrtf(p2) : p2);
+        }
+        p[f * STRIDE] = m;
+        part += m;
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    float tot = 0.f;
+    for (int w = 0; w < RW_THREADS / 32; ++w) tot += red[w];
+    const float inv_tot = tot > 0.f ? 1.f / tot : 0.f;
+    for (int f = threadIdx.x; f < M * M; f += RW_THREADS) p[f * STRIDE] *= inv_tot;
+    __syncthreads();
+    return tot;
+}
+
+// Shared scratch after the patch: p[M*M] floats, thr[M*M] words, sel[n_ssr]
+// ints, red[32].
 template <int M, int MODE, int NS>
 __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                              const float2* X, const float2* phu, const float2* phv,
@@ -857,67 +1046,19 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
                                              unsigned char* scratch, int d0 = 0, int d1 = -1) {
     // draws d0 .. d1-1 (a slice in coherent launches; d0 a multiple of RW_THREADS)
     if (d1 < 0) d1 = sys.n_ssr;
-    float* logp = reinterpret_cast<float*>(scratch);
-    int* sel = reinterpret_cast<int*>(logp + M * M);
+    constexpr int NG = M * M / 4;
+    float* p = reinterpret_cast<float*>(scratch);
+    uint4* thr4 = reinterpret_cast<uint4*>(p + M * M);
+    uint32_t* thr = reinterpret_cast<uint32_t*>(thr4);
+    int* sel = reinterpret_cast<int*>(thr + M * M);
     float* red = reinterpret_cast<float*>(sel + sys.n_ssr);
     const bool coh = sys.coherent != 0;
     const float norm = sys.norm;
-    // magnitudes and their sum
-    float part = 0.f;
-    for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
-        const int jvi = f / M, jui = f - (f / M) * M;
-        float dx, dy, dz;
-        float m = 0.f;
-        if (bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz)) {
-            const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
-            const float p2 = U.x * U.x + U.y * U.y;
-            m = sys.uniform ? 1.f : (coh ? sqrtf(p2) : p2);
-        }
-        logp[f] = m;
-        part += m;
-    }
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    sampled_probs<M>(sys, R, X, phu, phv, p, red);
+    for (int f = threadIdx.x; f < M * M; f += RW_THREADS) thr[f] = gumbel_screen_word(p[f]);
     __syncthreads();
-    float tot = 0.f;
-    for (int w = 0; w < RW_THREADS / 32; ++w) tot += red[w];
-    const float inv_tot = tot > 0.f ? 1.f / tot : 0.f;
-    for (int f = threadIdx.x; f < M * M; f += RW_THREADS) {
-        const float pj = logp[f] * inv_tot;
-        logp[f] = pj > 0.f ? logf(pj) : -INFINITY;
-    }
-    __syncthreads();
-    // one warp per draw; each lane scores groups of 4 bins sharing a Philox counter
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t k0 = (uint32_t)(sys.seed & 0xffffffffull), k1 = (uint32_t)(sys.seed >> 32);
-    for (int i = d0 + warp; i < d1; i += RW_THREADS / 32) {
-        float best = -INFINITY;
-        int bj = 0x7fffffff;
-        for (int G = lane; G * 4 < M * M; G += 32) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)i,
-                                                     (uint32_t)(R.gid + J.sid),
-                                                     (uint32_t)sys.rng_offset), k0, k1);
-            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int jb = 4 * G + q;
-                if (jb < M * M) {
-                    const float lp = logp[jb];
-                    if (lp > -INFINITY) {
-                        const float gmb = -logf(-logf(u01(ws[q])));
-                        const float sc = lp + gmb;
-                        if (sc > best || (sc == best && jb < bj)) { best = sc; bj = jb; }
-                    }
-                }
-            }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
-            if (ob > best || (ob == best && oj < bj)) { best = ob; bj = oj; }
-        }
-        if (lane == 0) sel[i] = (best > -INFINITY) ? bj : -1;
-    }
+    gumbel_draws<M>(p, thr4, sel, d0, d1, (uint32_t)R.rid, (uint32_t)sys.rng_offset,
+                    (uint32_t)(sys.seed & 0xffffffffull), (uint32_t)(sys.seed >> 32));
     __syncthreads();
     const float2 ain = make_float2(R.a_re, R.a_im);
     if (MODE == MODE_EMIT && threadIdx.x == 0) {
@@ -940,7 +1081,7 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
                 const int jvi = jb / M, jui = jb - (jb / M) * M;
                 ok = bin_direction(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz);
                 const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
-                a = cscale(cmul(ain, U), 1.f / (N * expf(logp[jb])));
+                a = cscale(cmul(ain, U), 1.f / (N * p[jb]));
                 if (ok) ok = trace_to_sensor<true>(sys, x, y, zl, dx, dy, dz, opl, status);
             }
             __syncwarp();
@@ -958,7 +1099,7 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
             const int jvi = jb / M, jui = jb - (jb / M) * M;
             ok = bin_direction<(NS >= 0)>(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz);
             const float2 U = spectrum_at<M>(X, phu, phv, jui, jvi, norm);
-            const float pj = expf(logp[jb]);
+            const float pj = p[jb];
             const float sc = coh ? 1.f / (N * pj) : rsqrtf(N * pj);
             a = cscale(cmul(ain, U), sc);
         }

@@ -7,7 +7,6 @@
 // device synchronisation -- use rw_generate_rays_static() instead: its job
 // table lives in the file-scope device array below, so the call needs no
 // context and allocates nothing.
-#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -17,33 +16,16 @@
 
 // Job table + prefix sums for at most RW_STATIC_MAX_JOBS jobs.  Every GPU
 // that loads the library holds this array until the process exits.
-#define RW_STATIC_TABLE_BYTES \
-    (sizeof(GenJob) * RW_STATIC_MAX_JOBS + sizeof(long long) * (RW_STATIC_MAX_JOBS + 1))
+#define RW_STATIC_PREFIX_OFF (sizeof(GenJob) * RW_STATIC_MAX_JOBS)
+#define RW_STATIC_TABLE_BYTES (RW_STATIC_PREFIX_OFF + sizeof(long long) * (RW_STATIC_MAX_JOBS + 1))
 static __device__ __align__(256) unsigned char g_static_gen_table[RW_STATIC_TABLE_BYTES];
 
-#define RW_STATIC_MAX_DEVICES 64
-static void* g_table_addr[RW_STATIC_MAX_DEVICES];   // device address per device
+// Host copy of the table, built under the mutex and copied from while it is
+// held (a copy from pageable memory has read its source when the call
+// returns).  A static buffer rather than a stack array: the callers this
+// entry point serves often run on threads with small stacks.
+static unsigned char g_host_table[RW_STATIC_TABLE_BYTES];
 static std::mutex g_table_mu;
-
-// Device address of g_static_gen_table on the current device.  In host code
-// the symbol names a host-side stand-in, so the kernel is given the address
-// that cudaGetSymbolAddress returns (looked up once per device, with that
-// device current).
-static cudaError_t table_address(void** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= RW_STATIC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_table_mu);
-    if (!g_table_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_gen_table);
-        if (e != cudaSuccess) return e;
-        g_table_addr[dev] = p;
-    }
-    *out = g_table_addr[dev];
-    return cudaSuccess;
-}
 
 extern "C" rw_status rw_generate_rays_static(double z_start, double n_object,
                                              const rw_job* jobs, int32_t njob,
@@ -54,43 +36,35 @@ extern "C" rw_status rw_generate_rays_static(double z_start, double n_object,
     if (rays->n > 0 && (!rays->ox || !rays->oy || !rays->oz || !rays->dx || !rays->dy ||
                         !rays->dz || !rays->a_re || !rays->a_im || !rays->opl))
         return RW_EINVAL;
-    // host copy of the table (stack, no allocation), then one async copy
-    unsigned char host[RW_STATIC_TABLE_BYTES];
-    GenJob* g = reinterpret_cast<GenJob*>(host);
-    long long* prefix = reinterpret_cast<long long*>(host + sizeof(GenJob) * RW_STATIC_MAX_JOBS);
-    prefix[0] = 0;
-    for (int i = 0; i < njob; ++i) {
-        const rw_job& j = jobs[i];
-        if (j.grid_n < 0 || j.ray_count != j.grid_n * j.grid_n) return RW_EINVAL;
-        if (j.ray_offset < 0 || j.ray_offset + j.ray_count > rays->n) return RW_EINVAL;
-        const double tx = std::tan(j.theta_x), ty = std::tan(j.theta_y);
-        const double nrm = std::sqrt(tx * tx + ty * ty + 1.0);
-        g[i].off = j.ray_offset;
-        g[i].n = j.grid_n;
-        g[i].spacing = j.spacing;
-        g[i].x0 = j.x0;
-        g[i].y0 = j.y0;
-        g[i].dx = (float)(tx / nrm);
-        g[i].dy = (float)(ty / nrm);
-        g[i].dz = (float)(1.0 / nrm);
-        g[i].pad = 0.f;
-        prefix[i + 1] = prefix[i] + j.ray_count;
-    }
-    if (prefix[njob] == 0) return RW_OK;
-    void* dev_table = nullptr;
-    if (table_address(&dev_table) != cudaSuccess) return RW_ECUDA;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    // Every call rewrites the whole table it uses; nothing has to start at zero.
-    if (cudaMemcpyAsync(dev_table, host, sizeof(GenJob) * njob, cudaMemcpyHostToDevice, st) !=
+    // A captured graph would replay the upload from the host buffer, whose
+    // contents belong to whichever call came last: refuse capture.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return RW_ECUDA;
+    if (cap != cudaStreamCaptureStatusNone) return RW_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RW_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RW_ECUDA;
+    // In host code the array's name is a host-side stand-in: the kernel gets
+    // the device address, looked up on every call with the device current
+    // (cheap, and never stale after a device reset).
+    void* dev_table = nullptr;
+    if (cudaGetSymbolAddress(&dev_table, g_static_gen_table) != cudaSuccess) return RW_ECUDA;
+
+    std::lock_guard<std::mutex> lock(g_table_mu);
+    GenJob* g = reinterpret_cast<GenJob*>(g_host_table);
+    long long* prefix = reinterpret_cast<long long*>(g_host_table + RW_STATIC_PREFIX_OFF);
+    if (gen_table_fill(jobs, njob, rays->n, g, prefix)) return RW_EINVAL;
+    if (prefix[njob] == 0) return RW_OK;
+    // Every call rewrites the part of the table it uses; nothing has to start at zero.
+    if (cudaMemcpyAsync(dev_table, g, sizeof(GenJob) * njob, cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
         return RW_ECUDA;
-    char* dprefix = (char*)dev_table + sizeof(GenJob) * RW_STATIC_MAX_JOBS;
+    char* dprefix = (char*)dev_table + RW_STATIC_PREFIX_OFF;
     if (cudaMemcpyAsync(dprefix, prefix, sizeof(long long) * (njob + 1), cudaMemcpyHostToDevice,
                         st) != cudaSuccess)
         return RW_ECUDA;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     LaunchCtx L;
     L.stream = st;
     L.num_sms = sms > 0 ? sms : 1;

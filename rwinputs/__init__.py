@@ -6,7 +6,7 @@ arithmetic: no tracing, no patch transform, no emission and no splatting.
 Both sides read exactly the same float32 arrays produced here.
 """
 from .systems import (  # noqa: F401
-    Surface, DOE, Sensor, System, Job, Workload, jobs_offsets,
+    Surface, DOE, Sensor, System, Job, Workload, jobs_offsets, ray_blocks,
     PLANE, SPHERE, ASPHERE, GAUSS, PLANAR, CONFORMAL,
 )
 from .maps import (  # noqa: F401

@@ -165,3 +165,21 @@ class Workload:
     @property
     def n_rays(self):
         return int(sum(j.n_rays for j in self.jobs))
+
+
+def ray_blocks(jobs: List[Job], per_job: int, seed: int):
+    """Seeded sample of incident rays for spot checks at full workload size:
+    per job one contiguous run of `per_job` ray indices (along grid rows)
+    starting at a random index.  Returns (starts [njob] int64, subsets
+    list of index arrays).  A contiguous run keeps every sampled ray at its
+    own index, so a launch over [offset + start, offset + start + per_job)
+    draws the same sampling stream as the whole workload."""
+    rng = np.random.default_rng(seed)
+    starts, subsets = [], []
+    for j in jobs:
+        n = int(j.n_rays)
+        m = min(per_job, n)
+        s0 = int(rng.integers(0, n - m + 1))
+        starts.append(s0)
+        subsets.append(np.arange(s0, s0 + m, dtype=np.int64))
+    return np.asarray(starts, dtype=np.int64), subsets

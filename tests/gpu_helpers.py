@@ -6,9 +6,24 @@ import torch
 from oracle import pipeline as OP
 
 
+def _as_array(x):
+    if isinstance(x, torch.Tensor):
+        x = x.detach().cpu().numpy()
+    return np.asarray(x)
+
+
 def rel_l2(a, b):
-    a = np.asarray(a, dtype=np.float64)
-    b = np.asarray(b, dtype=np.float64)
+    """||a - b|| / ||b|| over all entries; complex inputs keep both parts
+    (|a - b| and |b| of complex entries), nothing is cast away."""
+    a = _as_array(a)
+    b = _as_array(b)
+    if np.iscomplexobj(a) or np.iscomplexobj(b):
+        a = a.astype(np.complex128)
+        b = b.astype(np.complex128)
+    else:
+        a = a.astype(np.float64)
+        b = b.astype(np.float64)
+    assert a.shape == b.shape, (a.shape, b.shape)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 

@@ -1,0 +1,132 @@
+"""Parity at the benchmark's own configuration.
+
+The benchmark times the full C2 workload: 2048 x 2048 Zernike + holographic
+DOE at 1 um, two singlets, 9 jobs (3 wavelengths x 3 fields) of 1024 x 1024
+rays, 64 x 64 patches, 512 x 512 sensor at 2 um, through rw_forward_vis (mask
++ tape) and the taped rw_backward_vis.  Here the same calls run on the full
+map, sensor and job set, for a seeded run of rays per job (the oracle cannot
+afford 9.4M), and are compared with the FP64 oracle on exactly those rays:
+PSF relative L2 <= 1e-4 and the gradients of the Eq. 3 loss within 1e-3.
+
+A second case replaces the last lens surface by an even asphere, so that
+all eight surface-gradient slots (z, c, k, A4..A10, n) are checked through
+both adjoint kernels (fused, and split over the visibility mask).
+"""
+import numpy as np
+import pytest
+import torch
+
+import rwinputs as R
+from oracle import loss as OL
+from oracle import pipeline as OP
+
+from gpu_helpers import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["z", "c", "k", "A4", "A6", "A8", "A10", "n_after"]
+
+
+@pytest.fixture(scope="module")
+def RW():
+    from paper_2605_15418_gb300 import raywave
+    return raywave
+
+
+def _oracle_grads(w, subsets):
+    prm = OP.params_of(w.system, requires_grad=True)
+    phi = torch.from_numpy(w.system.doe.phi.astype(np.float64)).requires_grad_(True)
+    img = OP.psf(w, params=prm, phi=phi, subsets=subsets, chunk=32)
+    Lv, _ = OL.eq3_loss(img, torch.from_numpy(w.target.astype(np.float64)))
+    Lv.backward()
+    return img.detach().numpy(), phi.grad.numpy(), prm
+
+
+def _check_dsurf(ds, prm, slots, tol=1e-3):
+    """Each checked slot within tol of its own magnitude, floored at tol x
+    1e-3 of the largest curvature gradient (slots near zero)."""
+    cmax = max(abs(float(p["c"].grad or 0.0)) for p in prm)
+    for si in range(len(prm)):
+        for k in slots:
+            g = prm[si][NAMES[k]].grad
+            ref = 0.0 if g is None else float(g)
+            scale = max(abs(ref), 1e-3 * cmax)
+            assert abs(ds[si, k] - ref) <= tol * scale + 1e-12, (si, NAMES[k], ds[si, k], ref)
+
+
+def _subset_sim(RW, w, per_job, seed):
+    sim = RW.Simulator(w)                  # generates all rays of the workload
+    starts, subsets = R.ray_blocks(w.jobs, per_job, seed)
+    off = R.jobs_offsets(w.jobs)
+    sim.jobs = RW.jobs_struct(w.jobs, offsets=[int(off[j] + starts[j]) for j in range(len(w.jobs))],
+                              counts=[len(s) for s in subsets])
+    n_sub = int(sum(len(s) for s in subsets))
+    return sim, subsets, n_sub
+
+
+def test_bench_workload_forward_and_taped_adjoint_match_oracle(RW):
+    w = R.configs.c2()                     # the benchmark's workload, full size
+    assert w.system.doe.phi.shape == (2048, 2048) and w.system.sensor.nx == 512
+    sim, subsets, n_sub = _subset_sim(RW, w, per_job=64, seed=2024)
+    M = w.system.doe.M
+    vis = RW.alloc_vis(n_sub, M, sim.dev)
+    psf = sim.forward(vis=vis)
+    tgt = torch.as_tensor(w.target, device=sim.dev)
+    gI = torch.empty_like(psf)
+    sim.loss(psf, tgt, gI)
+    dphi, _, dsurf = sim.backward(gI, vis=vis)
+    torch.cuda.synchronize()
+    assert sim.ctx.device_status() == 0
+    img, gphi, prm = _oracle_grads(w, subsets)
+    got = psf.cpu().numpy()
+    assert img.sum() > 0
+    assert rel_l2(got, img) <= 1e-4, rel_l2(got, img)
+    assert rel_l2(dphi.cpu().numpy(), gphi) <= 1e-3, rel_l2(dphi.cpu().numpy(), gphi)
+    ds = dsurf.cpu().numpy()
+    _check_dsurf(ds, prm, (0, 1, 7))
+    # spheres and planes ignore k and A4..A10: zero gradient on both sides
+    assert np.all(ds[:, 2:7] == 0.0)
+
+
+def _c2_rear_asphere():
+    w = R.configs.c2(n_side=16, D=64, lams=(486e-6, 656e-6), fields_deg=(0.0, 1.5),
+                     sensor_n=96, map_side=512)
+    sysm = w.system
+    last = sysm.surfaces[-1]
+    # polynomial terms of a few um of sag over the 6 mm aperture
+    sysm.surfaces[-1] = R.Surface(R.ASPHERE, last.z, c=last.c, k=-0.6,
+                                  A=(1e-5, -2e-7, 3e-9, -2e-11), n_after=last.n_after,
+                                  r_ap=last.r_ap)
+    sysm.sensor.pitch = 8e-3
+    w.target = R.gaussian_spots_target(len(w.jobs), 96, 96, seed=31, n_spots=4)
+    return w
+
+
+@pytest.fixture(scope="module")
+def asphere_oracle():
+    w = _c2_rear_asphere()
+    return (w,) + _oracle_grads(w, None)
+
+
+@pytest.mark.parametrize("adjoint", ["fused", "split"])
+def test_asphere_after_doe_all_surface_slots_match_oracle(RW, asphere_oracle, adjoint):
+    w, img, gphi, prm = asphere_oracle
+    sim = RW.Simulator(w)
+    vis = RW.alloc_vis(sim.n_rays, w.system.doe.M, sim.dev) if adjoint == "split" else None
+    psf = sim.forward(vis=vis)
+    tgt = torch.as_tensor(w.target, device=sim.dev)
+    gI = torch.empty_like(psf)
+    sim.loss(psf, tgt, gI)
+    dphi, _, dsurf = sim.backward(gI, vis=vis)
+    torch.cuda.synchronize()
+    assert sim.ctx.device_status() == 0
+    assert rel_l2(psf.cpu().numpy(), img) <= 1e-4, rel_l2(psf.cpu().numpy(), img)
+    assert rel_l2(dphi.cpu().numpy(), gphi) <= 1e-3, rel_l2(dphi.cpu().numpy(), gphi)
+    ds = dsurf.cpu().numpy()
+    _check_dsurf(ds[:-1], prm[:-1], (0, 1, 7))
+    # the asphere: every slot, each against its own magnitude
+    last = prm[-1]
+    for k in range(8):
+        ref = float(last[NAMES[k]].grad)
+        assert ref != 0.0, NAMES[k]
+        assert abs(ds[-1, k] - ref) <= 1e-3 * abs(ref), (NAMES[k], ds[-1, k], ref)
