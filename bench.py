@@ -1,12 +1,21 @@
 """Benchmark: incident rays/s through forward + backward of the ray-wave DOE step.
 
-Workload (default): two spherical singlets behind a planar DOE with a seeded
-Zernike + holographic phase map (2048 x 2048 at 1 um), 1M collimated rays
-per field (1024 x 1024 grid at 2 um), fields {0, 1, 2} deg x wavelengths
-{486, 550, 656} nm = 9 jobs, 64 x 64 patches (exhaustive emission: 4096
-secondary rays per incident ray), incoherent 512 x 512 PSF per job at 2 um,
+Headline workload (default --config c5): the batched end-to-end design
+workload -- three spherical singlets behind a planar DOE carrying the seeded
+Zernike + holographic phase map (2048 x 2048 at 1 um); 31 wavelengths
+(400-700 nm) x 16 fields (4 x 4 over +-1.5 deg) = 496 jobs with uneven,
+log-uniform ray counts; 96 x 96 patches; sampled emission with 1024
+Gumbel-max draws per incident ray; incoherent 512 x 512 PSF per job at 2 um;
 FP32.  One step = ray generation (A0) + fused forward (A1..A7) + Eq. 3 loss
-(A8) + adjoint (A9) over all 9.4M incident rays.
+(A8) + adjoint with the straight-through Gumbel-softmax (A9) over every
+incident ray of all 496 jobs in one persistent launch per kernel.  The
+workload's ray counts are 64k..2M per job (2.8e8 rays); the sampled method
+costs N x M^2 = 9.4e6 Gumbel scores per incident ray and pass, so the
+benchmark divides every job's count range by --c5-scale (stated in config).
+
+Also measured (nested under "also"): the full C2 step (two singlets, planar
+DOE, 9 jobs of 1M rays, 64 x 64 patches, exhaustive emission with exact
+block culling, taped adjoint over the visibility mask).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -32,15 +41,16 @@ sys.path.insert(0, ROOT)
 METRIC = ("rays/s fwd+bwd through DOE ray–wave step at PSF err≤1e-4 vs FP64; "
           "% HBM/TC peak")
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per launch at the default workload, from one ncu
-# capture of the current kernel at n-side 256 scaled by the incident-ray
+MUFU_LANES_PER_SM = 16
+C5_FULL_LO, C5_FULL_HI = 65536, 2 * 1024 * 1024
+# DRAM bytes (read + write) per launch of the C2 step at full size, from one
+# ncu capture of the current kernel at n-side 256 scaled by the incident-ray
 # count (16x): see the profiles/ summaries.  A kernel missing here has no
 # capture of its current code.
-TRAFFIC = {"k_bs_scatter": 16 * (1.535592e9 + 0.192266e9),
-           "k_bs_trace": 16 * (1.408312e9 + 0.820282e9),
-           "k_cull": 16 * 0.023748e9,
-           "k_forward": 16 * (0.310524e9 + 1.472937e9)}
-NUM_SMS = 152
+C2_TRAFFIC = {"k_bs_scatter": 16 * (1.535592e9 + 0.192266e9),
+              "k_bs_trace": 16 * (1.408312e9 + 0.820282e9),
+              "k_cull": 16 * 0.023748e9,
+              "k_forward": 16 * (0.310524e9 + 1.472937e9)}
 
 
 def parse():
@@ -49,9 +59,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-side", type=int, default=1024, help="rays per field = n_side^2")
-    ap.add_argument("--cpu-rays", type=int, default=576,
-                    help="incident rays per oracle sample (cpu_baseline and the reference arm)")
+    ap.add_argument("--config", default="c5", choices=["c5", "c2"])
+    ap.add_argument("--c5-scale", type=int, default=4096,
+                    help="C5 ray counts per job divided by this (64k..2M -> 16..512 at 4096)")
+    ap.add_argument("--n-side", type=int, default=1024, help="C2 rays per field = n_side^2")
+    ap.add_argument("--also", default="c2",
+                    help="comma-separated extra workloads measured after the headline ('' = none)")
+    ap.add_argument("--also-steps", type=int, default=5)
+    ap.add_argument("--also-warmup", type=int, default=3)
+    ap.add_argument("--cpu-rays", type=int, default=0,
+                    help="incident rays per oracle sample (0: the workload's default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU time the cpu_baseline leg keeps sampling for")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -60,14 +77,24 @@ def parse():
     return ap.parse_args()
 
 
-def workload(n_side):
+# ------------------------------------------------------------------ workloads
+def workload(name, args):
     import rwinputs as R
-    return R.configs.c2(n_side=n_side)
+    if name == "c5":
+        s = max(1, int(args.c5_scale))
+        return R.configs.c5(count_lo=max(1, C5_FULL_LO // s), count_hi=max(4, C5_FULL_HI // s))
+    return R.configs.c2(n_side=args.n_side)
+
+
+def default_cpu_rays(name):
+    # incident rays per oracle sample: the C2 oracle runs ~500 rays/s, the C5
+    # one (1024 draws over 96^2 bins per ray, fwd + bwd) a few seconds per ray
+    return 576 if name == "c2" else 8
 
 
 # ------------------------------------------------------------------ algorithmic work
-# FP32 operations (each add, multiply, divide, square root and compare
-# counted once, an FMA twice) of the kernels of one step.
+# C2 (exhaustive emission, FP32 tracing): FP32 operations, each add,
+# multiply, divide, square root and compare counted once, an FMA twice.
 def fft_flops(M):
     """Radix FFT count of one M x M patch transform: 5 N log2 N, N = M^2."""
     return 5.0 * M * M * math.log2(M * M)
@@ -94,8 +121,8 @@ def block_test_flops(S):
     return 400.0 + 1290.0 * S
 
 
-def kernel_flops(name, M, D, S, n_rays, rays_with_items, items, blocks, kept):
-    """Algorithmic work of one launch of `name` in the benchmark step."""
+def c2_kernel_flops(name, M, D, S, n_rays, rays_with_items, items, blocks, kept):
+    """Algorithmic FP32 work of one launch of `name` in the C2 step."""
     if name == "k_forward":
         traced = 64.0 * kept if blocks else float(n_rays) * M * M
         return n_rays * fft_flops(M) + traced * bin_fwd_flops(S)
@@ -108,6 +135,31 @@ def kernel_flops(name, M, D, S, n_rays, rays_with_items, items, blocks, kept):
         return items * bin_bwd_flops(S)
     if name == "k_bs_scatter":
         return rays_with_items * (fft_flops(M) + 8.0 * D * D) + items * 20.0
+    return None
+
+
+# C5 (sampled emission): the work is the (draw, bin) Gumbel score, N x M^2
+# per incident ray and pass.  Counted in 32-bit lane operations at
+# instruction granularity (an FMA, an integer multiply-wide, a 3-input
+# logical op, a compare: one each); multi-function-unit operations (log2,
+# reciprocal) are counted separately against their own, eight times
+# lower, rate.  Philox4x32-10 takes 10 rounds x (2 multiply-wide + 2
+# three-input xor) = 40 ops per block of 4 words: 10 per score.
+#   forward: 10 (Philox) + 1 (threshold compare)                 = 11 ALU
+#   adjoint pass A: 10 + 13 (-log u: convert, 1 - u, series of 5 FMAs, the
+#     log2 branch, select) + 1 (t = p e) + 5 (sums) + 4 (screen test)
+#     + 2 (broadcast loads)                                     = 35 ALU, 2 MUFU
+#   adjoint pass B: 10 + 13 + 6 (accumulators)                   = 29 ALU, 2 MUFU
+C5_FWD_ALU, C5_BWD_ALU, C5_BWD_MUFU = 11.0, 35.0 + 29.0, 4.0
+
+
+def c5_kernel_work(name, n_rays, M, N):
+    """(ALU lane-ops, MUFU lane-ops) of one launch of `name` in the C5 step."""
+    pairs = float(n_rays) * N * M * M
+    if name == "k_forward":
+        return pairs * C5_FWD_ALU, 0.0
+    if name == "k_backward":
+        return pairs * C5_BWD_ALU, pairs * C5_BWD_MUFU
     return None
 
 
@@ -158,42 +210,70 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
 # ------------------------------------------------------------------ oracle (CPU)
-def oracle_step_seconds(w, n_rays, seed=0):
-    """Time the FP64 oracle forward + backward (autograd) on a seeded sample
-    of n_rays incident rays spread over the jobs.  Returns (seconds, rays)."""
+def oracle_sample(w, n_rays, seed):
+    """Seeded sample of about n_rays incident rays of `w`: contiguous runs of
+    ray indices (so that the GPU run on the same runs draws the same sampling
+    stream), at least 4 rays per sampled job (a PSF of a single incident ray
+    is dominated by the rounding of its few deposits).  Returns per-job index
+    lists."""
+    import rwinputs as R
+    njob = len(w.jobs)
+    per = max(1, n_rays // njob)
+    starts, subsets = R.ray_blocks(w.jobs, max(per, 4), seed)
+    if per < 4:
+        rng = np.random.default_rng(seed)
+        keep = set(rng.choice(njob, max(1, n_rays // 4), replace=False).tolist())
+        subsets = [s if j in keep else s[:0] for j, s in enumerate(subsets)]
+    return subsets
+
+
+def oracle_step(w, subsets):
+    """FP64 oracle forward + autograd backward of Eq. 3 on the sample; returns
+    (seconds, rays, PSF stack)."""
     import torch
     from oracle import loss as OL
     from oracle import pipeline as OP
-    rng = np.random.default_rng(seed)
-    per = max(1, n_rays // len(w.jobs))
-    subsets = [np.sort(rng.choice(j.n_rays, per, replace=False)) for j in w.jobs]
     tgt = torch.from_numpy(w.target.astype(np.float64))
+    chunk = 32 if w.system.doe.emit == "exhaustive" else 1
     t0 = time.perf_counter()
     prm = OP.params_of(w.system, requires_grad=True)
     phi = torch.from_numpy(w.system.doe.phi.astype(np.float64)).requires_grad_(True)
-    img = OP.psf(w, params=prm, phi=phi, subsets=subsets, chunk=32)
+    img = OP.psf(w, params=prm, phi=phi, subsets=subsets, chunk=chunk)
     Lv, _ = OL.eq3_loss(img, tgt)
     Lv.backward()
-    return time.perf_counter() - t0, per * len(w.jobs)
+    return time.perf_counter() - t0, int(sum(len(s) for s in subsets)), img.detach().numpy()
 
 
 def cpu_baseline(w, n_rays, budget_s):
     """Oracle throughput on the host: independent seeded samples of n_rays
-    incident rays each (the autograd graph of one sample holds ~10 MB per
-    ray), repeated until budget_s seconds of CPU work have been timed."""
+    incident rays, repeated until budget_s seconds of CPU work were timed.
+    Also returns the first sample and its PSF (the parity check)."""
     import torch
     secs, n, k = 0.0, 0, 0
+    first = None
     while k == 0 or secs < budget_s:
-        s, m = oracle_step_seconds(w, n_rays, seed=1000 + k)
+        sub = oracle_sample(w, n_rays, seed=1000 + k)
+        s, m, img = oracle_step(w, sub)
+        if first is None:
+            first = (sub, img)
         secs += s
         n += m
         k += 1
-    return {"value": n / secs, "unit": "rays/s", "cores": torch.get_num_threads(),
-            "kind": "oracle",
-            "sample": f"{k} seeded samples of {n // k} incident rays ({n // k // len(w.jobs)} "
-                      f"per job) of the same workload, each a float64 forward + autograd "
-                      f"backward of Eq. 3, {secs:.1f} s in total"}
+    return ({"value": n / secs, "unit": "rays/s", "cores": torch.get_num_threads(),
+             "kind": "oracle",
+             "sample": f"{k} seeded samples of {n // k} incident rays (contiguous runs in "
+                       f"seeded jobs) of the same workload, each a float64 forward + "
+                       f"autograd backward of Eq. 3, {secs:.1f} s in total"}, first)
 
 
 # ------------------------------------------------------------------ reference arm
@@ -201,13 +281,13 @@ def run_reference(args, rank):
     if rank != 0:
         return
     import torch
-    w = workload(args.n_side)
-    per_step = max(len(w.jobs), args.cpu_rays)
+    w = workload(args.config, args)
+    per_step = args.cpu_rays or default_cpu_rays(args.config)
     for i in range(args.warmup):
-        oracle_step_seconds(w, per_step, seed=100 + i)
+        oracle_step(w, oracle_sample(w, per_step, seed=100 + i))
     tot, nr = 0.0, 0
     for i in range(args.steps):
-        s, n = oracle_step_seconds(w, per_step, seed=i)
+        s, n, _ = oracle_step(w, oracle_sample(w, per_step, seed=i))
         tot += s
         nr += n
     val = nr / tot
@@ -215,14 +295,29 @@ def run_reference(args, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w.name, "incident_rays_per_step_sampled": per_step,
-                       "jobs": len(w.jobs), "D": w.system.doe.D},
+            "config": config_of(args.config, w, args),
             "cpu_baseline": {"value": val, "unit": "rays/s", "cores": torch.get_num_threads(),
                              "kind": "oracle",
                              "sample": f"{per_step} seeded incident rays per step"},
             "e2e": {"value": val, "unit": "rays/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def config_of(name, w, args):
+    """The workload description shared by both arms."""
+    d = w.system.doe
+    c = {"workload": w.name, "incident_rays": w.n_rays, "jobs": len(w.jobs), "D": d.D,
+         "emission": d.emit, "sensor": f"{w.system.sensor.nx}x{w.system.sensor.ny}x{len(w.jobs)}",
+         "surfaces_after_doe": len(w.system.surfaces) - w.system.doe_index - 1,
+         "l2": "flushed between steps (256 MB)"}
+    if name == "c5":
+        s = max(1, int(args.c5_scale))
+        c.update({"n_ssr": d.n_ssr, "ray_count_range": [max(1, C5_FULL_LO // s),
+                                                        max(4, C5_FULL_HI // s)],
+                  "reduced": f"ray counts per job divided by {s} (full workload: "
+                             f"{C5_FULL_LO}..{C5_FULL_HI} per job)"})
+    return c
 
 
 # ------------------------------------------------------------------ ranks
@@ -242,6 +337,196 @@ def weak_scaling_value(rays_per_rank, world, ms_per_step):
 
 
 # ------------------------------------------------------------------ our arm
+class Step:
+    """One fwd + Eq. 3 + bwd step of a workload through the C ABI."""
+
+    def __init__(self, name, w, dev, local):
+        import torch
+        from paper_2605_15418_gb300 import raywave as RW
+        self.RW, self.name, self.w = RW, name, w
+        self.sim = RW.Simulator(w, device=local)
+        sim = self.sim
+        self.tgt = torch.as_tensor(w.target, device=dev)
+        self.gI = torch.empty(sim.psf_shape, dtype=torch.float32, device=dev)
+        self.psf = torch.empty(sim.psf_shape, dtype=torch.float32, device=dev)
+        self.dphi = torch.zeros_like(sim.phi)
+        self.dsurf = torch.zeros(len(w.system.surfaces), 8, dtype=torch.float64, device=dev)
+        self.loss = torch.empty(3, dtype=torch.float64, device=dev)
+        # C2: one visibility bit per secondary ray, taped split adjoint
+        self.vis = RW.alloc_vis(sim.n_rays, w.system.doe.M, dev) if name == "c2" else None
+
+    def __call__(self, ev=None, stream=None):
+        RW, sim = self.RW, self.sim
+        s, keep = sim.sys_struct()
+        if ev: ev[0].record(stream)
+        RW.rw_generate_rays(sim.ctx, self.w.z_start, self.w.system.n_object, sim.jobs, sim.rays)
+        if ev: ev[1].record(stream)
+        if self.vis is not None:
+            RW.rw_forward_vis(sim.ctx, s, sim.jobs, sim.rays, self.psf, self.vis)
+        else:
+            RW.rw_forward(sim.ctx, s, sim.jobs, sim.rays, self.psf)
+        if ev: ev[2].record(stream)
+        RW.rw_loss_eq3(sim.ctx, self.psf, self.tgt, self.loss, self.gI)
+        self.dphi.zero_()
+        self.dsurf.zero_()
+        if ev: ev[3].record(stream)
+        if self.vis is not None:
+            RW.rw_backward_vis(sim.ctx, s, sim.jobs, sim.rays, self.gI, self.vis, self.dphi,
+                               None, self.dsurf)
+        else:
+            RW.rw_backward(sim.ctx, s, sim.jobs, sim.rays, self.gI, self.dphi, None, self.dsurf)
+        if ev: ev[4].record(stream)
+
+
+def time_steps(st, steps, warmup, flush, dev, autotune, dist, local, sample_clocks):
+    """Warm-up, then `steps` timed steps with an L2 flush between them;
+    per-kernel times from the library's CUDA events around every launch."""
+    import torch
+    sim = st.sim
+    stream = torch.cuda.current_stream(dev)
+    tuned = None
+    if autotune:
+        st()
+        tuned = sim.ctx.autotune(sim, st.gI, st.vis)
+    for _ in range(warmup):
+        st()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(steps)]
+    clk = ClockSampler(local) if sample_clocks else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = sim.ctx.launches
+    sim.ctx.profile(True)
+    if clk:
+        clk.start()
+    for k in range(steps):
+        flush.zero_()
+        st(evs[k], stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop() if clk else None
+    prof = sim.ctx.profile_read()
+    sim.ctx.profile(False)
+    launches = sim.ctx.launches - launches0
+    if dist:
+        dist.barrier()
+    t_step = [evs[k][0].elapsed_time(evs[k][4]) for k in range(steps)]
+    t_fwd = [evs[k][1].elapsed_time(evs[k][2]) for k in range(steps)]
+    t_bwd = [evs[k][3].elapsed_time(evs[k][4]) for k in range(steps)]
+    return {"ms": float(np.sum(t_step)), "fwd_ms": float(np.mean(t_fwd)),
+            "bwd_ms": float(np.mean(t_bwd)), "prof": prof, "launches": int(launches),
+            "clocks": clocks, "tuned": tuned}
+
+
+def e2e_rate(st, steps, dev, world):
+    """The same step through the public API with host buffers: the DOE map and
+    the target come from pinned host memory, and the PSF, dL/dphi, the surface
+    gradients and the loss go back, every step, inside the timed region."""
+    import torch
+    sim = st.sim
+    stream = torch.cuda.current_stream(dev)
+    phi_h = torch.from_numpy(np.ascontiguousarray(st.w.system.doe.phi)).pin_memory()
+    tgt_h = torch.from_numpy(np.ascontiguousarray(st.w.target)).pin_memory()
+    psf_h = torch.empty(sim.psf_shape, dtype=torch.float32).pin_memory()
+    dphi_h = torch.empty_like(phi_h).pin_memory()
+    dsurf_h = torch.empty(len(st.w.system.surfaces), 8, dtype=torch.float64).pin_memory()
+    loss_h = torch.empty(3, dtype=torch.float64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        sim.phi.copy_(phi_h, non_blocking=True)
+        st.tgt.copy_(tgt_h, non_blocking=True)
+        st()
+        psf_h.copy_(st.psf, non_blocking=True)
+        dphi_h.copy_(st.dphi, non_blocking=True)
+        dsurf_h.copy_(st.dsurf, non_blocking=True)
+        loss_h.copy_(st.loss, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    h2d = phi_h.numel() * 4 + tgt_h.numel() * 4
+    d2h = psf_h.numel() * 4 + dphi_h.numel() * 4 + dsurf_h.numel() * 8 + 24
+    return {"value": world * sim.n_rays / (ms / 1e3), "unit": "rays/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+def gpu_parity(st, subsets, ref):
+    """PSF relative L2 of the GPU on the oracle's sample against the oracle's
+    FP64 PSF of it (same rays, same launch configuration)."""
+    import rwinputs as R
+    import torch
+    RW, sim, w = st.RW, st.sim, st.w
+    off = R.jobs_offsets(w.jobs)
+    starts = [int(s[0]) if len(s) else 0 for s in subsets]
+    jobs = RW.jobs_struct(w.jobs, offsets=[int(off[j]) + starts[j] for j in range(len(w.jobs))],
+                          counts=[len(s) for s in subsets])
+    s, keep = sim.sys_struct()
+    psf = torch.empty(sim.psf_shape, dtype=torch.float32, device=st.psf.device)
+    RW.rw_forward(sim.ctx, s, jobs, sim.rays, psf)
+    torch.cuda.synchronize()
+    got = psf.cpu().numpy().astype(np.float64)
+    return float(np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300))
+
+
+def roofline_c5(tm, st, peaks, n_sms, clocks):
+    """ALU (and MUFU) roofline of the dominant kernel of the C5 step."""
+    prof = tm["prof"]
+    d = st.w.system.doe
+    M, N = d.M, d.n_ssr
+    kernel_ms = {k: v[0] / v[1] for k, v in prof.items() if v[1] > 0}
+    work = {k: c5_kernel_work(k, st.sim.n_rays, M, N) for k in kernel_ms}
+    name = max((k for k in kernel_ms if work[k] is not None), key=lambda k: prof[k][0])
+    t = kernel_ms[name] / 1e3
+    alu, mufu = work[name]
+    f = 2070e6
+    alu_peak = n_sms * FP32_LANES_PER_SM * f / 1e12
+    mufu_peak = n_sms * MUFU_LANES_PER_SM * f / 1e12
+    a_alu, a_mufu = alu / t / 1e12, mufu / t / 1e12
+    fr_alu, fr_mufu = a_alu / alu_peak, a_mufu / mufu_peak
+    return kernel_ms, {
+        "kernel": name, "bound": "alu", "achieved": a_alu, "peak": alu_peak,
+        "unit": "Tops/s (32-bit lane ops)", "frac": fr_alu, "traffic": None,
+        "peak_source": f"{n_sms} SMs x 128 lanes x 2070 MHz (one 32-bit op per lane per "
+                       "clock; nominal unit counts and the maximum SM clock)",
+        "other_bounds": {"mufu": {"achieved": a_mufu, "peak": mufu_peak, "frac": fr_mufu,
+                                  "peak_source": f"{n_sms} SMs x 16 MUFU lanes x 2070 MHz"},
+                         "hbm": {"frac": "<1e-3 (maps and images stay in L2; "
+                                         "~0.1 MB of rays per incident-ray tile)"}},
+        "work_per_launch": {"pairs": float(st.sim.n_rays) * N * M * M,
+                            "alu_ops_per_pair": C5_FWD_ALU if name == "k_forward"
+                            else C5_BWD_ALU,
+                            "mufu_ops_per_pair": 0.0 if name == "k_forward" else C5_BWD_MUFU}}
+
+
+def roofline_c2(tm, st, n_sms):
+    """FP32 roofline of the dominant kernel of the C2 step."""
+    import torch
+    prof = tm["prof"]
+    sysm = st.w.system
+    D, M = sysm.doe.D, sysm.doe.M
+    n_rays = st.sim.n_rays
+    lut = torch.tensor([bin(i).count("1") for i in range(256)], dtype=torch.int64,
+                       device=st.vis.device)
+    vrow = st.vis.view(n_rays, M * M // 32)
+    items = int(lut[vrow.view(torch.uint8).long()].sum().item())
+    rays_with_items = int((vrow != 0).any(1).sum().item())
+    blocks, kept = st.sim.ctx.cull_stats()
+    n_post = len(sysm.surfaces) - sysm.doe_index - 1
+    peak = n_sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    kernel_ms = {k: v[0] / v[1] for k, v in prof.items() if v[1] > 0}
+    modelled = {k: c2_kernel_flops(k, M, D, n_post, n_rays, rays_with_items, items, blocks,
+                                   kept) for k in kernel_ms}
+    name = max((k for k in kernel_ms if modelled[k] is not None), key=lambda k: prof[k][0])
+    achieved = modelled[name] / (kernel_ms[name] / 1e3) / 1e12
+    extra = {"visible_secondary_fraction": items / float(n_rays * M * M),
+             "traced_secondary_fraction": (64.0 * kept / (n_rays * M * M) if blocks else 1.0)}
+    return kernel_ms, extra, {
+        "kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": C2_TRAFFIC.get(name),
+        "peak_source": f"{n_sms} SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal)"}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -257,136 +542,68 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2605_15418_gb300 import raywave as RW
-
-    w = workload(args.n_side)
-    sysm = w.system
-    sim = RW.Simulator(w, device=local)
-    n_rays = sim.n_rays
-    tgt = torch.as_tensor(w.target, device=dev)
-    gI = torch.empty(sim.psf_shape, dtype=torch.float32, device=dev)
-    psf = torch.empty(sim.psf_shape, dtype=torch.float32, device=dev)
-    dphi = torch.zeros_like(sim.phi)
-    dsurf = torch.zeros(len(sysm.surfaces), 8, dtype=torch.float64, device=dev)
-    loss = torch.empty(3, dtype=torch.float64, device=dev)
-    vis = RW.alloc_vis(n_rays, sysm.doe.M, dev)      # 1 bit per secondary ray
+    n_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks, peak_kind = measured_peaks()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
-    stream = torch.cuda.current_stream(dev)
 
-    def step(ev=None):
-        s, keep = sim.sys_struct()
-        if ev: ev[0].record(stream)
-        RW.rw_generate_rays(sim.ctx, w.z_start, sysm.n_object, sim.jobs, sim.rays)
-        if ev: ev[1].record(stream)
-        RW.rw_forward_vis(sim.ctx, s, sim.jobs, sim.rays, psf, vis)
-        if ev: ev[2].record(stream)
-        RW.rw_loss_eq3(sim.ctx, psf, tgt, loss, gI)
-        dphi.zero_()
-        dsurf.zero_()
-        if ev: ev[3].record(stream)
-        RW.rw_backward_vis(sim.ctx, s, sim.jobs, sim.rays, gI, vis, dphi, None, dsurf)
-        if ev: ev[4].record(stream)
-
-    tuned = None
-    if not args.no_autotune:
-        # one step to size every buffer, then the library's launch tuning (A10)
-        step()
-        tuned = sim.ctx.autotune(sim, gI, vis)
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    launches0 = sim.ctx.launches
-    sim.ctx.profile(True)
-    clk.start()
-    for k in range(args.steps):
-        flush.zero_()
-        step(evs[k])
-    torch.cuda.synchronize()
-    clocks = clk.stop()
-    prof = sim.ctx.profile_read()
-    sim.ctx.profile(False)
-    launches = sim.ctx.launches - launches0
-    if dist:
-        dist.barrier()
-    t_step = [evs[k][0].elapsed_time(evs[k][4]) for k in range(args.steps)]
-    t_fwd = [evs[k][1].elapsed_time(evs[k][2]) for k in range(args.steps)]
-    t_bwd = [evs[k][3].elapsed_time(evs[k][4]) for k in range(args.steps)]
-    ms = max_over_ranks(float(np.sum(t_step)), dist, dev)
-    ms_per_step = ms / args.steps
-    value = weak_scaling_value(n_rays, world, ms_per_step)
-
-    # ---- end to end through the public API with host buffers
-    phi_h = torch.from_numpy(np.ascontiguousarray(sysm.doe.phi)).pin_memory()
-    tgt_h = torch.from_numpy(np.ascontiguousarray(w.target)).pin_memory()
-    psf_h = torch.empty(sim.psf_shape, dtype=torch.float32).pin_memory()
-    dphi_h = torch.empty_like(phi_h).pin_memory()
-    dsurf_h = torch.empty(len(sysm.surfaces), 8, dtype=torch.float64).pin_memory()
-    loss_h = torch.empty(3, dtype=torch.float64).pin_memory()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(1, min(args.steps, 3))
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        sim.phi.copy_(phi_h, non_blocking=True)
-        tgt.copy_(tgt_h, non_blocking=True)
-        step()
-        psf_h.copy_(psf, non_blocking=True)
-        dphi_h.copy_(dphi, non_blocking=True)
-        dsurf_h.copy_(dsurf, non_blocking=True)
-        loss_h.copy_(loss, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    h2d = phi_h.numel() * 4 + tgt_h.numel() * 4
-    d2h = psf_h.numel() * 4 + dphi_h.numel() * 4 + dsurf_h.numel() * 8 + 24
-
-    # ---- roofline of the dominant kernel (FP32 ALU bound), per-launch times
-    # from the library's CUDA events around every launch of the timed steps
-    D, M = sysm.doe.D, sysm.doe.M
-    lut = torch.tensor([bin(i).count("1") for i in range(256)], dtype=torch.int64, device=dev)
-    vrow = vis.view(n_rays, M * M // 32)
-    items = int(lut[vrow.view(torch.uint8).long()].sum().item())
-    rays_with_items = int((vrow != 0).any(1).sum().item())
-    vfrac = items / float(n_rays * M * M)
-    blocks, kept = sim.ctx.cull_stats()
-    n_post = len(sysm.surfaces) - sysm.doe_index - 1
-    fwd_ms = float(np.mean(t_fwd))
-    bwd_ms = float(np.mean(t_bwd))
-    peak = NUM_SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12      # TFLOP/s at max SM clock
-    kernel_ms = {k: v[0] / v[1] for k, v in prof.items() if v[1] > 0}
-    modelled = {k: kernel_flops(k, M, D, n_post, n_rays, rays_with_items, items, blocks, kept)
-                for k in kernel_ms}
-    name = max((k for k in kernel_ms if modelled[k] is not None), key=lambda k: prof[k][0])
-    tms = kernel_ms[name]
-    achieved = modelled[name] / (tms / 1e3) / 1e12
+    name = args.config
+    w = workload(name, args)
+    st = Step(name, w, dev, local)
+    tm = time_steps(st, args.steps, args.warmup, flush, dev,
+                    autotune=(name == "c2" and not args.no_autotune), dist=dist, local=local,
+                    sample_clocks=True)
+    ms_per_step = max_over_ranks(tm["ms"], dist, dev) / args.steps
+    value = weak_scaling_value(st.sim.n_rays, world, ms_per_step)
+    e2e = e2e_rate(st, max(1, min(args.steps, 3)), dev, world)
+    cfg = config_of(name, w, args)
+    cfg.update({"fwd_ms": tm["fwd_ms"], "bwd_ms": tm["bwd_ms"]})
+    if name == "c5":
+        kernel_ms, roof = roofline_c5(tm, st, peaks, n_sms, tm["clocks"])
+    else:
+        kernel_ms, extra, roof = roofline_c2(tm, st, n_sms)
+        cfg.update(extra)
+        cfg["tuned_grids"] = tm["tuned"]
+    cfg["kernel_ms"] = {k: round(v, 4) for k, v in kernel_ms.items()}
     line = {"metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": w.name, "incident_rays": n_rays, "jobs": len(w.jobs),
-                       "D": D, "secondary_rays_per_incident": D * D, "sensor": "512x512x9",
-                       "surfaces_after_doe": n_post, "l2": "flushed between steps (256 MB)",
-                       "visible_secondary_fraction": vfrac,
-                       "traced_secondary_fraction": (64.0 * kept / (n_rays * M * M)
-                                                     if blocks else 1.0),
-                       "fwd_ms": fwd_ms, "bwd_ms": bwd_ms,
-                       "kernel_ms": {k: round(v, 4) for k, v in kernel_ms.items()},
-                       "tuned_grids": tuned},
-            "roofline": {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": TRAFFIC.get(name),
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal)"},
-            "e2e": {"value": world * n_rays / (e2e_ms / 1e3), "unit": "rays/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(launches),
-            "clocks": clocks}
+            "data": "synthetic", "config": cfg, "roofline": roof, "e2e": e2e,
+            "gpu_launches": tm["launches"], "clocks": tm["clocks"],
+            "peak_memory_gb": torch.cuda.max_memory_allocated(dev) / 1e9}
+
+    # ---- the other workloads, fewer steps each
+    also = []
+    for other in [x for x in args.also.split(",") if x and x != name]:
+        wo = workload(other, args)
+        so = Step(other, wo, dev, local)
+        to = time_steps(so, args.also_steps, args.also_warmup, flush, dev,
+                        autotune=(other == "c2" and not args.no_autotune), dist=dist,
+                        local=local, sample_clocks=False)
+        mso = max_over_ranks(to["ms"], dist, dev) / args.also_steps
+        co = config_of(other, wo, args)
+        co.update({"fwd_ms": to["fwd_ms"], "bwd_ms": to["bwd_ms"]})
+        if other == "c5":
+            kmo, ro = roofline_c5(to, so, peaks, n_sms, None)
+        else:
+            kmo, exo, ro = roofline_c2(to, so, n_sms)
+            co.update(exo)
+        co["kernel_ms"] = {k: round(v, 4) for k, v in kmo.items()}
+        also.append({"value": weak_scaling_value(so.sim.n_rays, world, mso), "unit": "rays/s",
+                     "ms_per_step": mso, "steps": args.also_steps,
+                     "warmup": args.also_warmup, "config": co, "roofline": ro,
+                     "gpu_launches": to["launches"]})
+        del so
+        torch.cuda.empty_cache()
+    if also:
+        line["also"] = also
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_rays, args.cpu_seconds)
+        n_cpu = args.cpu_rays or default_cpu_rays(name)
+        cb, (sub, ref) = cpu_baseline(w, n_cpu, args.cpu_seconds)
+        line["cpu_baseline"] = cb
+        line["parity"] = {"psf_rel_l2": gpu_parity(st, sub, ref), "bar": 1e-4,
+                          "rays": int(sum(len(s) for s in sub)),
+                          "sample": "the cpu_baseline's first sample, same rays on both sides"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -349,9 +349,12 @@ rw_status rw_loss_eq3(rw_ctx* ctx, const float* psf, const float* target, int64_
  * the complex field U of the same inputs (one forward pass; the phase is not
  * in psf), forms dL/dU = 2 (dL/dpsf) U and reverses every secondary ray's
  * window sum, optical path included; surface gradients then carry the
- * optical-path terms of every segment.  With a conformal DOE the gradients
- * through its frame and bilinear gather are not formed (dphi and damp are,
- * and so are the surfaces behind the DOE). */
+ * optical-path terms of every segment.  With a conformal DOE (sphere or
+ * Gaussian bump) the hit point, the tangent frame (u, v, n) and the
+ * tangent-plane patch samples depend on the incident ray and on the
+ * substrate: their reverse gives the substrate's z and c (sphere) or z,
+ * height (c slot) and width (k slot) of the bump, and carries dL/d(ray)
+ * on to the surfaces before the DOE. */
 rw_status rw_backward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
                       int32_t njob, const rw_rays* rays, const float* dl_dpsf,
                       float* dphi, float* damp, double* dsurf);

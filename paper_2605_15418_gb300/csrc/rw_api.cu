@@ -224,8 +224,8 @@ static bool supported_M(int M) { return M == 16 || M == 32 || M == 64 || M == 96
 
 // Split-adjoint buffers for n incident rays and cap work items (the forward's
 // tape uses the same layout).
-static rw_status split_buffers(rw_ctx* ctx, long long n, long long cap, SplitBufs& B) {
-    const size_t per_ray = sizeof(RayAtDoe) + sizeof(long long) + sizeof(int) + 6 * sizeof(float);
+static rw_status split_buffers(rw_ctx* ctx, long long n, long long cap, int nrs, SplitBufs& B) {
+    const size_t per_ray = sizeof(RayAtDoe) + sizeof(long long) + sizeof(int) + nrs * sizeof(float);
     rw_status st = ensure_buf(ctx, ctx->split_rays, n * per_ray + 256, "split adjoint rays");
     if (st != RW_OK) return st;
     if (cap < 1) cap = 1;
@@ -455,6 +455,8 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
     d.spitch = (float)sen.pitch;
     d.inv_spitch = (float)(1.0 / sen.pitch);
     d.coherent = sen.coherent ? 1 : 0;
+    // per-ray adjoint sums: the conformal frame and patch gather add theirs
+    d.nrs = d.conformal ? RW_RS : (d.coherent ? 7 : 6);
     d.window = sen.window;
     d.n_sensor = (float)n_prev;
     return RW_OK;
@@ -525,7 +527,9 @@ static size_t shared_limit_ok(rw_ctx* ctx, const DSys& d) {
 // Prepare the transmission maps and device tables.  Returns device pointers.
 static rw_status prepare(rw_ctx* ctx, const rw_system* sys, const Packed& P, float2** T,
                          DJob** djobs, long long** dprefix) {
-    if (!shared_limit_ok(ctx, P.sys)) return fail(ctx, RW_EINVAL, "n_ssr too large for shared memory");
+    if (!shared_limit_ok(ctx, P.sys))
+        return fail(ctx, RW_EINVAL, "patch size / n_ssr too large for the forward's shared memory "
+                                    "(sampled emission: M <= 96)");
     std::vector<void*> ptrs;
     rw_status st = upload(ctx, {{P.jobs.data(), P.jobs.size() * sizeof(DJob)},
                                 {P.prefix.data(), P.prefix.size() * sizeof(long long)},
@@ -823,7 +827,7 @@ static rw_status forward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* j
                 // tape the visible secondary rays for the adjoint
                 long long cap = ctx->tape_hint;
                 if (cap <= 0) cap = std::max<long long>(1 << 20, P.total * P.sys.M * P.sys.M / 64);
-                if ((st = split_buffers(ctx, P.total, cap, tape)) != RW_OK) return st;
+                if ((st = split_buffers(ctx, P.total, cap, P.sys.nrs, tape)) != RW_OK) return st;
                 tape.counter = tape_counter(ctx);
                 RW_CUDA(cudaMemsetAsync(tape.counter, 0, sizeof(unsigned long long), ctx->stream),
                         "tape counter");
@@ -935,7 +939,7 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
                 ctx->tape_hint = nitems + nitems / 8 + 1024;
                 taped = false;
             } else {
-                if ((st = split_buffers(ctx, P.total, ctx->tape_cap, B)) != RW_OK) return st;
+                if ((st = split_buffers(ctx, P.total, ctx->tape_cap, P.sys.nrs, B)) != RW_OK) return st;
                 B.counter = tape_counter(ctx);
             }
         }
@@ -950,11 +954,12 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
                                     cudaMemcpyDeviceToHost, ctx->stream), "count read");
             RW_CUDA(cudaStreamSynchronize(ctx->stream), "count sync");
             nitems = (long long)*ctx->count_host;
-            if ((st = split_buffers(ctx, P.total, nitems, B)) != RW_OK) return st;
+            if ((st = split_buffers(ctx, P.total, nitems, P.sys.nrs, B)) != RW_OK) return st;
             B.counter = dcount;
             RW_CUDA(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long), ctx->stream), "counter");
         }
-        RW_CUDA(cudaMemsetAsync(B.rsum, 0, P.total * 6 * sizeof(float), ctx->stream), "sums");
+        RW_CUDA(cudaMemsetAsync(B.rsum, 0, P.total * P.sys.nrs * sizeof(float), ctx->stream),
+                "sums");
         RW_CUDA(launch_backward_split(lctx(ctx), P.sys, dj, dp, njob, P.total, rays_in(rays), T,
                                       sys->doe.amp, dl_dpsf, vis, B, nitems, taped ? 1 : 0, dphi,
                                       damp, dsurf, status_word(ctx)),
@@ -966,7 +971,7 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
     float* coh_rsum = nullptr;
     double* coh_jsum = nullptr;
     if (P.sys.coherent) {
-        if ((st = ensure_buf(ctx, ctx->coh_rsum, (size_t)P.total * 7 * sizeof(float),
+        if ((st = ensure_buf(ctx, ctx->coh_rsum, (size_t)P.total * P.sys.nrs * sizeof(float),
                              "coherent adjoint scratch")) != RW_OK)
             return st;
         if ((st = ensure_buf(ctx, ctx->coh_jsum, (size_t)njob * 2 * sizeof(double),
@@ -977,7 +982,7 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
         RW_CUDA(cudaMemsetAsync(coh_jsum, 0, (size_t)njob * 2 * sizeof(double), ctx->stream),
                 "job sums clear");
         // per-ray sums: bin slices of one ray add into them
-        RW_CUDA(cudaMemsetAsync(coh_rsum, 0, (size_t)P.total * 7 * sizeof(float), ctx->stream),
+        RW_CUDA(cudaMemsetAsync(coh_rsum, 0, (size_t)P.total * P.sys.nrs * sizeof(float), ctx->stream),
                 "ray sums clear");
         // I = |U|^2 loses the phase of U: recompute the field, then
         // dL/dU = 2 (dL/dI) U in place
@@ -1133,7 +1138,7 @@ static rw_status backward_dispersive(rw_ctx* ctx, const rw_system* sys, const rw
         float* coh_rsum = nullptr;
         double* coh_jsum = nullptr;
         if (coherent) {
-            if ((st = ensure_buf(ctx, ctx->coh_rsum, (size_t)P[g].total * 7 * sizeof(float),
+            if ((st = ensure_buf(ctx, ctx->coh_rsum, (size_t)P[g].total * P[g].sys.nrs * sizeof(float),
                                  "coherent adjoint scratch")) != RW_OK)
                 return st;
             if ((st = ensure_buf(ctx, ctx->coh_jsum, (size_t)nj * 2 * sizeof(double),
@@ -1143,7 +1148,7 @@ static rw_status backward_dispersive(rw_ctx* ctx, const rw_system* sys, const rw
             coh_jsum = (double*)ctx->coh_jsum.p;
             RW_CUDA(cudaMemsetAsync(coh_jsum, 0, (size_t)nj * 2 * sizeof(double), ctx->stream),
                     "job sums clear");
-            RW_CUDA(cudaMemsetAsync(coh_rsum, 0, (size_t)P[g].total * 7 * sizeof(float),
+            RW_CUDA(cudaMemsetAsync(coh_rsum, 0, (size_t)P[g].total * P[g].sys.nrs * sizeof(float),
                                     ctx->stream), "ray sums clear");
         }
         int nl = 0;

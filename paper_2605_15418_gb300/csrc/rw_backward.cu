@@ -151,26 +151,33 @@ __device__ __noinline__ void gumbel_pass_b(float* __restrict__ recf, const float
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int k = 0; k < 6; ++k) a4[q][k] = 0.f;
-        // draws whose bin is -1 carry h~ = c~ = 0: no test needed
+        // draws whose bin is -1 carry h~ = c~ = 0: no test needed; four Philox
+        // blocks (four draws) per step
         int i = s0;
-        for (; i + KS < N; i += 2 * KS) {
-            const uint4 wa = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)i, ray, off), k0, k1);
-            const uint4 wb = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)(i + KS), ray, off),
-                                           k0, k1);
-            const float4 ha = sa[i], hb = sa[i + KS];
-            const float2 h2a = sc2[i], h2b = sc2[i + KS];
-            const uint32_t wsa[4] = {wa.x, wa.y, wa.z, wa.w};
-            const uint32_t wsb[4] = {wb.x, wb.y, wb.z, wb.w};
+        for (; i + 3 * KS < N; i += 4 * KS) {
+            uint4 w[4];
+            float4 h[4];
+            float2 h2[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float ea = rcp_approx(gumbel_E_fast(wsa[q]));
-                const float eb = rcp_approx(gumbel_E_fast(wsb[q]));
-                a4[q][0] = fmaf(eb, hb.x, fmaf(ea, ha.x, a4[q][0]));
-                a4[q][1] = fmaf(eb, hb.y, fmaf(ea, ha.y, a4[q][1]));
-                a4[q][2] = fmaf(eb, hb.z, fmaf(ea, ha.z, a4[q][2]));
-                a4[q][3] = fmaf(eb, hb.w, fmaf(ea, ha.w, a4[q][3]));
-                a4[q][4] = fmaf(eb, h2b.x, fmaf(ea, h2a.x, a4[q][4]));
-                a4[q][5] = fmaf(eb, h2b.y, fmaf(ea, h2a.y, a4[q][5]));
+            for (int d = 0; d < 4; ++d) {
+                w[d] = philox4x32_10(make_uint4((uint32_t)G, (uint32_t)(i + d * KS), ray, off),
+                                     k0, k1);
+                h[d] = sa[i + d * KS];
+                h2[d] = sc2[i + d * KS];
+            }
+#pragma unroll
+            for (int d = 0; d < 4; ++d) {
+                const uint32_t ws[4] = {w[d].x, w[d].y, w[d].z, w[d].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float e = rcp_approx(gumbel_E_fast(ws[q]));
+                    a4[q][0] = fmaf(e, h[d].x, a4[q][0]);
+                    a4[q][1] = fmaf(e, h[d].y, a4[q][1]);
+                    a4[q][2] = fmaf(e, h[d].z, a4[q][2]);
+                    a4[q][3] = fmaf(e, h[d].w, a4[q][3]);
+                    a4[q][4] = fmaf(e, h2[d].x, a4[q][4]);
+                    a4[q][5] = fmaf(e, h2[d].y, a4[q][5]);
+                }
             }
         }
         for (; i < N; i += KS) {
@@ -415,7 +422,7 @@ __device__ __forceinline__ void exh_bin_adjoint_coh(const DSys& sys, const RayAt
                                                     const float2* X, const float2* phu,
                                                     const float2* phv,
                                                     const float2* __restrict__ gf, float2* G,
-                                                    float2 ain, int f, float (&acc)[7],
+                                                    float2 ain, int f, float (&acc)[RW_RS],
                                                     float* gs, unsigned* status) {
     const int jvi = f / M, jui = f - (f / M) * M;
     int mu = jui + M / 2; if (mu >= M) mu -= M;
@@ -450,7 +457,7 @@ template <int M, int NS>
 __device__ __forceinline__ void exh_bin_adjoint(const DSys& sys, const RayAtDoe& R,
                                                 const float2* X, const float2* phu,
                                                 const float2* phv, const float* __restrict__ gimg,
-                                                float2* G, float2 ain, int f, float (&acc)[7],
+                                                float2* G, float2 ain, int f, float (&acc)[RW_RS],
                                                 SurfGrads<NS>& SG, float* gs, unsigned* status) {
     const int jvi = f / M, jui = f - (f / M) * M;
     int mu = jui + M / 2; if (mu >= M) mu -= M;
@@ -501,8 +508,8 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
     float2* G = smp ? X : reinterpret_cast<float2*>(smem + sampled_scratch_offset(M));
     BwdRay* bray = reinterpret_cast<BwdRay*>(smem + sampled_scratch_offset(M) +
                                              (smp ? 0 : sizeof(float2) * Patch<M>::ELEMS));
-    float* red = reinterpret_cast<float*>(bray + RW_TILE);   // [8 warps][9]
-    unsigned char* sscr = reinterpret_cast<unsigned char*>(red + 9 * (RW_THREADS / 32));
+    float* red = reinterpret_cast<float*>(bray + RW_TILE);   // [8 warps][RW_RS]
+    unsigned char* sscr = reinterpret_cast<unsigned char*>(red + RW_RS * (RW_THREADS / 32));
     fft_twiddles<M>(tw);
     SurfGrads<NS> SG;
     SG.zero();
@@ -538,7 +545,9 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
             const float2 ain = make_float2(R.a_re, R.a_im);
             const float* gimg = gpsf + (long long)J.out * npx;
             const float2* gf = COH ? gfield + (long long)J.out * npx : nullptr;
-            float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float acc[RW_RS];
+#pragma unroll
+            for (int k = 0; k < RW_RS; ++k) acc[k] = 0.f;
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
                 constexpr int KW = M * M / RW_THREADS;   // visibility words per warp and ray
                 if (COH) {
@@ -594,86 +603,72 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                 sampled_ray_adjoint<M, NS, COH>(sys, R, J.k0, R.rid, X, phu, phv, gimg,
                                                 gf, sscr, acc, SG, gs, status);
             }
-            // ---- per-ray reduction of the geometric gradients
+            // ---- per-ray reduction of the geometric gradients (with a conformal
+            // DOE also the frame sums)
+            const int nk = sys.conformal ? RW_RS_GATHER : NACC;
 #pragma unroll
-            for (int k = 0; k < NACC; ++k)
-                for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+            for (int k = 0; k < RW_RS_GATHER; ++k)
+                if (k < nk)
+                    for (int o = 16; o > 0; o >>= 1)
+                        acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
             __syncthreads();
             if (lane == 0)
 #pragma unroll
-                for (int k = 0; k < NACC; ++k) red[warp * 9 + k] = acc[k];
+                for (int k = 0; k < RW_RS_GATHER; ++k)
+                    if (k < nk) red[warp * RW_RS + k] = acc[k];
             __syncthreads();
             if (threadIdx.x == 0) {
-                float s[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float* sb = bray[r].s;
+                for (int k = 0; k < RW_RS; ++k) sb[k] = 0.f;
                 for (int w = 0; w < RW_THREADS / 32; ++w)
-                    for (int k = 0; k < NACC; ++k) s[k] += red[w * 9 + k];
-                BwdRay& B = bray[r];
-                B.gpx = s[0]; B.gpy = s[1]; B.gpz = s[2];
-                // kappa_in = k0 n_in (d.u, d.v)
-                const float kn_in = J.k0 * sys.n_in;
-                B.gdx = kn_in * (s[3] * R.u[0] + s[4] * R.v[0]);
-                B.gdy = kn_in * (s[3] * R.u[1] + s[4] * R.v[1]);
-                B.gdz = kn_in * (s[3] * R.u[2] + s[4] * R.v[2]);
-                B.gnin = (R.kin_u * s[3] + R.kin_v * s[4]) / sys.n_in;
-                B.gnout = J.k0 * s[5];
-                B.gopl = s[6];
+                    for (int k = 0; k < nk; ++k) sb[k] += red[w * RW_RS + k];
                 if (COH) {
                     // the incident side runs in k_coh_incident once every ray's
                     // dL/dOPL is known (see there)
-                    float* o = coh_rsum + R.gid * 7;
+                    float* o = coh_rsum + R.gid * sys.nrs;
                     if (nslice > 1) {
-#pragma unroll
-                        for (int k = 0; k < 7; ++k) atomicAdd(o + k, s[k]);   // zeroed by the host
+                        for (int k = 0; k < nk; ++k) atomicAdd(o + k, sb[k]);   // zeroed by the host
                     } else {
-#pragma unroll
-                        for (int k = 0; k < 7; ++k) o[k] = s[k];
+                        for (int k = 0; k < nk; ++k) o[k] = sb[k];
                     }
-                    atomicAdd(coh_jsum + 2 * R.job, (double)s[6]);
+                    atomicAdd(coh_jsum + 2 * R.job, (double)sb[6]);
                     if (slice == 0) atomicAdd(coh_jsum + 2 * R.job + 1, 1.0);
                 }
             }
-            // ---- adjoint patch transform and map scatter
+            // ---- adjoint patch transform and map scatter (with a conformal DOE
+            // also the gradient of the patch sample positions)
             fft2d<M, true>(G, tw);
-            map_scatter<M>(sys, R, T, amp, G, J.phase_scale, dphi, damp);
+            float gq[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            map_scatter<M>(sys, R, T, amp, G, J.phase_scale, dphi, damp,
+                           sys.conformal ? gq : nullptr);
+            if (sys.conformal) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    for (int o = 16; o > 0; o >>= 1) gq[k] += __shfl_xor_sync(0xffffffffu, gq[k], o);
+                __syncthreads();
+                if (lane == 0)
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) red[warp * RW_RS + k] = gq[k];
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    float* sb = bray[r].s;
+                    for (int k = 0; k < 6; ++k) {
+                        float v = 0.f;
+                        for (int w = 0; w < RW_THREADS / 32; ++w) v += red[w * RW_RS + k];
+                        sb[RW_RS_GATHER + k] = v;
+                        if (COH) {
+                            float* o = coh_rsum + R.gid * sys.nrs + RW_RS_GATHER + k;
+                            if (nslice > 1) atomicAdd(o, v); else *o = v;
+                        }
+                    }
+                }
+            }
             __syncthreads();
         }
         // ---- incident side: DOE hit and pre-DOE surfaces, one lane per ray
-        if (!COH && threadIdx.x < RW_TILE && info[threadIdx.x].alive) {
-            const RayAtDoe& R = info[threadIdx.x];
-            const BwdRay& B = bray[threadIdx.x];
-            const DJob& J = jobs[R.job];
-            const long long ri = J.off + (R.gid - prefix[R.job]);
-            float x = rays.ox[ri], y = rays.oy[ri], zl = rays.oz[ri];
-            float dx = rays.dx[ri], dy = rays.dy[ri], dz = rays.dz[ri];
-            double dummy = 0.0;
-            SurfIn st[RW_MAXS];
-            for (int s = 0; s < sys.doe_index; ++s) {
-                st[s].x = x; st[s].y = y; st[s].zl = zl - sys.s[s].gap;
-                st[s].dx = dx; st[s].dy = dy; st[s].dz = dz;
-                trace_one<false>(sys.s[s], x, y, zl, dx, dy, dz, dummy, status);
-            }
-            // index gradients of the DOE emission
-            if (sys.nout_slot >= 0) gs[sys.nout_slot * RW_NGRAD + 7] += B.gnout;
-            if (sys.doe_index > 0) gs[(sys.doe_index - 1) * RW_NGRAD + 7] += B.gnin;
-            float gx = B.gpx, gy = B.gpy, gz = B.gpz;
-            float gdx = B.gdx, gdy = B.gdy, gdz = B.gdz;
-            if (!sys.conformal) {
-                // planar DOE hit: h = p + t d, t = (z_doe - p_z) / d_z
-                const float zld = zl - sys.s[sys.doe_index].gap;
-                const float t = -zld / dz;
-                const float gt = gx * dx + gy * dy + gz * dz;
-                gdx += gx * t; gdy += gy * t; gdz += gz * t;
-                gz += -gt / dz;
-                gdz += -gt * t / dz;
-                gs[sys.doe_index * RW_NGRAD + 0] += gt / dz;
-                for (int s = sys.doe_index - 1; s >= 0; --s) {
-                    float gnb = 0.f;
-                    trace_one_adjoint(sys.s[s], st[s], gx, gy, gz, gdx, gdy, gdz,
-                                      gs + s * RW_NGRAD, &gnb);
-                    if (s > 0) gs[(s - 1) * RW_NGRAD + 7] += gnb;
-                }
-            }
-        }
+        if (!COH && threadIdx.x < RW_TILE && info[threadIdx.x].alive)
+            incident_adjoint(sys, jobs, prefix, rays, info[threadIdx.x], bray[threadIdx.x].s, gs,
+                             status);
     }
     // ---- CTA reduction of surface-parameter gradients
     if (!dsurf) return;
@@ -725,9 +720,9 @@ k_coh_incident(const DSys sys, const DJob* __restrict__ jobs, const long long* _
         RayAtDoe R;
         incident_to_doe(sys, jobs, prefix, njob, total, rays, g, R, status);
         if (!R.alive) continue;
-        float s[7];
+        float s[RW_RS];
 #pragma unroll
-        for (int k = 0; k < 7; ++k) s[k] = rsum[g * 7 + k];
+        for (int k = 0; k < RW_RS; ++k) s[k] = k < sys.nrs ? rsum[g * sys.nrs + k] : 0.f;
         const double n = jsum[2 * R.job + 1];
         const float gopl = n > 0.0 ? (float)((double)s[6] - jsum[2 * R.job] / n) : s[6];
         incident_adjoint<true>(sys, jobs, prefix, rays, R, s, gs, status, gopl);
@@ -737,7 +732,7 @@ k_coh_incident(const DSys sys, const DJob* __restrict__ jobs, const long long* _
 
 inline size_t backward_smem_bytes(int M, int emit, int n_ssr) {
     size_t b = sampled_scratch_offset(M) + sizeof(BwdRay) * RW_TILE +
-               sizeof(float) * 9 * (RW_THREADS / 32);
+               sizeof(float) * RW_RS * (RW_THREADS / 32);
     if (emit == RW_EMIT_SAMPLED) b += sampled_bwd_bytes(M, n_ssr);   // dL/dX over X
     else b += sizeof(float2) * (size_t)M * (M + 2);
     size_t red = sizeof(double) * RW_MAXS * RW_NGRAD * (RW_THREADS / 32);

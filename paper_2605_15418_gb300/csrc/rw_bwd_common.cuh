@@ -4,11 +4,9 @@
 #pragma once
 #include "rw_kernels.cuh"
 
+// Per-ray sums of one incident ray of a tile (layout of RW_RS).
 struct BwdRay {
-    float gpx, gpy, gpz;      // dL/d(hit point)
-    float gdx, gdy, gdz;      // dL/d(incident direction at the DOE)
-    float gnin, gnout;        // dL/d(index before / after the DOE)
-    float gopl;               // dL/d(optical path at the DOE), coherent sensor
+    float s[RW_RS];
 };
 
 __device__ __forceinline__ void bilinear_grad(const DSys& sys, float cx, float cy, float x,
@@ -79,7 +77,7 @@ __device__ __forceinline__ bool secondary_adjoint(const DSys& sys, const RayAtDo
         }
         if (!ok) return false;
         const float zs = zl - sys.sensor_gap;
-        const float ts = -zs * rcp_fast(ez);
+        const float ts = -zs / ez;                 // as in the forward: correctly rounded
         const float xs = fmaf(ts, ex, x), ys = fmaf(ts, ey, y);
         float gxs, gys;
         bilinear_grad(sys, R.cx, R.cy, xs, ys, gimg, gw, gxs, gys);
@@ -259,7 +257,8 @@ __device__ __forceinline__ bool secondary_adjoint_coh(const DSys& sys, const Ray
 }
 
 // Reverse of d = (ku u + kv v + kn n) / K for bin (ju, jv): adds dL/d(origin),
-// dL/dkappa_u, dL/dkappa_v and dL/dK to acc[0..5].
+// dL/dkappa_u, dL/dkappa_v and dL/dK to acc[0..5] and, with a conformal DOE,
+// dL/d(u, v, n) to acc[RW_RS_FRAME ..] (acc then holds RW_RS entries).
 __device__ __forceinline__ void emission_adjoint(const DSys& sys, const RayAtDoe& R, int ju,
                                                  int jv, float dx, float dy, float dz,
                                                  float gx, float gy, float gz, float gdx,
@@ -277,6 +276,16 @@ __device__ __forceinline__ void emission_adjoint(const DSys& sys, const RayAtDoe
     acc[3] += (gdu - ku * ikn * gdn) * R.invK;
     acc[4] += (gdv - kv * ikn * gdn) * R.invK;
     acc[5] += gdn * ikn - (gdx * dx + gdy * dy + gdz * dz) * R.invK;
+    if (sys.conformal) {
+        // d = (a_u u + a_v v + a_n n) depends on the frame of the curved DOE
+        const float au = ku * R.invK, av = kv * R.invK, an = kn2 * ikn * R.invK;
+        acc[RW_RS_FRAME + 0] += au * gdx; acc[RW_RS_FRAME + 1] += au * gdy;
+        acc[RW_RS_FRAME + 2] += au * gdz;
+        acc[RW_RS_FRAME + 3] += av * gdx; acc[RW_RS_FRAME + 4] += av * gdy;
+        acc[RW_RS_FRAME + 5] += av * gdz;
+        acc[RW_RS_FRAME + 6] += an * gdx; acc[RW_RS_FRAME + 7] += an * gdy;
+        acc[RW_RS_FRAME + 8] += an * gdz;
+    }
 }
 
 
@@ -308,12 +317,15 @@ __device__ __forceinline__ void map_grad_at(const DSys& sys, long long p, float2
     }
 }
 
+// With gq (conformal DOE, bilinear gather), also the patch positions'
+// gradient: per sample, g_u = Re(conj(dL/dT) dT/d(fractional column)) and
+// g_v likewise, summed times 1, a and b into gq[0..5] (per thread).
 template <int M>
 __device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
                                             const float2* __restrict__ T,
                                             const float* __restrict__ amp, const float2* G,
                                             float scale, float* __restrict__ dphi,
-                                            float* __restrict__ damp) {
+                                            float* __restrict__ damp, float* gq = nullptr) {
     const int H = sys.H, W = sys.W, D = sys.D;
     if (sys.gather == RW_GATHER_NEAREST && dphi && !damp && !sys.two_phase && D == M &&
         R.r0 >= 0 &&
@@ -362,24 +374,140 @@ __device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
             const int i0 = R.c0 + (int)iuf, j0 = R.r0 + (int)ivf;
             const float wt[4] = {(1.f - wu) * (1.f - wv), wu * (1.f - wv), (1.f - wu) * wv, wu * wv};
             const int di[4] = {0, 1, 0, 1}, dj[4] = {0, 0, 1, 1};
+            float2 tv[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int rr = j0 + dj[q], cc = i0 + di[q];
-                if ((unsigned)rr < (unsigned)H && (unsigned)cc < (unsigned)W) {
-                    const long long p = (long long)rr * W + cc;
-                    map_grad_at(sys, p, __ldg(&T[p]), cscale(gT, wt[q]), amp, scale, dphi,
-                                damp);
-                }
+                const bool in = (unsigned)rr < (unsigned)H && (unsigned)cc < (unsigned)W;
+                const long long p = (long long)rr * W + cc;
+                tv[q] = in ? __ldg(&T[p]) : make_float2(0.f, 0.f);
+                if (in) map_grad_at(sys, p, tv[q], cscale(gT, wt[q]), amp, scale, dphi, damp);
+            }
+            if (gq) {
+                // T = sum of taps: dT/dwu, dT/dwv of the bilinear weights
+                const float2 du = make_float2((1.f - wv) * (tv[1].x - tv[0].x) + wv * (tv[3].x - tv[2].x),
+                                              (1.f - wv) * (tv[1].y - tv[0].y) + wv * (tv[3].y - tv[2].y));
+                const float2 dv = make_float2((1.f - wu) * (tv[2].x - tv[0].x) + wu * (tv[3].x - tv[1].x),
+                                              (1.f - wu) * (tv[2].y - tv[0].y) + wu * (tv[3].y - tv[1].y));
+                const float gu = gT.x * du.x + gT.y * du.y, gv = gT.x * dv.x + gT.y * dv.y;
+                gq[0] += gu; gq[1] += oa * gu; gq[2] += ob * gu;
+                gq[3] += gv; gq[4] += oa * gv; gq[5] += ob * gv;
             }
         }
     }
 }
 
-// Incident side of one ray from its summed emission gradients
-// s = (dL/dP (3), dL/dkappa_u, dL/dkappa_v, dL/dK): reverse of the DOE hit and
-// of the pre-DOE surfaces; adds surface gradients to gs.  OPLG: the optical
-// path at the DOE carries the gradient gopl (coherent sensor), reversed
-// through every segment n t.
+// Reverse of a conformal DOE's hit and tangent frame for one incident ray.
+// The ray arrives at (x, y, zld) (zld local to the DOE vertex) along d; the
+// forward recomputed here: run t to the substrate (conformal_hit), hit Q,
+// unit normal N(Q) (sphere: (-c Qx, -c Qy, sqrt(1 - c^2 s)); Gaussian bump:
+// (m, 1) / |(m, 1)|, m = 2 iw2 e (Qx, Qy), e = h exp(-s iw2), iw2 = 1/(2 w^2)),
+// n_o = N oriented along d, u = normalise(x - n_ox n_o), v = n_o x u, and the
+// outgoing normal n = n_o (transmissive) or -n_o (mirror).
+// In: s, the ray's per-ray sums (dL/d hit, dL/dkappa, frame and patch-gather
+// sums); gd, dL/dd from the incident wavevector already.  Out: dL/d(x, y,
+// zld) in (gx, gy, gz), dL/dd added to gd, and the substrate's z, c (sphere)
+// or z, height, width (bump) gradients added to gdoe[0..2].
+__device__ __forceinline__ void conformal_doe_adjoint(const DSys& sys, const DSurf& S,
+                                                      float kn_in, float x, float y, double zld,
+                                                      float dx, float dy, float dz,
+                                                      const float* s, float gopl_t,
+                                                      float& gx, float& gy, float& gz,
+                                                      float& gdx, float& gdy, float& gdz,
+                                                      float* gdoe) {
+    double td;
+    gx = gy = gz = 0.f;
+    if (!conformal_hit(S, x, y, zld, dx, dy, dz, td, nullptr)) return;
+    const float t = (float)td;
+    const float Qx = (float)((double)x + td * dx), Qy = (float)((double)y + td * dy);
+    const float Qz = (float)(zld + td * dz);
+    const float s2 = Qx * Qx + Qy * Qy;
+    const bool bump = S.kind == RW_GAUSS;
+    // ---- forward: normal, frame
+    float Nx, Ny, Nz, iw2 = 0.f, ex = 0.f, mx = 0.f, my = 0.f, inv = 1.f;
+    const float c = (float)S.cd;
+    if (bump) {
+        iw2 = (float)(0.5 / (S.kd * S.kd));
+        ex = (float)S.cd * expf(-s2 * iw2);
+        mx = 2.f * iw2 * ex * Qx; my = 2.f * iw2 * ex * Qy;
+        inv = rsqrtf(mx * mx + my * my + 1.f);
+        Nx = mx * inv; Ny = my * inv; Nz = inv;
+    } else {
+        Nx = -c * Qx; Ny = -c * Qy; Nz = sqrtf(fmaxf(1.f - c * c * s2, 0.f));
+    }
+    const float sg = (Nx * dx + Ny * dy + Nz * dz < 0.f) ? -1.f : 1.f;
+    const float nox = sg * Nx, noy = sg * Ny, noz = sg * Nz;
+    const float ax = 1.f - nox * nox, ay = -nox * noy, az = -nox * noz;
+    const float la = sqrtf(ax * ax + ay * ay + az * az), ila = 1.f / la;
+    const float ux = ax * ila, uy = ay * ila, uz = az * ila;
+    // ---- gradients on the frame: emitted directions, incident wavevector
+    // kappa_in = k0 n_in (d.u, d.v), and the patch sample positions
+    // Q + a p u + b p v read at their (x, y) (map column = x / p + const)
+    const float ip = 1.f / sys.pitchf;
+    float gUx = s[7] + kn_in * s[3] * dx + s[17], gUy = s[8] + kn_in * s[3] * dy + s[20];
+    float gUz = s[9] + kn_in * s[3] * dz;
+    const float gVx = s[10] + kn_in * s[4] * dx + s[18], gVy = s[11] + kn_in * s[4] * dy + s[21];
+    const float gVz = s[12] + kn_in * s[4] * dz;
+    const float fn = sys.reflective ? -1.f : 1.f;
+    float gNx = fn * s[13], gNy = fn * s[14], gNz = fn * s[15];
+    float gQx = s[0] + s[16] * ip, gQy = s[1] + s[19] * ip, gQz = s[2];
+    // v = n_o x u
+    gNx += uy * gVz - uz * gVy; gNy += uz * gVx - ux * gVz; gNz += ux * gVy - uy * gVx;
+    gUx += gVy * noz - gVz * noy; gUy += gVz * nox - gVx * noz; gUz += gVx * noy - gVy * nox;
+    // u = a / |a|, a = x - n_ox n_o
+    const float gu_u = gUx * ux + gUy * uy + gUz * uz;
+    const float gax = (gUx - gu_u * ux) * ila, gay = (gUy - gu_u * uy) * ila;
+    const float gaz = (gUz - gu_u * uz) * ila;
+    const float ga_n = gax * nox + gay * noy + gaz * noz;
+    gNx += -nox * gax - ga_n; gNy += -nox * gay; gNz += -nox * gaz;
+    // n_o = sg N
+    gNx *= sg; gNy *= sg; gNz *= sg;
+    float gpar1 = 0.f, gpar2 = 0.f;       // c | (height, width)
+    if (bump) {
+        const float gn_n = gNx * Nx + gNy * Ny + gNz * Nz;
+        const float gmx = (gNx - gn_n * Nx) * inv, gmy = (gNy - gn_n * Ny) * inv;
+        const float a1 = 2.f * iw2 * ex;
+        const float dmx_x = a1 * (1.f - 2.f * iw2 * Qx * Qx), dmy_y = a1 * (1.f - 2.f * iw2 * Qy * Qy);
+        const float dm_xy = -4.f * iw2 * iw2 * ex * Qx * Qy;
+        gQx += gmx * dmx_x + gmy * dm_xy;
+        gQy += gmx * dm_xy + gmy * dmy_y;
+        const float w = (float)S.kd;
+        const float eh = expf(-s2 * iw2);                       // de/dh
+        gpar1 += 2.f * iw2 * eh * (gmx * Qx + gmy * Qy);
+        gpar2 += -2.f * ex * (1.f - iw2 * s2) / (w * w * w) * (gmx * Qx + gmy * Qy);
+    } else {
+        const float iNz = 1.f / Nz;
+        gQx += -c * gNx - c * c * Qx * gNz * iNz;
+        gQy += -c * gNy - c * c * Qy * gNz * iNz;
+        gpar1 += -Qx * gNx - Qy * gNy - c * s2 * gNz * iNz;
+    }
+    // ---- the hit Q = p + t d with F(Q) = 0
+    float Ft, Fqx, Fqy, Fqz, Fp1, Fp2 = 0.f;
+    if (bump) {
+        const float w = (float)S.kd;
+        Ft = dz + 2.f * iw2 * ex * (Qx * dx + Qy * dy);
+        Fqx = 2.f * iw2 * ex * Qx; Fqy = 2.f * iw2 * ex * Qy; Fqz = 1.f;
+        Fp1 = -expf(-s2 * iw2);
+        Fp2 = -s2 * ex / (w * w * w);
+    } else {
+        Ft = 2.f * c * (Qx * dx + Qy * dy + Qz * dz) - 2.f * dz;
+        Fqx = 2.f * c * Qx; Fqy = 2.f * c * Qy; Fqz = 2.f * c * Qz - 2.f;
+        Fp1 = s2 + Qz * Qz;
+    }
+    const float g_t = gQx * dx + gQy * dy + gQz * dz + gopl_t;
+    const float gam = -g_t / Ft;
+    gx = gQx + gam * Fqx; gy = gQy + gam * Fqy; gz = gQz + gam * Fqz;
+    gdx += t * gx; gdy += t * gy; gdz += t * gz;
+    gdoe[0] += -gam * Fqz;
+    gdoe[1] += gam * Fp1 + gpar1;
+    if (bump) gdoe[2] += gam * Fp2 + gpar2;
+}
+
+// Incident side of one ray from its per-ray sums s (layout of RW_RS): reverse
+// of the DOE hit (planar, or a conformal substrate with its frame and patch
+// gather) and of the pre-DOE surfaces; adds surface gradients to gs.  OPLG:
+// the optical path at the DOE carries the gradient gopl (coherent sensor),
+// reversed through every segment n t.
 template <bool OPLG = false>
 __device__ __forceinline__ void incident_adjoint(const DSys& sys, const DJob* __restrict__ jobs,
                                                  const long long* __restrict__ prefix,
@@ -399,6 +527,7 @@ __device__ __forceinline__ void incident_adjoint(const DSys& sys, const DJob* __
     const long long ri = J.off + (R.gid - prefix[R.job]);
     float x = rays.ox[ri], y = rays.oy[ri], zl = rays.oz[ri];
     float dx = rays.dx[ri], dy = rays.dy[ri], dz = rays.dz[ri];
+    const double oz = (double)zl;
     double dummy = 0.0;
     SurfIn st[RW_MAXS];
     for (int si = 0; si < sys.doe_index; ++si) {
@@ -406,20 +535,37 @@ __device__ __forceinline__ void incident_adjoint(const DSys& sys, const DJob* __
         st[si].dx = dx; st[si].dy = dy; st[si].dz = dz;
         trace_one<false>(sys.s[si], x, y, zl, dx, dy, dz, dummy, status);
     }
-    if (sys.conformal) return;   // conformal frame / gather gradients are not propagated
-    // planar DOE hit: h = p + t d, t = (z_doe - p_z) / d_z
-    const float zld = zl - sys.s[sys.doe_index].gap;
-    const float t = -zld / dz;
-    float gt = gx * dx + gy * dy + gz * dz;
-    if (OPLG) {
-        // OPL at the DOE = OPL before + n_in t
-        gt += sys.n_in * gopl;
-        if (sys.doe_index > 0) gs[(sys.doe_index - 1) * RW_NGRAD + 7] += t * gopl;
+    const DSurf& SD = sys.s[sys.doe_index];
+    if (sys.conformal) {
+        // the conformal hit, frame and gather, as incident_to_doe forms them
+        const double zld = (sys.doe_index == 0)
+                               ? (oz - SD.z)
+                               : ((double)zl - (SD.z - sys.s[sys.doe_index - 1].z));
+        float hx, hy, hz;
+        conformal_doe_adjoint(sys, SD, kn_in, x, y, zld, dx, dy, dz, s,
+                              OPLG ? sys.n_in * gopl : 0.f, hx, hy, hz, gdx, gdy, gdz,
+                              gs + sys.doe_index * RW_NGRAD);
+        if (OPLG && sys.doe_index > 0) {
+            double td;
+            if (conformal_hit(SD, x, y, zld, dx, dy, dz, td, nullptr))
+                gs[(sys.doe_index - 1) * RW_NGRAD + 7] += (float)td * gopl;
+        }
+        gx = hx; gy = hy; gz = hz;
+    } else {
+        // planar DOE hit: h = p + t d, t = (z_doe - p_z) / d_z
+        const float zld = zl - SD.gap;
+        const float t = -zld / dz;
+        float gt = gx * dx + gy * dy + gz * dz;
+        if (OPLG) {
+            // OPL at the DOE = OPL before + n_in t
+            gt += sys.n_in * gopl;
+            if (sys.doe_index > 0) gs[(sys.doe_index - 1) * RW_NGRAD + 7] += t * gopl;
+        }
+        gdx += gx * t; gdy += gy * t; gdz += gz * t;
+        gz += -gt / dz;
+        gdz += -gt * t / dz;
+        gs[sys.doe_index * RW_NGRAD + 0] += gt / dz;
     }
-    gdx += gx * t; gdy += gy * t; gdz += gz * t;
-    gz += -gt / dz;
-    gdz += -gt * t / dz;
-    gs[sys.doe_index * RW_NGRAD + 0] += gt / dz;
     for (int si = sys.doe_index - 1; si >= 0; --si) {
         float gnb = 0.f;
         trace_one_adjoint<OPLG>(sys.s[si], st[si], gx, gy, gz, gdx, gdy, gdz, gs + si * RW_NGRAD,

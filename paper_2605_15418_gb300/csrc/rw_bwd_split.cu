@@ -135,7 +135,9 @@ k_bs_trace(const DSys sys, const float* __restrict__ gpsf, SplitBufs B, long lon
     const long long nround = (nitems + stride - 1) / stride;
     for (long long rd = 0; rd < nround; ++rd) {
         const long long t = rd * stride + blockIdx.x * (long long)blockDim.x + threadIdx.x;
-        float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float acc[RW_RS];
+#pragma unroll
+        for (int k = 0; k < RW_RS; ++k) acc[k] = 0.f;
         int g = -1;
         if (t < nitems) {
             g = __ldg(B.iray + t);
@@ -172,8 +174,11 @@ k_bs_trace(const DSys sys, const float* __restrict__ gpsf, SplitBufs B, long lon
         // end of my run: next head above me (or 32)
         const unsigned above = heads & ~(0xffffffffu >> (31 - lane));
         const int run_end = above ? (__ffs(above) - 1) : 32;
+        // planar: dL/dP, dL/dkappa, dL/dK; conformal also the frame sums
+        const int nk = sys.conformal ? RW_RS_GATHER : 6;
 #pragma unroll
-        for (int k = 0; k < 6; ++k) {
+        for (int k = 0; k < RW_RS_GATHER; ++k) {
+            if (k >= nk) continue;
             float v = acc[k];
             for (int o = 1; o < 32; o <<= 1) {
                 const float n = __shfl_down_sync(0xffffffffu, v, o);
@@ -184,10 +189,10 @@ k_bs_trace(const DSys sys, const float* __restrict__ gpsf, SplitBufs B, long lon
         if (lane == my_head && g >= 0) {
             bool any = false;
 #pragma unroll
-            for (int k = 0; k < 6; ++k) any |= acc[k] != 0.f;
+            for (int k = 0; k < RW_RS_GATHER; ++k) any |= (k < nk) && acc[k] != 0.f;
             if (any)
-#pragma unroll
-                for (int k = 0; k < 6; ++k) atomicAdd(B.rsum + (long long)g * 6 + k, acc[k]);
+                for (int k = 0; k < nk; ++k)
+                    atomicAdd(B.rsum + (long long)g * sys.nrs + k, acc[k]);
         }
     }
     // ---- surface sums: registers -> CTA -> global
@@ -264,16 +269,35 @@ k_bs_scatter(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
             }
             __syncthreads();
             fft2d<M, true>(G, tw);
+            float gq[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             map_scatter<M>(sys, R, Tmaps + (long long)jobs[R.job].slot * npix_map, amp, G,
-                           jobs[R.job].phase_scale, dphi, damp);
+                           jobs[R.job].phase_scale, dphi, damp, sys.conformal ? gq : nullptr);
+            if (sys.conformal) {
+                // patch-position sums of this ray: block reduction into its per-ray sums
+                float* red = reinterpret_cast<float*>(info + RW_TILE);
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    for (int o = 16; o > 0; o >>= 1) gq[k] += __shfl_xor_sync(0xffffffffu, gq[k], o);
+                __syncthreads();
+                if ((threadIdx.x & 31) == 0)
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) red[(threadIdx.x >> 5) * 6 + k] = gq[k];
+                __syncthreads();
+                if (threadIdx.x < 6) {
+                    float v = 0.f;
+                    for (int w = 0; w < RW_THREADS / 32; ++w) v += red[w * 6 + threadIdx.x];
+                    B.rsum[g * sys.nrs + RW_RS_GATHER + threadIdx.x] = v;
+                }
+            }
             __syncthreads();
         }
         // incident side from the per-ray sums
         if (threadIdx.x < RW_TILE && info[threadIdx.x].alive) {
             const RayAtDoe& R = info[threadIdx.x];
             const long long g = tile * RW_TILE + threadIdx.x;
-            float s[6];
-            for (int k = 0; k < 6; ++k) s[k] = B.rsum[g * 6 + k];
+            float s[RW_RS];
+#pragma unroll
+            for (int k = 0; k < RW_RS; ++k) s[k] = k < sys.nrs ? B.rsum[g * sys.nrs + k] : 0.f;
             incident_adjoint(sys, jobs, prefix, rays, R, s, gs, status);
         }
     }
@@ -347,7 +371,7 @@ static cudaError_t launch_split_d(const LaunchCtx& L, const DSys& sys, const DJo
         RW_MARK(L, nullptr);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    size_t smem3 = sampled_scratch_offset(M);
+    size_t smem3 = sampled_scratch_offset(M) + 256;   // + the patch-position reduction
     const size_t red = sizeof(double) * RW_MAXS * RW_NGRAD * (RW_THREADS / 32);
     if (smem3 < red) smem3 = red;
     e = persistent_launch_cfg(k_bs_scatter<M>, smem3, L.num_sms, ntiles,

@@ -19,6 +19,18 @@
 #define RW_TILE 32           // incident rays traced together by warp 0
 #define RW_MAXS RW_MAX_SURFACES
 
+// Per-incident-ray sums of the adjoint, as reduced over the ray's secondary
+// rays and patch samples and handed to the incident side:
+//   [0..2] dL/d(hit point), [3] dL/dkappa_u, [4] dL/dkappa_v, [5] dL/dK,
+//   [6] dL/dOPL at the DOE (coherent sensor);
+//   conformal DOE only: [7..9] dL/du, [10..12] dL/dv, [13..15] dL/dn (the
+//   outgoing normal) from the emitted directions, [16..21] the patch
+//   gather's sums of dL/d(fractional map column) times 1, a, b and of
+//   dL/d(fractional map row) times 1, a, b (a, b: sample offsets in pixels).
+#define RW_RS 22
+#define RW_RS_FRAME 7
+#define RW_RS_GATHER 16
+
 #define RW_ST_NOTCONV 1u
 #define RW_ST_CAPACITY 2u
 #define RW_ST_TIMEOUT 4u
@@ -60,6 +72,7 @@ struct DSys {
     int nsen_slot;     // surface whose n_after is the sensor medium (-1: object space)
     int M;             // transform size P D (zero-padded patch)
     int cull;          // 1: exhaustive incoherent forward drops blocks that miss the sensor
+    int nrs;           // per-ray adjoint sums kept: 6 (planar), 7 (planar, coherent), RW_RS
     float norm;        // spectrum scale: 1/M^2 (coherent sensor) or 1/(D M)
     double pitch;
     float pitchf, inv_pitch;
@@ -93,6 +106,12 @@ struct RayAtDoe {
     float u[3], v[3], n[3];
     float kin_u, kin_v, K;  // tangential incident wavevector, k0 n_out
     float invK;
+    // bin directions in units of K: tangential components of bin 0 and the
+    // step per bin, formed in double and rounded once (a wavevector of order
+    // 1e4 / mm kept in float would carry ~4e-8 rad of rounding into every
+    // secondary direction), and the rounding residuals (near-grazing bins)
+    float tu, tv, tstep;
+    float tu_lo, tv_lo, tstep_lo;
     float a_re, a_im;
     double opl;
     double pxd, pyd;        // hit in double (patch indexing)

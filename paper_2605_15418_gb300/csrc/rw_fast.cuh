@@ -3,11 +3,11 @@
 // parameter, so the loop unrolls, surface constants become immediate
 // constant-bank operands and per-surface state stays in registers.
 //
-// Precision: divisions and square roots use the approximate hardware forms
-// (relative error ~2^-22).  Every divide here either moves the point along
-// the ray (its error is absorbed by the next intersection) or scales a
-// quantity of relative size << 1, so positions on the sensor stay within
-// ~1e-4 pixel of the correctly rounded FP32 trace.
+// Precision: the divisions and square roots whose error moves the point
+// along the ray (absorbed by the next intersection) or scales a quantity of
+// relative size << 1 use the approximate hardware forms (relative error
+// ~2^-22); Snell's cos(theta_t), which sets the new direction, and the run
+// to the sensor plane, the longest lever, are correctly rounded.
 #pragma once
 #include "rw_device.cuh"
 
@@ -56,7 +56,7 @@ __device__ __forceinline__ bool fast_step(const PSurf& S, float& x, float& y, fl
     const float eta = S.eta;
     const float k = fmaf(-eta * eta, fmaf(-ci, ci, 1.f), 1.f);
     if (k < 0.f) return false;
-    const float beta = sqrt_fast(k) - eta * ci;
+    const float beta = sqrtf(k) - eta * ci;     // sets the direction: correctly rounded
     dx = fmaf(eta, dx, beta * nx);
     dy = fmaf(eta, dy, beta * ny);
     dz = fmaf(eta, dz, beta * nz);
@@ -71,7 +71,7 @@ __device__ __forceinline__ bool fast_to_sensor(const DSys& sys, float& x, float&
     for (int i = 0; i < NS; ++i)
         if (!fast_step(sys.post[i], x, y, zl, dx, dy, dz)) return false;
     zl -= sys.sensor_gap;
-    const float t = -zl * rcp_fast(dz);
+    const float t = -zl / dz;                     // the longest run: correctly rounded
     x = fmaf(t, dx, x);
     y = fmaf(t, dy, y);
     return true;

@@ -119,10 +119,23 @@ __host__ __device__ constexpr int cull_keep_words(int M) { return ((M / 8) * (M 
 __host__ __device__ inline size_t cull_scratch_bytes(int M) {
     return align16(sizeof(unsigned) * (size_t)(M * M / 32 + RW_THREADS / 32 + 4));
 }
+// Candidate queue of the sampled forward's draws, per warp: RW_GQ entries of
+// (Philox word, lane << 16 | bin), each lane's packed best key
+// (order(score) << 32 | ~bin: the maximum is the best score, then the lowest
+// bin) and a fill counter.
+#define RW_GQ 512
+__host__ __device__ constexpr size_t gumbel_queue_bytes() {
+    return (size_t)(RW_THREADS / 32) * (RW_GQ * 8 + 32 * 8 + 16);
+}
+// sampled forward scratch: p and screening words per bin, chosen bin per
+// draw, reduction, then the per-warp candidate queues (16-byte aligned)
+__host__ __device__ inline size_t sampled_queue_offset(int M, int n_ssr) {
+    return align16(8 * (size_t)M * M + sizeof(int) * (size_t)n_ssr + 128);
+}
 inline size_t forward_smem_bytes(int M, int emit = RW_EMIT_EXHAUSTIVE, int n_ssr = 0) {
     size_t b = sampled_scratch_offset(M);
-    // sampled: p and screening words per bin, chosen bin per draw, reduction
-    if (emit == RW_EMIT_SAMPLED) b += 8 * (size_t)M * M + sizeof(int) * n_ssr + 128;
+    if (emit == RW_EMIT_SAMPLED)
+        b += sampled_queue_offset(M, n_ssr) + gumbel_queue_bytes();
     else b += cull_scratch_bytes(M);
     return b;
 }
@@ -153,6 +166,46 @@ __device__ __forceinline__ int find_job(const long long* prefix, int njob, long 
         if (prefix[mid] <= g) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// ------------------------------------------------------------------ A2 conformal hit
+// Run t from the ray point (x, y, zld) (zld: local to the DOE vertex) to a
+// conformal DOE substrate, in double.  Sphere: FP32 root refined by two FP64
+// Newton steps on c |Q|^2 - 2 Q_z = 0.  Gaussian bump sag(s) = h
+// exp(-s / (2 w^2)): Newton in double on g(t) = zld + t dz - sag(|q(t)|^2),
+// started on the plane through the sag at the ray's (x, y).  False if missed
+// (status bit on non-convergence).
+__device__ __forceinline__ bool conformal_hit(const DSurf& S, float x, float y, double zld,
+                                              float dx, float dy, float dz, double& t,
+                                              unsigned* status) {
+    if (S.kind == RW_GAUSS) {
+        const double h = S.cd, iw2 = 0.5 / (S.kd * S.kd);
+        const double X0 = x, Y0 = y, DX = dx, DY = dy, DZ = dz;
+        t = (h * exp(-(X0 * X0 + Y0 * Y0) * iw2) - zld) / DZ;
+        for (int it = 0; it < 40; ++it) {
+            const double qx = X0 + t * DX, qy = Y0 + t * DY;
+            const double e = h * exp(-(qx * qx + qy * qy) * iw2);
+            const double gp = DZ + 2.0 * iw2 * e * (qx * DX + qy * DY);
+            if (gp == 0.0) break;
+            const double step = (zld + t * DZ - e) / gp;
+            t -= step;
+            if (fabs(step) <= 1e-13 * (1.0 + fabs(t))) return true;
+        }
+        if (status) atomicOr(status, RW_ST_NOTCONV);
+        return false;
+    }
+    float tf;
+    if (!intersect_local(S, x, y, (float)zld, dx, dy, dz, tf, status)) return false;
+    t = (double)tf;
+    const double c = S.cd;
+    for (int it = 0; it < 2; ++it) {
+        double qx = (double)x + t * dx, qy = (double)y + t * dy, qz = zld + t * dz;
+        double f = c * (qx * qx + qy * qy + qz * qz) - 2.0 * qz;
+        double fp = 2.0 * c * (qx * dx + qy * dy + qz * dz) - 2.0 * dz;
+        if (fp == 0.0) return false;
+        t -= f / fp;
+    }
+    return true;
 }
 
 // ------------------------------------------------------------------ A1 + A2
@@ -186,39 +239,8 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     float nx, ny, nz;
     if (!sys.conformal) {
         t = -zld / (double)dz;
-    } else if (S.kind == RW_GAUSS) {
-        // Gaussian bump sag(s) = h exp(-s / (2 w^2)): Newton in double on
-        // g(t) = zld + t dz - sag(|q(t)|^2), started on the plane through the
-        // sag at the ray's (x, y)
-        const double h = S.cd, iw2 = 0.5 / (S.kd * S.kd);
-        const double X0 = x, Y0 = y, DX = dx, DY = dy, DZ = dz;
-        t = (h * exp(-(X0 * X0 + Y0 * Y0) * iw2) - zld) / DZ;
-        bool conv = false;
-        for (int it = 0; it < 40; ++it) {
-            const double qx = X0 + t * DX, qy = Y0 + t * DY;
-            const double e = h * exp(-(qx * qx + qy * qy) * iw2);
-            const double gp = DZ + 2.0 * iw2 * e * (qx * DX + qy * DY);
-            if (gp == 0.0) break;
-            const double step = (zld + t * DZ - e) / gp;
-            t -= step;
-            if (fabs(step) <= 1e-13 * (1.0 + fabs(t))) { conv = true; break; }
-        }
-        if (!conv) {
-            if (status) atomicOr(status, RW_ST_NOTCONV);
-            return;
-        }
-    } else {
-        float tf;
-        if (!intersect_local(S, x, y, (float)zld, dx, dy, dz, tf, status)) return;
-        t = (double)tf;
-        const double c = S.cd;
-        for (int it = 0; it < 2; ++it) {
-            double qx = (double)x + t * dx, qy = (double)y + t * dy, qz = zld + t * dz;
-            double f = c * (qx * qx + qy * qy + qz * qz) - 2.0 * qz;
-            double fp = 2.0 * c * (qx * dx + qy * dy + qz * dz) - 2.0 * dz;
-            if (fp == 0.0) return;
-            t -= f / fp;
-        }
+    } else if (!conformal_hit(S, x, y, zld, dx, dy, dz, t, status)) {
+        return;
     }
     const double pxd = __dadd_rn((double)x, __dmul_rn(t, (double)dx));
     const double pyd = __dadd_rn((double)y, __dmul_rn(t, (double)dy));
@@ -255,6 +277,15 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     R.kin_v = k0 * sys.n_in * (dx * vx + dy * vy + dz * vz);
     R.K = k0 * sys.n_out;
     R.invK = 1.f / R.K;
+    {
+        const double rn = sys.n_in_d / (double)sys.n_out;
+        const double tu = rn * ((double)dx * ux + (double)dy * uy + (double)dz * uz);
+        const double tv = rn * ((double)dx * vx + (double)dy * vy + (double)dz * vz);
+        const double ts = J.lambda / ((double)sys.M * sys.pitch * (double)sys.n_out);
+        R.tu = (float)tu; R.tu_lo = (float)(tu - (double)R.tu);
+        R.tv = (float)tv; R.tv_lo = (float)(tv - (double)R.tv);
+        R.tstep = (float)ts; R.tstep_lo = (float)(ts - (double)R.tstep);
+    }
     R.px = (float)pxd; R.py = (float)pyd; R.pz = (float)pzl;
     R.pxd = pxd; R.pyd = pyd;
     R.a_re = rays.are[ri]; R.a_im = rays.aim[ri];
@@ -607,29 +638,36 @@ __device__ __forceinline__ void splat_coherent_warp(const DSys& sys, float k0, f
     }
 }
 
-// Direction of spectral bin (ju, jv) for the incident state R; false if evanescent.
+// Direction of spectral bin (ju, jv) for the incident state R; false if
+// evanescent.  In units of K = k0 n_out: (a_u, a_v) = (tu, tv) + tstep (ju, jv)
+// (one rounding each), a_n = sqrt(1 - a_u^2 - a_v^2) correctly rounded (the
+// run to the next surface divides by it), d = a_u u + a_v v + a_n n.  Near
+// grazing (a_n^2 < 1e-2) the float rounding of a_u, a_v would be amplified
+// by 1 / a_n, so a_n^2 is formed in double from the double-float (tu, tv,
+// tstep).
 template <bool FAST = false>
 __device__ __forceinline__ bool bin_direction(const DSys& sys, const RayAtDoe& R, int ju, int jv,
                                               float& dx, float& dy, float& dz) {
-    const float ku = R.kin_u + sys.kstep * (float)ju;
-    const float kv = R.kin_v + sys.kstep * (float)jv;
-    const float K2 = R.K * R.K;
-    const float kt2 = ku * ku + kv * kv;
-    if (kt2 >= K2) return false;
-    float kn;
-    if (FAST) asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(kn) : "f"(K2 - kt2));
-    else kn = sqrtf(K2 - kt2);
-    const float invK = R.invK;
+    const float au = fmaf(R.tstep, (float)ju, R.tu);
+    const float av = fmaf(R.tstep, (float)jv, R.tv);
+    float an2 = fmaf(-av, av, fmaf(-au, au, 1.f));
+    if (an2 < 1e-2f) {
+        const double aud = ((double)R.tstep + (double)R.tstep_lo) * ju + ((double)R.tu + (double)R.tu_lo);
+        const double avd = ((double)R.tstep + (double)R.tstep_lo) * jv + ((double)R.tv + (double)R.tv_lo);
+        an2 = (float)fma(-avd, avd, fma(-aud, aud, 1.0));
+    }
+    if (!(an2 > 0.f)) return false;
+    const float an = sqrtf(an2);
     if (FAST && !sys.conformal) {
         // planar DOE: u = x, v = (0, s, 0), outgoing normal (0, 0, +-s), s = +-1
-        dx = ku * invK;
-        dy = (kv * R.v[1]) * invK;
-        dz = (kn * R.n[2]) * invK;
+        dx = au;
+        dy = av * R.v[1];
+        dz = an * R.n[2];
         return true;
     }
-    dx = (ku * R.u[0] + kv * R.v[0] + kn * R.n[0]) * invK;
-    dy = (ku * R.u[1] + kv * R.v[1] + kn * R.n[1]) * invK;
-    dz = (ku * R.u[2] + kv * R.v[2] + kn * R.n[2]) * invK;
+    dx = fmaf(au, R.u[0], fmaf(av, R.v[0], an * R.n[0]));
+    dy = fmaf(au, R.u[1], fmaf(av, R.v[1], an * R.n[1]));
+    dz = fmaf(au, R.u[2], fmaf(av, R.v[2], an * R.n[2]));
     return true;
 }
 
@@ -950,54 +988,104 @@ __device__ __forceinline__ void gumbel_full_scan(const float* p, uint32_t i, uin
     }
 }
 
+// Order-preserving map of a float to 32 bits (for packed atomic maxima).
+__device__ __forceinline__ uint32_t float_order(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float float_unorder(uint32_t o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+
 // Draws d0 .. d1-1 of one incident ray into sel[] (-1: no bin can be
 // drawn).  The 32 lanes of a warp make 32 draws together, walking the bins in
-// step so that the thresholds are broadcast reads; four independent Philox
-// blocks per step keep the integer pipes busy, and the rare candidates are
-// scored after the block's compares.  Not inlined: the hot loop gets the
-// registers of its own, apart from the rest of the fused kernel.
+// step so that the thresholds are broadcast reads; eight independent Philox
+// blocks per step keep the integer pipes busy.  The rare screening
+// candidates are only queued in the loop; the warp scores them together
+// afterwards (or when the queue fills) and keeps each draw's best with a
+// packed atomic maximum, so the scoring never diverges inside the loop.  A
+// draw whose queue share overflowed, or whose best candidate does not clear
+// the floor, rescans every bin.  Not inlined: the hot loop gets registers of
+// its own, apart from the rest of the fused kernel.
 template <int M>
 __device__ __noinline__ void gumbel_draws(const float* __restrict__ p,
                                           const uint4* __restrict__ thr4, int* __restrict__ sel,
                                           int d0, int d1, uint32_t ray, uint32_t off,
-                                          uint32_t k0, uint32_t k1) {
-    constexpr int NG = M * M / 4;
-    static_assert(NG % 4 == 0, "bin groups in blocks of four");
+                                          uint32_t k0, uint32_t k1, unsigned char* qmem) {
+    constexpr int NG = M * M / 4, CH = 8;
+    static_assert(NG % CH == 0, "bin groups in blocks of eight");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned char* wm = qmem + (size_t)warp * (RW_GQ * 8 + 32 * 8 + 16);
+    uint2* wq = reinterpret_cast<uint2*>(wm);
+    unsigned long long* wk = reinterpret_cast<unsigned long long*>(wm + RW_GQ * 8);
+    int* qn = reinterpret_cast<int*>(wm + RW_GQ * 8 + 32 * 8);
+    auto flush = [&]() {
+        __syncwarp();
+        const int n = min(*qn, RW_GQ);
+        for (int t = lane; t < n; t += 32) {
+            const uint2 e = wq[t];
+            const int jb = (int)(e.y & 0xffffu), il = (int)(e.y >> 16);
+            const float sc = gumbel_score(p[jb], e.x);
+            atomicMax(&wk[il], ((unsigned long long)float_order(sc) << 32) |
+                                   (unsigned long long)(0xffffffffu - (uint32_t)jb));
+        }
+        __syncwarp();
+        if (lane == 0) *qn = 0;
+        __syncwarp();
+    };
     for (int i0 = d0 + warp * 32; i0 < d1; i0 += RW_THREADS) {
         const uint32_t i = (uint32_t)(i0 + lane);
-        float best = -INFINITY;
-        int bj = 0x7fffffff;
-        for (int G = 0; G < NG; G += 4) {
-            uint32_t ws[16];
+        wk[lane] = 0ull;
+        if (lane == 0) *qn = 0;
+        bool ovf = false;
+        __syncwarp();
+        for (int G = 0; G < NG; G += CH) {
+            uint4 w[CH];
+#pragma unroll
+            for (int k = 0; k < CH; ++k)
+                w[k] = philox4x32_10(make_uint4((uint32_t)(G + k), i, ray, off), k0, k1);
             unsigned mask = 0u;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint4 w = philox4x32_10(make_uint4((uint32_t)(G + k), i, ray, off), k0, k1);
+            for (int k = 0; k < CH; ++k) {
                 const uint4 t = thr4[G + k];
-                ws[4 * k] = w.x; ws[4 * k + 1] = w.y; ws[4 * k + 2] = w.z; ws[4 * k + 3] = w.w;
-                mask |= ((unsigned)(w.x >= t.x) | ((unsigned)(w.y >= t.y) << 1) |
-                         ((unsigned)(w.z >= t.z) << 2) | ((unsigned)(w.w >= t.w) << 3)) << (4 * k);
+                mask |= ((unsigned)(w[k].x >= t.x) | ((unsigned)(w[k].y >= t.y) << 1) |
+                         ((unsigned)(w[k].z >= t.z) << 2) | ((unsigned)(w[k].w >= t.w) << 3))
+                        << (4 * k);
             }
             if (mask) {
+                const int n = __popc(mask);
+                int c = atomicAdd(qn, n);
+                if (c + n > RW_GQ) {
+                    ovf = true;
+                } else {
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    if ((mask >> q) & 1u) {
-                        const int jb = 4 * G + q;
-                        const float pj = p[jb];
-                        if (pj > 0.f) gumbel_keep(gumbel_score(pj, ws[q]), jb, best, bj);
+                    for (int k = 0; k < CH; ++k) {
+                        const uint32_t ws[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+                            if ((mask >> (4 * k + r)) & 1u)
+                                wq[c++] = make_uint2(ws[r], ((uint32_t)lane << 16) |
+                                                                (uint32_t)(4 * (G + k) + r));
                     }
                 }
             }
+            __syncwarp();
+            if (*qn > RW_GQ / 2) flush();
         }
+        flush();
         if ((int)i < d1) {
-            if (!(best > RW_GUMBEL_FLOOR)) {
+            const unsigned long long kk = wk[lane];
+            float best = kk ? float_unorder((uint32_t)(kk >> 32)) : -INFINITY;
+            int bj = kk ? (int)(0xffffffffu - (uint32_t)(kk & 0xffffffffull)) : 0x7fffffff;
+            if (ovf || !(best > RW_GUMBEL_FLOOR)) {
                 best = -INFINITY;
                 bj = 0x7fffffff;
                 gumbel_full_scan<M>(p, i, ray, off, k0, k1, best, bj);
             }
             sel[i] = (best > -INFINITY) ? bj : -1;
         }
+        __syncwarp();
     }
 }
 
@@ -1058,7 +1146,8 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
     for (int f = threadIdx.x; f < M * M; f += RW_THREADS) thr[f] = gumbel_screen_word(p[f]);
     __syncthreads();
     gumbel_draws<M>(p, thr4, sel, d0, d1, (uint32_t)R.rid, (uint32_t)sys.rng_offset,
-                    (uint32_t)(sys.seed & 0xffffffffull), (uint32_t)(sys.seed >> 32));
+                    (uint32_t)(sys.seed & 0xffffffffull), (uint32_t)(sys.seed >> 32),
+                    scratch + sampled_queue_offset(M, sys.n_ssr));
     __syncthreads();
     const float2 ain = make_float2(R.a_re, R.a_im);
     if (MODE == MODE_EMIT && threadIdx.x == 0) {
