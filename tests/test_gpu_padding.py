@@ -101,7 +101,7 @@ def test_forward_coherent_padded(RW, ctx):
         sim = RW.Simulator(w, ctx=ctx)
         psf = sim.forward().cpu().numpy()
         ref = oracle_psf(w)
-        assert rel_l2(psf, ref) <= 1e-3, (window, rel_l2(psf, ref))
+        assert rel_l2(psf, ref) <= PSF_TOL, (window, rel_l2(psf, ref))
 
 
 # ------------------------------------------------------------------ emission

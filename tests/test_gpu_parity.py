@@ -153,7 +153,7 @@ def test_forward_coherent_window_and_full(RW, ctx):
         sim = RW.Simulator(w, ctx=ctx)
         psf = sim.forward().cpu().numpy()
         ref = oracle_psf(w)
-        assert rel_l2(psf, ref) <= 1e-3, (window, rel_l2(psf, ref))
+        assert rel_l2(psf, ref) <= PSF_TOL, (window, rel_l2(psf, ref))
 
 
 def test_forward_rays_outside_map_and_empty_job(RW, ctx):
@@ -343,12 +343,12 @@ def test_backward_sampled_gumbel_straight_through_matches_oracle(RW, ctx):
     assert rel_l2(psf.cpu().numpy(), img.detach().numpy()) < 1e-3
     Lv, _ = OL.eq3_loss(img, torch.from_numpy(w.target.astype(np.float64)))
     Lv.backward()
-    assert rel_l2(dphi.cpu().numpy(), phi.grad.numpy()) <= 1e-2, \
+    assert rel_l2(dphi.cpu().numpy(), phi.grad.numpy()) <= 1e-3, \
         rel_l2(dphi.cpu().numpy(), phi.grad.numpy())
     ds = dsurf.cpu().numpy()
     for si in range(1, len(prm)):
         ref = float(prm[si]["c"].grad)
-        assert abs(ds[si, 1] - ref) <= 1e-2 * abs(ref) + 1e-6, (si, ds[si, 1], ref)
+        assert abs(ds[si, 1] - ref) <= 1e-3 * abs(ref) + 1e-6, (si, ds[si, 1], ref)
 
 
 def test_batched_uneven_jobs_one_launch(RW, ctx):
@@ -412,3 +412,31 @@ def test_visibility_mask_backward_equals_full_backward(RW, ctx, D, n_side):
         ref = (ray["alive"] & (u > -1) & (u < sen.nx) & (v > -1) & (v < sen.ny)).numpy()
     got = bits[: 8 * D * D].astype(bool)
     assert (got != ref).mean() < 1e-3
+
+
+def test_sampled_draws_agree_with_the_oracle_to_1e5(RW, ctx):
+    """The chosen bins of ~2e5 draws: the GPU decides from FP32 scores of FP32
+    spectra, the oracle from FP64 ones, so a draw whose two best scores lie
+    within rounding of each other may differ; at most 1e-5 of the draws may."""
+    w = _c2_small(n_side=10, D=16, map_side=128, lams=(550e-6, 656e-6), fields=(0.0,))
+    w.system.doe.emit = "sampled"
+    w.system.doe.n_ssr = 1024
+    w.system.doe.seed = (777 << 32) | 3
+    sim = RW.Simulator(w, ctx=ctx)
+    out = sim.emit()
+    torch.cuda.synchronize()
+    N = w.system.doe.n_ssr
+    bins = out["bin"].cpu().numpy().reshape(-1, N)
+    base = 0
+    flips = total = 0
+    for job in w.jobs:
+        for c0 in range(0, job.n_rays, 10):
+            idx = np.arange(c0, min(job.n_rays, c0 + 10))
+            with torch.no_grad():
+                em, _ = OP.emit_job(w.system, job, w.z_start, OP.params_of(w.system),
+                                    *OP.map_tensors(w.system), idx=idx, ray_base=base)
+            flips += int((bins[base + idx] != em["idx"].numpy()).sum())
+            total += idx.size * N
+        base += job.n_rays
+    assert total >= 200000
+    assert flips <= 1e-5 * total, (flips, total)

@@ -115,8 +115,9 @@ def test_gaussian_bump_emission_directions_match_oracle(RW, ctx):
     """Secondary directions and weights of the reflective conformal DOE (FP64
     Newton hit, normal of the bump, outgoing normal reversed).  At a pitch of
     lambda/2 the spectrum reaches grazing directions (sin theta -> 1), where an
-    FP32 error e of the tangential wavevector turns the direction by ~e K / kn:
-    1e-6 rad holds where |d_z| >= 0.3, 1e-5 rad over every propagating bin."""
+    error e of the tangential components would turn the direction by ~e / a_n;
+    near grazing the normal component is formed in double from double-float
+    tangential components, so 1e-6 rad holds over every propagating bin."""
     from gpu_helpers import angle
     w = RC.gauss(n_side=5, coherent=False, field_deg=3.0)
     sim = RW.Simulator(w, ctx=ctx)
@@ -131,9 +132,7 @@ def test_gaussian_bump_emission_directions_match_oracle(RW, ctx):
     alive = em["alive"].numpy()
     dref = em["d"].numpy()
     ang = angle(d[alive], dref[alive])
-    steep = np.abs(dref[alive][:, 2]) >= 0.3
-    assert ang[steep].max() <= 1e-6, ang[steep].max()
-    assert ang.max() <= 1e-5, ang.max()
+    assert ang.max() <= 1e-6, ang.max()
     # every secondary ray leaves on the incident side of the local surface
     # (grazing ones may still have d_z > 0 where the bump is tilted)
     n_out = em["frame"][2].numpy()                      # outgoing normal per ray
