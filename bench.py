@@ -15,7 +15,10 @@ benchmark divides every job's count range by --c5-scale (stated in config).
 
 Also measured (nested under "also"): the full C2 step (two singlets, planar
 DOE, 9 jobs of 1M rays, 64 x 64 patches, exhaustive emission with exact
-block culling, taped adjoint over the visibility mask).
+block culling, taped adjoint over the visibility mask); the C4 forward
+(conformal DOE on a sphere behind an even asphere, 4096^2 map, 27 jobs of
+4M rays, bilinear 64 x 64 patches) with the FP32 FFT ("c4") and with the
+tcgen05 patch transform fused into the forward ("c4tc").
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -63,8 +66,11 @@ def parse():
     ap.add_argument("--c5-scale", type=int, default=4096,
                     help="C5 ray counts per job divided by this (64k..2M -> 16..512 at 4096)")
     ap.add_argument("--n-side", type=int, default=1024, help="C2 rays per field = n_side^2")
-    ap.add_argument("--also", default="c2",
-                    help="comma-separated extra workloads measured after the headline ('' = none)")
+    ap.add_argument("--also", default="c2,c4,c4tc",
+                    help="comma-separated extra workloads measured after the headline ('' = "
+                         "none); c4tc is the C4 forward with the tensor-core patch transform")
+    ap.add_argument("--c4-n-side", type=int, default=2048,
+                    help="C4 rays per field = n_side^2 (2048: 4M, the stated workload)")
     ap.add_argument("--also-steps", type=int, default=5)
     ap.add_argument("--also-warmup", type=int, default=3)
     ap.add_argument("--cpu-rays", type=int, default=0,
@@ -83,6 +89,8 @@ def workload(name, args):
     if name == "c5":
         s = max(1, int(args.c5_scale))
         return R.configs.c5(count_lo=max(1, C5_FULL_LO // s), count_hi=max(4, C5_FULL_HI // s))
+    if name in ("c4", "c4tc"):
+        return R.configs.c4(n_side=args.c4_n_side)
     return R.configs.c2(n_side=args.n_side)
 
 
@@ -121,6 +129,19 @@ def block_test_flops(S):
     return 400.0 + 1290.0 * S
 
 
+def c4_kernel_flops(name, M, n_rays, blocks, kept):
+    """Algorithmic FP32 work of one launch of `name` in the C4 forward
+    (conformal DOE, bilinear patch gather, no surface behind the DOE)."""
+    if name in ("k_forward", "k_forward_tc"):
+        # gather: per sample 4 complex taps x 2 FMAs + the weights (~20);
+        # every kept bin is emitted and splat (no surface to trace)
+        return n_rays * (fft_flops(M) + 20.0 * M * M) + 64.0 * kept * bin_fwd_flops(0)
+    if name == "k_cull":
+        # conformal DOE: one affine test per (ray, 8 x 8 block of bins)
+        return float(blocks) * block_test_flops(0)
+    return None
+
+
 def c2_kernel_flops(name, M, D, S, n_rays, rays_with_items, items, blocks, kept):
     """Algorithmic FP32 work of one launch of `name` in the C2 step."""
     if name == "k_forward":
@@ -151,6 +172,13 @@ def c2_kernel_flops(name, M, D, S, n_rays, rays_with_items, items, blocks, kept)
 #     + 2 (broadcast loads)                                     = 35 ALU, 2 MUFU
 #   adjoint pass B: 10 + 13 + 6 (accumulators)                   = 29 ALU, 2 MUFU
 C5_FWD_ALU, C5_BWD_ALU, C5_BWD_MUFU = 11.0, 35.0 + 29.0, 4.0
+
+
+def tc_mma_flops(D):
+    """Tensor-core work of one D x D patch transform in the BF16x3 form: two
+    stages, each one real (2D x 2D) by (2D x D) product per split term
+    (hi hi, hi lo, lo hi), 2 M N K flops apiece."""
+    return 2 * 3 * 2.0 * (2 * D) * D * (2 * D)
 
 
 def c5_kernel_work(name, n_rays, M, N):
@@ -340,11 +368,15 @@ def weak_scaling_value(rays_per_rank, world, ms_per_step):
 class Step:
     """One fwd + Eq. 3 + bwd step of a workload through the C ABI."""
 
-    def __init__(self, name, w, dev, local):
+    def __init__(self, name, w, dev, local, dft="fft32"):
         import torch
         from paper_2605_15418_gb300 import raywave as RW
         self.RW, self.name, self.w = RW, name, w
-        self.sim = RW.Simulator(w, device=local)
+        self.fwd_only = name in ("c4", "c4tc")  # the C4 workload is a forward study
+        if w.target is None:
+            w.target = np.zeros((len(w.jobs), w.system.sensor.ny, w.system.sensor.nx),
+                                np.float32)
+        self.sim = RW.Simulator(w, device=local, dft=dft)
         sim = self.sim
         self.tgt = torch.as_tensor(w.target, device=dev)
         self.gI = torch.empty(sim.psf_shape, dtype=torch.float32, device=dev)
@@ -366,6 +398,9 @@ class Step:
         else:
             RW.rw_forward(sim.ctx, s, sim.jobs, sim.rays, self.psf)
         if ev: ev[2].record(stream)
+        if self.fwd_only:
+            if ev: ev[3].record(stream); ev[4].record(stream)
+            return
         RW.rw_loss_eq3(sim.ctx, self.psf, self.tgt, self.loss, self.gI)
         self.dphi.zero_()
         self.dsurf.zero_()
@@ -499,6 +534,31 @@ def roofline_c5(tm, st, peaks, n_sms, clocks):
                             "mufu_ops_per_pair": 0.0 if name == "k_forward" else C5_BWD_MUFU}}
 
 
+def roofline_c4(tm, st, n_sms, peaks=None):
+    """FP32 roofline of the dominant kernel of the C4 forward; with the
+    tensor-core transform also its tcgen05 throughput against the measured
+    bf16 peak."""
+    prof = tm["prof"]
+    M = st.w.system.doe.M
+    blocks, kept = st.sim.ctx.cull_stats()
+    peak = n_sms * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12
+    kernel_ms = {k: v[0] / v[1] for k, v in prof.items() if v[1] > 0}
+    modelled = {k: c4_kernel_flops(k, M, st.sim.n_rays, blocks, kept) for k in kernel_ms}
+    name = max((k for k in kernel_ms if modelled[k] is not None), key=lambda k: prof[k][0])
+    achieved = modelled[name] / (kernel_ms[name] / 1e3) / 1e12
+    extra = {"traced_secondary_fraction": (64.0 * kept / (st.sim.n_rays * M * M)
+                                           if blocks else 1.0)}
+    if name == "k_forward_tc" and peaks is not None:
+        tens = st.sim.n_rays * tc_mma_flops(M) / (kernel_ms[name] / 1e3) / 1e12
+        extra["tensor_core"] = {"achieved": tens, "peak": peaks["bf16_tflops"],
+                                "unit": "TFLOP/s", "frac": tens / peaks["bf16_tflops"],
+                                "flops_per_ray": tc_mma_flops(M)}
+    return kernel_ms, extra, {
+        "kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+        "peak_source": f"{n_sms} SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal)"}
+
+
 def roofline_c2(tm, st, n_sms):
     """FP32 roofline of the dominant kernel of the C2 step."""
     import torch
@@ -575,7 +635,7 @@ def main():
     also = []
     for other in [x for x in args.also.split(",") if x and x != name]:
         wo = workload(other, args)
-        so = Step(other, wo, dev, local)
+        so = Step(other, wo, dev, local, dft="tc" if other == "c4tc" else "fft32")
         to = time_steps(so, args.also_steps, args.also_warmup, flush, dev,
                         autotune=(other == "c2" and not args.no_autotune), dist=dist,
                         local=local, sample_clocks=False)
@@ -584,6 +644,12 @@ def main():
         co.update({"fwd_ms": to["fwd_ms"], "bwd_ms": to["bwd_ms"]})
         if other == "c5":
             kmo, ro = roofline_c5(to, so, peaks, n_sms, None)
+        elif other in ("c4", "c4tc"):
+            kmo, exo, ro = roofline_c4(to, so, n_sms, peaks)
+            co.update(exo)
+            co["step"] = "ray generation + forward (the C4 workload is a forward study)"
+            co["patch_transform"] = ("tcgen05 BF16x3 F X F^T" if other == "c4tc"
+                                     else "FP32 shared-memory FFT")
         else:
             kmo, exo, ro = roofline_c2(to, so, n_sms)
             co.update(exo)

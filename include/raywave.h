@@ -135,7 +135,7 @@ typedef struct {
     int32_t emit;          /* RW_EMIT_* */
     int32_t n_ssr;         /* draws per incident ray in sampled mode */
     int32_t phase_model;   /* RW_PHASE_* */
-    int32_t dft;           /* RW_DFT_*: TC only in rw_patch_spectra (fused calls: FFT32) */
+    int32_t dft;           /* RW_DFT_*: patch transform (see rw_forward, rw_patch_spectra) */
     uint64_t seed;         /* Philox key for sampled mode */
     uint64_t rng_offset;   /* Philox counter word 3 for sampled mode: draw i of the
                             * incident ray stored at index r of the ray arrays
@@ -297,7 +297,11 @@ rw_status rw_doe_emit(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
 /* ---- A1..A7: forward to the sensor ------------------------------------- */
 
 /* psf: device float [njob][ny][nx], overwritten (zeroed then accumulated).
- * Incoherent: sum of bilinear |a|^2 deposits; coherent: |Eq. 2|^2. */
+ * Incoherent: sum of bilinear |a|^2 deposits; coherent: |Eq. 2|^2.
+ * doe.dft = RW_DFT_TC forms each patch spectrum by the tensor-core
+ * contraction of rw_patch_spectra inside the fused kernel (D = 64 without
+ * padding, exhaustive emission, incoherent sensor; otherwise RW_EINVAL);
+ * RW_DFT_FFT32 uses the FP32 shared-memory FFT. */
 rw_status rw_forward(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs,
                      int32_t njob, const rw_rays* rays, float* psf);
 
@@ -341,7 +345,9 @@ rw_status rw_loss_eq3(rw_ctx* ctx, const float* psf, const float* target, int64_
  *   damp  device float [H][W]   (may be NULL; needs doe.amp)
  *   dsurf device double [nsurf][8] = d/d(z, c, k, A4, A6, A8, A10, n_after)
  *         (may be NULL).
- * Patches and spectra are recomputed, not stored.  Supported: incoherent
+ * Patches and spectra are recomputed, not stored, with the FP32 FFT whatever
+ * doe.dft selects (a mask or tape from a RW_DFT_TC forward is accepted).
+ * Supported: incoherent
  * and coherent sensor, exhaustive or sampled emission (straight-through
  * Gumbel-softmax with temperature 1), M = pad * D <= 96 (M = 128 only
  * through rw_backward_vis with exhaustive emission and the incoherent

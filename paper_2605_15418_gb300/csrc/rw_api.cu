@@ -772,9 +772,11 @@ static rw_status forward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* j
     Packed P;
     rw_status st = pack_system(ctx, sys, P);
     if (st != RW_OK) return st;
-    if (sys->doe.dft == RW_DFT_TC)
-        return fail(ctx, RW_EINVAL, "the fused kernels use the FP32 FFT; the tensor-core "
-                                    "transform is available through rw_patch_spectra");
+    const bool tc = sys->doe.dft == RW_DFT_TC;
+    if (tc && (P.sys.D != 64 || P.sys.M != 64 || P.sys.emit != RW_EMIT_EXHAUSTIVE ||
+               P.sys.coherent))
+        return fail(ctx, RW_EINVAL, "the fused tensor-core patch transform needs D = 64 without "
+                                    "padding, exhaustive emission and the incoherent sensor");
     if ((st = check_rays(ctx, rays)) != RW_OK) return st;
     if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
     if (!psf) return fail(ctx, RW_EINVAL, "psf is NULL");
@@ -838,10 +840,17 @@ static rw_status forward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* j
                 ctx->tape_cap = cap;
             }
         }
-        RW_CUDA(launch_forward(lctx(ctx), MODE_SPLAT, P.sys, dj, dp, njob, P.total,
-                               rays_in(rays), T, (double*)ctx->acc.p, nullptr, eo,
-                               status_word(ctx), vis, keep, vis ? &tape : nullptr),
-                "forward kernel");
+        if (tc) {
+            RW_CUDA(launch_forward_tc(lctx(ctx), P.sys, dj, dp, njob, P.total, rays_in(rays), T,
+                                      (double*)ctx->acc.p, status_word(ctx), vis, keep,
+                                      vis ? &tape : nullptr),
+                    "tensor-core forward kernel");
+        } else {
+            RW_CUDA(launch_forward(lctx(ctx), MODE_SPLAT, P.sys, dj, dp, njob, P.total,
+                                   rays_in(rays), T, (double*)ctx->acc.p, nullptr, eo,
+                                   status_word(ctx), vis, keep, vis ? &tape : nullptr),
+                    "forward kernel");
+        }
         ctx->launches++;
         RW_CUDA(launch_psf_finalize(lctx(ctx), (const double*)ctx->acc.p, psf, npx), "psf finalize");
         ctx->launches++;
@@ -885,9 +894,8 @@ static rw_status backward_impl(rw_ctx* ctx, const rw_system* sys, const rw_job* 
     Packed P;
     rw_status st = pack_system(ctx, sys, P);
     if (st != RW_OK) return st;
-    if (sys->doe.dft == RW_DFT_TC)
-        return fail(ctx, RW_EINVAL, "the fused kernels use the FP32 FFT; the tensor-core "
-                                    "transform is available through rw_patch_spectra");
+    // the adjoint re-forms the patch spectra with the FP32 FFT whatever
+    // doe.dft selects (see rw_backward)
     if ((st = check_rays(ctx, rays)) != RW_OK) return st;
     if ((st = pack_jobs(ctx, sys, jobs, njob, rays->n, P)) != RW_OK) return st;
     if (!dl_dpsf) return fail(ctx, RW_EINVAL, "dl_dpsf is NULL");

@@ -293,6 +293,45 @@ __global__ void k_coherent_grad(float2* __restrict__ field, const float* __restr
 }
 
 // ------------------------------------------------------------- launchers
+template <int M, int NS>
+static cudaError_t launch_cull_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
+                                const long long* prefix, int njob, long long total,
+                                const RaysIn& rays, unsigned* keep, unsigned* status) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cull<M, NS>,
+                                                                  RW_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    long long ntiles = (total + RW_TILE - 1) / RW_TILE;
+    long long grid = pick_grid(L, RW_K_CULL, (long long)L.num_sms * (per_sm > 0 ? per_sm : 1));
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    RW_MARK(L, "k_cull");
+    k_cull<M, NS><<<(unsigned)grid, RW_THREADS, 0, L.stream>>>(sys, jobs, prefix, njob, total,
+                                                              rays, keep, status);
+    RW_MARK(L, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cull(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
+                        const long long* prefix, int njob, long long total, const RaysIn& rays,
+                        unsigned* keep, unsigned* status) {
+#define RW_CULL_NS(DD)                                                                          \
+    switch (sys.n_post) {                                                                       \
+        case 0: return launch_cull_d<DD, 0>(L, sys, jobs, prefix, njob, total, rays, keep, status); \
+        case 2: return launch_cull_d<DD, 2>(L, sys, jobs, prefix, njob, total, rays, keep, status); \
+        case 4: return launch_cull_d<DD, 4>(L, sys, jobs, prefix, njob, total, rays, keep, status); \
+        case 6: return launch_cull_d<DD, 6>(L, sys, jobs, prefix, njob, total, rays, keep, status); \
+        default: return cudaErrorInvalidValue;                                                  \
+    }
+    switch (sys.M) {
+        case 16: RW_CULL_NS(16)
+        case 32: RW_CULL_NS(32)
+        case 64: RW_CULL_NS(64)
+        default: return cudaErrorInvalidValue;
+    }
+#undef RW_CULL_NS
+}
+
 template <int M, int MODE, int NS>
 static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                     const long long* prefix, int njob, long long total,
@@ -304,19 +343,9 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
     if constexpr (MODE == MODE_SPLAT && NS >= 0 && M <= 64) {
         if (keep) {
             // block culling: kept-block bits for every incident ray first
-            int per_sm = 0;
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cull<M, NS>,
-                                                                          RW_THREADS, 0);
+            cudaError_t e = launch_cull_d<M, NS>(L, sys, jobs, prefix, njob, total, rays, keep,
+                                                 status);
             if (e != cudaSuccess) return e;
-            long long ntiles = (total + RW_TILE - 1) / RW_TILE;
-            long long grid = pick_grid(L, RW_K_CULL, (long long)L.num_sms * (per_sm > 0 ? per_sm : 1));
-            if (grid > ntiles) grid = ntiles;
-            if (grid < 1) grid = 1;
-            RW_MARK(L, "k_cull");
-            k_cull<M, NS><<<(unsigned)grid, RW_THREADS, 0, L.stream>>>(sys, jobs, prefix, njob,
-                                                                      total, rays, keep, status);
-            RW_MARK(L, nullptr);
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if (tapep && vis) {
             tape = *tapep;

@@ -116,8 +116,8 @@ __host__ __device__ inline size_t sampled_scratch_offset(int M) {
 // incident ray (set: the block is kept); the forward stages the current
 // ray's visibility words and the tape's per-warp counts in shared memory
 __host__ __device__ constexpr int cull_keep_words(int M) { return ((M / 8) * (M / 8) + 31) / 32; }
-__host__ __device__ inline size_t cull_scratch_bytes(int M) {
-    return align16(sizeof(unsigned) * (size_t)(M * M / 32 + RW_THREADS / 32 + 4));
+__host__ __device__ constexpr size_t cull_scratch_bytes(int M) {
+    return ((sizeof(unsigned) * (size_t)(M * M / 32 + RW_THREADS / 32 + 4)) + 15) & ~size_t(15);
 }
 // Candidate queue of the sampled forward's draws, per warp: RW_GQ entries of
 // (Philox word, lane << 16 | bin), each lane's packed best key
@@ -1215,6 +1215,16 @@ cudaError_t launch_generate_rays(const LaunchCtx& L, const GenJob* jobs, const l
 // surfaces without RW_DOE_TRACE_ALL); `keep` then needs cull_keep_words(M)
 // words per incident ray.
 bool forward_culls(const DSys& sys);
+// k_cull alone (M <= 64, plane/sphere surfaces behind the DOE).
+cudaError_t launch_cull(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
+                        const long long* prefix, int njob, long long total, const RaysIn& rays,
+                        unsigned* keep, unsigned* status);
+// The fused forward with the tensor-core patch transform (D = M = 64,
+// exhaustive emission, incoherent sensor; culling when `keep` is given).
+cudaError_t launch_forward_tc(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
+                              const long long* prefix, int njob, long long total,
+                              const RaysIn& rays, const float2* T, double* psf, unsigned* status,
+                              unsigned* vis, unsigned* keep, const SplitBufs* tape);
 cudaError_t launch_forward(const LaunchCtx& L, int mode, const DSys& sys, const DJob* jobs,
                            const long long* prefix, int njob, long long total,
                            const RaysIn& rays, const float2* T, double* psf, float2* field,

@@ -22,6 +22,8 @@
 // spectrum is written coalesced, with the phase factors that refer it to
 // the hit point and the normalisation (1/D^2 without padding) applied on the
 // way out.
+#include <cstring>
+
 #include "rw_kernels.cuh"
 #include "rw_tc.cuh"
 
@@ -277,7 +279,7 @@ k_spectra_tc(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
     if (failed) {
         if (tid == 0) atomicOr(status, RW_ST_TIMEOUT);
         // let any MMA still in flight finish before the tensor memory is released
-        mbar_wait_bounded(bar, parity, RW_TC_WAIT);
+        mbar_wait_bounded(bar, parity ^ 1u, RW_TC_WAIT);   // the phase that timed out
     }
     tc_fence_before();
     __syncthreads();
@@ -334,4 +336,257 @@ cudaError_t launch_spectra(const LaunchCtx& L, const DSys& sys, int tc, const DJ
         case 128: return launch_spectra_fft_d<128>(L, sys, jobs, prefix, njob, total, rays, T, out, status);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// ------------------------------------------------------------------ fused forward, tensor cores
+// The incoherent exhaustive forward of rw_forward / rw_forward_vis with the
+// patch transform on the tensor cores (D = 64, no padding): per incident ray
+// the patch is gathered straight into the bf16 hi/lo B operand, the two
+// stages of k_spectra_tc run, and stage 2's accumulator is read back from
+// tensor memory into the shared spectrum buffer X in the layout the FFT path
+// leaves (row stride 65, FFT order), so that block culling, emission, the
+// sensor splat, the visibility mask and the adjoint's tape are the FFT path's
+// own.  One CTA per SM (the constant operand takes 64 KB of shared memory).
+namespace tcfwd {
+using namespace tcdft;
+constexpr uint32_t OFF_X = OFF_B + 2 * TILE_B;                      // 96 KB
+constexpr uint32_t X_BYTES = (uint32_t)(Patch<D>::ELEMS * sizeof(float2));
+constexpr uint32_t OFF_PH2 = OFF_X + X_BYTES;
+constexpr uint32_t OFF_INFO2 = OFF_PH2 + 2 * D * sizeof(float2);
+constexpr uint32_t OFF_VW = (uint32_t)((OFF_INFO2 + RW_TILE * sizeof(RayAtDoe) + 15) & ~15u);
+constexpr uint32_t OFF_BAR2 = (uint32_t)(OFF_VW + cull_scratch_bytes(D));
+constexpr uint32_t SMEM = OFF_BAR2 + 64;
+}  // namespace tcfwd
+
+template <int NS>
+__global__ void __launch_bounds__(RW_THREADS, 1)
+k_forward_tc(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
+             int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
+             double* __restrict__ psf, unsigned* status, unsigned* __restrict__ vis,
+             const unsigned* __restrict__ keep, SplitBufs tape) {
+    using namespace tcfwd;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float2* X = reinterpret_cast<float2*>(smem + OFF_X);
+    float2* phu = reinterpret_cast<float2*>(smem + OFF_PH2);
+    float2* phv = phu + D;
+    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(smem + OFF_INFO2);
+    unsigned* vw = reinterpret_cast<unsigned*>(smem + OFF_VW);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + OFF_BAR2);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + OFF_BAR2 + 8);
+    __shared__ unsigned skeep[RW_TILE * 2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tape.epoch && blockIdx.x == 0 && tid == 0) {
+        const unsigned long long e = atomicAdd(tape.epoch, 1ull) + 1ull;
+        if (tape.iray) tape.epoch[1] = e;
+    }
+    if (vis)
+        for (int i = tid; i < D * D / 32; i += RW_THREADS) vw[i] = 0u;
+    // ---- constant operand: F_big = [[F_re, -F_im], [F_im, F_re]], split in bf16
+    for (int i = tid; i < M * K; i += RW_THREADS) {
+        const int r = i / K, k = i - (i / K) * K;
+        const int po = r / D, m = r - po * D, pi = k / D, kk = k - pi * D;
+        float s, c;
+        sincospif(2.f * (float)((m * kk) % D) / (float)D, &s, &c);   // F = c - i s
+        const float v = (po == pi) ? c : (po == 0 ? s : -s);
+        __nv_bfloat16 hi, lo;
+        bf16_split(v, hi, lo);
+        const uint32_t off = kmajor_off(r, k, K);
+        put_bf16(smem + OFF_AHI, off, hi);
+        put_bf16(smem + OFF_ALO, off, lo);
+    }
+    if (tid == 0) mbar_init(bar, 1);
+    if (warp == 0) tmem_alloc(tslot, TMEM_COLS);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t d1 = tmem, d2 = tmem + N;
+    const int q = warp & 3;                      // TMEM lane quarter of this warp
+    const int row = q * 32 + lane;               // accumulator row = TMEM lane
+    const int cbase = (warp >> 2) * (N / 2);     // this warp's half of the columns
+    const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+    uint32_t parity = 0;
+    bool failed = false;
+    const long long npix_map = (long long)sys.H * sys.W;
+    const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
+    for (long long tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+        __syncthreads();
+        if (tid < RW_TILE) {
+            const long long g = tile * RW_TILE + tid;
+            incident_to_doe(sys, jobs, prefix, njob, total, rays, g, info[tid], status);
+            if (tape.rinfo && g < total) tape.rinfo[g] = info[tid];
+        }
+        if (keep) {
+            constexpr int KW = cull_keep_words(D);
+            const long long w0 = tile * RW_TILE * KW;
+            if (tid < RW_TILE * KW && KW <= 2)
+                skeep[tid] = (w0 + tid < total * KW) ? __ldg(keep + w0 + tid) : 0u;
+        }
+        __syncthreads();
+        for (int r = 0; r < RW_TILE; ++r) {
+            const long long g = tile * RW_TILE + r;
+            const RayAtDoe& R = info[r];
+            if (!R.alive) {
+                if (vis && g < total)
+                    for (int f = tid; f < D * D / 32; f += RW_THREADS)
+                        vis[g * (long long)(D * D / 32) + f] = 0u;
+                continue;
+            }
+            const DJob& J = jobs[R.job];
+            const float2* T = Tmaps + (long long)J.slot * npix_map;
+            // ---- A3: patch -> B (rows n = a, K = (re/im, b)), complex split to bf16 hi/lo
+            for (int f = tid; f < D * D; f += RW_THREADS) {
+                const int b = f / D, a = f - (f / D) * D;
+                float2 t;
+                if (sys.gather == RW_GATHER_NEAREST) {
+                    t = tmap(T, sys.H, sys.W, R.r0 + b, R.c0 + a);
+                } else {
+                    const float oa = (float)(a - D / 2), ob = (float)(b - D / 2);
+                    const float fu = R.s0 + oa * R.u[0] + ob * R.v[0];
+                    const float fv = R.t0 + oa * R.u[1] + ob * R.v[1];
+                    const float iuf = floorf(fu), ivf = floorf(fv);
+                    const float wu = fu - iuf, wv = fv - ivf;
+                    const int i0 = R.c0 + (int)iuf, j0 = R.r0 + (int)ivf;
+                    const float2 t00 = tmap(T, sys.H, sys.W, j0, i0), t10 = tmap(T, sys.H, sys.W, j0, i0 + 1);
+                    const float2 t01 = tmap(T, sys.H, sys.W, j0 + 1, i0), t11 = tmap(T, sys.H, sys.W, j0 + 1, i0 + 1);
+                    const float w00 = (1.f - wu) * (1.f - wv), w10 = wu * (1.f - wv);
+                    const float w01 = (1.f - wu) * wv, w11 = wu * wv;
+                    t = make_float2(w00 * t00.x + w10 * t10.x + w01 * t01.x + w11 * t11.x,
+                                    w00 * t00.y + w10 * t10.y + w01 * t01.y + w11 * t11.y);
+                }
+                __nv_bfloat16 hi, lo;
+                bf16_split(t.x, hi, lo);
+                put_bf16(smem + OFF_BHI, kmajor_off(a, b, K), hi);
+                put_bf16(smem + OFF_BLO, kmajor_off(a, b, K), lo);
+                bf16_split(t.y, hi, lo);
+                put_bf16(smem + OFF_BHI, kmajor_off(a, D + b, K), hi);
+                put_bf16(smem + OFF_BLO, kmajor_off(a, D + b, K), lo);
+            }
+            phase_factors<D>(sys, R, phu, phv);
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            // ---- A4 stage 1: Y = F X
+            if (tid == 0) {
+                tc_issue_stage(smem, d1);
+                tc_commit(bar);
+            }
+            bool ok = mbar_wait_bounded(bar, parity, RW_TC_WAIT);
+            parity ^= 1u;
+            if (__syncthreads_or(!ok)) { failed = true; break; }
+            tc_fence_after();
+            // ---- Y (TMEM rows (re/im, m_v), columns a) -> B rows n = m_v, K = (re/im, a)
+            {
+                const int p = row / D, mv = row - (row / D) * D;
+#pragma unroll
+                for (int cc = 0; cc < N / 2; cc += 16) {
+                    float v[16];
+                    tmem_ld16(d1 + lane_addr + (uint32_t)(cbase + cc), v);
+#pragma unroll
+                    for (int j = 0; j < 16; j += 8) {
+                        __align__(16) __nv_bfloat16 hi8[8], lo8[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) bf16_split(v[j + e], hi8[e], lo8[e]);
+                        const uint32_t off = kmajor_off(mv, p * D + cbase + cc + j, K);
+                        *reinterpret_cast<uint4*>(smem + OFF_BHI + off) = *reinterpret_cast<uint4*>(hi8);
+                        *reinterpret_cast<uint4*>(smem + OFF_BLO + off) = *reinterpret_cast<uint4*>(lo8);
+                    }
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            // ---- stage 2: Z^T = F Y^T
+            if (tid == 0) {
+                tc_issue_stage(smem, d2);
+                tc_commit(bar);
+            }
+            ok = mbar_wait_bounded(bar, parity, RW_TC_WAIT);
+            parity ^= 1u;
+            if (__syncthreads_or(!ok)) { failed = true; break; }
+            tc_fence_after();
+            // ---- Z^T (rows (re/im, m_u), columns m_v) -> X[m_v][m_u], row stride D + 1
+            {
+                const int p = row / D, mu = row - (row / D) * D;
+                float* Xf = reinterpret_cast<float*>(X);
+#pragma unroll
+                for (int cc = 0; cc < N / 2; cc += 16) {
+                    float v[16];
+                    tmem_ld16(d2 + lane_addr + (uint32_t)(cbase + cc), v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        Xf[2 * ((cbase + cc + j) * Patch<D>::S + mu) + p] = v[j];
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+            // ---- A5..A7: the FFT path's emission on the same spectrum
+            emit_exhaustive<D, MODE_SPLAT, NS>(sys, J, R, X, phu, phv, psf, nullptr, EmitOut{},
+                                               g, status, vis,
+                                               keep ? skeep + r * cull_keep_words(D) : nullptr,
+                                               vw, tape);
+            __syncthreads();
+        }
+    }
+    if (failed) {
+        if (tid == 0) atomicOr(status, RW_ST_TIMEOUT);
+        // let any MMA still in flight finish before the tensor memory is released
+        mbar_wait_bounded(bar, parity ^ 1u, RW_TC_WAIT);   // the phase that timed out
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+}
+
+template <int NS>
+static cudaError_t launch_forward_tc_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
+                                       const long long* prefix, int njob, long long total,
+                                       const RaysIn& rays, const float2* T, double* psf,
+                                       unsigned* status, unsigned* vis, unsigned* keep,
+                                       const SplitBufs* tapep) {
+    SplitBufs tape;
+    std::memset(&tape, 0, sizeof(tape));
+    if (keep) {
+        cudaError_t e = launch_cull(L, sys, jobs, prefix, njob, total, rays, keep, status);
+        if (e != cudaSuccess) return e;
+        if (tapep && vis) tape = *tapep;
+    } else if (tapep && vis) {
+        tape = *tapep;
+        tape.iray = nullptr;                    // only the culled path tapes
+    }
+    auto kern = k_forward_tc<NS>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tcfwd::SMEM);
+    if (e != cudaSuccess) return e;
+    const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
+    long long grid = pick_grid(L, RW_K_FORWARD, (long long)L.num_sms);
+    if (grid > ntiles) grid = ntiles;
+    if (grid < 1) grid = 1;
+    RW_MARK(L, "k_forward_tc");
+    kern<<<(unsigned)grid, RW_THREADS, tcfwd::SMEM, L.stream>>>(sys, jobs, prefix, njob, total,
+                                                               rays, T, psf, status, vis, keep,
+                                                               tape);
+    RW_MARK(L, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward_tc(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
+                              const long long* prefix, int njob, long long total,
+                              const RaysIn& rays, const float2* T, double* psf, unsigned* status,
+                              unsigned* vis, unsigned* keep, const SplitBufs* tape) {
+    if (sys.M != tcdft::D || sys.D != tcdft::D) return cudaErrorInvalidValue;
+    if (sys.fast_ok) {
+        switch (sys.n_post) {
+            case 0: return launch_forward_tc_d<0>(L, sys, jobs, prefix, njob, total, rays, T, psf, status, vis, keep, tape);
+            case 2: return launch_forward_tc_d<2>(L, sys, jobs, prefix, njob, total, rays, T, psf, status, vis, keep, tape);
+            case 4: return launch_forward_tc_d<4>(L, sys, jobs, prefix, njob, total, rays, T, psf, status, vis, keep, tape);
+            case 6: return launch_forward_tc_d<6>(L, sys, jobs, prefix, njob, total, rays, T, psf, status, vis, keep, tape);
+            default: break;
+        }
+    }
+    return launch_forward_tc_d<-1>(L, sys, jobs, prefix, njob, total, rays, T, psf, status, vis,
+                                   nullptr, tape);
 }
