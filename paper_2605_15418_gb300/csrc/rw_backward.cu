@@ -49,9 +49,9 @@ __host__ __device__ inline size_t sampled_bwd_bytes(int M, int N) {
 // Block-wide sum (all threads get the result); `red` holds >= 8 floats.
 __device__ __forceinline__ float block_sum(float v, float* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
+    main_sync();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
-    __syncthreads();
+    main_sync();
     float t = 0.f;
     for (int w = 0; w < RW_THREADS / 32; ++w) t += red[w];
     return t;
@@ -70,7 +70,8 @@ __device__ __forceinline__ int xpos(int f) {
 // warp's 32 draws walk the bins in step (per-bin records and weights are
 // broadcast reads), two Philox blocks per step; the t-weighted sums are
 // straight-line code and the rare screening candidates are scored after
-// them.  Not inlined, so that the loop has registers of its own.
+// them.  Every thread of the block takes part (helper warps included).  Not
+// inlined, so that the loop has registers of its own.
 template <int M>
 __device__ __noinline__ void gumbel_pass_a(const float2* __restrict__ rec,
                                            const float2* __restrict__ X, int* __restrict__ sel,
@@ -79,7 +80,7 @@ __device__ __noinline__ void gumbel_pass_a(const float2* __restrict__ rec,
                                            uint32_t k1) {
     constexpr int NG = M * M / 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i0 = warp * 32; i0 < N; i0 += RW_THREADS) {
+    for (int i0 = warp * 32; i0 < N; i0 += (int)blockDim.x) {
         const uint32_t i = (uint32_t)(i0 + lane);
         float Z = 0.f, Su = 0.f, Sv = 0.f, Sn = 0.f, Sr = 0.f, Si = 0.f;
         float best = -INFINITY;
@@ -130,11 +131,17 @@ __device__ __noinline__ void gumbel_pass_a(const float2* __restrict__ rec,
     }
 }
 
+constexpr int lanes_per_group(int ng, int nt) {
+    for (int ks = 1; ks <= 32; ks *= 2)
+        if ((ng * ks) % nt == 0) return ks;
+    return ng < nt ? nt / ng : 1;
+}
+
 // Pass B of the sampled adjoint: a lane owns a group of 4 bins (KS lanes
 // share one when there are fewer groups than threads) and walks the draws,
 // two Philox blocks per step, accumulating e_ij h~_i and e_ij c~_i; then
 // recf[2 j + 1] = dL/dlog p_j.  Not inlined, like pass A.
-template <int M>
+template <int M, int NT>
 __device__ __noinline__ void gumbel_pass_b(float* __restrict__ recf, const float2* __restrict__ X,
                                            const int* __restrict__ sel,
                                            const float4* __restrict__ sa,
@@ -142,9 +149,11 @@ __device__ __noinline__ void gumbel_pass_b(float* __restrict__ recf, const float
                                            uint32_t off, uint32_t k0, uint32_t k1, float kin_u,
                                            float kin_v, float ks) {
     constexpr int NG = M * M / 4;
-    constexpr int KS = NG >= RW_THREADS ? 1 : RW_THREADS / NG;     // lanes per bin group
+    // lanes per bin group (they split the draws): the fewest that give all NT
+    // threads the same number of groups
+    constexpr int KS = lanes_per_group(NG, NT);
     static_assert(KS <= 32 && (KS & (KS - 1)) == 0, "lanes per group: a power of two <= 32");
-    for (int tt = threadIdx.x; tt < NG * KS; tt += RW_THREADS) {
+    for (int tt = threadIdx.x; tt < NG * KS; tt += NT) {
         const int G = tt / KS, s0 = tt - (tt / KS) * KS;
         float a4[4][6];
 #pragma unroll
@@ -244,7 +253,30 @@ __device__ __noinline__ void gumbel_pass_b(float* __restrict__ recf, const float
 //     h~_i = (q_i, gd_i.u/K, gd_i.v/K, gd_i.n/K) / Z_i, c~_i = c_i / Z_i,
 //     dL/dlog p_j = p_j (<H_j, (w_j, kappa_u, kappa_v, kn_j)> - C_j).
 // No soft value is stored and no atomic is issued per pair.
-template <int M, int NS, bool COH>
+// Shared scratch of sampled_ray_adjoint after the patch (also read by the
+// helper warps of k_backward).
+struct SampledScr {
+    float2* rec;     // [M*M] (p_j, kn_j); .y becomes dL/dlog p_j after pass B
+    int* sel;        // [n_ssr] the forward's bin of each draw
+    float4* sa;      // [n_ssr] pass A sums (Z, S_u, S_v, S_n), then h~
+    float4* sb;      // [n_ssr] pass A sums of w (re, im)
+    float2* sc2;     // [n_ssr] (h~_n, c~)
+    float2* hU;      // [n_ssr] hard-path dL/dU~ of the draw's bin
+    float* red;      // block reductions
+    __device__ SampledScr(unsigned char* scr, int NB, int N) {
+        rec = reinterpret_cast<float2*>(scr);
+        sel = reinterpret_cast<int*>(rec + NB);
+        sa = reinterpret_cast<float4*>(sel + ((N + 3) & ~3));
+        sb = sa + N;
+        sc2 = reinterpret_cast<float2*>(sb + N);
+        hU = sc2 + N;
+        red = reinterpret_cast<float*>(hU + N);
+    }
+};
+
+// Barriers: the four marked "CTA" are taken by every thread of the block
+// (helper warps included, see sampled_helpers); the rest by the main threads.
+template <int M, int NS, bool COH, int NT>
 __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAtDoe& R,
                                                     float k0, long long stream,
                                                     float2* X, const float2* phu,
@@ -259,14 +291,15 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
     constexpr int S_ = Patch<M>::S;
     const int N = sys.n_ssr;
     const float norm = sys.norm;
-    float2* rec = reinterpret_cast<float2*>(scr);
+    const SampledScr P(scr, NB, N);
+    float2* rec = P.rec;
     float* recf = reinterpret_cast<float*>(rec);
-    int* sel = reinterpret_cast<int*>(rec + NB);
-    float4* sa = reinterpret_cast<float4*>(sel + ((N + 3) & ~3));
-    float4* sb = sa + N;
-    float2* sc2 = reinterpret_cast<float2*>(sb + N);
-    float2* hU = sc2 + N;
-    float* red = reinterpret_cast<float*>(hU + N);
+    int* sel = P.sel;
+    float4* sa = P.sa;
+    float4* sb = P.sb;
+    float2* sc2 = P.sc2;
+    float2* hU = P.hU;
+    float* red = P.red;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float2 ain = make_float2(R.a_re, R.a_im);
     const float sN = COH ? (float)N : sqrtf((float)N);
@@ -288,12 +321,12 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
         }
         X[xpos<M>(f)] = w;
     }
-    __syncthreads();
+    __syncthreads();                                               // CTA
     const uint32_t k0w = (uint32_t)(sys.seed & 0xffffffffull), k1w = (uint32_t)(sys.seed >> 32);
     const uint32_t ray = (uint32_t)stream, off = (uint32_t)sys.rng_offset;
     // ---- pass A: per draw, the forward's screened argmax and the t-weighted sums
     gumbel_pass_a<M>(rec, X, sel, sa, sb, N, ray, off, k0w, k1w);
-    __syncthreads();
+    __syncthreads();                                               // CTA
     // ---- every draw: trace + reverse of its (hard) secondary ray; h~, c~ and
     // the hard path's dL/dU~ of its bin
     const float ks = sys.kstep;
@@ -370,9 +403,10 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
     const float Sgp = block_sum(sgp, red);
     // ---- pass B: per bin, the draws' softmax weights against h~ and c~ (the
     // uniform density does not depend on U~: no soft path)
+    __syncthreads();                                               // CTA
     if (!sys.uniform)
-        gumbel_pass_b<M>(recf, X, sel, sa, sc2, N, ray, off, k0w, k1w, R.kin_u, R.kin_v, ks);
-    __syncthreads();
+        gumbel_pass_b<M, NT>(recf, X, sel, sa, sc2, N, ray, off, k0w, k1w, R.kin_u, R.kin_v, ks);
+    __syncthreads();                                               // CTA
     float sg = 0.f;
     if (!sys.uniform)
         for (int f = threadIdx.x; f < NB; f += RW_THREADS) sg += recf[2 * f + 1];
@@ -400,7 +434,7 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
         const float2 ph = cmul(phu[jui], phv[jvi]);
         X[xp] = cscale(cmulc(gU, ph), norm);
     }
-    __syncthreads();
+    main_sync();
     // ---- hard path of every draw into its bin
     for (int i = threadIdx.x; i < N; i += RW_THREADS) {
         const int jb = sel[i];
@@ -413,7 +447,7 @@ __device__ __forceinline__ void sampled_ray_adjoint(const DSys& sys, const RayAt
         atomicAdd(&dst->x, gx.x);
         atomicAdd(&dst->y, gx.y);
     }
-    __syncthreads();
+    main_sync();
 }
 
 // Coherent sensor: reverse of exhaustive bin f; writes its dL/dX.
@@ -487,8 +521,45 @@ __device__ __forceinline__ void exh_bin_adjoint(const DSys& sys, const RayAtDoe&
 template <int M>
 struct BwdOcc { static constexpr int value = M >= 96 ? 1 : 2; };
 
-template <int M, int NS, bool COH>
-__global__ void __launch_bounds__(RW_THREADS, BwdOcc<M>::value)
+// Helper warps of the sampled adjoint: threads RW_THREADS.. of the block.
+// They walk the same tiles and rays as the main threads, meet them at the
+// CTA barriers (tile start, and around the two Gumbel passes of every live
+// ray) and run their share of the passes, whose (draw, bin) pairs are nearly
+// all of the sampled adjoint's work; everything else is left to the main
+// threads.  More warps on an SM hide the passes' dependent-latency stalls.
+template <int M, int NT>
+__device__ __noinline__ void sampled_helpers(const DSys& sys, long long total,
+                                             const RayAtDoe* info, float2* X,
+                                             unsigned char* sscr) {
+    constexpr int NB = M * M;
+    const int N = sys.n_ssr;
+    const SampledScr P(sscr, NB, N);
+    const uint32_t k0w = (uint32_t)(sys.seed & 0xffffffffull), k1w = (uint32_t)(sys.seed >> 32);
+    const uint32_t off = (uint32_t)sys.rng_offset;
+    const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();                     // CTA: tile start
+        __syncthreads();                     // CTA: the tile's rays are at the DOE
+        for (int r = 0; r < RW_TILE; ++r) {
+            const RayAtDoe& R = info[r];
+            if (!R.alive) continue;
+            const uint32_t ray = (uint32_t)R.rid;
+            __syncthreads();                 // CTA: p_j, kn_j and w~_j ready
+            gumbel_pass_a<M>(P.rec, X, P.sel, P.sa, P.sb, N, ray, off, k0w, k1w);
+            __syncthreads();                 // CTA: pass A done
+            __syncthreads();                 // CTA: h~ and c~ ready
+            if (!sys.uniform)
+                gumbel_pass_b<M, NT>(reinterpret_cast<float*>(P.rec), X, P.sel, P.sa, P.sc2, N,
+                                     ray, off, k0w, k1w, R.kin_u, R.kin_v, sys.kstep);
+            __syncthreads();                 // CTA: pass B done
+        }
+    }
+}
+
+// HW helper warps (sampled emission only, see sampled_helpers); HW = 0 is
+// the plain kernel.
+template <int M, int NS, bool COH, int HW = 0>
+__global__ void __launch_bounds__(RW_THREADS + 32 * HW, BwdOcc<M>::value)
 k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
            int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
            const float* __restrict__ amp, const float* __restrict__ gpsf,
@@ -510,6 +581,12 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                                              (smp ? 0 : sizeof(float2) * Patch<M>::ELEMS));
     float* red = reinterpret_cast<float*>(bray + RW_TILE);   // [8 warps][RW_RS]
     unsigned char* sscr = reinterpret_cast<unsigned char*>(red + RW_RS * (RW_THREADS / 32));
+    if constexpr (HW > 0) {
+        if (threadIdx.x >= RW_THREADS) {
+            sampled_helpers<M, RW_THREADS + 32 * HW>(sys, total, info, X, sscr);
+            return;
+        }
+    }
     fft_twiddles<M>(tw);
     SurfGrads<NS> SG;
     SG.zero();
@@ -529,18 +606,18 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
         const long long tile = COH ? unit / nslice : unit;
         const int slice = COH ? (int)(unit - tile * nslice) : 0;
         const int f0 = slice * per, f1 = COH ? min(M * M, f0 + per) : M * M;
-        __syncthreads();
+        __syncthreads();                                           // CTA
         if (threadIdx.x < RW_TILE)
             incident_to_doe(sys, jobs, prefix, njob, total, rays, tile * RW_TILE + threadIdx.x,
                             info[threadIdx.x], status);
-        __syncthreads();
+        __syncthreads();                                           // CTA
         for (int r = 0; r < RW_TILE; ++r) {
             const RayAtDoe& R = info[r];
             if (!R.alive) continue;
             const DJob& J = jobs[R.job];
             const float2* T = Tmaps + (long long)J.slot * npix_map;
             gather_patch<M>(sys, R, T, X, phu, phv);
-            __syncthreads();
+            main_sync();
             fft2d<M, false>(X, tw);
             const float2 ain = make_float2(R.a_re, R.a_im);
             const float* gimg = gpsf + (long long)J.out * npx;
@@ -555,7 +632,7 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                         // bins outside the slice contribute nothing to this dL/dX
                         for (int f = threadIdx.x; f < Patch<M>::ELEMS; f += RW_THREADS)
                             G[f] = make_float2(0.f, 0.f);
-                        __syncthreads();
+                        main_sync();
                     }
                     for (int f = f0 + threadIdx.x; f < f1; f += RW_THREADS)
                         exh_bin_adjoint_coh<M>(sys, R, J.k0, X, phu, phv, gf, G, ain, f, acc, gs,
@@ -566,7 +643,7 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                     // and reverse them in converged rounds of 32.
                     for (int f = threadIdx.x; f < Patch<M>::ELEMS; f += RW_THREADS)
                         G[f] = make_float2(0.f, 0.f);
-                    __syncthreads();
+                    main_sync();
                     const unsigned* vw = vis + R.gid * (long long)(M * M / 32);
                     const unsigned myw = lane < KW ? __ldg(vw + lane * (RW_THREADS / 32) + warp) : 0u;
                     const int cnt = __popc(myw);
@@ -600,8 +677,8 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                                                status);
                 }
             } else {
-                sampled_ray_adjoint<M, NS, COH>(sys, R, J.k0, R.rid, X, phu, phv, gimg,
-                                                gf, sscr, acc, SG, gs, status);
+                sampled_ray_adjoint<M, NS, COH, RW_THREADS + 32 * HW>(
+                    sys, R, J.k0, R.rid, X, phu, phv, gimg, gf, sscr, acc, SG, gs, status);
             }
             // ---- per-ray reduction of the geometric gradients (with a conformal
             // DOE also the frame sums)
@@ -611,12 +688,12 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                 if (k < nk)
                     for (int o = 16; o > 0; o >>= 1)
                         acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
-            __syncthreads();
+            main_sync();
             if (lane == 0)
 #pragma unroll
                 for (int k = 0; k < RW_RS_GATHER; ++k)
                     if (k < nk) red[warp * RW_RS + k] = acc[k];
-            __syncthreads();
+            main_sync();
             if (threadIdx.x == 0) {
                 float* sb = bray[r].s;
                 for (int k = 0; k < RW_RS; ++k) sb[k] = 0.f;
@@ -645,11 +722,11 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
 #pragma unroll
                 for (int k = 0; k < 6; ++k)
                     for (int o = 16; o > 0; o >>= 1) gq[k] += __shfl_xor_sync(0xffffffffu, gq[k], o);
-                __syncthreads();
+                main_sync();
                 if (lane == 0)
 #pragma unroll
                     for (int k = 0; k < 6; ++k) red[warp * RW_RS + k] = gq[k];
-                __syncthreads();
+                main_sync();
                 if (threadIdx.x == 0) {
                     float* sb = bray[r].s;
                     for (int k = 0; k < 6; ++k) {
@@ -663,7 +740,7 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
                     }
                 }
             }
-            __syncthreads();
+            main_sync();
         }
         // ---- incident side: DOE hit and pre-DOE surfaces, one lane per ray
         if (!COH && threadIdx.x < RW_TILE && info[threadIdx.x].alive)
@@ -682,7 +759,7 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
         }
         gs[sys.doe_index * RW_NGRAD + 7] += SG.f_doe_n;
     }
-    __syncthreads();
+    main_sync();
     double* dred = reinterpret_cast<double*>(smem);
     for (int s = 0; s < sys.nsurf; ++s) {
         for (int k = 0; k < RW_NGRAD; ++k) {
@@ -691,7 +768,7 @@ k_backward(const DSys sys, const DJob* __restrict__ jobs, const long long* __res
             if (lane == 0) dred[(s * RW_NGRAD + k) * (RW_THREADS / 32) + warp] = (double)v;
         }
     }
-    __syncthreads();
+    main_sync();
     for (int i = threadIdx.x; i < sys.nsurf * RW_NGRAD; i += RW_THREADS) {
         double v = 0.0;
         for (int w = 0; w < RW_THREADS / 32; ++w) v += dred[i * (RW_THREADS / 32) + w];
@@ -741,7 +818,11 @@ inline size_t backward_smem_bytes(int M, int emit, int n_ssr) {
 
 size_t backward_smem_needed(const DSys& sys) { return backward_smem_bytes(sys.M, sys.emit, sys.n_ssr); }
 
-template <int M, int NS, bool COH = false>
+// Helper warps of the sampled adjoint at M = 96 (one CTA per SM): 8 more
+// warps, so 16 per SM, at 128 registers a thread.
+#define RW_BWD_HELPERS 8
+
+template <int M, int NS, bool COH = false, int HW = 0>
 static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                      const long long* prefix, int njob, long long total,
                                      const RaysIn& rays, const float2* T, const float* amp,
@@ -749,13 +830,20 @@ static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const 
                                      float* damp, double* dsurf, unsigned* status,
                                      const unsigned* vis, float* coh_rsum = nullptr,
                                      double* coh_jsum = nullptr) {
+    if constexpr (HW == 0 && !COH && M == 96) {
+        if (sys.emit == RW_EMIT_SAMPLED)
+            return launch_backward_d<M, NS, COH, RW_BWD_HELPERS>(L, sys, jobs, prefix, njob, total,
+                                                                 rays, T, amp, gpsf, gfield, dphi,
+                                                                 damp, dsurf, status, vis);
+    }
+    constexpr int NT = RW_THREADS + 32 * HW;
     const size_t smem = backward_smem_bytes(M, sys.emit, sys.n_ssr);
-    auto kern = k_backward<M, NS, COH>;
+    auto kern = k_backward<M, NS, COH, HW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RW_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     long long ntiles = (total + RW_TILE - 1) / RW_TILE;
@@ -772,7 +860,7 @@ static cudaError_t launch_backward_d(const LaunchCtx& L, const DSys& sys, const 
     if (grid > ntiles * s.nslice) grid = ntiles * s.nslice;
     if (grid < 1) grid = 1;
     RW_MARK(L, "k_backward");
-    kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(s, jobs, prefix, njob, total, rays, T,
+    kern<<<(unsigned)grid, NT, smem, L.stream>>>(s, jobs, prefix, njob, total, rays, T,
                                                           amp, gpsf, gfield, dphi, damp, dsurf,
                                                           status, vis, coh_rsum, coh_jsum);
     RW_MARK(L, nullptr);

@@ -19,6 +19,16 @@
 #define RW_TILE 32           // incident rays traced together by warp 0
 #define RW_MAXS RW_MAX_SURFACES
 
+// Barrier of a CTA's RW_THREADS main threads.  A kernel launched with exactly
+// RW_THREADS threads syncs the CTA; one that adds helper warps behind them
+// (threads RW_THREADS.. of the block, which only join the Gumbel passes of
+// the sampled adjoint) syncs the main threads on named barrier 1, so that
+// the helpers are never waited for outside those passes.
+__device__ __forceinline__ void main_sync() {
+    if (blockDim.x == RW_THREADS) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"n"(RW_THREADS) : "memory");
+}
+
 // Per-incident-ray sums of the adjoint, as reduced over the ray's secondary
 // rays and patch samples and handed to the incident side:
 //   [0..2] dL/d(hit point), [3] dL/dkappa_u, [4] dL/dkappa_v, [5] dL/dK,

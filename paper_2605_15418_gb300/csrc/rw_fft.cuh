@@ -130,7 +130,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* tw) {
             dft_small<R, INV>(v[k]);
         }
     }
-    __syncthreads();
+    main_sync();
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int f = threadIdx.x + k * RW_THREADS;
@@ -146,7 +146,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, const float2* tw) {
             }
         }
     }
-    __syncthreads();
+    main_sync();
 }
 
 template <int N, bool INV, bool COLS>
@@ -193,7 +193,7 @@ __device__ __forceinline__ void fft_stage_from_staged(float2* buf, int off) {
             dft_small<R, INV>(v[k]);
         }
     }
-    __syncthreads();
+    main_sync();
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int f = threadIdx.x + k * RW_THREADS;
@@ -204,7 +204,7 @@ __device__ __forceinline__ void fft_stage_from_staged(float2* buf, int off) {
             for (int q = 0; q < R; ++q) buf[b * S + i * R + q] = v[k][q];
         }
     }
-    __syncthreads();
+    main_sync();
 }
 
 // 2D FFT of an N = 64 patch staged as rows of N + 2 samples (bulk copies),

@@ -1113,14 +1113,14 @@ __device__ __forceinline__ float sampled_probs(const DSys& sys, const RayAtDoe& 
         part += m;
     }
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    __syncthreads();
+    main_sync();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-    __syncthreads();
+    main_sync();
     float tot = 0.f;
     for (int w = 0; w < RW_THREADS / 32; ++w) tot += red[w];
     const float inv_tot = tot > 0.f ? 1.f / tot : 0.f;
     for (int f = threadIdx.x; f < M * M; f += RW_THREADS) p[f * STRIDE] *= inv_tot;
-    __syncthreads();
+    main_sync();
     return tot;
 }
 
