@@ -383,6 +383,10 @@ static rw_status pack_system(rw_ctx* ctx, const rw_system* sys, Packed& P) {
         o.r_ap2 = s.r_ap > 0 ? (float)(s.r_ap * s.r_ap) : 0.f;
         o.gap = (float)(s.z - prev_z);
         o.z = s.z;
+        o.A4d = s.A4; o.A6d = s.A6; o.A8d = s.A8; o.A10d = s.A10;
+        o.nbd = n_prev;
+        o.nad = s.n_after;
+        o.r_ap2d = s.r_ap > 0 ? s.r_ap * s.r_ap : 0.0;
         if (i == sys->doe_index) {
             if (s.kind == RW_ASPHERE)
                 return fail(ctx, RW_EINVAL, "DOE surface must be PLANE, SPHERE or GAUSS");
@@ -494,6 +498,8 @@ static rw_status pack_jobs(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs
         d.cnt = j.ray_count;
         d.cx = (float)j.sensor_cx;
         d.cy = (float)j.sensor_cy;
+        d.cxd = j.sensor_cx;
+        d.cyd = j.sensor_cy;
         d.slot = slot;
         d.out = outs ? outs[i] : i;
         P.prefix[i + 1] = P.prefix[i] + j.ray_count;

@@ -409,6 +409,7 @@ __device__ __forceinline__ void map_scatter(const DSys& sys, const RayAtDoe& R,
 // zld) in (gx, gy, gz), dL/dd added to gd, and the substrate's z, c (sphere)
 // or z, height, width (bump) gradients added to gdoe[0..2].
 __device__ __forceinline__ void conformal_doe_adjoint(const DSys& sys, const DSurf& S,
+                                                      const RayAtDoe& R,
                                                       float kn_in, float x, float y, double zld,
                                                       float dx, float dy, float dz,
                                                       const float* s, float gopl_t,
@@ -436,10 +437,14 @@ __device__ __forceinline__ void conformal_doe_adjoint(const DSys& sys, const DSu
         Nx = -c * Qx; Ny = -c * Qy; Nz = sqrtf(fmaxf(1.f - c * c * s2, 0.f));
     }
     const float sg = (Nx * dx + Ny * dy + Nz * dz < 0.f) ? -1.f : 1.f;
-    const float nox = sg * Nx, noy = sg * Ny, noz = sg * Nz;
+    // the frame the forward used (formed in double, rounded once): the sums
+    // s[] were taken against it, so the projections below must use the same
+    // vectors, or their ~1e-7 difference leaks into small gradients
+    const float fo = sys.reflective ? -1.f : 1.f;
+    const float nox = fo * R.n[0], noy = fo * R.n[1], noz = fo * R.n[2];
     const float ax = 1.f - nox * nox, ay = -nox * noy, az = -nox * noz;
     const float la = sqrtf(ax * ax + ay * ay + az * az), ila = 1.f / la;
-    const float ux = ax * ila, uy = ay * ila, uz = az * ila;
+    const float ux = R.u[0], uy = R.u[1], uz = R.u[2];
     // ---- gradients on the frame: emitted directions, incident wavevector
     // kappa_in = k0 n_in (d.u, d.v), and the patch sample positions
     // Q + a p u + b p v read at their (x, y) (map column = x / p + const)
@@ -542,7 +547,7 @@ __device__ __forceinline__ void incident_adjoint(const DSys& sys, const DJob* __
                                ? (oz - SD.z)
                                : ((double)zl - (SD.z - sys.s[sys.doe_index - 1].z));
         float hx, hy, hz;
-        conformal_doe_adjoint(sys, SD, kn_in, x, y, zld, dx, dy, dz, s,
+        conformal_doe_adjoint(sys, SD, R, kn_in, x, y, zld, dx, dy, dz, s,
                               OPLG ? sys.n_in * gopl : 0.f, hx, hy, hz, gdx, gdy, gdz,
                               gs + sys.doe_index * RW_NGRAD);
         if (OPLG && sys.doe_index > 0) {

@@ -19,14 +19,33 @@
 #define RW_TILE 32           // incident rays traced together by warp 0
 #define RW_MAXS RW_MAX_SURFACES
 
-// Barrier of a CTA's RW_THREADS main threads.  A kernel launched with exactly
-// RW_THREADS threads syncs the CTA; one that adds helper warps behind them
-// (threads RW_THREADS.. of the block, which only join the Gumbel passes of
-// the sampled adjoint) syncs the main threads on named barrier 1, so that
-// the helpers are never waited for outside those passes.
+// Thread groups.  Most kernels run one group of RW_THREADS threads per CTA.
+// A kernel may run several (threads g * RW_THREADS .. of the block form
+// group g): the tensor-core forward runs two groups on separate rays, and
+// the sampled adjoint adds helper warps (group 1) that only join its Gumbel
+// passes.  Shared device code indexes work by ltid() and syncs with
+// main_sync(), so that it runs unchanged in any group.
+__device__ __forceinline__ int ltid() { return (int)(threadIdx.x % RW_THREADS); }
+
+// Barrier of the calling thread's group: the CTA barrier when the CTA is one
+// group, else named barrier 1 + g for the RW_THREADS threads of group g.
 __device__ __forceinline__ void main_sync() {
     if (blockDim.x == RW_THREADS) __syncthreads();
-    else asm volatile("bar.sync 1, %0;" ::"n"(RW_THREADS) : "memory");
+    else asm volatile("bar.sync %0, %1;" ::"r"(1u + threadIdx.x / RW_THREADS), "n"(RW_THREADS)
+                      : "memory");
+}
+
+// main_sync() that also returns whether v holds for any thread of the group.
+__device__ __forceinline__ bool group_or(bool v) {
+    if (blockDim.x == RW_THREADS) return __syncthreads_or(v) != 0;
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n"
+        " bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(1u + threadIdx.x / RW_THREADS), "n"(RW_THREADS)
+        : "memory");
+    return r != 0;
 }
 
 // Per-incident-ray sums of the adjoint, as reduced over the ray's secondary
@@ -53,7 +72,9 @@ struct DSurf {
     float gap;         // z_vertex - z of the previous local reference (float)
     double z;          // global vertex z
     double cd;         // curvature (Gaussian bump: height) in double, FP64 hit refinement
-    double kd;         // Gaussian bump: width, in double
+    double kd;         // conic constant (Gaussian bump: width), in double
+    // double copies for the FP64 trace before the DOE (see trace_one_d)
+    double A4d, A6d, A8d, A10d, nbd, nad, r_ap2d;
 };
 
 // Post-DOE plane/sphere in the form the specialised trace uses.
@@ -105,6 +126,7 @@ struct DJob {
     float phase_scale; // lambda0 / lambda (HEIGHT) or 1
     long long off, cnt;
     float cx, cy;
+    double cxd, cyd;   // the same in double (sensor run from a last-surface DOE)
     int slot;          // wavelength slot of the transmission map
     int out;           // index of the job's image in the psf / dL/dpsf arrays
 };
@@ -129,6 +151,10 @@ struct RayAtDoe {
     float s0, t0;           // nearest: offset of sample 0 from the hit / (M p);
                             // bilinear: fractional pixel coordinate of the hit
     float cx, cy;           // sensor window centre of the job
+    // DOE the last surface: hit minus window centre and the axial run to the
+    // sensor plane, formed in double and kept as float pairs (hi, lo) for the
+    // secondary rays' run to the sensor (see sensor_offset)
+    float sx, sx_lo, sy, sy_lo, sl, sl_lo;
     long long gid;          // position of the ray in the launch's job order
     long long rid;          // index of the ray in the caller's ray arrays: its sampling stream
 };
@@ -239,6 +265,103 @@ __device__ __forceinline__ bool refract(float& dx, float& dy, float& dz, float n
     dx = eta * dx + beta * nx;
     dy = eta * dy + beta * ny;
     dz = eta * dz + beta * nz;
+    return true;
+}
+
+// ---------------------------------------------------------------- FP64 trace before the DOE
+// The incident rays are traced to the DOE in double: the patch is sampled at
+// the DOE hit point, and on a map with pixel-scale structure a hit that is
+// off by 1e-3 of a pixel (0.5 nm at 0.5 um pitch) changes the spectrum by
+// ~1e-3 -- about what an FP32 direction error of 1e-7 does over a few mm.
+// One trace per incident ray, so the cost is that of a few hundred FP64
+// operations against the thousands of bins behind it.
+struct SagD { double z, dz; bool ok; };
+
+__device__ __forceinline__ SagD sag_eval_d(const DSurf& S, double s) {
+    SagD r;
+    if (S.kind == RW_PLANE) { r.z = 0.0; r.dz = 0.0; r.ok = true; return r; }
+    const double kap = (S.kind == RW_ASPHERE) ? 1.0 + S.kd : 1.0;
+    const double arg = 1.0 - kap * S.cd * S.cd * s;
+    r.ok = arg > 0.0;
+    const double q = sqrt(r.ok ? arg : 1.0);
+    r.z = S.cd * s / (1.0 + q);
+    r.dz = S.cd / (2.0 * q);
+    if (S.kind == RW_ASPHERE) {
+        const double s2 = s * s;
+        r.z += s2 * (S.A4d + s * (S.A6d + s * (S.A8d + s * S.A10d)));
+        r.dz += s * (2.0 * S.A4d + s * (3.0 * S.A6d + s * (4.0 * S.A8d + s * 5.0 * S.A10d)));
+    }
+    return r;
+}
+
+// t along d from (x, y, zl) (zl local to the vertex) to the surface; the
+// even asphere by Newton from the base-sphere root, to 1e-12 relative.
+__device__ __forceinline__ bool intersect_local_d(const DSurf& S, double x, double y, double zl,
+                                                  double dx, double dy, double dz, double& t,
+                                                  unsigned* status) {
+    if (dz == 0.0) return false;
+    const double t0 = -zl / dz;
+    if (S.kind == RW_PLANE) { t = t0; return true; }
+    const double x1 = x + t0 * dx, y1 = y + t0 * dy;
+    const double c = S.cd;
+    const double B = c * (x1 * dx + y1 * dy) - dz;
+    const double C = c * (x1 * x1 + y1 * y1);
+    const double disc = B * B - c * C;
+    if (disc < 0.0) return false;
+    const double q = -B - copysign(sqrt(disc), B);
+    if (q == 0.0) return false;
+    double t1 = C / q;
+    if (S.kind == RW_ASPHERE) {
+        bool conv = false;
+        for (int it = 0; it < 50; ++it) {
+            const double xh = x1 + t1 * dx, yh = y1 + t1 * dy;
+            const SagD sg = sag_eval_d(S, xh * xh + yh * yh);
+            if (!sg.ok) return false;
+            const double g = t1 * dz - sg.z;
+            const double gp = dz - sg.dz * 2.0 * (xh * dx + yh * dy);
+            if (gp == 0.0) return false;
+            const double step = g / gp;
+            t1 -= step;
+            if (fabs(step) <= 1e-12 * (fabs(t1) + fabs(sg.z) + 1e-3)) { conv = true; break; }
+        }
+        if (!conv) { if (status) atomicOr(status, RW_ST_NOTCONV); return false; }
+    }
+    t = t0 + t1;
+    return true;
+}
+
+__device__ __forceinline__ bool refract_d(double& dx, double& dy, double& dz, double nx,
+                                          double ny, double nz, double eta) {
+    double ci = nx * dx + ny * dy + nz * dz;
+    if (ci < 0.0) { nx = -nx; ny = -ny; nz = -nz; ci = -ci; }
+    const double k = 1.0 - eta * eta * (1.0 - ci * ci);
+    if (k < 0.0) return false;
+    const double beta = sqrt(k) - eta * ci;
+    dx = eta * dx + beta * nx;
+    dy = eta * dy + beta * ny;
+    dz = eta * dz + beta * nz;
+    return true;
+}
+
+// One surface before the DOE in double, global z; adds n_before * t |d| to opl.
+__device__ __forceinline__ bool trace_one_d(const DSurf& S, double& x, double& y, double& z,
+                                            double& dx, double& dy, double& dz, double& opl,
+                                            unsigned* status) {
+    double t;
+    if (!intersect_local_d(S, x, y, z - S.z, dx, dy, dz, t, status)) return false;
+    const double dn = sqrt(dx * dx + dy * dy + dz * dz);
+    x += t * dx; y += t * dy; z += t * dz;
+    if (S.r_ap2d > 0.0 && x * x + y * y > S.r_ap2d) return false;
+    double nx = 0.0, ny = 0.0, nz = 1.0;
+    if (S.kind != RW_PLANE) {
+        const SagD sg = sag_eval_d(S, x * x + y * y);
+        if (!sg.ok) return false;
+        const double mx = -2.0 * x * sg.dz, my = -2.0 * y * sg.dz;
+        const double inv = 1.0 / sqrt(mx * mx + my * my + 1.0);
+        nx = mx * inv; ny = my * inv; nz = inv;
+    }
+    if (!refract_d(dx, dy, dz, nx, ny, nz, S.nbd / S.nad)) return false;
+    opl += S.nbd * t * dn;
     return true;
 }
 

@@ -208,6 +208,29 @@ __device__ __forceinline__ bool conformal_hit(const DSurf& S, float x, float y, 
     return true;
 }
 
+// conformal_hit from a ray state in double (the FP64 trace before the DOE):
+// the sphere's root in closed form in double, the bump as above.
+__device__ __forceinline__ bool conformal_hit(const DSurf& S, double x, double y, double zld,
+                                              double dx, double dy, double dz, double& t,
+                                              unsigned* status) {
+    if (S.kind == RW_GAUSS) {
+        const double h = S.cd, iw2 = 0.5 / (S.kd * S.kd);
+        t = (h * exp(-(x * x + y * y) * iw2) - zld) / dz;
+        for (int it = 0; it < 40; ++it) {
+            const double qx = x + t * dx, qy = y + t * dy;
+            const double e = h * exp(-(qx * qx + qy * qy) * iw2);
+            const double gp = dz + 2.0 * iw2 * e * (qx * dx + qy * dy);
+            if (gp == 0.0) break;
+            const double step = (zld + t * dz - e) / gp;
+            t -= step;
+            if (fabs(step) <= 1e-13 * (1.0 + fabs(t))) return true;
+        }
+        if (status) atomicOr(status, RW_ST_NOTCONV);
+        return false;
+    }
+    return intersect_local_d(S, x, y, zld, dx, dy, dz, t, status);
+}
+
 // ------------------------------------------------------------------ A1 + A2
 // Trace incident ray g (concatenated job order) to the DOE, build the
 // tangent frame and everything the patch step needs.  The DOE hit is
@@ -224,49 +247,54 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     const DJob& J = jobs[j];
     const long long ri = J.off + (g - prefix[j]);
     R.rid = ri;
-    float x = rays.ox[ri], y = rays.oy[ri], zl = rays.oz[ri];
-    float dx = rays.dx[ri], dy = rays.dy[ri], dz = rays.dz[ri];
+    // the run to the DOE in double (see trace_one_d), from the float ray
+    double xd = rays.ox[ri], yd = rays.oy[ri], zd = rays.oz[ri];
+    double dxd = rays.dx[ri], dyd = rays.dy[ri], dzd = rays.dz[ri];
     double opl = rays.opl[ri];
-    const double oz = (double)zl;
     for (int s = 0; s < sys.doe_index; ++s)
-        if (!trace_one<true>(sys.s[s], x, y, zl, dx, dy, dz, opl, status)) return;
+        if (!trace_one_d(sys.s[s], xd, yd, zd, dxd, dyd, dzd, opl, status)) return;
     const DSurf& S = sys.s[sys.doe_index];
-    const double zld = (sys.doe_index == 0)
-                           ? (oz - S.z)
-                           : ((double)zl - (S.z - sys.s[sys.doe_index - 1].z));
-    if (dz == 0.f) return;
+    const double zld = zd - S.z;
+    if (dzd == 0.0) return;
     double t;
     float nx, ny, nz;
     if (!sys.conformal) {
-        t = -zld / (double)dz;
-    } else if (!conformal_hit(S, x, y, zld, dx, dy, dz, t, status)) {
+        t = -zld / dzd;
+    } else if (!conformal_hit(S, xd, yd, zld, dxd, dyd, dzd, t, status)) {
         return;
     }
-    const double pxd = __dadd_rn((double)x, __dmul_rn(t, (double)dx));
-    const double pyd = __dadd_rn((double)y, __dmul_rn(t, (double)dy));
-    const double pzl = sys.conformal ? zld + t * (double)dz : 0.0;   // planar: on the plane
-    if (!sys.conformal) {
-        nx = 0.f; ny = 0.f; nz = 1.f;
-    } else if (S.kind == RW_GAUSS) {
+    const float dx = (float)dxd, dy = (float)dyd, dz = (float)dzd;
+    const double pxd = __dadd_rn(xd, __dmul_rn(t, dxd));
+    const double pyd = __dadd_rn(yd, __dmul_rn(t, dyd));
+    const double pzl = sys.conformal ? zld + t * dzd : 0.0;   // planar: on the plane
+    // the tangent frame in double, rounded once: every secondary direction is
+    // built from it, and on an oblique field a float frame's ~1e-7 error moves
+    // a ray's whole fan by nanometres at a sensor tens of mm away
+    double nxd = 0.0, nyd = 0.0, nzd = 1.0;
+    if (S.kind == RW_GAUSS && sys.conformal) {
         // normal grad(z - sag) with -dsag/dx = x h e^{-s/(2 w^2)} / w^2 (same for y)
         const double iw2 = 0.5 / (S.kd * S.kd);
         const double e = S.cd * exp(-(pxd * pxd + pyd * pyd) * iw2);
         const double mx = 2.0 * iw2 * e * pxd, my = 2.0 * iw2 * e * pyd;
         const double inv = 1.0 / sqrt(mx * mx + my * my + 1.0);
-        nx = (float)(mx * inv); ny = (float)(my * inv); nz = (float)inv;
-    } else {
+        nxd = mx * inv; nyd = my * inv; nzd = inv;
+    } else if (sys.conformal) {
         const double c = S.cd;
         const double s2 = pxd * pxd + pyd * pyd;
         const double a = 1.0 - c * c * s2;
         if (a <= 0.0) return;
-        nx = (float)(-c * pxd); ny = (float)(-c * pyd); nz = (float)sqrt(a);
+        nxd = -c * pxd; nyd = -c * pyd; nzd = sqrt(a);
     }
-    if (nx * dx + ny * dy + nz * dz < 0.f) { nx = -nx; ny = -ny; nz = -nz; }
+    if (nxd * dxd + nyd * dyd + nzd * dzd < 0.0) { nxd = -nxd; nyd = -nyd; nzd = -nzd; }
     // u = normalise(x - (x.n) n), v = n x u
-    float ux = 1.f - nx * nx, uy = -nx * ny, uz = -nx * nz;
-    float inv = rsqrtf(ux * ux + uy * uy + uz * uz);
-    ux *= inv; uy *= inv; uz *= inv;
-    float vx = ny * uz - nz * uy, vy = nz * ux - nx * uz, vz = nx * uy - ny * ux;
+    double uxd = 1.0 - nxd * nxd, uyd = -nxd * nyd, uzd = -nxd * nzd;
+    const double invu = 1.0 / sqrt(uxd * uxd + uyd * uyd + uzd * uzd);
+    uxd *= invu; uyd *= invu; uzd *= invu;
+    const double vxd = nyd * uzd - nzd * uyd, vyd = nzd * uxd - nxd * uzd,
+                 vzd = nxd * uyd - nyd * uxd;
+    nx = (float)nxd; ny = (float)nyd; nz = (float)nzd;
+    const float ux = (float)uxd, uy = (float)uyd, uz = (float)uzd;
+    const float vx = (float)vxd, vy = (float)vyd, vz = (float)vzd;
     R.u[0] = ux; R.u[1] = uy; R.u[2] = uz;
     R.v[0] = vx; R.v[1] = vy; R.v[2] = vz;
     // R.n is the normal the secondary rays leave along: reversed by a mirror
@@ -279,8 +307,8 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     R.invK = 1.f / R.K;
     {
         const double rn = sys.n_in_d / (double)sys.n_out;
-        const double tu = rn * ((double)dx * ux + (double)dy * uy + (double)dz * uz);
-        const double tv = rn * ((double)dx * vx + (double)dy * vy + (double)dz * vz);
+        const double tu = rn * (dxd * ux + dyd * uy + dzd * uz);   // on the float frame
+        const double tv = rn * (dxd * vx + dyd * vy + dzd * vz);
         const double ts = J.lambda / ((double)sys.M * sys.pitch * (double)sys.n_out);
         R.tu = (float)tu; R.tu_lo = (float)(tu - (double)R.tu);
         R.tv = (float)tv; R.tv_lo = (float)(tv - (double)R.tv);
@@ -289,9 +317,16 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     R.px = (float)pxd; R.py = (float)pyd; R.pz = (float)pzl;
     R.pxd = pxd; R.pyd = pyd;
     R.a_re = rays.are[ri]; R.a_im = rays.aim[ri];
-    R.opl = opl + sys.n_in_d * t * dnorm(dx, dy, dz);
+    R.opl = opl + sys.n_in_d * t * sqrt(dxd * dxd + dyd * dyd + dzd * dzd);
     R.job = j;
     R.cx = J.cx; R.cy = J.cy;
+    {
+        const double sx = pxd - J.cxd, sy = pyd - J.cyd;
+        const double sl = (sys.sensor_z - S.z) - pzl;
+        R.sx = (float)sx; R.sx_lo = (float)(sx - (double)R.sx);
+        R.sy = (float)sy; R.sy_lo = (float)(sy - (double)R.sy);
+        R.sl = (float)sl; R.sl_lo = (float)(sl - (double)R.sl);
+    }
     const double p = sys.pitch;
     if (sys.gather == RW_GATHER_NEAREST) {
         const double cs = floor(pxd / p + (double)sys.W / 2.0);
@@ -322,18 +357,19 @@ __device__ __forceinline__ float2 tmap(const float2* __restrict__ T, int H, int 
 template <int M>
 __device__ __forceinline__ void phase_factors(const DSys& sys, const RayAtDoe& R, float2* phu,
                                               float2* phv) {
-    if (threadIdx.x < M) {
-        const float j = (float)((int)threadIdx.x - M / 2);
+    const int t = ltid();
+    if (t < M) {
+        const float j = (float)(t - M / 2);
         float s, c;
         if (sys.gather == RW_GATHER_NEAREST) {
             sincospif(-2.f * j * R.s0, &s, &c);
-            phu[threadIdx.x] = make_float2(c, s);
+            phu[t] = make_float2(c, s);
             sincospif(-2.f * j * R.t0, &s, &c);
-            phv[threadIdx.x] = make_float2(c, s);
+            phv[t] = make_float2(c, s);
         } else {
             sincospif(j / (float)(M / sys.D), &s, &c);
-            phu[threadIdx.x] = make_float2(c, s);
-            phv[threadIdx.x] = make_float2(c, s);
+            phu[t] = make_float2(c, s);
+            phv[t] = make_float2(c, s);
         }
     }
 }
@@ -450,6 +486,36 @@ __device__ __forceinline__ bool trace_to_sensor(const DSys& sys, float& x, float
 // Bilinear |a|^2 deposit.  The image is accumulated in double: a focal
 // pixel can receive ~1e6 deposits, and float accumulation there would drop
 // small contributions.
+// Where a secondary ray leaving the DOE along (dx, dy, dz) meets the sensor
+// plane, relative to the job's window centre, when the DOE is the last
+// surface: (p - c) + L (dx, dy) / dz with p - c and L from the incident ray
+// in double (RayAtDoe::sx, sy, sl).  Evaluated in float pairs: the run is
+// tens of mm and the window centre of an oblique field tens of mm off axis,
+// where a float coordinate is only good to ~2 nm (1e-3 of a 2 um pixel).
+__device__ __forceinline__ void sensor_offset(const RayAtDoe& R, float dx, float dy, float dz,
+                                              float& ox, float& oy) {
+    const float iz = __frcp_rn(dz);
+    const float d2[2] = {dx, dy};
+    const float p_hi[2] = {R.sx, R.sy}, p_lo[2] = {R.sx_lo, R.sy_lo};
+    float o[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        // q = d / dz as hi + lo
+        const float q = d2[c] * iz;
+        const float ql = fmaf(-q, dz, d2[c]) * iz;
+        // L q as hi + lo
+        const float m = R.sl * q;
+        const float ml = fmaf(R.sl, ql, fmaf(R.sl_lo, q, fmaf(R.sl, q, -m)));
+        // (p_hi + m) + (p_lo + ml), the first sum exactly (two-sum)
+        const float s = p_hi[c] + m;
+        const float bb = s - p_hi[c];
+        const float err = (p_hi[c] - (s - bb)) + (m - bb);
+        o[c] = s + (err + (p_lo[c] + ml));
+    }
+    ox = o[0];
+    oy = o[1];
+}
+
 __device__ __forceinline__ bool splat_bilinear(const DSys& sys, float cx, float cy, float x,
                                                float y, float w, double* __restrict__ img) {
     const float u = (x - cx) * sys.inv_spitch + 0.5f * sys.nx - 0.5f;
@@ -691,7 +757,11 @@ __device__ __forceinline__ bool deposit(const DSys& sys, const DJob& J, const Ra
     float x = R.px, y = R.py, zl = R.pz;
     double opl = R.opl;
     const long long npx = (long long)sys.nx * sys.ny;
-    if (MODE == MODE_SPLAT && NS >= 0) {
+    if (MODE == MODE_SPLAT && NS == 0) {
+        float ox, oy;
+        sensor_offset(R, dx, dy, dz, ox, oy);
+        return splat_bilinear(sys, 0.f, 0.f, ox, oy, w, psf + (long long)J.out * npx);
+    } else if (MODE == MODE_SPLAT && NS > 0) {
         if (!fast_to_sensor<NS>(sys, x, y, zl, dx, dy, dz)) return false;
         return splat_bilinear(sys, R.cx, R.cy, x, y, w, psf + (long long)J.out * npx);
     } else if (MODE == MODE_SPLAT) {
@@ -751,7 +821,7 @@ __device__ __forceinline__ void emit_culled(const DSys& sys, const DJob& J, cons
     const float2 ain = make_float2(R.a_re, R.a_im);
     const float norm = sys.norm;
     const float ain2 = (ain.x * ain.x + ain.y * ain.y) * norm * norm;
-    for (int i = threadIdx.x; i < 64 * nkept; i += RW_THREADS) {
+    for (int i = ltid(); i < 64 * nkept; i += RW_THREADS) {
         // block of the (i / 64)-th set bit, bin i % 64 inside it
         int k = i >> 6, bi = 0;
 #pragma unroll
@@ -775,21 +845,21 @@ __device__ __forceinline__ void emit_culled(const DSys& sys, const DJob& J, cons
         }
     }
     if (vis) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < NW; i += RW_THREADS) vis[g * (long long)NW + i] = vw[i];
+        main_sync();
+        for (int i = ltid(); i < NW; i += RW_THREADS) vis[g * (long long)NW + i] = vw[i];
         if (!tape.iray)
-            for (int i = threadIdx.x; i < NW; i += RW_THREADS) vw[i] = 0u;
+            for (int i = ltid(); i < NW; i += RW_THREADS) vw[i] = 0u;
     }
     if (vis && tape.iray) {
         constexpr int KV = (NW + RW_THREADS - 1) / RW_THREADS;   // words per thread
         constexpr int NWARP = RW_THREADS / 32;
         int* wsum = reinterpret_cast<int*>(vw + NW);
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int lane = ltid() & 31, warp = ltid() >> 5;
         unsigned word[KV];
         int cnt = 0;
 #pragma unroll
         for (int k = 0; k < KV; ++k) {
-            const int wi = threadIdx.x * KV + k;
+            const int wi = ltid() * KV + k;
             word[k] = wi < NW ? vw[wi] : 0u;
             if (wi < NW) vw[wi] = 0u;
             cnt += __popc(word[k]);
@@ -800,8 +870,8 @@ __device__ __forceinline__ void emit_culled(const DSys& sys, const DJob& J, cons
             if (lane >= o) incl += v;
         }
         if (lane == 31) wsum[warp] = incl;
-        __syncthreads();
-        if (threadIdx.x == 0) {
+        main_sync();
+        if (ltid() == 0) {
             int t = 0;
             for (int w = 0; w < NWARP; ++w) { const int v = wsum[w]; wsum[w] = t; t += v; }
             long long base = 0;
@@ -813,7 +883,7 @@ __device__ __forceinline__ void emit_culled(const DSys& sys, const DJob& J, cons
             wsum[NWARP + 1] = (int)(base >> 31);
             wsum[NWARP + 2] = t;
         }
-        __syncthreads();
+        main_sync();
         if (wsum[NWARP + 2] > 0) {
             long long pos = (long long)wsum[NWARP] + ((long long)wsum[NWARP + 1] << 31) +
                             wsum[warp] + (incl - cnt);
@@ -824,7 +894,7 @@ __device__ __forceinline__ void emit_culled(const DSys& sys, const DJob& J, cons
                 while (wk) {
                     const int b = __ffs(wk) - 1;
                     wk &= wk - 1u;
-                    const int f = (threadIdx.x * KV + k) * 32 + b;
+                    const int f = (ltid() * KV + k) * 32 + b;
                     const int jvi = f / M, jui = f - (f / M) * M;
                     tape.iray[pos] = (int)g;
                     tape.ibin[pos] = f;
@@ -857,11 +927,11 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
     const float2 ain = make_float2(R.a_re, R.a_im);
     const float norm = sys.norm;
     const float ain2 = (ain.x * ain.x + ain.y * ain.y) * norm * norm;
-    if (MODE == MODE_EMIT && threadIdx.x == 0) {
+    if (MODE == MODE_EMIT && ltid() == 0) {
         eo.hx[g] = R.px; eo.hy[g] = R.py; eo.hz[g] = (float)((double)R.pz + sys.s[sys.doe_index].z);
         eo.opl[g] = R.opl;
     }
-    for (int f = f0 + threadIdx.x; f < f1; f += RW_THREADS) {
+    for (int f = f0 + ltid(); f < f1; f += RW_THREADS) {
         const int jvi = f / M, jui = f - (f / M) * M;
         float dx, dy, dz;
         const bool prop = bin_direction<(NS >= 0)>(sys, R, jui - M / 2, jvi - M / 2, dx, dy, dz);
@@ -909,7 +979,7 @@ __device__ __forceinline__ void emit_exhaustive(const DSys& sys, const DJob& J, 
         if (MODE == MODE_SPLAT && vis) {
             // one visibility bit per secondary ray: bin f -> word g * M^2/32 + f/32
             const unsigned word = __ballot_sync(0xffffffffu, landed);
-            if ((threadIdx.x & 31) == 0) vis[g * (long long)(M * M / 32) + (f >> 5)] = word;
+            if ((ltid() & 31) == 0) vis[g * (long long)(M * M / 32) + (f >> 5)] = word;
         }
     }
 }

@@ -88,11 +88,13 @@ constexpr uint32_t IDESC = tc_idesc_bf16(M, N);
 static_assert(D * D * sizeof(float2) <= 2 * TILE_B, "staging must fit the B region");
 }  // namespace tcdft
 
-// Issue one stage: D[tmem] = A_hi B_hi + A_hi B_lo + A_lo B_hi over K.
-__device__ __forceinline__ void tc_issue_stage(unsigned char* smem, uint32_t d_tmem) {
+// Issue one stage: D[tmem] = A_hi B_hi + A_hi B_lo + A_lo B_hi over K, with
+// A hi / lo at a, a + TILE_A and B hi / lo at b, b + TILE_B.
+__device__ __forceinline__ void tc_issue_stage_at(const unsigned char* a, const unsigned char* b,
+                                                  uint32_t d_tmem) {
     using namespace tcdft;
-    const uint32_t a_hi = smem_addr(smem + OFF_AHI), a_lo = smem_addr(smem + OFF_ALO);
-    const uint32_t b_hi = smem_addr(smem + OFF_BHI), b_lo = smem_addr(smem + OFF_BLO);
+    const uint32_t a_hi = smem_addr(a), a_lo = smem_addr(a + TILE_A);
+    const uint32_t b_hi = smem_addr(b), b_lo = smem_addr(b + TILE_B);
     const uint32_t sbo = 16 * K;
 #pragma unroll
     for (int s = 0; s < K / 16; ++s) {
@@ -104,6 +106,10 @@ __device__ __forceinline__ void tc_issue_stage(unsigned char* smem, uint32_t d_t
         tc_mma_bf16(d_tmem, tc_smem_desc(a_lo + ks, 128, sbo), tc_smem_desc(b_hi + ks, 128, sbo),
                     IDESC, 1);
     }
+}
+
+__device__ __forceinline__ void tc_issue_stage(unsigned char* smem, uint32_t d_tmem) {
+    tc_issue_stage_at(smem + tcdft::OFF_AHI, smem + tcdft::OFF_BHI, d_tmem);
 }
 
 __device__ __forceinline__ void put_bf16(unsigned char* base, uint32_t off, __nv_bfloat16 v) {
@@ -349,133 +355,170 @@ cudaError_t launch_spectra(const LaunchCtx& L, const DSys& sys, int tc, const DJ
 // own.  One CTA per SM (the constant operand takes 64 KB of shared memory).
 namespace tcfwd {
 using namespace tcdft;
-constexpr uint32_t OFF_X = OFF_B + 2 * TILE_B;                      // 96 KB
+// Two groups of RW_THREADS threads per CTA share the constant operand and the
+// tensor core; each group runs its own tiles of rays with its own operand,
+// spectrum and scratch, so that one group's gather, conversions and
+// emission overlap the other's MMAs and memory latency.
+constexpr int NGRP = 2;
 constexpr uint32_t X_BYTES = (uint32_t)(Patch<D>::ELEMS * sizeof(float2));
-constexpr uint32_t OFF_PH2 = OFF_X + X_BYTES;
-constexpr uint32_t OFF_INFO2 = OFF_PH2 + 2 * D * sizeof(float2);
-constexpr uint32_t OFF_VW = (uint32_t)((OFF_INFO2 + RW_TILE * sizeof(RayAtDoe) + 15) & ~15u);
-constexpr uint32_t OFF_BAR2 = (uint32_t)(OFF_VW + cull_scratch_bytes(D));
-constexpr uint32_t SMEM = OFF_BAR2 + 64;
+constexpr uint32_t G_B = 0;                                   // B hi, then B lo
+constexpr uint32_t G_X = 2 * TILE_B;
+constexpr uint32_t G_PH = G_X + X_BYTES;
+constexpr uint32_t G_INFO = G_PH + 2 * D * sizeof(float2);
+constexpr uint32_t G_VW = (uint32_t)((G_INFO + RW_TILE * sizeof(RayAtDoe) + 15) & ~15u);
+constexpr uint32_t G_KEEP = (uint32_t)(G_VW + cull_scratch_bytes(D));
+constexpr uint32_t G_BAR = G_KEEP + RW_TILE * 2 * sizeof(unsigned);
+constexpr uint32_t G_BYTES = (G_BAR + 16 + 1023) & ~1023u;
+constexpr uint32_t OFF_G = 2 * TILE_A;                        // after A hi, A lo
+constexpr uint32_t OFF_SLOT = OFF_G + NGRP * G_BYTES;
+constexpr uint32_t SMEM = OFF_SLOT + 16;
+constexpr uint32_t COLS = NGRP * 2 * N;                       // two accumulators per group
+static_assert(SMEM <= 227 * 1024, "shared memory of the two-group tensor-core forward");
 }  // namespace tcfwd
 
+// A3 for the tensor-core forward: patch sample (a, b) of ray R (nearest or
+// bilinear, as gather_patch) for rows b0 .. b0+7 of column a, split into
+// bf16 hi / lo and stored as the 16-byte K runs of the stage-1 operand
+// (row n = a, K = (re/im, b)).
+__device__ __forceinline__ void tc_gather8(const DSys& sys, const RayAtDoe& R,
+                                           const float2* __restrict__ T, int a, int b0,
+                                           unsigned char* B) {
+    using namespace tcdft;
+    __align__(16) __nv_bfloat16 hr[8], lr[8], hi_[8], li[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int b = b0 + j;
+        float2 t;
+        if (sys.gather == RW_GATHER_NEAREST) {
+            t = tmap(T, sys.H, sys.W, R.r0 + b, R.c0 + a);
+        } else {
+            const float oa = (float)(a - D / 2), ob = (float)(b - D / 2);
+            const float fu = R.s0 + oa * R.u[0] + ob * R.v[0];
+            const float fv = R.t0 + oa * R.u[1] + ob * R.v[1];
+            const float iuf = floorf(fu), ivf = floorf(fv);
+            const float wu = fu - iuf, wv = fv - ivf;
+            const int i0 = R.c0 + (int)iuf, j0 = R.r0 + (int)ivf;
+            const float2 t00 = tmap(T, sys.H, sys.W, j0, i0), t10 = tmap(T, sys.H, sys.W, j0, i0 + 1);
+            const float2 t01 = tmap(T, sys.H, sys.W, j0 + 1, i0), t11 = tmap(T, sys.H, sys.W, j0 + 1, i0 + 1);
+            const float w00 = (1.f - wu) * (1.f - wv), w10 = wu * (1.f - wv);
+            const float w01 = (1.f - wu) * wv, w11 = wu * wv;
+            t = make_float2(w00 * t00.x + w10 * t10.x + w01 * t01.x + w11 * t11.x,
+                            w00 * t00.y + w10 * t10.y + w01 * t01.y + w11 * t11.y);
+        }
+        bf16_split(t.x, hr[j], lr[j]);
+        bf16_split(t.y, hi_[j], li[j]);
+    }
+    const uint32_t ore = kmajor_off(a, b0, K), oim = kmajor_off(a, D + b0, K);
+    *reinterpret_cast<uint4*>(B + ore) = *reinterpret_cast<const uint4*>(hr);
+    *reinterpret_cast<uint4*>(B + TILE_B + ore) = *reinterpret_cast<const uint4*>(lr);
+    *reinterpret_cast<uint4*>(B + oim) = *reinterpret_cast<const uint4*>(hi_);
+    *reinterpret_cast<uint4*>(B + TILE_B + oim) = *reinterpret_cast<const uint4*>(li);
+}
+
+// The fused forward with the tensor-core patch transform (D = 64, no
+// padding, exhaustive emission, incoherent sensor): per incident ray the
+// patch is gathered into the stage-1 operand, U = F X F^T is formed on the
+// tensor cores (BF16x3, FP32 accumulation in tensor memory), the spectrum
+// lands in shared memory in the FFT's layout, and the FFT path's emission
+// (culled blocks, mask, tape) runs on it unchanged.  Every wait on the
+// tensor core is bounded: on a timeout the status word gets RW_ST_TIMEOUT
+// and the group stops.
 template <int NS>
-__global__ void __launch_bounds__(RW_THREADS, 1)
+__global__ void __launch_bounds__(tcfwd::NGRP * RW_THREADS, 1)
 k_forward_tc(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
              int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
              double* __restrict__ psf, unsigned* status, unsigned* __restrict__ vis,
              const unsigned* __restrict__ keep, SplitBufs tape) {
     using namespace tcfwd;
     extern __shared__ __align__(1024) unsigned char smem[];
-    float2* X = reinterpret_cast<float2*>(smem + OFF_X);
-    float2* phu = reinterpret_cast<float2*>(smem + OFF_PH2);
+    const int grp = threadIdx.x / RW_THREADS, lt = ltid(), lwarp = lt >> 5, lane = lt & 31;
+    unsigned char* gb = smem + OFF_G + grp * G_BYTES;
+    unsigned char* B = gb + G_B;
+    float2* X = reinterpret_cast<float2*>(gb + G_X);
+    float2* phu = reinterpret_cast<float2*>(gb + G_PH);
     float2* phv = phu + D;
-    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(smem + OFF_INFO2);
-    unsigned* vw = reinterpret_cast<unsigned*>(smem + OFF_VW);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + OFF_BAR2);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + OFF_BAR2 + 8);
-    __shared__ unsigned skeep[RW_TILE * 2];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (tape.epoch && blockIdx.x == 0 && tid == 0) {
+    RayAtDoe* info = reinterpret_cast<RayAtDoe*>(gb + G_INFO);
+    unsigned* vw = reinterpret_cast<unsigned*>(gb + G_VW);
+    unsigned* skeep = reinterpret_cast<unsigned*>(gb + G_KEEP);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(gb + G_BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + OFF_SLOT);
+    if (tape.epoch && blockIdx.x == 0 && threadIdx.x == 0) {
         const unsigned long long e = atomicAdd(tape.epoch, 1ull) + 1ull;
         if (tape.iray) tape.epoch[1] = e;
     }
     if (vis)
-        for (int i = tid; i < D * D / 32; i += RW_THREADS) vw[i] = 0u;
+        for (int i = lt; i < D * D / 32; i += RW_THREADS) vw[i] = 0u;
     // ---- constant operand: F_big = [[F_re, -F_im], [F_im, F_re]], split in bf16
-    for (int i = tid; i < M * K; i += RW_THREADS) {
+    for (int i = threadIdx.x; i < M * K; i += NGRP * RW_THREADS) {
         const int r = i / K, k = i - (i / K) * K;
         const int po = r / D, m = r - po * D, pi = k / D, kk = k - pi * D;
-        float s, c;
-        sincospif(2.f * (float)((m * kk) % D) / (float)D, &s, &c);   // F = c - i s
-        const float v = (po == pi) ? c : (po == 0 ? s : -s);
+        float sn, cs;
+        sincospif(2.f * (float)((m * kk) % D) / (float)D, &sn, &cs);   // F = c - i s
+        const float v = (po == pi) ? cs : (po == 0 ? sn : -sn);
         __nv_bfloat16 hi, lo;
         bf16_split(v, hi, lo);
         const uint32_t off = kmajor_off(r, k, K);
         put_bf16(smem + OFF_AHI, off, hi);
         put_bf16(smem + OFF_ALO, off, lo);
     }
-    if (tid == 0) mbar_init(bar, 1);
-    if (warp == 0) tmem_alloc(tslot, TMEM_COLS);
+    if (lt == 0) mbar_init(bar, 1);
+    if (threadIdx.x < 32) tmem_alloc(tslot, COLS);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-    const uint32_t d1 = tmem, d2 = tmem + N;
-    const int q = warp & 3;                      // TMEM lane quarter of this warp
+    const uint32_t d1 = tmem + (uint32_t)(grp * 2 * N), d2 = d1 + N;
+    const int q = lwarp & 3;                     // TMEM lane quarter of this warp
     const int row = q * 32 + lane;               // accumulator row = TMEM lane
-    const int cbase = (warp >> 2) * (N / 2);     // this warp's half of the columns
+    const int cbase = (lwarp >> 2) * (N / 2);    // this warp's half of the columns
     const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
     uint32_t parity = 0;
     bool failed = false;
     const long long npix_map = (long long)sys.H * sys.W;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
-    for (long long tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-        __syncthreads();
-        if (tid < RW_TILE) {
-            const long long g = tile * RW_TILE + tid;
-            incident_to_doe(sys, jobs, prefix, njob, total, rays, g, info[tid], status);
-            if (tape.rinfo && g < total) tape.rinfo[g] = info[tid];
+    for (long long tile = (long long)blockIdx.x * NGRP + grp; tile < ntiles && !failed;
+         tile += (long long)gridDim.x * NGRP) {
+        main_sync();
+        if (lt < RW_TILE) {
+            const long long g = tile * RW_TILE + lt;
+            incident_to_doe(sys, jobs, prefix, njob, total, rays, g, info[lt], status);
+            if (tape.rinfo && g < total) tape.rinfo[g] = info[lt];
         }
         if (keep) {
             constexpr int KW = cull_keep_words(D);
             const long long w0 = tile * RW_TILE * KW;
-            if (tid < RW_TILE * KW && KW <= 2)
-                skeep[tid] = (w0 + tid < total * KW) ? __ldg(keep + w0 + tid) : 0u;
+            if (lt < RW_TILE * KW && KW <= 2)
+                skeep[lt] = (w0 + lt < total * KW) ? __ldg(keep + w0 + lt) : 0u;
         }
-        __syncthreads();
+        main_sync();
         for (int r = 0; r < RW_TILE; ++r) {
             const long long g = tile * RW_TILE + r;
             const RayAtDoe& R = info[r];
             if (!R.alive) {
                 if (vis && g < total)
-                    for (int f = tid; f < D * D / 32; f += RW_THREADS)
+                    for (int f = lt; f < D * D / 32; f += RW_THREADS)
                         vis[g * (long long)(D * D / 32) + f] = 0u;
                 continue;
             }
             const DJob& J = jobs[R.job];
             const float2* T = Tmaps + (long long)J.slot * npix_map;
-            // ---- A3: patch -> B (rows n = a, K = (re/im, b)), complex split to bf16 hi/lo
-            for (int f = tid; f < D * D; f += RW_THREADS) {
-                const int b = f / D, a = f - (f / D) * D;
-                float2 t;
-                if (sys.gather == RW_GATHER_NEAREST) {
-                    t = tmap(T, sys.H, sys.W, R.r0 + b, R.c0 + a);
-                } else {
-                    const float oa = (float)(a - D / 2), ob = (float)(b - D / 2);
-                    const float fu = R.s0 + oa * R.u[0] + ob * R.v[0];
-                    const float fv = R.t0 + oa * R.u[1] + ob * R.v[1];
-                    const float iuf = floorf(fu), ivf = floorf(fv);
-                    const float wu = fu - iuf, wv = fv - ivf;
-                    const int i0 = R.c0 + (int)iuf, j0 = R.r0 + (int)ivf;
-                    const float2 t00 = tmap(T, sys.H, sys.W, j0, i0), t10 = tmap(T, sys.H, sys.W, j0, i0 + 1);
-                    const float2 t01 = tmap(T, sys.H, sys.W, j0 + 1, i0), t11 = tmap(T, sys.H, sys.W, j0 + 1, i0 + 1);
-                    const float w00 = (1.f - wu) * (1.f - wv), w10 = wu * (1.f - wv);
-                    const float w01 = (1.f - wu) * wv, w11 = wu * wv;
-                    t = make_float2(w00 * t00.x + w10 * t10.x + w01 * t01.x + w11 * t11.x,
-                                    w00 * t00.y + w10 * t10.y + w01 * t01.y + w11 * t11.y);
-                }
-                __nv_bfloat16 hi, lo;
-                bf16_split(t.x, hi, lo);
-                put_bf16(smem + OFF_BHI, kmajor_off(a, b, K), hi);
-                put_bf16(smem + OFF_BLO, kmajor_off(a, b, K), lo);
-                bf16_split(t.y, hi, lo);
-                put_bf16(smem + OFF_BHI, kmajor_off(a, D + b, K), hi);
-                put_bf16(smem + OFF_BLO, kmajor_off(a, D + b, K), lo);
-            }
+            // ---- A3: patch -> stage-1 operand, eight rows of one column per item
+            for (int it = lt; it < D * (D / 8); it += RW_THREADS)
+                tc_gather8(sys, R, T, it & (D - 1), 8 * (it / D), B);
             phase_factors<D>(sys, R, phu, phv);
             fence_async_smem();
             tc_fence_before();
-            __syncthreads();
+            main_sync();
             tc_fence_after();
             // ---- A4 stage 1: Y = F X
-            if (tid == 0) {
-                tc_issue_stage(smem, d1);
+            if (lt == 0) {
+                tc_issue_stage_at(smem + OFF_AHI, B, d1);
                 tc_commit(bar);
             }
             bool ok = mbar_wait_bounded(bar, parity, RW_TC_WAIT);
             parity ^= 1u;
-            if (__syncthreads_or(!ok)) { failed = true; break; }
+            if (group_or(!ok)) { failed = true; break; }
             tc_fence_after();
             // ---- Y (TMEM rows (re/im, m_v), columns a) -> B rows n = m_v, K = (re/im, a)
             {
@@ -490,23 +533,23 @@ k_forward_tc(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
 #pragma unroll
                         for (int e = 0; e < 8; ++e) bf16_split(v[j + e], hi8[e], lo8[e]);
                         const uint32_t off = kmajor_off(mv, p * D + cbase + cc + j, K);
-                        *reinterpret_cast<uint4*>(smem + OFF_BHI + off) = *reinterpret_cast<uint4*>(hi8);
-                        *reinterpret_cast<uint4*>(smem + OFF_BLO + off) = *reinterpret_cast<uint4*>(lo8);
+                        *reinterpret_cast<uint4*>(B + off) = *reinterpret_cast<uint4*>(hi8);
+                        *reinterpret_cast<uint4*>(B + TILE_B + off) = *reinterpret_cast<uint4*>(lo8);
                     }
                 }
             }
             fence_async_smem();
             tc_fence_before();
-            __syncthreads();
+            main_sync();
             tc_fence_after();
             // ---- stage 2: Z^T = F Y^T
-            if (tid == 0) {
-                tc_issue_stage(smem, d2);
+            if (lt == 0) {
+                tc_issue_stage_at(smem + OFF_AHI, B, d2);
                 tc_commit(bar);
             }
             ok = mbar_wait_bounded(bar, parity, RW_TC_WAIT);
             parity ^= 1u;
-            if (__syncthreads_or(!ok)) { failed = true; break; }
+            if (group_or(!ok)) { failed = true; break; }
             tc_fence_after();
             // ---- Z^T (rows (re/im, m_u), columns m_v) -> X[m_v][m_u], row stride D + 1
             {
@@ -522,23 +565,23 @@ k_forward_tc(const DSys sys, const DJob* __restrict__ jobs, const long long* __r
                 }
             }
             tc_fence_before();
-            __syncthreads();
+            main_sync();
             // ---- A5..A7: the FFT path's emission on the same spectrum
             emit_exhaustive<D, MODE_SPLAT, NS>(sys, J, R, X, phu, phv, psf, nullptr, EmitOut{},
                                                g, status, vis,
                                                keep ? skeep + r * cull_keep_words(D) : nullptr,
                                                vw, tape);
-            __syncthreads();
+            main_sync();
         }
     }
     if (failed) {
-        if (tid == 0) atomicOr(status, RW_ST_TIMEOUT);
-        // let any MMA still in flight finish before the tensor memory is released
+        if (lt == 0) atomicOr(status, RW_ST_TIMEOUT);
+        // let the group's MMA still in flight finish before the tensor memory is released
         mbar_wait_bounded(bar, parity ^ 1u, RW_TC_WAIT);   // the phase that timed out
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TMEM_COLS);
+    if (threadIdx.x < 32) tmem_dealloc(tmem, COLS);
 }
 
 template <int NS>
@@ -562,13 +605,13 @@ static cudaError_t launch_forward_tc_d(const LaunchCtx& L, const DSys& sys, cons
                                          (int)tcfwd::SMEM);
     if (e != cudaSuccess) return e;
     const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
+    const long long units = (ntiles + tcfwd::NGRP - 1) / tcfwd::NGRP;   // tiles per CTA step
     long long grid = pick_grid(L, RW_K_FORWARD, (long long)L.num_sms);
-    if (grid > ntiles) grid = ntiles;
+    if (grid > units) grid = units;
     if (grid < 1) grid = 1;
     RW_MARK(L, "k_forward_tc");
-    kern<<<(unsigned)grid, RW_THREADS, tcfwd::SMEM, L.stream>>>(sys, jobs, prefix, njob, total,
-                                                               rays, T, psf, status, vis, keep,
-                                                               tape);
+    kern<<<(unsigned)grid, tcfwd::NGRP * RW_THREADS, tcfwd::SMEM, L.stream>>>(
+        sys, jobs, prefix, njob, total, rays, T, psf, status, vis, keep, tape);
     RW_MARK(L, nullptr);
     return cudaGetLastError();
 }

@@ -11,6 +11,11 @@ PSF relative L2 <= 1e-4 and the gradients of the Eq. 3 loss within 1e-3.
 A second case replaces the last lens surface by an even asphere, so that
 all eight surface-gradient slots (z, c, k, A4..A10, n) are checked through
 both adjoint kernels (fused, and split over the visibility mask).
+
+The C4 forward the benchmark also times (conformal DOE on a sphere behind an
+even asphere, 4096 x 4096 map at 0.5 um, bilinear 64 x 64 patches, 27 jobs
+of 2048 x 2048 rays up to 30 degrees off axis) is checked the same way, with
+the FP32 FFT and with the tensor-core transform.
 """
 import numpy as np
 import pytest
@@ -56,8 +61,8 @@ def _check_dsurf(ds, prm, slots, tol=1e-3):
     assert not bad, (gmax, bad)
 
 
-def _subset_sim(RW, w, per_job, seed):
-    sim = RW.Simulator(w)                  # generates all rays of the workload
+def _subset_sim(RW, w, per_job, seed, dft="fft32"):
+    sim = RW.Simulator(w, dft=dft)         # generates all rays of the workload
     starts, subsets = R.ray_blocks(w.jobs, per_job, seed)
     off = R.jobs_offsets(w.jobs)
     sim.jobs = RW.jobs_struct(w.jobs, offsets=[int(off[j] + starts[j]) for j in range(len(w.jobs))],
@@ -169,3 +174,28 @@ def test_c5_sampled_d96_forward_and_adjoint_match_oracle(RW):
     assert rel_l2(dphi.cpu().numpy(), gphi) <= 1e-2, rel_l2(dphi.cpu().numpy(), gphi)
     ds = dsurf.cpu().numpy()
     _check_dsurf(ds, prm, (0, 1, 7), tol=1e-2)
+
+
+@pytest.fixture(scope="module")
+def c4_full():
+    w = R.configs.c4()                     # the benchmark's C4 workload, full size
+    assert w.system.doe.phi.shape == (4096, 4096) and len(w.jobs) == 27
+    starts, subsets = R.ray_blocks(w.jobs, 24, 2025)
+    with torch.no_grad():
+        ref = OP.psf(w, subsets=subsets, chunk=24).numpy()
+    return w, ref
+
+
+@pytest.mark.parametrize("dft", ["fft32", "tc"])
+def test_c4_workload_forward_matches_oracle(RW, c4_full, dft):
+    w, ref = c4_full
+    sim, subsets, n_sub = _subset_sim(RW, w, per_job=24, seed=2025, dft=dft)
+    psf = sim.forward()
+    torch.cuda.synchronize()
+    # With A4..A10 ~ N(0, 1e-6) mm the asphere's sag polynomial dominates
+    # beyond ~4 mm: at +-22.5 and +-30 degrees many rays meet it where
+    # Newton's method does not converge (FP64 on both sides); both drop
+    # those rays, and the GPU raises the non-convergence bit only.
+    assert sim.ctx.device_status() & ~1 == 0
+    assert (ref.reshape(len(w.jobs), -1).sum(1) > 0).sum() >= 12
+    assert rel_l2(psf.cpu().numpy(), ref) <= 1e-4, rel_l2(psf.cpu().numpy(), ref)
