@@ -71,8 +71,38 @@ __global__ void k_generate_rays(const GenJob* __restrict__ jobs, const long long
 template <int M>
 struct FwdOcc { static constexpr int value = M <= 64 ? 4 : 1; };
 
-template <int M, int MODE, int NS>
-__global__ void __launch_bounds__(RW_THREADS, FwdOcc<M>::value)
+// Helper warps of the sampled forward: threads RW_THREADS.. of the block.
+// They walk the same tiles and rays as the main threads, meet them at the
+// CTA barriers (tile start, and around the draws of every live ray) and make
+// their share of the draws -- the (draw, bin) Philox screening that is
+// nearly all of the sampled forward's work; the rest stays with the main
+// threads.
+template <int M>
+__device__ __noinline__ void sampled_draw_helpers(const DSys& sys, long long total,
+                                                  const RayAtDoe* info, unsigned char* scratch) {
+    const float* p = reinterpret_cast<const float*>(scratch);
+    const uint4* thr4 = reinterpret_cast<const uint4*>(p + M * M);
+    int* sel = reinterpret_cast<int*>(scratch + 8 * (size_t)M * M);
+    unsigned char* qmem = scratch + sampled_queue_offset(M, sys.n_ssr);
+    const uint32_t k0 = (uint32_t)(sys.seed & 0xffffffffull), k1 = (uint32_t)(sys.seed >> 32);
+    const long long ntiles = (total + RW_TILE - 1) / RW_TILE;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        __syncthreads();                     // CTA: tile start
+        __syncthreads();                     // CTA: the tile's rays are at the DOE
+        for (int r = 0; r < RW_TILE; ++r) {
+            if (!info[r].alive) continue;
+            __syncthreads();                 // CTA: p_j and the thresholds ready
+            gumbel_draws<M, RW_GQ_HELPED>(p, thr4, sel, 0, sys.n_ssr, (uint32_t)info[r].rid,
+                                          (uint32_t)sys.rng_offset, k0, k1, qmem);
+            __syncthreads();                 // CTA: draws done
+        }
+    }
+}
+
+// HW helper warps (sampled emission into the incoherent image only, see
+// sampled_draw_helpers); HW = 0 is the plain kernel.
+template <int M, int MODE, int NS, int HW = 0>
+__global__ void __launch_bounds__(RW_THREADS + 32 * HW, FwdOcc<M>::value)
 k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __restrict__ prefix,
           int njob, long long total, RaysIn rays, const float2* __restrict__ Tmaps,
           double* __restrict__ psf, float2* __restrict__ field, EmitOut eo, unsigned* status,
@@ -83,6 +113,12 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
     float2* phu = tw + M;
     float2* phv = phu + M;
     RayAtDoe* info = reinterpret_cast<RayAtDoe*>(phv + M);
+    if constexpr (HW > 0) {
+        if (threadIdx.x >= RW_THREADS) {
+            sampled_draw_helpers<M>(sys, total, info, smem + sampled_scratch_offset(M));
+            return;
+        }
+    }
     // exhaustive emission with block culling: visibility words of the ray
     unsigned* vw = reinterpret_cast<unsigned*>(smem + sampled_scratch_offset(M));
     if (tape.epoch && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -108,7 +144,7 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
         const long long tile = (MODE == MODE_COHERENT) ? unit / nslice : unit;
         const int f0 = (MODE == MODE_COHERENT) ? (int)(unit - tile * nslice) * per : 0;
         const int f1 = (MODE == MODE_COHERENT) ? min(nwork, f0 + per) : M * M;
-        __syncthreads();
+        __syncthreads();                                           // CTA
         if (threadIdx.x < RW_TILE) {
             const long long g = tile * RW_TILE + threadIdx.x;
             incident_to_doe(sys, jobs, prefix, njob, total, rays, g, info[threadIdx.x], status);
@@ -120,7 +156,7 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             if (threadIdx.x < RW_TILE * KW && KW <= 2)
                 skeep[threadIdx.x] = (w0 + threadIdx.x < total * KW) ? __ldg(keep + w0 + threadIdx.x) : 0u;
         }
-        __syncthreads();
+        __syncthreads();                                           // CTA
         for (int r = 0; r < RW_TILE; ++r) {
             const RayAtDoe& R = info[r];
             if (!R.alive) {
@@ -146,7 +182,7 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             }
             if (!staged) {
                 gather_patch<M>(sys, R, Tj, X, phu, phv);
-                __syncthreads();
+                main_sync();
                 fft2d<M, false>(X, tw);
             }
             if (sys.emit == RW_EMIT_EXHAUSTIVE) {
@@ -155,7 +191,8 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
                                              keep ? skeep + r * cull_keep_words(M) : nullptr,
                                              vw, tape, f0, f1);
             } else {
-                emit_sampled<M, MODE, NS>(sys, J, R, X, phu, phv, psf, field, eo,
+                emit_sampled<M, MODE, NS, HW ? RW_GQ_HELPED : RW_GQ>(sys, J, R, X, phu, phv, psf,
+                                                                     field, eo,
                                           tile * RW_TILE + r, status,
                                           smem + sampled_scratch_offset(M),
                                           MODE == MODE_COHERENT ? f0 : 0,
@@ -163,7 +200,7 @@ k_forward(const DSys sys, const DJob* __restrict__ jobs, const long long* __rest
             }
             // the next patch's bulk copies write X through the async proxy
             if (M == 64) fence_async_smem();
-            __syncthreads();
+            main_sync();
         }
     }
 }
@@ -332,12 +369,27 @@ cudaError_t launch_cull(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
 #undef RW_CULL_NS
 }
 
-template <int M, int MODE, int NS>
+// Helper warps of the sampled forward at M = 96 (one CTA per SM): 8 more
+// warps, so 16 per SM, when their queues still fit in shared memory.
+#define RW_FWD_HELPERS 8
+
+template <int M, int MODE, int NS, int HW = 0>
 static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                                     const long long* prefix, int njob, long long total,
                                     const RaysIn& rays, const float2* T, double* psf,
                                     float2* field, const EmitOut& eo, unsigned* status,
                                     unsigned* vis, unsigned* keep, const SplitBufs* tapep) {
+    if constexpr (HW == 0 && M == 96 && MODE == MODE_SPLAT) {
+        int dev = 0, optin = 0;
+        if (sys.emit == RW_EMIT_SAMPLED && cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) ==
+                cudaSuccess &&
+            forward_smem_bytes(M, sys.emit, sys.n_ssr, RW_FWD_HELPERS) <= (size_t)optin)
+            return launch_forward_d<M, MODE, NS, RW_FWD_HELPERS>(L, sys, jobs, prefix, njob,
+                                                                 total, rays, T, psf, field, eo,
+                                                                 status, vis, keep, tapep);
+    }
+    constexpr int NT = RW_THREADS + 32 * HW;
     SplitBufs tape;
     std::memset(&tape, 0, sizeof(tape));
     if constexpr (MODE == MODE_SPLAT && NS >= 0 && M <= 64) {
@@ -354,13 +406,13 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
     } else {
         keep = nullptr;
     }
-    size_t smem = forward_smem_bytes(M, sys.emit, sys.n_ssr);
-    auto kern = k_forward<M, MODE, NS>;
+    size_t smem = forward_smem_bytes(M, sys.emit, sys.n_ssr, HW);
+    auto kern = k_forward<M, MODE, NS, HW>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RW_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     long long ntiles = (total + RW_TILE - 1) / RW_TILE;
@@ -381,9 +433,8 @@ static cudaError_t launch_forward_d(const LaunchCtx& L, const DSys& sys, const D
     if (grid > units) grid = units;
     if (grid < 1) grid = 1;
     RW_MARK(L, "k_forward");
-    kern<<<(unsigned)grid, RW_THREADS, smem, L.stream>>>(s, jobs, prefix, njob, total, rays,
-                                                          T, psf, field, eo, status, vis, keep,
-                                                          tape);
+    kern<<<(unsigned)grid, NT, smem, L.stream>>>(s, jobs, prefix, njob, total, rays, T, psf,
+                                                  field, eo, status, vis, keep, tape);
     RW_MARK(L, nullptr);
     return cudaGetLastError();
 }

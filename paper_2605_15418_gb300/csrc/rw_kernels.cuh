@@ -124,18 +124,27 @@ __host__ __device__ constexpr size_t cull_scratch_bytes(int M) {
 // (order(score) << 32 | ~bin: the maximum is the best score, then the lowest
 // bin) and a fill counter.
 #define RW_GQ 512
-__host__ __device__ constexpr size_t gumbel_queue_bytes() {
-    return (size_t)(RW_THREADS / 32) * (RW_GQ * 8 + 32 * 8 + 16);
+// with helper warps (16 warps in all) each warp's queue holds half as many
+#define RW_GQ_HELPED 256
+__host__ __device__ constexpr size_t gumbel_warp_queue_bytes(int gq) {
+    return (size_t)gq * 8 + 32 * 8 + 16;
+}
+__host__ __device__ constexpr size_t gumbel_queue_bytes(int nwarps = RW_THREADS / 32,
+                                                        int gq = RW_GQ) {
+    return (size_t)nwarps * gumbel_warp_queue_bytes(gq);
 }
 // sampled forward scratch: p and screening words per bin, chosen bin per
 // draw, reduction, then the per-warp candidate queues (16-byte aligned)
 __host__ __device__ inline size_t sampled_queue_offset(int M, int n_ssr) {
     return align16(8 * (size_t)M * M + sizeof(int) * (size_t)n_ssr + 128);
 }
-inline size_t forward_smem_bytes(int M, int emit = RW_EMIT_EXHAUSTIVE, int n_ssr = 0) {
+// hw: helper warps of the sampled forward (see k_forward)
+inline size_t forward_smem_bytes(int M, int emit = RW_EMIT_EXHAUSTIVE, int n_ssr = 0,
+                                 int hw = 0) {
     size_t b = sampled_scratch_offset(M);
     if (emit == RW_EMIT_SAMPLED)
-        b += sampled_queue_offset(M, n_ssr) + gumbel_queue_bytes();
+        b += sampled_queue_offset(M, n_ssr) +
+             (hw ? gumbel_queue_bytes(RW_THREADS / 32 + hw, RW_GQ_HELPED) : gumbel_queue_bytes());
     else b += cull_scratch_bytes(M);
     return b;
 }
@@ -1078,7 +1087,7 @@ __device__ __forceinline__ float float_unorder(uint32_t o) {
 // draw whose queue share overflowed, or whose best candidate does not clear
 // the floor, rescans every bin.  Not inlined: the hot loop gets registers of
 // its own, apart from the rest of the fused kernel.
-template <int M>
+template <int M, int GQ = RW_GQ>
 __device__ __noinline__ void gumbel_draws(const float* __restrict__ p,
                                           const uint4* __restrict__ thr4, int* __restrict__ sel,
                                           int d0, int d1, uint32_t ray, uint32_t off,
@@ -1086,13 +1095,13 @@ __device__ __noinline__ void gumbel_draws(const float* __restrict__ p,
     constexpr int NG = M * M / 4, CH = 8;
     static_assert(NG % CH == 0, "bin groups in blocks of eight");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned char* wm = qmem + (size_t)warp * (RW_GQ * 8 + 32 * 8 + 16);
+    unsigned char* wm = qmem + (size_t)warp * gumbel_warp_queue_bytes(GQ);
     uint2* wq = reinterpret_cast<uint2*>(wm);
-    unsigned long long* wk = reinterpret_cast<unsigned long long*>(wm + RW_GQ * 8);
-    int* qn = reinterpret_cast<int*>(wm + RW_GQ * 8 + 32 * 8);
+    unsigned long long* wk = reinterpret_cast<unsigned long long*>(wm + GQ * 8);
+    int* qn = reinterpret_cast<int*>(wm + GQ * 8 + 32 * 8);
     auto flush = [&]() {
         __syncwarp();
-        const int n = min(*qn, RW_GQ);
+        const int n = min(*qn, GQ);
         for (int t = lane; t < n; t += 32) {
             const uint2 e = wq[t];
             const int jb = (int)(e.y & 0xffffu), il = (int)(e.y >> 16);
@@ -1104,7 +1113,7 @@ __device__ __noinline__ void gumbel_draws(const float* __restrict__ p,
         if (lane == 0) *qn = 0;
         __syncwarp();
     };
-    for (int i0 = d0 + warp * 32; i0 < d1; i0 += RW_THREADS) {
+    for (int i0 = d0 + warp * 32; i0 < d1; i0 += (int)blockDim.x) {
         const uint32_t i = (uint32_t)(i0 + lane);
         wk[lane] = 0ull;
         if (lane == 0) *qn = 0;
@@ -1126,7 +1135,7 @@ __device__ __noinline__ void gumbel_draws(const float* __restrict__ p,
             if (mask) {
                 const int n = __popc(mask);
                 int c = atomicAdd(qn, n);
-                if (c + n > RW_GQ) {
+                if (c + n > GQ) {
                     ovf = true;
                 } else {
 #pragma unroll
@@ -1141,7 +1150,7 @@ __device__ __noinline__ void gumbel_draws(const float* __restrict__ p,
                 }
             }
             __syncwarp();
-            if (*qn > RW_GQ / 2) flush();
+            if (*qn > GQ / 2) flush();
         }
         flush();
         if ((int)i < d1) {
@@ -1196,7 +1205,7 @@ __device__ __forceinline__ float sampled_probs(const DSys& sys, const RayAtDoe& 
 
 // Shared scratch after the patch: p[M*M] floats, thr[M*M] words, sel[n_ssr]
 // ints, red[32].
-template <int M, int MODE, int NS>
+template <int M, int MODE, int NS, int GQ = RW_GQ>
 __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, const RayAtDoe& R,
                                              const float2* X, const float2* phu, const float2* phv,
                                              double* psf, float2* field, const EmitOut& eo,
@@ -1214,11 +1223,11 @@ __device__ __forceinline__ void emit_sampled(const DSys& sys, const DJob& J, con
     const float norm = sys.norm;
     sampled_probs<M>(sys, R, X, phu, phv, p, red);
     for (int f = threadIdx.x; f < M * M; f += RW_THREADS) thr[f] = gumbel_screen_word(p[f]);
-    __syncthreads();
-    gumbel_draws<M>(p, thr4, sel, d0, d1, (uint32_t)R.rid, (uint32_t)sys.rng_offset,
-                    (uint32_t)(sys.seed & 0xffffffffull), (uint32_t)(sys.seed >> 32),
-                    scratch + sampled_queue_offset(M, sys.n_ssr));
-    __syncthreads();
+    __syncthreads();           // CTA: helper warps (k_forward) join the draws
+    gumbel_draws<M, GQ>(p, thr4, sel, d0, d1, (uint32_t)R.rid, (uint32_t)sys.rng_offset,
+                        (uint32_t)(sys.seed & 0xffffffffull), (uint32_t)(sys.seed >> 32),
+                        scratch + sampled_queue_offset(M, sys.n_ssr));
+    __syncthreads();           // CTA
     const float2 ain = make_float2(R.a_re, R.a_im);
     if (MODE == MODE_EMIT && threadIdx.x == 0) {
         eo.hx[g] = R.px; eo.hy[g] = R.py; eo.hz[g] = (float)((double)R.pz + sys.s[sys.doe_index].z);
