@@ -66,9 +66,12 @@ def parse():
     ap.add_argument("--c5-scale", type=int, default=4096,
                     help="C5 ray counts per job divided by this (64k..2M -> 16..512 at 4096)")
     ap.add_argument("--n-side", type=int, default=1024, help="C2 rays per field = n_side^2")
-    ap.add_argument("--also", default="c2,c4,c4tc",
+    ap.add_argument("--also", default="c2,c4,c4tc,c1",
                     help="comma-separated extra workloads measured after the headline ('' = "
-                         "none); c4tc is the C4 forward with the tensor-core patch transform")
+                         "none); c4tc is the C4 forward with the tensor-core patch transform, "
+                         "c1 the grating's secondary rays written to HBM (rw_doe_emit)")
+    ap.add_argument("--c1-n-side", type=int, default=512,
+                    help="C1 rays per incidence angle = n_side^2 (emit line)")
     ap.add_argument("--c4-n-side", type=int, default=2048,
                     help="C4 rays per field = n_side^2 (2048: 4M, the stated workload)")
     ap.add_argument("--also-steps", type=int, default=5)
@@ -91,6 +94,8 @@ def workload(name, args):
         return R.configs.c5(count_lo=max(1, C5_FULL_LO // s), count_hi=max(4, C5_FULL_HI // s))
     if name in ("c4", "c4tc"):
         return R.configs.c4(n_side=args.c4_n_side)
+    if name == "c1":
+        return R.configs.c1(n_side=args.c1_n_side)
     return R.configs.c2(n_side=args.n_side)
 
 
@@ -534,6 +539,57 @@ def roofline_c5(tm, st, peaks, n_sms, clocks):
                             "mufu_ops_per_pair": 0.0 if name == "k_forward" else C5_BWD_MUFU}}
 
 
+# bytes rw_doe_emit writes per secondary ray (dx, dy, dz, a_re, a_im, bin)
+# and per incident ray (hit x, y, z, optical path), and reads per incident ray
+# (its nine ray fields); the map and the job table stay in L2
+EMIT_W_SEC, EMIT_W_RAY, EMIT_R_RAY = 24, 20, 36
+
+
+def emit_line(w, args, dev, local, flush, peaks):
+    """C1: the planar grating's secondary rays written to HBM by rw_doe_emit,
+    timed with CUDA events on the launching stream (the output, larger than
+    L2, is written every step; the flush buffer is zeroed between steps)."""
+    import torch
+    from paper_2605_15418_gb300 import raywave as RW
+    sim = RW.Simulator(w, device=local)
+    M = w.system.doe.M
+    out = RW.alloc_emitted(sim.n_rays, M * M, dev)
+    s, keep = sim.sys_struct()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.also_warmup):
+        RW.rw_doe_emit(sim.ctx, s, sim.jobs, sim.rays, out)
+    torch.cuda.synchronize()
+    ms = []
+    sim.ctx.profile(True)
+    for _ in range(args.also_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        RW.rw_doe_emit(sim.ctx, s, sim.jobs, sim.rays, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    prof = sim.ctx.profile_read()
+    sim.ctx.profile(False)
+    kernel_ms = {k: v[0] / v[1] for k, v in prof.items() if v[1] > 0}
+    t = float(np.mean(ms))
+    kt = kernel_ms.get("k_forward", t)
+    nbytes = sim.n_rays * (M * M * EMIT_W_SEC + EMIT_W_RAY + EMIT_R_RAY)
+    gbs = nbytes / (kt / 1e3) / 1e9
+    cfg = {"workload": w.name, "incident_rays": sim.n_rays, "jobs": len(w.jobs), "D": M,
+           "emission": "exhaustive", "step": "rw_doe_emit: every secondary ray to HBM",
+           "bytes_per_launch": nbytes, "kernel_ms": {k: round(v, 4) for k, v in kernel_ms.items()}}
+    roof = {"kernel": "k_forward (MODE_EMIT)", "bound": "hbm", "achieved": gbs,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
+            "traffic": None}
+    res = {"value": sim.n_rays / (t / 1e3), "unit": "rays/s", "ms_per_step": t,
+           "steps": args.also_steps, "warmup": args.also_warmup, "config": cfg,
+           "roofline": roof}
+    del out, sim
+    torch.cuda.empty_cache()
+    return res
+
+
 def roofline_c4(tm, st, n_sms, peaks=None):
     """FP32 roofline of the dominant kernel of the C4 forward; with the
     tensor-core transform also its tcgen05 throughput against the measured
@@ -635,6 +691,9 @@ def main():
     also = []
     for other in [x for x in args.also.split(",") if x and x != name]:
         wo = workload(other, args)
+        if other == "c1":
+            also.append(emit_line(wo, args, dev, local, flush, peaks))
+            continue
         so = Step(other, wo, dev, local, dft="tc" if other == "c4tc" else "fft32")
         to = time_steps(so, args.also_steps, args.also_warmup, flush, dev,
                         autotune=(other == "c2" and not args.no_autotune), dist=dist,

@@ -105,7 +105,9 @@ __device__ __noinline__ void gumbel_pass_a(const float2* __restrict__ rec,
                 Sn = fmaf(t, pk.y, Sn);
                 Sr = fmaf(t, wt.x, Sr);
                 Si = fmaf(t, wt.y, Si);
-                mask |= (unsigned)(pk.x > 0.f && E < fmaf(RW_GUMBEL_TAU * 1.001f, pk.x, 1e-6f)) << q;
+                // a bin that cannot be drawn (p = 0) passes only when E < 1e-6
+                // and then scores -inf, which never wins
+                mask |= (unsigned)(E < fmaf(RW_GUMBEL_TAU * 1.001f, pk.x, 1e-6f)) << q;
             }
             Z += z8;
             Su += fmaf((float)(ju0 - M / 2), z8, zq);

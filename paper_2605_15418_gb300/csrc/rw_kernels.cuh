@@ -1027,17 +1027,19 @@ __device__ __forceinline__ uint32_t gumbel_screen_word(float p) {
     return tm <= 0.f ? 0u : ((uint32_t)tm << 9);
 }
 
-// E = -log u of the uniform of word w, to a few 1e-7 relative: near u = 1
-// (v = 1 - u < 1/16, where a logarithm of u loses relative accuracy) the
-// series -log(1 - v) = v + v^2/2 + v^3/3 + v^4/4 + v^5/5 (truncation
-// < v^5/6 relative), elsewhere the hardware base-2 logarithm.
+// E = -log u of the uniform of word w, to 1e-5 relative (it weighs the soft
+// Gumbel-softmax terms of the adjoint, never a draw): near u = 1 (v = 1 - u
+// < 1/32, where a logarithm of u loses relative accuracy) the series
+// -log(1 - v) = v + v^2/2 + v^3/3 (truncation < v^3/4 = 8e-6 relative),
+// elsewhere the hardware base-2 logarithm (absolute error ~2^-22.6 in log2,
+// at most 4e-6 relative for u <= 31/32).
 __device__ __forceinline__ float gumbel_E_fast(uint32_t w) {
     const float m = (float)(w >> 9);
     const float v = (8388607.5f - m) * 1.1920928955078125e-7f;            // 1 - u, exact
-    const float series = v * (1.f + v * (0.5f + v * (0.33333334f + v * (0.25f + v * 0.2f))));
+    const float series = v * (1.f + v * (0.5f + v * 0.33333334f));
     float lg;
     asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(lg) : "f"((m + 0.5f) * 1.1920928955078125e-7f));
-    return v < 0.0625f ? series : -0.69314718f * lg;
+    return v < 0.03125f ? series : -0.69314718f * lg;
 }
 
 __device__ __forceinline__ float rcp_approx(float x) {
