@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--also-warmup", type=int, default=3)
     ap.add_argument("--cpu-rays", type=int, default=0,
                     help="incident rays per oracle sample (0: the workload's default)")
+    ap.add_argument("--parity-rays", type=int, default=0,
+                    help="incident rays of the parity sample (0: the workload's default)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="CPU time the cpu_baseline leg keeps sampling for")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -285,6 +287,24 @@ def oracle_step(w, subsets):
     Lv, _ = OL.eq3_loss(img, tgt)
     Lv.backward()
     return time.perf_counter() - t0, int(sum(len(s) for s in subsets)), img.detach().numpy()
+
+
+def parity_sample(w, n_rays, seed=4242):
+    """The oracle's FP64 PSF (forward only) of a seeded sample of about n_rays
+    incident rays, for the GPU's parity on the same rays."""
+    import torch
+    from oracle import pipeline as OP
+    sub = oracle_sample(w, n_rays, seed)
+    chunk = 32 if w.system.doe.emit == "exhaustive" else 1
+    with torch.no_grad():
+        img = OP.psf(w, subsets=sub, chunk=chunk).numpy()
+    return sub, img
+
+
+def default_parity_rays(name):
+    # the sampled PSF of a few rays is a few thousand deposits, each carrying
+    # its own hit rounding: parity wants enough rays for deposits to overlap
+    return 576 if name == "c2" else 64
 
 
 def cpu_baseline(w, n_rays, budget_s):
@@ -724,11 +744,13 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n_cpu = args.cpu_rays or default_cpu_rays(name)
-        cb, (sub, ref) = cpu_baseline(w, n_cpu, args.cpu_seconds)
+        cb, _ = cpu_baseline(w, n_cpu, args.cpu_seconds)
         line["cpu_baseline"] = cb
+        sub, ref = parity_sample(w, args.parity_rays or default_parity_rays(name))
         line["parity"] = {"psf_rel_l2": gpu_parity(st, sub, ref), "bar": 1e-4,
                           "rays": int(sum(len(s) for s in sub)),
-                          "sample": "the cpu_baseline's first sample, same rays on both sides"}
+                          "sample": "seeded contiguous runs of incident rays, the same rays "
+                                    "on both sides, oracle forward in FP64"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -144,16 +144,29 @@ def test_asphere_after_doe_all_surface_slots_match_oracle(RW, asphere_oracle, ad
         assert abs(ds[-1, k] - ref) <= 1e-3 * abs(ref), (NAMES[k], ds[-1, k], ref)
 
 
+def _oracle_grads_sampled(w, subsets):
+    prm = OP.params_of(w.system, requires_grad=True)
+    phi = torch.from_numpy(w.system.doe.phi.astype(np.float64)).requires_grad_(True)
+    img = OP.psf(w, params=prm, phi=phi, subsets=subsets, chunk=1)
+    Lv, _ = OL.eq3_loss(img, torch.from_numpy(w.target.astype(np.float64)))
+    Lv.backward()
+    return img.detach().numpy(), phi.grad.numpy(), prm
+
+
 def test_c5_sampled_d96_forward_and_adjoint_match_oracle(RW):
     """The headline workload's emission regime: 96 x 96 patches, 1024
     Gumbel-max draws per incident ray, three singlets, at the workload's own
-    map, sensor and job table.  Two incident rays (one contiguous run in each
-    of two jobs, so both sides draw the same stream): the GPU's forward and
-    straight-through adjoint against the FP64 oracle on exactly those rays."""
+    map, sensor and job table.  64 incident rays (contiguous runs of 8 in 8
+    seeded jobs, so both sides draw the same stream): the GPU's forward and
+    straight-through adjoint against the FP64 oracle on exactly those rays.
+    A sampled PSF is 1024 bilinear deposits per ray, each carrying the
+    rounding of its own FP32 sensor hit (~0.3 nm after six refractions, 1.5e-4
+    of a 2 um pixel); with fewer rays the deposits rarely overlap and the
+    image's relative error sits at that level (1.1e-4 at 32 rays)."""
     w = R.configs.c5(count_lo=16, count_hi=512)
     assert w.system.doe.D == 96 and w.system.doe.n_ssr == 1024 and len(w.jobs) == 496
-    starts, subsets = R.ray_blocks(w.jobs, 1, 77)
-    keep = (3, 250)
+    starts, subsets = R.ray_blocks(w.jobs, 8, 77)
+    keep = set(np.random.default_rng(78).choice(len(w.jobs), 8, replace=False).tolist())
     subsets = [s if j in keep else s[:0] for j, s in enumerate(subsets)]
     sim = RW.Simulator(w)
     off = R.jobs_offsets(w.jobs)
@@ -166,14 +179,19 @@ def test_c5_sampled_d96_forward_and_adjoint_match_oracle(RW):
     dphi, _, dsurf = sim.backward(gI)
     torch.cuda.synchronize()
     assert sim.ctx.device_status() == 0
-    img, gphi, prm = _oracle_grads(w, subsets)
+    img, gphi, prm = _oracle_grads_sampled(w, subsets)
     got = psf.cpu().numpy()
     assert img.sum() > 0
-    # draws decided in FP32 (GPU) and FP64 (oracle) may differ on near-ties
-    assert rel_l2(got, img) <= 1e-3, rel_l2(got, img)
-    assert rel_l2(dphi.cpu().numpy(), gphi) <= 1e-2, rel_l2(dphi.cpu().numpy(), gphi)
+    e_psf = rel_l2(got, img)
+    e_phi = rel_l2(dphi.cpu().numpy(), gphi)
     ds = dsurf.cpu().numpy()
-    _check_dsurf(ds, prm, (0, 1, 7), tol=1e-2)
+    print("c5 parity", e_psf, e_phi, [(si, k, ds[si, k], float(prm[si][NAMES[k]].grad))
+                                      for si in range(len(prm)) for k in (0, 1, 7)
+                                      if prm[si][NAMES[k]].grad is not None])
+    # draws decided in FP32 (GPU) and FP64 (oracle) may differ on near-ties
+    assert e_psf <= 1e-4, e_psf
+    assert e_phi <= 1e-3, e_phi
+    _check_dsurf(ds, prm, (0, 1, 7), tol=1e-3)
 
 
 @pytest.fixture(scope="module")
