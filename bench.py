@@ -56,6 +56,14 @@ C2_TRAFFIC = {"k_bs_scatter": 16 * (1.535592e9 + 0.192266e9),
               "k_forward": 16 * (0.310524e9 + 1.472937e9)}
 
 
+# DRAM bytes (read + write) per incident ray of the C5 kernels, from one ncu
+# capture of the current kernels on the same workload with its ray counts
+# divided by 32768 (9,270 rays; the launch's traffic grows with the rays:
+# dL/dPSF reads and PSF atomics per draw): see the profiles/ summaries.
+C5_TRAFFIC_PER_RAY = {"k_backward": (913.137408e6 + 274.656512e6) / 9270,
+                      "k_forward": (594.386944e6 + 50.164224e6) / 9270}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -546,13 +554,15 @@ def roofline_c5(tm, st, peaks, n_sms, clocks):
     fr_alu, fr_mufu = a_alu / alu_peak, a_mufu / mufu_peak
     return kernel_ms, {
         "kernel": name, "bound": "alu", "achieved": a_alu, "peak": alu_peak,
-        "unit": "Tops/s (32-bit lane ops)", "frac": fr_alu, "traffic": None,
+        "unit": "Tops/s (32-bit lane ops)", "frac": fr_alu,
+        "traffic": (C5_TRAFFIC_PER_RAY[name] * st.sim.n_rays
+                    if name in C5_TRAFFIC_PER_RAY else None),
         "peak_source": f"{n_sms} SMs x 128 lanes x 2070 MHz (one 32-bit op per lane per "
                        "clock; nominal unit counts and the maximum SM clock)",
         "other_bounds": {"mufu": {"achieved": a_mufu, "peak": mufu_peak, "frac": fr_mufu,
                                   "peak_source": f"{n_sms} SMs x 16 MUFU lanes x 2070 MHz"},
-                         "hbm": {"frac": "<1e-3 (maps and images stay in L2; "
-                                         "~0.1 MB of rays per incident-ray tile)"}},
+                         "hbm": {"frac": (C5_TRAFFIC_PER_RAY.get(name, 0.0) * st.sim.n_rays
+                                          / t / 1e9 / peaks["hbm_gbs"])}},
         "work_per_launch": {"pairs": float(st.sim.n_rays) * N * M * M,
                             "alu_ops_per_pair": C5_FWD_ALU if name == "k_forward"
                             else C5_BWD_ALU,
