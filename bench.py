@@ -645,6 +645,26 @@ def roofline_c4(tm, st, n_sms, peaks=None):
         "peak_source": f"{n_sms} SMs x 128 FP32 lanes x 2 x 2070 MHz (nominal)"}
 
 
+def red_peak(sim, dev, win=64, nwin=1 << 18):
+    """Float atomic-add (reduction) throughput of this GPU in the adjoint's
+    scatter pattern: rw_probe_red onto a 2048 x 2048 map (L2-resident, like
+    dL/dphi), CUDA events, best of three after a warm-up; adds per second."""
+    import torch
+    m = torch.zeros(2048, 2048, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sim.ctx.probe_red(m, win, nwin)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.ctx.probe_red(m, win, nwin)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return float(win) * win * nwin / (best / 1e3)
+
+
 def roofline_c2(tm, st, n_sms):
     """FP32 roofline of the dominant kernel of the C2 step."""
     import torch
@@ -667,6 +687,17 @@ def roofline_c2(tm, st, n_sms):
     achieved = modelled[name] / (kernel_ms[name] / 1e3) / 1e12
     extra = {"visible_secondary_fraction": items / float(n_rays * M * M),
              "traced_secondary_fraction": (64.0 * kept / (n_rays * M * M) if blocks else 1.0)}
+    if "k_bs_scatter" in kernel_ms:
+        # the scatter's dL/dphi adds (one per patch sample of every ray with
+        # visible bins; two with an amplitude map) against the measured
+        # reduction throughput in the same pattern
+        adds = rays_with_items * D * D * (2 if sysm.doe.amp is not None else 1)
+        rate = adds / (kernel_ms["k_bs_scatter"] / 1e3)
+        peak = red_peak(st.sim, st.vis.device)
+        extra["k_bs_scatter_red"] = {"achieved": rate, "peak": peak, "unit": "adds/s",
+                                     "frac": rate / peak,
+                                     "peak_source": "rw_probe_red: 64 x 64 windows on a "
+                                                    "2048^2 float map, measured here"}
     return kernel_ms, extra, {
         "kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
         "unit": "TFLOP/s", "frac": achieved / peak, "traffic": C2_TRAFFIC.get(name),

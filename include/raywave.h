@@ -276,6 +276,16 @@ rw_status rw_autotune(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int
  * e.g. to reuse an earlier rw_autotune result.  Errors: RW_EINVAL. */
 rw_status rw_set_grids(rw_ctx* ctx, const int64_t* grids);
 
+/* Measurement aid (no paper counterpart): enqueue win * win * nwin float
+ * atomic adds (results unused) onto map (device float [H][W], modified),
+ * in nwin windows of win x win pixels at pseudo-random offsets, a warp on
+ * adjacent pixels of a row -- the pattern of the adjoint's map scatter.
+ * Timing it gives the reduction ceiling the scatter's roofline is read
+ * against.  Errors: RW_EINVAL (NULL map, win outside [1, min(H, W)],
+ * nwin < 0). */
+rw_status rw_probe_red(rw_ctx* ctx, float* map, int32_t H, int32_t W, int32_t win,
+                       int64_t nwin);
+
 /* ---- A0: ray generation ------------------------------------------------ */
 
 /* Fill rays[ray_offset ..) of every job with its collimated grid launched

@@ -88,6 +88,8 @@ EXPORTS = {
                               C.POINTER(rw_rays), C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
                               C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]),
     "rw_set_grids": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "rw_probe_red": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_int32,
+                               C.c_int64]),
     "rw_profile_read": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32)]),
     "rw_profile_entry": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_char_p),
                                    C.POINTER(C.c_double), C.POINTER(C.c_int64)]),

@@ -13,6 +13,8 @@
 
 cudaError_t launch_loss_eq3(const LaunchCtx& L, const float* I, const float* T, long long n,
                             double* acc, double* out, float* g);
+cudaError_t launch_probe_red(const LaunchCtx& L, float* map, int H, int W, int win,
+                             long long nwin);
 cudaError_t launch_backward(const LaunchCtx& L, const DSys& sys, const DJob* jobs,
                             const long long* prefix, int njob, long long total,
                             const RaysIn& rays, const float2* T, const float* amp,
@@ -1241,6 +1243,20 @@ rw_status rw_autotune(rw_ctx* ctx, const rw_system* sys, const rw_job* jobs, int
         grids_out[k] = ctx->grid[k];
     }
     return st;
+}
+
+rw_status rw_probe_red(rw_ctx* ctx, float* map, int32_t H, int32_t W, int32_t win,
+                       int64_t nwin) {
+    if (!ctx) return RW_EINVAL;
+    ctx->err.clear();
+    if (!map) return fail(ctx, RW_EINVAL, "map is NULL");
+    if (H < 1 || W < 1 || win < 1 || win > H || win > W || nwin < 0)
+        return fail(ctx, RW_EINVAL, "need 1 <= win <= H, W and nwin >= 0");
+    if (nwin == 0) return RW_OK;
+    RW_CUDA(cudaSetDevice(ctx->device), "cudaSetDevice");
+    RW_CUDA(launch_probe_red(lctx(ctx), map, H, W, win, nwin), "reduction probe");
+    ctx->launches++;
+    return RW_OK;
 }
 
 rw_status rw_set_grids(rw_ctx* ctx, const int64_t* grids) {

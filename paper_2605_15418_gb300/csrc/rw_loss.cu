@@ -63,3 +63,34 @@ cudaError_t launch_loss_eq3(const LaunchCtx& L, const float* I, const float* T, 
     RW_MARK(L, nullptr);
     return cudaGetLastError();
 }
+
+// Reduction-throughput probe (the RED ceiling of the adjoint's map scatter):
+// `nwin` windows of win x win pixels at pseudo-random offsets of an H x W
+// float map, one atomic add per pixel with the result unused, a warp's lanes
+// on adjacent pixels of a row -- the access pattern of the patch scatter.
+__global__ void k_probe_red(float* __restrict__ map, int H, int W, int win, long long nwin) {
+    for (long long wdx = blockIdx.x; wdx < nwin; wdx += gridDim.x) {
+        // splitmix-style hash of the window index (integer only)
+        unsigned long long z = (unsigned long long)wdx * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const int r0 = (int)((z & 0xffffffffull) % (unsigned long long)(H - win + 1));
+        const int c0 = (int)((z >> 32) % (unsigned long long)(W - win + 1));
+        for (int f = threadIdx.x; f < win * win; f += blockDim.x) {
+            const int b = f / win, a = f - (f / win) * win;
+            atomicAdd(map + (long long)(r0 + b) * W + (c0 + a), 1e-3f);
+        }
+    }
+}
+
+cudaError_t launch_probe_red(const LaunchCtx& L, float* map, int H, int W, int win,
+                             long long nwin) {
+    long long grid = (long long)L.num_sms * 8;
+    if (grid > nwin) grid = nwin;
+    if (grid < 1) grid = 1;
+    RW_MARK(L, "k_probe_red");
+    k_probe_red<<<(unsigned)grid, 256, 0, L.stream>>>(map, H, W, win, nwin);
+    RW_MARK(L, nullptr);
+    return cudaGetLastError();
+}

@@ -100,6 +100,13 @@ class Context:
         arr = (C.c_int64 * len(A.KERNEL_KINDS))(*[int(grids.get(k, 0)) for k in A.KERNEL_KINDS])
         self.check(self.lib.rw_set_grids(self.h, arr), "rw_set_grids")
 
+    def probe_red(self, map2d, win, nwin):
+        """Enqueue win*win*nwin float atomic adds onto map2d (device float
+        [H][W]) in the pattern of the adjoint's map scatter (rw_probe_red)."""
+        H, W = map2d.shape
+        self.check(self.lib.rw_probe_red(self.h, map2d.data_ptr(), H, W, win, nwin),
+                   "rw_probe_red")
+
     def cull_stats(self):
         """(8 x 8 bin blocks, blocks kept) of the last culled forward."""
         self._stream()
