@@ -693,9 +693,9 @@ def roofline_c2(tm, st, n_sms):
         # reduction throughput in the same pattern
         adds = rays_with_items * D * D * (2 if sysm.doe.amp is not None else 1)
         rate = adds / (kernel_ms["k_bs_scatter"] / 1e3)
-        peak = red_peak(st.sim, st.vis.device)
-        extra["k_bs_scatter_red"] = {"achieved": rate, "peak": peak, "unit": "adds/s",
-                                     "frac": rate / peak,
+        red_pk = red_peak(st.sim, st.vis.device)
+        extra["k_bs_scatter_red"] = {"achieved": rate, "peak": red_pk, "unit": "adds/s",
+                                     "frac": rate / red_pk,
                                      "peak_source": "rw_probe_red: 64 x 64 windows on a "
                                                     "2048^2 float map, measured here"}
     return kernel_ms, extra, {
