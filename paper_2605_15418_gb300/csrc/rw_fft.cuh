@@ -174,13 +174,34 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* tw) {
 // First row stage (radix R, no twiddles) reading rows staged with stride
 // N + 2 at column offset `off` and writing the usual stride N + 1 layout in
 // place: every load of the stage happens before its barrier.
+// Staged rows have the even stride N + 2 (16-byte aligned bulk copies), so
+// the usual map (a warp on 32 consecutive rows, one butterfly) would put rows
+// b and b + 8 of a half-warp on the same banks.  For N = 64, radix 8 a
+// half-warp instead takes 8 consecutive rows x 2 adjacent butterflies:
+// (4 b + 2 i) mod 32 then covers every bank once on the staged reads, and
+// (2 b + 16 i) mod 32 on the stride N + 1 writes.
+template <int N, int NB, int PER>
+struct StagedMap {
+    static constexpr bool SPLIT = (N == 64) && (NB == 8) && (N * NB == PER * RW_THREADS);
+    __device__ static __forceinline__ void at(int k, int& b, int& i) {
+        if constexpr (SPLIT) {
+            const int f = ltid() + k * RW_THREADS;
+            const int j = f & 15, hw = f >> 4;
+            b = 8 * (hw & 7) + (j >> 1);
+            i = 2 * (hw >> 3) + (j & 1);
+        } else {
+            StageMap<N, NB, PER, false>::at(k, b, i);
+        }
+    }
+};
+
 template <int N, int R, bool INV>
 __device__ __forceinline__ void fft_stage_from_staged(float2* buf, int off) {
     constexpr int S = Patch<N>::S, SS = N + 2;
     constexpr int NB = N / R;
     constexpr int TOT = N * NB;
     constexpr int PER = (TOT + RW_THREADS - 1) / RW_THREADS;
-    using Map = StageMap<N, NB, PER, false>;
+    using Map = StagedMap<N, NB, PER>;
     float2 v[PER][R];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
