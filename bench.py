@@ -47,13 +47,12 @@ FP32_LANES_PER_SM = 128
 MUFU_LANES_PER_SM = 16
 C5_FULL_LO, C5_FULL_HI = 65536, 2 * 1024 * 1024
 # DRAM bytes (read + write) per launch of the C2 step at full size, from one
-# ncu capture of the current kernel at n-side 256 scaled by the incident-ray
-# count (16x): see the profiles/ summaries.  A kernel missing here has no
-# capture of its current code.
-C2_TRAFFIC = {"k_bs_scatter": 16 * (1.535592e9 + 0.192266e9),
-              "k_bs_trace": 16 * (1.408312e9 + 0.820282e9),
-              "k_cull": 16 * 0.023748e9,
-              "k_forward": 16 * (0.310524e9 + 1.472937e9)}
+# ncu capture of the current kernels at n-side 256 scaled by the incident-ray
+# count (16x): see profiles/traffic_c2_n256.md.
+C2_TRAFFIC = {"k_bs_scatter": 16 * (1.584282e9 + 0.201948e9),
+              "k_bs_trace": 16 * (1.421939e9 + 0.822920e9),
+              "k_cull": 16 * 0.023777e9,
+              "k_forward": 16 * (0.316977e9 + 1.525885e9)}
 
 
 # DRAM bytes (read + write) per incident ray of the C5 kernels, from one ncu
