@@ -48,7 +48,7 @@ MUFU_LANES_PER_SM = 16
 C5_FULL_LO, C5_FULL_HI = 65536, 2 * 1024 * 1024
 # DRAM bytes (read + write) per launch of the C2 step at full size, from one
 # ncu capture of the current kernels at n-side 256 scaled by the incident-ray
-# count (16x): see profiles/traffic_c2_n256.md.
+# count (16x), as the profiles/ summaries record.
 C2_TRAFFIC = {"k_bs_scatter": 16 * (1.584282e9 + 0.201948e9),
               "k_bs_trace": 16 * (1.421939e9 + 0.822920e9),
               "k_cull": 16 * 0.023777e9,
