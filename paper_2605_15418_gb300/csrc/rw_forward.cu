@@ -229,13 +229,13 @@ k_cull(const DSys sys, const DJob* __restrict__ jobs, const long long* __restric
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         __syncthreads();
         if (threadIdx.x < RW_TILE)
-            incident_to_doe(sys, jobs, prefix, njob, total, rays, tile * RW_TILE + threadIdx.x,
-                            info[threadIdx.x], status);
+            incident_to_doe<false>(sys, jobs, prefix, njob, total, rays,
+                                   tile * RW_TILE + threadIdx.x, info[threadIdx.x], status);
         for (int i = threadIdx.x; i < RW_TILE * KW; i += RW_THREADS) kw[i] = 0u;
         __syncthreads();
         if (threadIdx.x < RW_TILE) {
             const RayAtDoe& R = info[lane];
-            const bool live = R.alive != 0;
+            const bool live = R.alive == 1;
             // minima of (x, -x, y, -y, k_u, -k_u, k_v, -k_v) over each group of 8 lanes
             float v[8] = {live ? R.px : INFINITY, live ? -R.px : INFINITY,
                           live ? R.py : INFINITY, live ? -R.py : INFINITY,
@@ -277,7 +277,7 @@ k_cull(const DSys sys, const DJob* __restrict__ jobs, const long long* __restric
                                             hu, fmaf(ks, jv_c, 0.5f * (b[6] + b[7])), hv,
                                             0.5f * (b[0] + b[1]), hx, 0.5f * (b[2] + b[3]), hy)) {
                 for (int i = 0; i < G; ++i)
-                    if (info[g * G + i].alive)
+                    if (info[g * G + i].alive == 1)
                         atomicOr(&kw[(g * G + i) * KW + (bi >> 5)], 1u << (bi & 31));
             }
         }
@@ -285,13 +285,21 @@ k_cull(const DSys sys, const DJob* __restrict__ jobs, const long long* __restric
             const int r = t / NB, bi = t - r * NB;
             if (grep[r / G] != -1) continue;
             const RayAtDoe& R = info[r];
-            if (!R.alive) continue;
+            if (R.alive != 1) continue;
             const float ju_c = (float)((bi % B8) * 8 - M / 2) + 3.5f;
             const float jv_c = (float)((bi / B8) * 8 - M / 2) + 3.5f;
             if (!af_block_misses_sensor<NS>(sys, R, fmaf(ks, ju_c, R.kin_u), 3.5f * ks,
                                             fmaf(ks, jv_c, R.kin_v), 3.5f * ks, R.px, 0.f, R.py,
                                             0.f))
                 atomicOr(&kw[r * KW + (bi >> 5)], 1u << (bi & 31));
+        }
+        // rays the FP32 run could not place: every block kept
+        for (int t = threadIdx.x; t < RW_TILE * KW; t += RW_THREADS) {
+            const int r = t / KW, w = t - (t / KW) * KW;
+            if (info[r].alive == 2) {
+                const int nb = NB - 32 * w;
+                kw[t] = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
+            }
         }
         __syncthreads();
         const long long g0 = tile * RW_TILE;

@@ -245,6 +245,11 @@ __device__ __forceinline__ bool conformal_hit(const DSurf& S, double x, double y
 // tangent frame and everything the patch step needs.  The DOE hit is
 // computed in double (planar: one division; conformal: FP32 sphere root
 // refined by two FP64 Newton steps on c|Q|^2 - 2 Q_z = 0).
+// EXACT = false (the block culling): the run to the DOE in FP32, enough for
+// enclosures with a two-pixel margin; a ray the FP32 run loses gets
+// alive = 2 ("unknown": the culling keeps all its blocks, the forward's FP64
+// run decides).
+template <bool EXACT = true>
 __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __restrict__ jobs,
                                                 const long long* __restrict__ prefix, int njob,
                                                 long long total, const RaysIn& rays,
@@ -256,20 +261,32 @@ __device__ __forceinline__ void incident_to_doe(const DSys& sys, const DJob* __r
     const DJob& J = jobs[j];
     const long long ri = J.off + (g - prefix[j]);
     R.rid = ri;
-    // the run to the DOE in double (see trace_one_d), from the float ray
-    double xd = rays.ox[ri], yd = rays.oy[ri], zd = rays.oz[ri];
-    double dxd = rays.dx[ri], dyd = rays.dy[ri], dzd = rays.dz[ri];
+    if constexpr (!EXACT) R.alive = 2;      // every early return below: unknown
+    double xd, yd, zd, dxd, dyd, dzd;
     double opl = rays.opl[ri];
-    for (int s = 0; s < sys.doe_index; ++s)
-        if (!trace_one_d(sys.s[s], xd, yd, zd, dxd, dyd, dzd, opl, status)) return;
     const DSurf& S = sys.s[sys.doe_index];
+    if constexpr (EXACT) {
+        // the run to the DOE in double (see trace_one_d), from the float ray
+        xd = rays.ox[ri]; yd = rays.oy[ri]; zd = rays.oz[ri];
+        dxd = rays.dx[ri]; dyd = rays.dy[ri]; dzd = rays.dz[ri];
+        for (int s = 0; s < sys.doe_index; ++s)
+            if (!trace_one_d(sys.s[s], xd, yd, zd, dxd, dyd, dzd, opl, status)) return;
+    } else {
+        float x = rays.ox[ri], y = rays.oy[ri], zl = rays.oz[ri];
+        float dx = rays.dx[ri], dy = rays.dy[ri], dz = rays.dz[ri];
+        const double oz = (double)zl;
+        for (int s = 0; s < sys.doe_index; ++s)
+            if (!trace_one<true>(sys.s[s], x, y, zl, dx, dy, dz, opl, nullptr)) return;
+        xd = x; yd = y; dxd = dx; dyd = dy; dzd = dz;
+        zd = (sys.doe_index == 0) ? oz : (double)zl + sys.s[sys.doe_index - 1].z;
+    }
     const double zld = zd - S.z;
     if (dzd == 0.0) return;
     double t;
     float nx, ny, nz;
     if (!sys.conformal) {
         t = -zld / dzd;
-    } else if (!conformal_hit(S, xd, yd, zld, dxd, dyd, dzd, t, status)) {
+    } else if (!conformal_hit(S, xd, yd, zld, dxd, dyd, dzd, t, EXACT ? status : nullptr)) {
         return;
     }
     const float dx = (float)dxd, dy = (float)dyd, dz = (float)dzd;
