@@ -1077,3 +1077,21 @@ def test_coherent_window_covers_the_hand_listed_pixels():
         assert np.array_equal(fw != 0, mask)
         assert np.abs(fw[mask] - ff[mask]).max() < 1e-15
         assert np.all(np.abs(ff[mask]) > 0)
+
+
+def test_c4_asphere_newton_fails_off_axis_as_stated():
+    """C4's even asphere with A4..A10 ~ N(0, 1e-6) (mm units, as the workload
+    states): its polynomial dominates the sag beyond r ~ 4 mm, where the
+    oblique fields' bundles land, so Newton's method (FP64, 50 steps, the
+    oracle's) fails for a large share of the rays at +-22.5 and +-30 degrees
+    and for none on axis or at +-15 degrees; both sides drop those rays."""
+    w = R.configs.c4(n_side=32)
+    prm = G.surface_params(w.system.surfaces[0])
+    fail = {}
+    for job in w.jobs[:9]:                      # one wavelength, all nine fields
+        r = P.job_rays(job, w.z_start, w.system.n_object)
+        _, ok = G.intersect(r["o"], r["d"], prm)
+        fail[round(math.degrees(job.theta_y), 1)] = 1.0 - float(ok.double().mean())
+    assert fail[0.0] == 0.0 and fail[15.0] == 0.0 and fail[-15.0] == 0.0
+    assert 0.05 < fail[22.5] < 0.4 and 0.05 < fail[-22.5] < 0.4
+    assert fail[30.0] > 0.7 and fail[-30.0] > 0.7
