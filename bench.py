@@ -574,7 +574,7 @@ def roofline_c5(tm, st, peaks, n_sms, clocks):
 EMIT_W_SEC, EMIT_W_RAY, EMIT_R_RAY = 24, 20, 36
 
 
-def emit_line(w, args, dev, local, flush, peaks):
+def emit_line(w, args, dev, local, flush, peaks, dist=None, world=1):
     """C1: the planar grating's secondary rays written to HBM by rw_doe_emit,
     timed with CUDA events on the launching stream (the output, larger than
     L2, is written every step; the flush buffer is zeroed between steps)."""
@@ -601,7 +601,7 @@ def emit_line(w, args, dev, local, flush, peaks):
     prof = sim.ctx.profile_read()
     sim.ctx.profile(False)
     kernel_ms = {k: v[0] / v[1] for k, v in prof.items() if v[1] > 0}
-    t = float(np.mean(ms))
+    t = max_over_ranks(float(np.mean(ms)), dist, dev)
     kt = kernel_ms.get("k_forward", t)
     nbytes = sim.n_rays * (M * M * EMIT_W_SEC + EMIT_W_RAY + EMIT_R_RAY)
     gbs = nbytes / (kt / 1e3) / 1e9
@@ -611,7 +611,7 @@ def emit_line(w, args, dev, local, flush, peaks):
     roof = {"kernel": "k_forward (MODE_EMIT)", "bound": "hbm", "achieved": gbs,
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"],
             "traffic": None}
-    res = {"value": sim.n_rays / (t / 1e3), "unit": "rays/s", "ms_per_step": t,
+    res = {"value": weak_scaling_value(sim.n_rays, world, t), "unit": "rays/s", "ms_per_step": t,
            "steps": args.also_steps, "warmup": args.also_warmup, "config": cfg,
            "roofline": roof}
     del out, sim
@@ -752,7 +752,7 @@ def main():
     for other in [x for x in args.also.split(",") if x and x != name]:
         wo = workload(other, args)
         if other == "c1":
-            also.append(emit_line(wo, args, dev, local, flush, peaks))
+            also.append(emit_line(wo, args, dev, local, flush, peaks, dist, world))
             continue
         so = Step(other, wo, dev, local, dft="tc" if other == "c4tc" else "fft32")
         to = time_steps(so, args.also_steps, args.also_warmup, flush, dev,
